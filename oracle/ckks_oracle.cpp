@@ -1,0 +1,1039 @@
+// ============================================================================
+// ORACLE -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, obviously-correct CPU implementation of the RNS-CKKS
+// arithmetic that CryptoInvSqrt (Alg. 1) runs on, and of CryptoInvSqrt itself
+// (Chebyshev initial value, Sec. 2.3; Newton iteration, Sec. 2.2).  Modular
+// arithmetic uses unsigned __int128 and the '%' operator; floating point is
+// FP64.  Nothing is blocked, fused or reordered for speed.
+//
+// Only the tests, the smoke check and the CPU-baseline leg of the benchmark may
+// load this library.  It shares no code, header or table generator with the
+// GPU library; the two meet only through seeded inputs and compared outputs.
+//
+// The paper cites CKKS (Sec. 2.1) but states none of its ring-level details.
+// The conventions implemented here are the textbook ones, fixed as follows:
+//  * primes: for each requested bit size b, candidates 2^b + k*2N + 1 and
+//    2^b - k*2N + 1 for k = 1, 2, ... (above first), first prime not yet used;
+//  * psi: the first x^((q-1)/2N), x = 2, 3, ..., whose N-th power is -1;
+//  * NTT: out[j] = sum_i a_i psi^(i(2 br(j) + 1)) (bit-reversed evaluation
+//    order), inverse includes N^-1;
+//  * slots: z_j = m(zeta^(5^j)), zeta = exp(i pi / N) (CKKS canonical
+//    embedding restricted to the 5^j orbit);
+//  * rescale and ModDown round to nearest (centred remainders);
+//  * key switching: hybrid, digits of alpha consecutive Q primes (Han-Ki 2020);
+//  * randomness: SplitMix64 (Steele, Lea, Flood 2014), one stream per object,
+//    errors from the centred binomial distribution with eta = 21 (sigma ~ 3.24,
+//    Alkim et al. 2016), ternary secrets dense or of fixed Hamming weight.
+// ============================================================================
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef unsigned __int128 u128;
+typedef std::complex<double> cd;
+typedef std::vector<u64> Limb;
+typedef std::vector<Limb> Poly;  // [limb][coefficient]
+
+static thread_local std::string g_err;
+
+// ---------------------------------------------------------------- arithmetic
+static u64 mulmod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+static u64 addmod(u64 a, u64 b, u64 q) { u64 s = a + b; return s >= q ? s - q : s; }
+static u64 submod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + (q - b); }
+static u64 powmod(u64 a, u64 e, u64 q) {
+  u64 r = 1 % q; a %= q;
+  while (e) { if (e & 1) r = mulmod(r, a, q); a = mulmod(a, a, q); e >>= 1; }
+  return r;
+}
+static u64 invmod(u64 a, u64 q) { return powmod(a, q - 2, q); }  // q prime
+// signed integer -> residue
+static u64 smod(i64 v, u64 q) {
+  if (v >= 0) return (u64)v % q;
+  u64 m = (u64)(-(v + 1)) % q;  // -(v+1) >= 0
+  return submod(q - 1, m, q);   // v = -(m'+1)
+}
+
+// Exact residue of an integer-valued double.  |x| may exceed 2^63: write
+// x = M * 2^e with M a 53-bit integer and reduce each factor.
+static u64 double_to_mod(double x, u64 q) {
+  bool neg = x < 0; double ax = std::fabs(x);
+  u64 r;
+  if (ax < 9.2e18) {
+    r = (u64)ax % q;
+  } else {
+    int e; double m = std::frexp(ax, &e);  // ax = m * 2^e, m in [0.5,1)
+    u64 M = (u64)std::ldexp(m, 53);        // exact
+    r = mulmod(M % q, powmod(2, (u64)(e - 53), q), q);
+  }
+  return neg ? (r == 0 ? 0 : q - r) : r;
+}
+static double round_half_away(double x) { return std::round(x); }
+
+// ---------------------------------------------------------------- primes
+static bool is_prime(u64 n) {
+  if (n < 2) return false;
+  static const u64 sp[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (u64 p : sp) { if (n % p == 0) return n == p; }
+  u64 d = n - 1; int s = 0;
+  while ((d & 1) == 0) { d >>= 1; ++s; }
+  for (u64 a : sp) {  // deterministic for n < 2^64 (Jaeschke / Sorenson-Webster)
+    u64 x = powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int r = 1; r < s; ++r) { x = mulmod(x, x, n); if (x == n - 1) { comp = false; break; } }
+    if (comp) return false;
+  }
+  return true;
+}
+
+static std::vector<u64> prime_chain(int log_n, const std::vector<int>& bits) {
+  u64 two_n = 2ull << log_n;
+  std::vector<u64> out;
+  for (int b : bits) {
+    if (b < log_n + 2 || b > 60) throw std::runtime_error("prime bit size out of range [log_n+2, 60]");
+    u64 base = 1ull << b;
+    for (u64 k = 1;; ++k) {
+      u64 up = base + k * two_n + 1;
+      if (is_prime(up) && std::find(out.begin(), out.end(), up) == out.end()) { out.push_back(up); break; }
+      if (k * two_n < base) {
+        u64 dn = base - k * two_n + 1;
+        if (is_prime(dn) && std::find(out.begin(), out.end(), dn) == out.end()) { out.push_back(dn); break; }
+      }
+    }
+  }
+  return out;
+}
+
+static u64 find_psi(u64 q, int log_n) {
+  u64 N = 1ull << log_n;
+  for (u64 x = 2;; ++x) {
+    u64 psi = powmod(x, (q - 1) / (2 * N), q);
+    if (powmod(psi, N, q) == q - 1) return psi;
+  }
+}
+
+static u64 bitrev(u64 x, int bits) {
+  u64 r = 0;
+  for (int i = 0; i < bits; ++i) { r = (r << 1) | (x & 1); x >>= 1; }
+  return r;
+}
+
+// ---------------------------------------------------------------- PRNG
+// SplitMix64 (Steele, Lea, Flood 2014): state += golden gamma, then the
+// 64-bit finaliser.  A stream for (seed, tag) starts at
+// mix64(seed) ^ mix64(tag ^ 0x5851F42D4C957F2D).
+static u64 mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+struct Stream {
+  u64 s;
+  Stream(u64 seed, u64 tag) : s(mix64(seed) ^ mix64(tag ^ 0x5851F42D4C957F2Dull)) {}
+  u64 next() { s += 0x9E3779B97F4A7C15ull; return mix64(s); }
+};
+// object tags
+static u64 tag_evk_a(u64 g, u64 j) { return (2ull << 56) | (g << 8) | j; }
+static u64 tag_evk_e(u64 g, u64 j) { return (3ull << 56) | (g << 8) | j; }
+static const u64 TAG_SK = 1, TAG_ENC_A = 4ull << 56, TAG_ENC_E = 5ull << 56;
+
+static u64 sample_uniform(Stream& st, u64 q) {
+  int bits = 64 - __builtin_clzll(q);
+  for (;;) { u64 x = st.next() >> (64 - bits); if (x < q) return x; }
+}
+// centred binomial, eta = 21: popcount of 21 low bits minus popcount of the next 21
+static i64 sample_cbd(Stream& st) {
+  u64 r = st.next();
+  return (i64)__builtin_popcountll(r & 0x1FFFFFull) - (i64)__builtin_popcountll((r >> 21) & 0x1FFFFFull);
+}
+static std::vector<i64> sample_ternary(Stream& st, int log_n, int h) {
+  size_t N = 1ull << log_n;
+  std::vector<i64> s(N, 0);
+  if (h == 0) {
+    for (size_t i = 0; i < N; ++i) { u64 x; do { x = st.next() >> 62; } while (x >= 3); s[i] = (i64)x - 1; }
+  } else {
+    int cnt = 0;
+    while (cnt < h) {
+      u64 r = st.next(); u64 pos = r >> (64 - log_n);
+      if (s[pos] == 0) { s[pos] = (r & 1) ? 1 : -1; ++cnt; }
+    }
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- big integers (CRT)
+struct Big {  // unsigned, little-endian 32-bit words
+  std::vector<uint32_t> w;
+  static Big from(u64 v) { Big b; b.w = {(uint32_t)v, (uint32_t)(v >> 32)}; b.trim(); return b; }
+  void trim() { while (!w.empty() && w.back() == 0) w.pop_back(); }
+};
+static Big big_mul(const Big& a, u64 m) {
+  Big r; u128 carry = 0;
+  for (uint32_t x : a.w) { u128 t = (u128)x * m + carry; r.w.push_back((uint32_t)t); carry = t >> 32; }
+  while (carry) { r.w.push_back((uint32_t)carry); carry >>= 32; }
+  r.trim(); return r;
+}
+static Big big_add(const Big& a, const Big& b) {
+  Big r; u64 c = 0; size_t n = std::max(a.w.size(), b.w.size());
+  for (size_t i = 0; i < n; ++i) {
+    u64 t = c + (i < a.w.size() ? a.w[i] : 0) + (i < b.w.size() ? b.w[i] : 0);
+    r.w.push_back((uint32_t)t); c = t >> 32;
+  }
+  if (c) r.w.push_back((uint32_t)c);
+  r.trim(); return r;
+}
+static int big_cmp(const Big& a, const Big& b) {
+  if (a.w.size() != b.w.size()) return a.w.size() < b.w.size() ? -1 : 1;
+  for (size_t i = a.w.size(); i-- > 0;) if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+  return 0;
+}
+static Big big_sub(const Big& a, const Big& b) {  // a >= b
+  Big r; i64 br = 0;
+  for (size_t i = 0; i < a.w.size(); ++i) {
+    i64 t = (i64)a.w[i] - (i < b.w.size() ? (i64)b.w[i] : 0) - br;
+    br = t < 0; if (t < 0) t += (1ll << 32);
+    r.w.push_back((uint32_t)t);
+  }
+  r.trim(); return r;
+}
+static double big_to_double(const Big& a) {
+  double r = 0;
+  for (size_t i = a.w.size(); i-- > 0;) r = r * 4294967296.0 + (double)a.w[i];
+  return r;
+}
+
+// ---------------------------------------------------------------- encoding
+// Special FFT over the 5^j orbit (the CKKS decoding map), written as its
+// radix-2 recursion: for a size-n problem with a root of order M = 4n,
+//   z_j = E_j + w_j O_j,  z_{j+n/2} = E_j - w_j O_j,  w_j = exp(2 pi i 5^j / M),
+// where E, O are the size-n/2 transforms of the even / odd inputs.
+static std::vector<cd> special_fft(const std::vector<cd>& w, u64 M) {
+  size_t n = w.size();
+  if (n == 1) return w;
+  std::vector<cd> ev(n / 2), od(n / 2);
+  for (size_t k = 0; k < n / 2; ++k) { ev[k] = w[2 * k]; od[k] = w[2 * k + 1]; }
+  std::vector<cd> E = special_fft(ev, M / 2), O = special_fft(od, M / 2), z(n);
+  u64 g = 1;
+  for (size_t j = 0; j < n / 2; ++j) {
+    cd r = std::polar(1.0, 2.0 * M_PI * (double)g / (double)M);
+    z[j] = E[j] + r * O[j];
+    z[j + n / 2] = E[j] - r * O[j];
+    g = (g * 5) % M;
+  }
+  return z;
+}
+static std::vector<cd> special_ifft(const std::vector<cd>& z, u64 M) {
+  size_t n = z.size();
+  if (n == 1) return z;
+  std::vector<cd> E(n / 2), O(n / 2);
+  u64 g = 1;
+  for (size_t j = 0; j < n / 2; ++j) {
+    cd r = std::polar(1.0, 2.0 * M_PI * (double)g / (double)M);
+    E[j] = (z[j] + z[j + n / 2]) * 0.5;
+    O[j] = (z[j] - z[j + n / 2]) * 0.5 / r;
+    g = (g * 5) % M;
+  }
+  std::vector<cd> ev = special_ifft(E, M / 2), od = special_ifft(O, M / 2), w(n);
+  for (size_t k = 0; k < n / 2; ++k) { w[2 * k] = ev[k]; w[2 * k + 1] = od[k]; }
+  return w;
+}
+
+// ---------------------------------------------------------------- context
+struct KeyDigit { Poly b, a; };  // NTT domain over all Q and P primes
+struct Ctx {
+  int log_n = 0; size_t N = 0; int n_q = 0, n_p = 0, alpha = 1; double scale = 0; int hw = 0; u64 seed = 0;
+  std::vector<u64> q;                    // n_q + n_p primes (Q first, then P)
+  std::vector<u64> psi;
+  std::vector<Limb> psi_rev, ipsi_rev;  // per prime, psi^(br(i)) and psi^(-br(i))
+  std::vector<u64> n_inv;
+  std::vector<i64> s;                    // secret coefficients
+  Poly s_ntt;                            // per prime
+  std::map<u64, std::vector<KeyDigit>> keys;  // galois element (0 = relinearisation) -> digits
+  int L() const { return n_q - 1; }
+};
+struct Ct { Poly c[2]; int level = 0; double scale = 1; };
+
+static void ntt_forward(const Ctx& C, Limb& a, int pi) {
+  // Cooley-Tukey decimation in time with the psi twist merged into the twiddles
+  u64 q = C.q[pi]; size_t N = C.N, t = N;
+  for (size_t m = 1; m < N; m <<= 1) {
+    t >>= 1;
+    for (size_t i = 0; i < m; ++i) {
+      u64 S = C.psi_rev[pi][m + i]; size_t j1 = 2 * i * t;
+      for (size_t j = j1; j < j1 + t; ++j) {
+        u64 U = a[j], V = mulmod(a[j + t], S, q);
+        a[j] = addmod(U, V, q); a[j + t] = submod(U, V, q);
+      }
+    }
+  }
+}
+static void ntt_inverse(const Ctx& C, Limb& a, int pi) {
+  // Gentleman-Sande decimation in frequency, then multiplication by N^-1
+  u64 q = C.q[pi]; size_t N = C.N, t = 1;
+  for (size_t m = N >> 1; m >= 1; m >>= 1) {
+    size_t j1 = 0;
+    for (size_t i = 0; i < m; ++i) {
+      u64 S = C.ipsi_rev[pi][m + i];
+      for (size_t j = j1; j < j1 + t; ++j) {
+        u64 U = a[j], V = a[j + t];
+        a[j] = addmod(U, V, q); a[j + t] = mulmod(submod(U, V, q), S, q);
+      }
+      j1 += 2 * t;
+    }
+    t <<= 1;
+  }
+  for (size_t j = 0; j < N; ++j) a[j] = mulmod(a[j], C.n_inv[pi], q);
+}
+
+static Limb residues_of(const Ctx& C, const std::vector<i64>& v, int pi) {
+  Limb r(C.N);
+  for (size_t i = 0; i < C.N; ++i) r[i] = smod(v[i], C.q[pi]);
+  return r;
+}
+// the evk digit j for a key switch from s' (NTT over all primes) to s
+static KeyDigit make_key_digit(const Ctx& C, const Poly& sp, u64 g, int j) {
+  int total = C.n_q + C.n_p;
+  KeyDigit kd; kd.a.assign(total, Limb(C.N)); kd.b.assign(total, Limb(C.N));
+  Stream sa(C.seed, tag_evk_a(g, j));
+  for (int t = 0; t < total; ++t) for (size_t i = 0; i < C.N; ++i) kd.a[t][i] = sample_uniform(sa, C.q[t]);
+  Stream se(C.seed, tag_evk_e(g, j));
+  std::vector<i64> e(C.N); for (size_t i = 0; i < C.N; ++i) e[i] = sample_cbd(se);
+  int lo = j * C.alpha, hi = std::min(lo + C.alpha, C.n_q);
+  for (int t = 0; t < total; ++t) {
+    u64 qt = C.q[t];
+    Limb et = residues_of(C, e, t); ntt_forward(C, et, t);
+    u64 Pmod = 1 % qt;
+    for (int k = 0; k < C.n_p; ++k) Pmod = mulmod(Pmod, C.q[C.n_q + k] % qt, qt);
+    bool in_digit = t >= lo && t < hi;
+    for (size_t i = 0; i < C.N; ++i) {
+      u64 v = submod(et[i], mulmod(kd.a[t][i], C.s_ntt[t][i], qt), qt);
+      if (in_digit) v = addmod(v, mulmod(Pmod, sp[t][i], qt), qt);
+      kd.b[t][i] = v;
+    }
+  }
+  return kd;
+}
+static int n_digits(const Ctx& C, int level) { return (level + 1 + C.alpha - 1) / C.alpha; }
+
+static u64 galois_of_rotation(const Ctx& C, i64 r) {
+  u64 M = 2 * C.N, h = C.N / 2;
+  i64 rr = ((r % (i64)h) + (i64)h) % (i64)h;
+  return powmod(5, (u64)rr, M);
+}
+// coefficient-domain automorphism X -> X^g (g odd)
+static Limb automorph_coeff(const Ctx& C, const Limb& a, u64 g, u64 q) {
+  Limb r(C.N, 0); u64 M = 2 * C.N;
+  for (size_t i = 0; i < C.N; ++i) {
+    u64 e = (u64)(((u128)i * g) % M);
+    if (e < C.N) r[e] = a[i]; else r[e - C.N] = a[i] == 0 ? 0 : q - a[i];
+  }
+  return r;
+}
+
+static void gen_key(Ctx& C, u64 g) {
+  if (C.keys.count(g)) return;
+  int total = C.n_q + C.n_p;
+  Poly sp(total);
+  for (int t = 0; t < total; ++t) {
+    if (g == 0) {  // relinearisation: s^2
+      sp[t].resize(C.N);
+      for (size_t i = 0; i < C.N; ++i) sp[t][i] = mulmod(C.s_ntt[t][i], C.s_ntt[t][i], C.q[t]);
+    } else {       // s(X^g)
+      Limb sc = residues_of(C, C.s, t);
+      sp[t] = automorph_coeff(C, sc, g, C.q[t]);
+      ntt_forward(C, sp[t], t);
+    }
+  }
+  std::vector<KeyDigit> ds;
+  for (int j = 0; j < n_digits(C, C.L()); ++j) ds.push_back(make_key_digit(C, sp, g, j));
+  C.keys[g] = std::move(ds);
+}
+
+static Ctx* ctx_create(int log_n, const std::vector<int>& qb, const std::vector<int>& pb, int alpha,
+                       double log_scale, int hw, u64 seed) {
+  if (log_n < 3 || log_n > 17) throw std::runtime_error("log_n out of range");
+  if (qb.empty() || pb.empty() || alpha < 1) throw std::runtime_error("bad prime counts");
+  std::unique_ptr<Ctx> C(new Ctx);
+  C->log_n = log_n; C->N = 1ull << log_n; C->n_q = (int)qb.size(); C->n_p = (int)pb.size();
+  C->alpha = alpha; C->scale = std::pow(2.0, log_scale); C->hw = hw; C->seed = seed;
+  std::vector<int> all = qb; all.insert(all.end(), pb.begin(), pb.end());
+  C->q = prime_chain(log_n, all);
+  int total = (int)C->q.size();
+  C->psi.resize(total); C->psi_rev.resize(total); C->ipsi_rev.resize(total); C->n_inv.resize(total);
+  for (int t = 0; t < total; ++t) {
+    u64 q = C->q[t], psi = find_psi(q, log_n), ipsi = invmod(psi, q);
+    C->psi[t] = psi;
+    C->psi_rev[t].resize(C->N); C->ipsi_rev[t].resize(C->N);
+    for (size_t i = 0; i < C->N; ++i) {
+      u64 e = bitrev(i, log_n);
+      C->psi_rev[t][i] = powmod(psi, e, q);
+      C->ipsi_rev[t][i] = powmod(ipsi, e, q);
+    }
+    C->n_inv[t] = invmod(C->N % q, q);
+  }
+  Stream ss(seed, TAG_SK);
+  C->s = sample_ternary(ss, log_n, hw);
+  C->s_ntt.resize(total);
+  for (int t = 0; t < total; ++t) { C->s_ntt[t] = residues_of(*C, C->s, t); ntt_forward(*C, C->s_ntt[t], t); }
+  gen_key(*C, 0);
+  return C.release();
+}
+
+// ---------------------------------------------------------------- encode / decode
+// slots (n = N/2 complex values) -> integer coefficients round(scale * m_k)
+static std::vector<double> encode_coeffs(const Ctx& C, const std::vector<cd>& z, double scale) {
+  size_t n = C.N / 2;
+  if (z.size() != n) throw std::runtime_error("only full-slot packing (N/2 slots) is supported");
+  std::vector<cd> w = special_ifft(z, 2 * C.N);
+  std::vector<double> m(C.N);
+  for (size_t k = 0; k < n; ++k) {
+    m[k] = round_half_away(w[k].real() * scale);
+    m[k + n] = round_half_away(w[k].imag() * scale);
+  }
+  return m;
+}
+static Poly coeffs_to_ntt(const Ctx& C, const std::vector<double>& m, int level) {
+  Poly p(level + 1, Limb(C.N));
+  for (int i = 0; i <= level; ++i) {
+    for (size_t k = 0; k < C.N; ++k) p[i][k] = double_to_mod(m[k], C.q[i]);
+    ntt_forward(C, p[i], i);
+  }
+  return p;
+}
+// exact CRT of coefficient-domain residues (limbs 0..level), centred, as doubles
+static std::vector<double> crt_centred(const Ctx& C, const Poly& coef, int level) {
+  int n = level + 1;
+  Big Q = Big::from(1); for (int i = 0; i < n; ++i) Q = big_mul(Q, C.q[i]);
+  std::vector<Big> qhat(n); std::vector<u64> qhat_inv(n);
+  for (int i = 0; i < n; ++i) {
+    Big h = Big::from(1); u64 hm = 1;
+    for (int k = 0; k < n; ++k) if (k != i) { h = big_mul(h, C.q[k]); hm = mulmod(hm, C.q[k] % C.q[i], C.q[i]); }
+    qhat[i] = h; qhat_inv[i] = invmod(hm, C.q[i]);
+  }
+  Big halfQ = big_mul(Q, 1);  // compare 2x against Q
+  std::vector<double> out(C.N);
+  for (size_t k = 0; k < C.N; ++k) {
+    Big x;
+    for (int i = 0; i < n; ++i) x = big_add(x, big_mul(qhat[i], mulmod(coef[i][k], qhat_inv[i], C.q[i])));
+    while (big_cmp(x, Q) >= 0) x = big_sub(x, Q);
+    Big x2 = big_mul(x, 2);
+    if (big_cmp(x2, halfQ) > 0) out[k] = -big_to_double(big_sub(Q, x));
+    else out[k] = big_to_double(x);
+  }
+  return out;
+}
+static std::vector<cd> decode_coeffs(const Ctx& C, const std::vector<double>& m, double scale) {
+  size_t n = C.N / 2;
+  std::vector<cd> w(n);
+  for (size_t k = 0; k < n; ++k) w[k] = cd(m[k] / scale, m[k + n] / scale);
+  return special_fft(w, 2 * C.N);
+}
+
+// ---------------------------------------------------------------- ciphertext ops
+static Ct encrypt(const Ctx& C, const std::vector<cd>& z, int level, u64 seed) {
+  if (level < 0 || level > C.L()) throw std::runtime_error("level out of range");
+  std::vector<double> m = encode_coeffs(C, z, C.scale);
+  Ct ct; ct.level = level; ct.scale = C.scale;
+  ct.c[0].assign(level + 1, Limb(C.N)); ct.c[1].assign(level + 1, Limb(C.N));
+  Stream sa(seed, TAG_ENC_A);
+  for (int i = 0; i <= level; ++i) for (size_t k = 0; k < C.N; ++k) ct.c[1][i][k] = sample_uniform(sa, C.q[i]);
+  Stream se(seed, TAG_ENC_E);
+  std::vector<i64> e(C.N); for (size_t k = 0; k < C.N; ++k) e[k] = sample_cbd(se);
+  for (int i = 0; i <= level; ++i) {
+    u64 q = C.q[i];
+    Limb mi(C.N);
+    for (size_t k = 0; k < C.N; ++k) mi[k] = addmod(double_to_mod(m[k], q), smod(e[k], q), q);
+    ntt_forward(C, mi, i);
+    for (size_t k = 0; k < C.N; ++k) ct.c[0][i][k] = submod(mi[k], mulmod(ct.c[1][i][k], C.s_ntt[i][k], q), q);
+  }
+  return ct;
+}
+static std::vector<double> decrypt_coeffs(const Ctx& C, const Ct& ct) {
+  Poly m(ct.level + 1, Limb(C.N));
+  for (int i = 0; i <= ct.level; ++i) {
+    u64 q = C.q[i];
+    for (size_t k = 0; k < C.N; ++k) m[i][k] = addmod(ct.c[0][i][k], mulmod(ct.c[1][i][k], C.s_ntt[i][k], q), q);
+    ntt_inverse(C, m[i], i);
+  }
+  return crt_centred(C, m, ct.level);
+}
+static std::vector<cd> decrypt(const Ctx& C, const Ct& ct) { return decode_coeffs(C, decrypt_coeffs(C, ct), ct.scale); }
+
+static Ct drop_to(const Ct& a, int level) {
+  if (level > a.level || level < 0) throw std::runtime_error("drop_to: bad level");
+  Ct r = a; r.level = level;
+  for (int c = 0; c < 2; ++c) r.c[c].resize(level + 1);
+  return r;
+}
+static void check_scales(double a, double b) {
+  if (std::fabs(a / b - 1.0) > 1e-12) throw std::runtime_error("scale mismatch");
+}
+static Ct add_sub(const Ctx& C, const Ct& a0, const Ct& b0, bool sub) {
+  int l = std::min(a0.level, b0.level);
+  Ct a = drop_to(a0, l), b = drop_to(b0, l);
+  check_scales(a.scale, b.scale);
+  for (int c = 0; c < 2; ++c) for (int i = 0; i <= l; ++i) for (size_t k = 0; k < C.N; ++k)
+    a.c[c][i][k] = sub ? submod(a.c[c][i][k], b.c[c][i][k], C.q[i]) : addmod(a.c[c][i][k], b.c[c][i][k], C.q[i]);
+  return a;
+}
+// rescale by the last prime q_l, rounding to nearest:
+//   c'_i = (c_i - [c_l]_centred) * q_l^-1 mod q_i
+static Poly rescale_poly(const Ctx& C, const Poly& p, int l) {
+  u64 ql = C.q[l], h = ql >> 1;
+  Limb last = p[l]; ntt_inverse(C, last, l);
+  Poly out(l, Limb(C.N));
+  for (int i = 0; i < l; ++i) {
+    u64 qi = C.q[i], inv = invmod(ql % qi, qi);
+    Limb r(C.N);
+    for (size_t k = 0; k < C.N; ++k) {
+      u64 v = last[k];  // centred representative: v if v <= h else v - q_l
+      r[k] = v <= h ? v % qi : submod(v % qi, ql % qi, qi);
+    }
+    ntt_forward(C, r, i);
+    for (size_t k = 0; k < C.N; ++k) out[i][k] = mulmod(submod(p[i][k], r[k], qi), inv, qi);
+  }
+  return out;
+}
+static Ct rescale(const Ctx& C, const Ct& a) {
+  if (a.level < 1) throw std::runtime_error("rescale: level exhausted");
+  Ct r; r.level = a.level - 1; r.scale = a.scale / (double)C.q[a.level];
+  for (int c = 0; c < 2; ++c) r.c[c] = rescale_poly(C, a.c[c], a.level);
+  return r;
+}
+
+// ModUp of digit j at level l: coefficient-domain residues of the digit's primes ->
+// residues on every prime of Q_l u P (fast basis conversion, no correction):
+//   y_t = sum_{i in digit} [x_i * qhat_i^-1]_{q_i} * qhat_i  mod t
+static Poly modup_coeff(const Ctx& C, const Poly& dcoef, int l, int j) {
+  int lo = j * C.alpha, hi = std::min(lo + C.alpha, l + 1);
+  std::vector<int> ext; for (int i = 0; i <= l; ++i) ext.push_back(i);
+  for (int k = 0; k < C.n_p; ++k) ext.push_back(C.n_q + k);
+  std::vector<u64> qhat_inv(hi - lo);
+  for (int i = lo; i < hi; ++i) {
+    u64 h = 1; for (int k = lo; k < hi; ++k) if (k != i) h = mulmod(h, C.q[k] % C.q[i], C.q[i]);
+    qhat_inv[i - lo] = invmod(h, C.q[i]);
+  }
+  Poly out(ext.size(), Limb(C.N));
+  for (size_t e = 0; e < ext.size(); ++e) {
+    int t = ext[e]; u64 qt = C.q[t];
+    if (t >= lo && t < hi) { out[e] = dcoef[t]; continue; }
+    std::vector<u64> qhat_t(hi - lo);
+    for (int i = lo; i < hi; ++i) {
+      u64 h = 1 % qt; for (int k = lo; k < hi; ++k) if (k != i) h = mulmod(h, C.q[k] % qt, qt);
+      qhat_t[i - lo] = h;
+    }
+    for (size_t n = 0; n < C.N; ++n) {
+      u64 acc = 0;
+      for (int i = lo; i < hi; ++i) {
+        u64 y = mulmod(dcoef[i][n], qhat_inv[i - lo], C.q[i]);
+        acc = addmod(acc, mulmod(y % qt, qhat_t[i - lo], qt), qt);
+      }
+      out[e][n] = acc;
+    }
+  }
+  return out;
+}
+// ModDown at level l: coefficient-domain residues over Q_l u P -> round(x / P) on Q_l:
+//   c'_i = (c_i + [floor(P/2)]_{q_i} - BConv_{P->q_i}([c + floor(P/2)]_P)) * P^-1 mod q_i
+static Poly moddown_coeff(const Ctx& C, const Poly& x, int l) {
+  int K = C.n_p;
+  std::vector<u64> phat_inv(K);
+  for (int k = 0; k < K; ++k) {
+    u64 pk = C.q[C.n_q + k], h = 1;
+    for (int m = 0; m < K; ++m) if (m != k) h = mulmod(h, C.q[C.n_q + m] % pk, pk);
+    phat_inv[k] = invmod(h, pk);
+  }
+  auto half_mod = [&](u64 m) {  // floor(P/2) = (P-1)/2 mod m, P odd
+    u64 Pm = 1 % m; for (int k = 0; k < K; ++k) Pm = mulmod(Pm, C.q[C.n_q + k] % m, m);
+    return mulmod(submod(Pm, 1 % m, m), invmod(2 % m, m), m);
+  };
+  std::vector<u64> half_p(K); for (int k = 0; k < K; ++k) half_p[k] = half_mod(C.q[C.n_q + k]);
+  Poly out(l + 1, Limb(C.N));
+  for (int i = 0; i <= l; ++i) {
+    u64 qi = C.q[i], hq = half_mod(qi);
+    u64 Pm = 1 % qi; for (int k = 0; k < K; ++k) Pm = mulmod(Pm, C.q[C.n_q + k] % qi, qi);
+    u64 Pinv = invmod(Pm, qi);
+    std::vector<u64> phat_q(K);
+    for (int k = 0; k < K; ++k) {
+      u64 h = 1 % qi; for (int m = 0; m < K; ++m) if (m != k) h = mulmod(h, C.q[C.n_q + m] % qi, qi);
+      phat_q[k] = h;
+    }
+    for (size_t n = 0; n < C.N; ++n) {
+      u64 v = 0;
+      for (int k = 0; k < K; ++k) {
+        u64 pk = C.q[C.n_q + k];
+        u64 r = addmod(x[l + 1 + k][n], half_p[k], pk);
+        v = addmod(v, mulmod(mulmod(r, phat_inv[k], pk) % qi, phat_q[k], qi), qi);
+      }
+      out[i][n] = mulmod(submod(addmod(x[i][n], hq, qi), v, qi), Pinv, qi);
+    }
+  }
+  return out;
+}
+// hybrid key switch of d (NTT domain, limbs 0..l) under key g -> (ks0, ks1), NTT domain
+static void key_switch(const Ctx& C, const Poly& d, int l, u64 g, Poly& o0, Poly& o1) {
+  auto it = C.keys.find(g);
+  if (it == C.keys.end()) throw std::runtime_error("missing switching key");
+  const std::vector<KeyDigit>& key = it->second;
+  Poly dcoef = d; for (int i = 0; i <= l; ++i) ntt_inverse(C, dcoef[i], i);
+  std::vector<int> ext; for (int i = 0; i <= l; ++i) ext.push_back(i);
+  for (int k = 0; k < C.n_p; ++k) ext.push_back(C.n_q + k);
+  Poly acc0(ext.size(), Limb(C.N, 0)), acc1(ext.size(), Limb(C.N, 0));
+  for (int j = 0; j < n_digits(C, l); ++j) {
+    Poly y = modup_coeff(C, dcoef, l, j);
+    for (size_t e = 0; e < ext.size(); ++e) {
+      int t = ext[e]; u64 qt = C.q[t];
+      ntt_forward(C, y[e], t);
+      for (size_t n = 0; n < C.N; ++n) {
+        acc0[e][n] = addmod(acc0[e][n], mulmod(y[e][n], key[j].b[t][n], qt), qt);
+        acc1[e][n] = addmod(acc1[e][n], mulmod(y[e][n], key[j].a[t][n], qt), qt);
+      }
+    }
+  }
+  for (size_t e = 0; e < ext.size(); ++e) { ntt_inverse(C, acc0[e], ext[e]); ntt_inverse(C, acc1[e], ext[e]); }
+  o0 = moddown_coeff(C, acc0, l); o1 = moddown_coeff(C, acc1, l);
+  for (int i = 0; i <= l; ++i) { ntt_forward(C, o0[i], i); ntt_forward(C, o1[i], i); }
+}
+// tensor product + relinearisation (no rescale); both inputs at the same level
+static Ct mul_relin(const Ctx& C, const Ct& a0, const Ct& b0) {
+  int l = std::min(a0.level, b0.level);
+  Ct a = drop_to(a0, l), b = drop_to(b0, l);
+  Poly d0(l + 1, Limb(C.N)), d1(l + 1, Limb(C.N)), d2(l + 1, Limb(C.N));
+  for (int i = 0; i <= l; ++i) {
+    u64 q = C.q[i];
+    for (size_t k = 0; k < C.N; ++k) {
+      d0[i][k] = mulmod(a.c[0][i][k], b.c[0][i][k], q);
+      d1[i][k] = addmod(mulmod(a.c[0][i][k], b.c[1][i][k], q), mulmod(a.c[1][i][k], b.c[0][i][k], q), q);
+      d2[i][k] = mulmod(a.c[1][i][k], b.c[1][i][k], q);
+    }
+  }
+  Poly k0, k1; key_switch(C, d2, l, 0, k0, k1);
+  Ct r; r.level = l; r.scale = a.scale * b.scale;
+  r.c[0] = d0; r.c[1] = d1;
+  for (int i = 0; i <= l; ++i) for (size_t k = 0; k < C.N; ++k) {
+    r.c[0][i][k] = addmod(r.c[0][i][k], k0[i][k], C.q[i]);
+    r.c[1][i][k] = addmod(r.c[1][i][k], k1[i][k], C.q[i]);
+  }
+  return r;
+}
+static Ct mul(const Ctx& C, const Ct& a, const Ct& b) { return rescale(C, mul_relin(C, a, b)); }
+
+// automorphism X -> X^g applied to both parts, then key switch back to s
+static Ct apply_galois(Ctx& C, const Ct& a, u64 g) {
+  gen_key(C, g);
+  int l = a.level;
+  Poly p0(l + 1), p1(l + 1);
+  for (int i = 0; i <= l; ++i) {
+    Limb x0 = a.c[0][i], x1 = a.c[1][i];
+    ntt_inverse(C, x0, i); ntt_inverse(C, x1, i);
+    p0[i] = automorph_coeff(C, x0, g, C.q[i]); p1[i] = automorph_coeff(C, x1, g, C.q[i]);
+    ntt_forward(C, p0[i], i); ntt_forward(C, p1[i], i);
+  }
+  Poly k0, k1; key_switch(C, p1, l, g, k0, k1);
+  Ct r; r.level = l; r.scale = a.scale; r.c[0] = p0; r.c[1] = k1;
+  for (int i = 0; i <= l; ++i) for (size_t k = 0; k < C.N; ++k) r.c[0][i][k] = addmod(p0[i][k], k0[i][k], C.q[i]);
+  return r;
+}
+static Ct rotate(Ctx& C, const Ct& a, i64 steps) { return apply_galois(C, a, galois_of_rotation(C, steps)); }
+static Ct conjugate(Ctx& C, const Ct& a) { return apply_galois(C, a, 2 * C.N - 1); }
+
+// multiply by a real constant c encoded at plaintext scale sp, then rescale
+static Ct mul_const_sp(const Ctx& C, const Ct& a, double c, double sp) {
+  double v = round_half_away(c * sp);
+  Ct r = a;
+  for (int i = 0; i <= a.level; ++i) {
+    u64 cm = double_to_mod(v, C.q[i]);
+    for (int p = 0; p < 2; ++p) for (size_t k = 0; k < C.N; ++k) r.c[p][i][k] = mulmod(r.c[p][i][k], cm, C.q[i]);
+  }
+  r.scale = a.scale * sp;
+  return rescale(C, r);
+}
+// multiply by c so that the result (one level lower) has exactly scale target
+static Ct mul_const_to(const Ctx& C, const Ct& a, double c, double target) {
+  double sp = target * (double)C.q[a.level] / a.scale;
+  Ct r = mul_const_sp(C, a, c, sp);
+  r.scale = target;
+  return r;
+}
+static Ct add_const(const Ctx& C, const Ct& a, double c) {
+  double v = round_half_away(c * a.scale);
+  Ct r = a;
+  for (int i = 0; i <= a.level; ++i) {
+    u64 cm = double_to_mod(v, C.q[i]);
+    for (size_t k = 0; k < C.N; ++k) r.c[0][i][k] = addmod(r.c[0][i][k], cm, C.q[i]);
+  }
+  return r;
+}
+static Ct mul_int(const Ctx& C, const Ct& a, i64 m) {
+  Ct r = a;
+  for (int i = 0; i <= a.level; ++i) {
+    u64 mm = smod(m, C.q[i]);
+    for (int p = 0; p < 2; ++p) for (size_t k = 0; k < C.N; ++k) r.c[p][i][k] = mulmod(r.c[p][i][k], mm, C.q[i]);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- Chebyshev (Sec. 2.3)
+// Interpolant of f at the d+1 Chebyshev nodes of the first kind on [lo, hi]:
+//   c_j = (2 - [j=0]) / (d+1) * sum_k f(x_k) cos(j pi (k + 1/2) / (d+1)),
+//   x_k = (lo+hi)/2 + (hi-lo)/2 cos(pi (k + 1/2) / (d+1)),  f(x) = 1/sqrt(x).
+static std::vector<double> cheb_coeffs(double lo, double hi, int d) {
+  int n = d + 1;
+  std::vector<double> fx(n), c(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double x = 0.5 * (lo + hi) + 0.5 * (hi - lo) * std::cos(M_PI * (k + 0.5) / n);
+    fx[k] = 1.0 / std::sqrt(x);
+  }
+  for (int j = 0; j < n; ++j) {
+    double s = 0;
+    for (int k = 0; k < n; ++k) s += fx[k] * std::cos(M_PI * j * (k + 0.5) / n);
+    c[j] = (j == 0 ? 1.0 : 2.0) / n * s;
+  }
+  return c;
+}
+// Clenshaw evaluation of sum_j c_j T_j(t)
+static double clenshaw(const std::vector<double>& c, double t) {
+  double b1 = 0, b2 = 0;
+  for (size_t j = c.size(); j-- > 1;) { double b0 = 2 * t * b1 - b2 + c[j]; b2 = b1; b1 = b0; }
+  return t * b1 - b2 + c[0];
+}
+
+// Homomorphic evaluation in the Chebyshev basis: baby steps T_1..T_k (k = 2^ceil(m/2),
+// m = ceil(log2(d+1))), giant steps T_k, T_2k, ..., and the split
+//   p = q * T_G + r,  q_0 = c_G, q_i = 2 c_{G+i},  r_i = c_i - c_{2G-i} (2G-i <= deg),
+// which follows from 2 T_G T_{j-G} = T_j + T_{2G-j}.  Every partial result is
+// produced at a prescribed (level, scale), so additions never need adjustment.
+struct ChebEval {
+  Ctx& C;
+  std::map<int, Ct> T;  // index -> T_index(t)
+  int k = 1;
+  std::vector<int> giants;
+  explicit ChebEval(Ctx& c) : C(c) {}
+
+  static int deg_of(const std::vector<double>& p) { return (int)p.size() - 1; }
+  void split(const std::vector<double>& p, int G, std::vector<double>& qp, std::vector<double>& rp) const {
+    int D = deg_of(p);
+    qp.assign(D - G + 1, 0.0);
+    qp[0] = p[G];
+    for (int i = 1; i <= D - G; ++i) qp[i] = 2.0 * p[G + i];
+    rp.assign(p.begin(), p.begin() + G);
+    for (int i = 0; i < G; ++i) if (2 * G - i <= D) rp[i] -= p[2 * G - i];
+  }
+  int giant_for(int D) const {
+    int G = 0;
+    for (int g : giants) if (g <= D) G = g;
+    return G;
+  }
+  // highest level at which p can be produced
+  int best_level(const std::vector<double>& p) const {
+    int D = deg_of(p);
+    if (D < k) {
+      int lv = 1 << 30;
+      for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j).level - 1);
+      return lv;
+    }
+    int G = giant_for(D);
+    std::vector<double> qp, rp; split(p, G, qp, rp);
+    int lq = deg_of(qp) == 0 ? (1 << 30) : best_level(qp);
+    int lvl = std::min(std::min(lq, T.at(G).level) - 1, best_level(rp));
+    return lvl;
+  }
+  Ct eval(const std::vector<double>& p, int level, double scale) {
+    int D = deg_of(p);
+    if (D < k) {  // leaf: sum_j c_j T_j at (level, scale), then + c_0
+      Ct acc;
+      for (int j = 1; j <= D; ++j) {
+        const Ct& tj = T.at(j);
+        Ct term = mul_const_to(C, drop_to(tj, level + 1), p[j], scale);
+        acc = (j == 1) ? term : add_sub(C, acc, term, false);
+      }
+      return add_const(C, acc, p[0]);
+    }
+    int G = giant_for(D);
+    std::vector<double> qp, rp; split(p, G, qp, rp);
+    const Ct& tg = T.at(G);
+    Ct prod;
+    if (deg_of(qp) == 0) {
+      prod = mul_const_to(C, drop_to(tg, level + 1), qp[0], scale);
+    } else {
+      double sq = scale * (double)C.q[level + 1] / tg.scale;
+      Ct qv = eval(qp, level + 1, sq);
+      prod = rescale(C, mul_relin(C, qv, drop_to(tg, level + 1)));
+      prod.scale = scale;  // = sq * tg.scale / q_{level+1} by construction
+    }
+    Ct rv = eval(rp, level, scale);
+    return add_sub(C, prod, rv, false);
+  }
+  // T_a * T_b -> 2 T_a T_b - T_c  with T_c = T_{|a-b|} (or the constant 1 when a == b)
+  Ct cheb_product(const Ct& ta, const Ct& tb, int c_index) {
+    Ct prod = mul(C, ta, tb);
+    Ct diff;
+    if (c_index == 0) diff = add_const(C, prod, -0.5);
+    else {
+      const Ct& tc = T.at(c_index);
+      Ct half = mul_const_to(C, drop_to(tc, prod.level + 1), 0.5, prod.scale);
+      diff = add_sub(C, prod, half, true);
+    }
+    return mul_int(C, diff, 2);
+  }
+  Ct run(const Ct& t, const std::vector<double>& coeffs) {
+    int d = deg_of(coeffs);
+    int m = 0; while ((1 << m) < d + 1) ++m;
+    int lb = (m + 1) / 2; if (lb < 1) lb = 1;
+    k = 1 << lb;
+    T.clear(); T[1] = t;
+    for (int j = 2; j <= k; ++j) {
+      if (j % 2 == 0) T[j] = cheb_product(T.at(j / 2), T.at(j / 2), 0);
+      else T[j] = cheb_product(T.at(j / 2), T.at(j / 2 + 1), 1);
+    }
+    giants.clear();
+    for (int g = k; g < (1 << m); g *= 2) {
+      giants.push_back(g);
+      if (!T.count(g)) T[g] = cheb_product(T.at(g / 2), T.at(g / 2), 0);
+    }
+    int lvl = best_level(coeffs);
+    if (lvl < 0) throw std::runtime_error("Chebyshev evaluation: level exhausted");
+    return eval(coeffs, lvl, C.scale);
+  }
+};
+
+// ---------------------------------------------------------------- CryptoInvSqrt (Alg. 1)
+struct InvSqrtCfg { double lo, hi, B; int degree, iters, pre_bts; u64 bts_mask; };
+
+// One Newton step y <- 1.5 y - (0.5 a) y^3 (Sec. 2.2), in the operation order of
+// Alg. 1's loop body; tmp_alpha is produced last so that its scale can be set to
+// exactly the scale of tmp_beta.
+static Ct newton_step(Ctx& C, const Ct& x, const Ct& y) {
+  int ly = y.level;
+  Ct yy = mul(C, y, y);                            // y^2
+  Ct xy = mul(C, drop_to(x, std::min(x.level, ly)), y);  // (0.5 a) y
+  Ct tb = mul(C, xy, yy);                           // tmp_beta = (0.5 a) y^3
+  Ct ta = mul_const_to(C, drop_to(y, tb.level + 1), 1.5, tb.scale);  // tmp_alpha = 1.5 y
+  return add_sub(C, ta, tb, true);
+}
+
+static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
+  if (cfg.B <= 0 || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.iters < 0)
+    throw std::runtime_error("invsqrt: bad configuration");
+  if (cfg.pre_bts || cfg.bts_mask) throw std::runtime_error("invsqrt: bootstrapping not available in this context");
+  double lo = cfg.lo / cfg.B, hi = cfg.hi / cfg.B;
+  // pre-normalisation (Sec. 2.3): a -> a/B, then the affine map onto [-1, 1]
+  // for the Chebyshev basis, folded into one constant multiplication
+  double alpha = 2.0 / (cfg.B * (hi - lo)), beta = -(hi + lo) / (hi - lo);
+  if (in.level < 2) throw std::runtime_error("invsqrt: level exhausted");
+  Ct t = add_const(C, mul_const_to(C, in, alpha, C.scale), beta);
+  Ct x = mul_const_to(C, in, 0.5 / cfg.B, C.scale);  // ct_x = 0.5 * a/B
+  std::vector<double> coeffs = cheb_coeffs(lo, hi, cfg.degree);
+  ChebEval ev(C);
+  Ct y = ev.run(t, coeffs);
+  for (int i = 0; i < cfg.iters; ++i) {
+    if (std::min(y.level, x.level) < 2) throw std::runtime_error("invsqrt: level exhausted in Newton loop");
+    y = newton_step(C, x, y);
+  }
+  if (cfg.B != 1.0) y = mul_const_to(C, y, 1.0 / std::sqrt(cfg.B), y.scale);
+  return y;
+}
+
+// FP64 model of the same algorithm (the plaintext floor): Clenshaw + Newton
+static void plain_invsqrt(const double* a, size_t n, const InvSqrtCfg& cfg, double* out) {
+  double lo = cfg.lo / cfg.B, hi = cfg.hi / cfg.B;
+  std::vector<double> c = cheb_coeffs(lo, hi, cfg.degree);
+  for (size_t s = 0; s < n; ++s) {
+    double x = a[s] / cfg.B;
+    double t = (2.0 * x - (hi + lo)) / (hi - lo);
+    double y = clenshaw(c, t);
+    for (int i = 0; i < cfg.iters; ++i) y = 0.5 * y * (3.0 - x * y * y);
+    out[s] = y / std::sqrt(cfg.B);
+  }
+}
+
+// ============================================================================ C API
+#define API extern "C" __attribute__((visibility("default")))
+#define GUARD(...) try { __VA_ARGS__ } catch (const std::exception& e) { g_err = e.what(); }
+
+API const char* orc_last_error() { return g_err.c_str(); }
+
+API void* orc_ctx_create(uint32_t log_n, uint32_t n_q, const uint32_t* q_bits, uint32_t n_p, const uint32_t* p_bits,
+                         uint32_t alpha, double log_scale, uint32_t hw, uint64_t seed) {
+  GUARD(
+    std::vector<int> qb(q_bits, q_bits + n_q), pb(p_bits, p_bits + n_p);
+    return ctx_create((int)log_n, qb, pb, (int)alpha, log_scale, (int)hw, seed);
+  )
+  return nullptr;
+}
+API void orc_ctx_destroy(void* c) { delete (Ctx*)c; }
+API int orc_ctx_info(void* c, uint32_t* log_n, uint32_t* n_q, uint32_t* n_p, uint32_t* alpha, double* scale) {
+  Ctx* C = (Ctx*)c; *log_n = C->log_n; *n_q = C->n_q; *n_p = C->n_p; *alpha = C->alpha; *scale = C->scale; return 0;
+}
+API int orc_ctx_primes(void* c, uint64_t* out) {
+  Ctx* C = (Ctx*)c; for (size_t i = 0; i < C->q.size(); ++i) out[i] = C->q[i]; return 0;
+}
+API int orc_ctx_psi(void* c, uint64_t* out) {
+  Ctx* C = (Ctx*)c; for (size_t i = 0; i < C->psi.size(); ++i) out[i] = C->psi[i]; return 0;
+}
+API int orc_export_secret(void* c, int64_t* out) {
+  Ctx* C = (Ctx*)c; for (size_t i = 0; i < C->N; ++i) out[i] = C->s[i]; return 0;
+}
+API int orc_gen_galois_key(void* c, uint64_t g) { GUARD(gen_key(*(Ctx*)c, g); return 0;) return -1; }
+API uint64_t orc_galois_of_rotation(void* c, int64_t r) { return galois_of_rotation(*(Ctx*)c, r); }
+// key digit j for galois element g (0 = relinearisation), each part [n_q+n_p][N], NTT domain
+API int orc_export_key(void* c, uint64_t g, uint32_t j, uint64_t* out_b, uint64_t* out_a) {
+  GUARD(
+    Ctx* C = (Ctx*)c; gen_key(*C, g);
+    const KeyDigit& kd = C->keys.at(g).at(j);
+    size_t total = C->q.size();
+    for (size_t t = 0; t < total; ++t) {
+      std::memcpy(out_b + t * C->N, kd.b[t].data(), C->N * 8);
+      std::memcpy(out_a + t * C->N, kd.a[t].data(), C->N * 8);
+    }
+    return 0;
+  )
+  return -1;
+}
+// single-limb transforms by prime index
+API int orc_ntt(void* c, uint64_t* a, uint32_t pi, int inverse) {
+  Ctx* C = (Ctx*)c; Limb v(a, a + C->N);
+  if (inverse) ntt_inverse(*C, v, (int)pi); else ntt_forward(*C, v, (int)pi);
+  std::memcpy(a, v.data(), C->N * 8); return 0;
+}
+// coefficient-domain RNS steps (arrays are [limb][N])
+API int orc_modup_coeff(void* c, const uint64_t* in, int level, int digit, uint64_t* out) {
+  GUARD(
+    Ctx* C = (Ctx*)c; Poly d(level + 1);
+    for (int i = 0; i <= level; ++i) d[i].assign(in + (size_t)i * C->N, in + (size_t)(i + 1) * C->N);
+    Poly y = modup_coeff(*C, d, level, digit);
+    for (size_t e = 0; e < y.size(); ++e) std::memcpy(out + e * C->N, y[e].data(), C->N * 8);
+    return 0;
+  )
+  return -1;
+}
+API int orc_moddown_coeff(void* c, const uint64_t* in, int level, uint64_t* out) {
+  GUARD(
+    Ctx* C = (Ctx*)c; Poly x(level + 1 + C->n_p);
+    for (size_t i = 0; i < x.size(); ++i) x[i].assign(in + i * C->N, in + (i + 1) * C->N);
+    Poly y = moddown_coeff(*C, x, level);
+    for (int i = 0; i <= level; ++i) std::memcpy(out + (size_t)i * C->N, y[i].data(), C->N * 8);
+    return 0;
+  )
+  return -1;
+}
+API int orc_rescale_ntt(void* c, const uint64_t* in, int level, uint64_t* out) {
+  GUARD(
+    Ctx* C = (Ctx*)c; Poly x(level + 1);
+    for (int i = 0; i <= level; ++i) x[i].assign(in + (size_t)i * C->N, in + (size_t)(i + 1) * C->N);
+    Poly y = rescale_poly(*C, x, level);
+    for (int i = 0; i < level; ++i) std::memcpy(out + (size_t)i * C->N, y[i].data(), C->N * 8);
+    return 0;
+  )
+  return -1;
+}
+// encode / decode (full-slot): coefficients as integer-valued doubles
+API int orc_encode_coeffs(void* c, const double* re, const double* im, double scale, double* out) {
+  GUARD(
+    Ctx* C = (Ctx*)c; size_t n = C->N / 2; std::vector<cd> z(n);
+    for (size_t j = 0; j < n; ++j) z[j] = cd(re[j], im ? im[j] : 0.0);
+    std::vector<double> m = encode_coeffs(*C, z, scale);
+    std::memcpy(out, m.data(), C->N * 8); return 0;
+  )
+  return -1;
+}
+API int orc_decode_coeffs(void* c, const double* m, double scale, double* re, double* im) {
+  GUARD(
+    Ctx* C = (Ctx*)c; std::vector<double> mv(m, m + C->N);
+    std::vector<cd> z = decode_coeffs(*C, mv, scale);
+    for (size_t j = 0; j < z.size(); ++j) { re[j] = z[j].real(); if (im) im[j] = z[j].imag(); }
+    return 0;
+  )
+  return -1;
+}
+// ciphertext handles: limbs are [2][level+1][N], NTT domain
+API void* orc_ct_import(void* c, const uint64_t* limbs, int level, double scale) {
+  GUARD(
+    Ctx* C = (Ctx*)c; if (level < 0 || level > C->L()) throw std::runtime_error("bad level");
+    Ct* ct = new Ct; ct->level = level; ct->scale = scale;
+    for (int p = 0; p < 2; ++p) {
+      ct->c[p].resize(level + 1);
+      for (int i = 0; i <= level; ++i) {
+        const uint64_t* src = limbs + ((size_t)p * (level + 1) + i) * C->N;
+        ct->c[p][i].assign(src, src + C->N);
+        for (size_t k = 0; k < C->N; ++k) if (ct->c[p][i][k] >= C->q[i]) { delete ct; throw std::runtime_error("residue out of range"); }
+      }
+    }
+    return ct;
+  )
+  return nullptr;
+}
+API int orc_ct_info(void* h, int* level, double* scale) { Ct* ct = (Ct*)h; *level = ct->level; *scale = ct->scale; return 0; }
+API int orc_ct_export(void* c, void* h, uint64_t* out) {
+  Ctx* C = (Ctx*)c; Ct* ct = (Ct*)h;
+  for (int p = 0; p < 2; ++p) for (int i = 0; i <= ct->level; ++i)
+    std::memcpy(out + ((size_t)p * (ct->level + 1) + i) * C->N, ct->c[p][i].data(), C->N * 8);
+  return 0;
+}
+API void orc_ct_free(void* h) { delete (Ct*)h; }
+API void* orc_encrypt(void* c, const double* re, const double* im, uint64_t n_slots, int level, uint64_t seed) {
+  GUARD(
+    Ctx* C = (Ctx*)c; std::vector<cd> z(n_slots);
+    for (size_t j = 0; j < n_slots; ++j) z[j] = cd(re[j], im ? im[j] : 0.0);
+    return new Ct(encrypt(*C, z, level, seed));
+  )
+  return nullptr;
+}
+API int orc_decrypt(void* c, void* h, double* re, double* im) {
+  GUARD(
+    std::vector<cd> z = decrypt(*(Ctx*)c, *(Ct*)h);
+    for (size_t j = 0; j < z.size(); ++j) { re[j] = z[j].real(); if (im) im[j] = z[j].imag(); }
+    return 0;
+  )
+  return -1;
+}
+API int orc_decrypt_coeffs(void* c, void* h, double* out) {
+  GUARD(
+    std::vector<double> m = decrypt_coeffs(*(Ctx*)c, *(Ct*)h);
+    std::memcpy(out, m.data(), m.size() * 8); return 0;
+  )
+  return -1;
+}
+#define CT_OP(...) GUARD(return new Ct(__VA_ARGS__);) return nullptr;
+API void* orc_add(void* c, void* a, void* b) { CT_OP(add_sub(*(Ctx*)c, *(Ct*)a, *(Ct*)b, false)) }
+API void* orc_sub(void* c, void* a, void* b) { CT_OP(add_sub(*(Ctx*)c, *(Ct*)a, *(Ct*)b, true)) }
+API void* orc_mul_relin(void* c, void* a, void* b) { CT_OP(mul_relin(*(Ctx*)c, *(Ct*)a, *(Ct*)b)) }
+API void* orc_mul(void* c, void* a, void* b) { CT_OP(mul(*(Ctx*)c, *(Ct*)a, *(Ct*)b)) }
+API void* orc_rescale(void* c, void* a) { CT_OP(rescale(*(Ctx*)c, *(Ct*)a)) }
+API void* orc_rotate(void* c, void* a, int64_t steps) { CT_OP(rotate(*(Ctx*)c, *(Ct*)a, steps)) }
+API void* orc_conjugate(void* c, void* a) { CT_OP(conjugate(*(Ctx*)c, *(Ct*)a)) }
+API void* orc_mul_const(void* c, void* a, double v, double target_scale) { CT_OP(mul_const_to(*(Ctx*)c, *(Ct*)a, v, target_scale)) }
+API void* orc_add_const(void* c, void* a, double v) { CT_OP(add_const(*(Ctx*)c, *(Ct*)a, v)) }
+API void* orc_mul_int(void* c, void* a, int64_t m) { CT_OP(mul_int(*(Ctx*)c, *(Ct*)a, m)) }
+API void* orc_drop(void* c, void* a, int level) { (void)c; CT_OP(drop_to(*(Ct*)a, level)) }
+API void* orc_invsqrt(void* c, void* a, double lo, double hi, double B, uint32_t degree, uint32_t iters,
+                      uint32_t pre_bts, uint64_t bts_mask) {
+  InvSqrtCfg cfg{lo, hi, B, (int)degree, (int)iters, (int)pre_bts, bts_mask};
+  CT_OP(invsqrt(*(Ctx*)c, *(Ct*)a, cfg))
+}
+API int orc_cheb_coeffs(double lo, double hi, uint32_t d, double* out) {
+  std::vector<double> c = cheb_coeffs(lo, hi, (int)d);
+  std::memcpy(out, c.data(), c.size() * 8); return 0;
+}
+API double orc_clenshaw(const double* c, uint32_t d, double t) {
+  std::vector<double> cv(c, c + d + 1); return clenshaw(cv, t);
+}
+API int orc_plain_invsqrt(const double* a, uint64_t n, double lo, double hi, double B, uint32_t degree, uint32_t iters,
+                          double* out) {
+  InvSqrtCfg cfg{lo, hi, B, (int)degree, (int)iters, 0, 0};
+  plain_invsqrt(a, n, cfg, out); return 0;
+}
+// raw PRNG / sampler access for pins
+API uint64_t orc_splitmix_stream(uint64_t seed, uint64_t tag, uint64_t n, uint64_t* out) {
+  Stream s(seed, tag); for (uint64_t i = 0; i < n; ++i) out[i] = s.next(); return n;
+}
