@@ -1,0 +1,320 @@
+"""Benchmark: CryptoInvSqrt ciphertexts per second at N = 2^16 on one GB300.
+
+One step = CryptoInvSqrt (Alg. 1: Chebyshev initial value + Newton) on a batch
+of resident ciphertexts (N = 2^16, 32768 slots, 24 x 50-bit Q primes + 2 x
+60-bit P primes, two primes per key-switching digit, scale 2^50, inputs
+uniform in [1e-3, 1]) with a (degree, Newton steps) pair whose decrypted MRE
+is at most 1e-7.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain C++ implementation the GPU
+path is checked against) on the host cores, for the same workload, metric and
+unit.  Under torchrun each rank runs its own replica (no collective); rank 0
+prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "InvSqrt ct/s at N=2^16 (MRE<=1e-7), batched vs plain; NTT GB/s; p99 latency"
+UNIT = "ct/s"
+PRESET = "n16"
+LO, HI, B = 1e-3, 1.0, 1.0
+MRE_TARGET = 1e-7
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8, help="ciphertexts per step")
+    ap.add_argument("--degree", type=int, default=31)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, batch):
+    p = __import__("paper_2606_10477_gb300.inputs", fromlist=["PRESETS"]).PRESETS[PRESET]
+    return {
+        "workload": (f"CryptoInvSqrt, N=2^{p['log_n']} ({2 ** (p['log_n'] - 1)} slots), {len(p['q_bits'])}x"
+                     f"{p['q_bits'][0]}-bit Q + {len(p['p_bits'])}x{p['p_bits'][0]}-bit P primes, "
+                     f"{p['alpha']} primes/digit, scale 2^{p['log_scale']}, inputs U[{LO},{HI}], "
+                     f"Chebyshev degree {args.degree}, {args.iters} Newton steps, input level {len(p['q_bits']) - 1}"),
+        "batch_ciphertexts": batch,
+        "l2": "inputs larger than L2: batch of resident ciphertexts (24 MiB each) plus the 312 MiB relinearisation key",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_invsqrt_seconds(args, seed=1):
+    """One full oracle CryptoInvSqrt on the benchmark workload; returns (seconds, threads, MRE)."""
+    import oracle
+    from paper_2606_10477_gb300 import inputs
+    p = inputs.PRESETS[PRESET]
+    ctx = oracle.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], seed)
+    a = inputs.uniform_values(seed, ctx.N // 2, LO, HI)
+    ct = ctx.encrypt(a, ctx.n_q - 1, seed + 100)
+    t0 = time.perf_counter()
+    out = ctx.invsqrt(ct, LO, HI, B, args.degree, args.iters)
+    dt = time.perf_counter() - t0
+    y = ctx.decrypt(out).real
+    ref = 1 / np.sqrt(a)
+    return dt, oracle.threads(), float(np.mean(np.abs(y - ref) / ref))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    steps = max(1, args.steps)
+    times = []
+    mre = None
+    for i in range(args.warmup + steps):
+        dt, threads, mre = oracle_invsqrt_seconds(args, seed=1 + i)
+        if i >= args.warmup:
+            times.append(dt)
+        if i == 0 and dt * (args.warmup + steps) > 240:  # keep the whole run within a few minutes
+            args.warmup, steps = 0, 1
+            times = [dt]
+            break
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(args, 1),
+        "mre": mre,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "one full oracle CryptoInvSqrt of one ciphertext per step (same parameters)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU path
+def run_ours(args):
+    import torch
+    from paper_2606_10477_gb300 import hedap, inputs
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    p = inputs.PRESETS[PRESET]
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1 + rank,
+                        stream=stream.cuda_stream)
+    L = ctx.n_q - 1
+    batch = args.batch
+    vals = [inputs.uniform_values(1000 * rank + i, ctx.N // 2, LO, HI) for i in range(batch)]
+    cts = [ctx.encrypt(v, L, 7 + i) for i, v in enumerate(vals)]
+
+    def step():
+        return [ctx.invsqrt(c, LO, HI, B, args.degree, args.iters) for c in cts]
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # accuracy of this configuration on the batch (untimed)
+    outs = step()
+    mres = []
+    for v, o in zip(vals, outs):
+        y = ctx.decrypt(o).real
+        ref = 1 / np.sqrt(v)
+        mres.append(float(np.mean(np.abs(y - ref) / ref)))
+    out_level = outs[0].level
+    del outs
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps on resident inputs
+    clocks = ClockSampler(local)
+    launches0 = hedap.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = hedap.launch_count() - launches0
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = ws * batch * args.steps / (elapsed_ms / 1e3)
+
+    # ---- per-ciphertext latency (plain path: one ciphertext per call sequence)
+    lat = []
+    for c in cts:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.invsqrt(c, LO, HI, B, args.degree, args.iters)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+
+    # ---- same steps with the per-kernel-class event profiler on
+    hedap.profile_enable(True)
+    for _ in range(max(1, min(args.steps, 2))):
+        step()
+    torch.cuda.synchronize()
+    prof = hedap.profile_read()
+    hedap.profile_enable(False)
+    total_prof_ms = sum(v[1] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_dom, ms_dom, by_dom = prof[dom]
+    peaks, peak_kind = measured_peaks()
+    achieved = by_dom / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+    ntt = prof["ntt"]
+    ntt_gbs = ntt[2] / (ntt[1] / 1e3) / 1e9 if ntt[1] > 0 else None
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    host_in = [torch.empty((2, L + 1, ctx.N), dtype=torch.int64, pin_memory=True) for _ in range(batch)]
+    for h, c in zip(host_in, cts):
+        h.numpy()[...] = c.limbs().view(np.int64)
+    host_out = [torch.empty((2, out_level + 1, ctx.N), dtype=torch.int64, pin_memory=True) for _ in range(batch)]
+    h2d = sum(h.numel() * 8 for h in host_in)
+    d2h = sum(h.numel() * 8 for h in host_out)
+
+    def e2e_step():
+        for hi, ho in zip(host_in, host_out):
+            ci = ctx.ct_import(hi, L, ctx.scale)
+            co = ctx.invsqrt(ci, LO, HI, B, args.degree, args.iters)
+            co.export_to(ho)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    k_e2e = max(1, min(args.steps, 3))
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * batch * k_e2e / e2e_s
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        dt, threads, omre = oracle_invsqrt_seconds(args)
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "one full oracle CryptoInvSqrt of one ciphertext on the same workload", "mre": omre}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(args, batch),
+            "mre": max(mres), "mre_target": MRE_TARGET,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "ntt_gbs": ntt_gbs,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {
+                "kernel": dom, "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None, "peak_source": peak_kind,
+                "launch_groups": n_dom, "avg_group_us": 1e3 * ms_dom / max(1, n_dom),
+            },
+            "profile_share": {k: round(v[1] / total_prof_ms, 4) for k, v in prof.items()} if total_prof_ms else {},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

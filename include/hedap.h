@@ -1,0 +1,179 @@
+/*
+ * hedap.h -- C ABI of the GB300 RNS-CKKS library behind CryptoInvSqrt.
+ *
+ * The operations follow the paper's statement of the problem: keys owned by
+ * the server (Sec. 4.2, "the server uses its own public and secret keys"),
+ * Enc(values, l) at a chosen level (Alg. 3), CryptoInvSqrt(ct, d, n) with
+ * pre-normalisation by B (Alg. 1, Sec. 2.3), Dec (Alg. 2), and the CKKS
+ * operations Add/Sub/Mul_P/Mul_C, level management and rotation (Sec. 2.1).
+ * The ring-level conventions (prime chain, NTT order, rounding, key
+ * switching, sampling) are the textbook RNS-CKKS ones; the paper states none.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns hedap_status: 0 on success, a negative code on
+ *    error; nothing throws across the ABI.  hedap_last_error() gives a
+ *    message for the calling thread's most recent error.
+ *  - Handles (hedap_ctx, hedap_ct) are created and freed by the library.
+ *    A ciphertext handle owns device memory; hedap_ct_free releases it
+ *    stream-ordered on the context's stream.
+ *  - Host arrays passed in are owned by the caller and copied on entry;
+ *    host arrays passed out are caller-allocated with the stated capacity.
+ *    Arguments named `on_device` select whether a uint64_t* points to device
+ *    memory (1, accessed on the context's stream) or host memory (0).
+ *  - Ciphertext limb layout: [2][level+1][N] uint64_t, part-major (c0 then
+ *    c1), limb i holding residues modulo q_i in the NTT (evaluation) domain;
+ *    evaluation j sits at psi_i^(2*bitrev(j)+1), psi_i a primitive 2N-th root
+ *    of unity modulo q_i.
+ *  - A context is single-threaded: calls on one context must not overlap.
+ *    All work is issued on the context's CUDA stream; functions that return
+ *    host data synchronise that stream.
+ */
+#ifndef HEDAP_H
+#define HEDAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HEDAP_OK = 0,
+  HEDAP_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad index)   */
+  HEDAP_ERR_LEVEL = -2,    /* not enough levels left for the requested operation     */
+  HEDAP_ERR_SCALE = -3,    /* operands' scales differ                                */
+  HEDAP_ERR_OOM = -4,      /* device allocation failed                               */
+  HEDAP_ERR_CUDA = -5,     /* a CUDA runtime call failed                             */
+  HEDAP_ERR_TIMEOUT = -6,  /* a bounded device wait ran out                          */
+  HEDAP_ERR_RANGE = -7,    /* input values outside the configured interval           */
+  HEDAP_ERR_KEY = -8       /* a required switching key was not generated             */
+} hedap_status;
+
+typedef struct hedap_ctx hedap_ctx;
+typedef struct hedap_ct hedap_ct;
+
+/* CKKS parameters.  Q primes are generated in the order given (q_0 first);
+ * each is the first prime 2^b + k*2N + 1, then 2^b - k*2N + 1, k = 1, 2, ...,
+ * not already used; the P (special) primes follow.  Bit sizes 33..60.
+ * alpha = primes per key-switching digit (dnum = ceil(n_q / alpha)).
+ * secret_hw = Hamming weight of the ternary secret (0 = dense uniform). */
+typedef struct {
+  uint32_t log_n;
+  uint32_t n_q;
+  const uint32_t* q_bits;
+  uint32_t n_p;
+  const uint32_t* p_bits;
+  uint32_t alpha;
+  double log_scale;
+  uint32_t secret_hw;
+} hedap_params;
+
+/* CryptoInvSqrt configuration (Alg. 1 with the pre-normalisation of Sec. 2.3):
+ * inputs a lie in [lo, hi]; a/B lies in (0, 1]; the initial value is the
+ * degree-`degree` Chebyshev interpolant of 1/sqrt(x) on [lo/B, hi/B];
+ * `newton_iters` Newton steps y <- y (3 - (a/B) y^2) / 2 follow; the output is
+ * y / sqrt(B).  pre_bts and bts_mask request bootstrapping and must be 0 on a
+ * context without bootstrapping keys. */
+typedef struct {
+  double lo, hi, B;
+  uint32_t degree;
+  uint32_t newton_iters;
+  uint32_t pre_bts;
+  uint64_t bts_mask;
+} hedap_invsqrt_cfg;
+
+const char* hedap_status_str(hedap_status s);
+const char* hedap_last_error(void);
+
+/* Context: prime chain, NTT tables, secret key and relinearisation key,
+ * generated from `seed` (SplitMix64 streams).  cuda_stream may be NULL (the
+ * legacy default stream) or a cudaStream_t owned by the caller that outlives
+ * the context. */
+hedap_status hedap_ctx_create(const hedap_params* params, uint64_t seed, void* cuda_stream, hedap_ctx** out);
+void hedap_ctx_destroy(hedap_ctx* ctx);
+/* primes: n_q + n_p values (Q then P) into out[cap]. */
+hedap_status hedap_ctx_primes(const hedap_ctx* ctx, uint64_t* out, size_t cap);
+hedap_status hedap_sync(hedap_ctx* ctx);
+
+/* Switching keys.  Galois element g (odd, < 2N); rotation by r slots uses
+ * g = 5^r mod 2N, conjugation g = 2N - 1.  Keys are generated on first use;
+ * these calls generate them ahead of time. */
+hedap_status hedap_gen_galois_key(hedap_ctx* ctx, uint64_t galois);
+/* Export digit j of the key for g (g = 0: relinearisation key) into host
+ * arrays b, a of [n_q + n_p][N] words each (NTT domain). */
+hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t galois, uint32_t digit, uint64_t* b, uint64_t* a);
+
+/* Enc (symmetric, with the server's secret key): n_slots must be N/2. */
+hedap_status hedap_encrypt(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, int level,
+                           uint64_t seed, hedap_ct** out);
+/* Dec + decode into re/im (im may be NULL); n_slots must be N/2. */
+hedap_status hedap_decrypt(hedap_ctx* ctx, const hedap_ct* ct, double* re, double* im, size_t n_slots);
+
+hedap_status hedap_ct_import(hedap_ctx* ctx, const uint64_t* limbs, int level, double scale, int on_device,
+                             hedap_ct** out);
+/* Export [2][level+1][N] words into out (capacity cap words). */
+hedap_status hedap_ct_export(hedap_ctx* ctx, const hedap_ct* ct, uint64_t* out, size_t cap, int on_device);
+hedap_status hedap_ct_info(const hedap_ct* ct, int* level, double* scale);
+void hedap_ct_free(hedap_ct* ct);
+
+/* Sec. 2.1 operations.  Binary operations first bring both operands to the
+ * lower level by dropping limbs.  Add/Sub require equal scales. */
+hedap_status hedap_add(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out);
+hedap_status hedap_sub(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out);
+/* Mul_C: tensor product + relinearisation (hybrid key switching), no rescale. */
+hedap_status hedap_mul_relin(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out);
+/* Mul_C followed by rescale (one level consumed). */
+hedap_status hedap_mul(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out);
+/* Divide by the last prime q_l with rounding; scale /= q_l, level -= 1. */
+hedap_status hedap_rescale(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
+hedap_status hedap_rotate(hedap_ctx* ctx, const hedap_ct* a, int64_t steps, hedap_ct** out);
+hedap_status hedap_conjugate(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
+/* Mul_P by a real constant c, rescaled so that the result has exactly
+ * scale `target_scale` (the constant is encoded at target*q_l/scale). */
+hedap_status hedap_mul_const(hedap_ctx* ctx, const hedap_ct* a, double c, double target_scale, hedap_ct** out);
+/* Add_P of a real constant (encoded at the ciphertext's scale). */
+hedap_status hedap_add_const(hedap_ctx* ctx, const hedap_ct* a, double c, hedap_ct** out);
+/* Multiply by a small integer (no level consumed). */
+hedap_status hedap_mul_int(hedap_ctx* ctx, const hedap_ct* a, int64_t m, hedap_ct** out);
+hedap_status hedap_drop_level(hedap_ctx* ctx, const hedap_ct* a, int level, hedap_ct** out);
+
+/* CryptoInvSqrt (Alg. 1). */
+hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_invsqrt_cfg* cfg, hedap_ct** out);
+
+/* Negacyclic NTT (inverse=0) or inverse NTT with N^-1 (inverse=1) of n_limbs
+ * consecutive length-N limbs in place; limb i uses prime index first_prime+i
+ * (global index over Q then P). */
+hedap_status hedap_ntt(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, uint32_t first_prime, int inverse,
+                       int on_device);
+
+/* Steps of hybrid key switching, for parity tests (host arrays, [limb][N]).
+ * hedap_modup: coefficient-domain input over q_0..q_level -> for every digit j
+ *   (alpha consecutive primes) the fast basis conversion onto Q_level u P,
+ *   out [dnum][level+1+n_p][N] coefficient domain (digit j's own limbs copy the input).
+ * hedap_moddown: two coefficient-domain polynomials over Q_level u P,
+ *   in [2][level+1+n_p][N] -> round(x / P) up to the conversion slack, out [2][level+1][N].
+ * hedap_key_switch: NTT-domain d over q_0..q_level and the key for `galois`
+ *   (0 = relinearisation) -> (ks0, ks1), out [2][level+1][N] NTT domain. */
+hedap_status hedap_modup(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
+hedap_status hedap_moddown(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
+hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint64_t galois, uint64_t* out);
+
+/* Profiling (process-wide, not part of the paper's interface).
+ * hedap_profile_enable(1) resets the counters and, until disabled, records a
+ * CUDA event pair around every launch group of these kernel classes:
+ * "ntt" (one forward or inverse transform of a limb batch: two launches),
+ * "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph",
+ * "elementwise".  hedap_profile_read synchronises and returns, for one class,
+ * the number of timed groups, their summed event time in ms, and their summed
+ * algorithmic bytes (each input word read once, each output word written once).
+ * hedap_launch_count returns the number of kernels this library has launched
+ * since it was loaded (profiling on or off). */
+hedap_status hedap_profile_enable(int on);
+hedap_status hedap_profile_read(const char* kernel_class, uint64_t* groups, double* ms, double* bytes);
+hedap_status hedap_launch_count(uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEDAP_H */

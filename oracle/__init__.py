@@ -36,7 +36,9 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     base = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fvisibility=hidden", _SRC]
-    subprocess.run(base + ["-o", tmp], check=True)
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp], capture_output=True)
+    if r.returncode != 0:  # no OpenMP runtime: the same code, one thread
+        subprocess.run(base + ["-o", tmp], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -93,6 +95,8 @@ def _declare(L):
         "orc_clenshaw": (C.c_double, [f64p, C.c_uint32, C.c_double]),
         "orc_plain_invsqrt": (C.c_int, [f64p, C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_uint32,
                                         C.c_uint32, f64p]),
+        "orc_key_switch": (C.c_int, [vp, u64p, C.c_int, C.c_uint64, u64p]),
+        "orc_threads": (C.c_int, []),
         "orc_splitmix_stream": (C.c_uint64, [C.c_uint64, C.c_uint64, C.c_uint64, u64p]),
     }
     for name, (res, args) in sig.items():
@@ -213,6 +217,12 @@ class Context:
         _check(lib().orc_rescale_ntt(self.h, x, level, out))
         return out
 
+    def key_switch(self, d: np.ndarray, level: int, galois: int) -> np.ndarray:
+        x = np.ascontiguousarray(d, dtype=np.uint64)
+        out = np.empty((2, level + 1, self.N), dtype=np.uint64)
+        _check(lib().orc_key_switch(self.h, x, level, galois, out))
+        return out
+
     def encode_coeffs(self, re, im=None, scale=None) -> np.ndarray:
         re = np.ascontiguousarray(re, dtype=np.float64)
         im = np.zeros_like(re) if im is None else np.ascontiguousarray(im, dtype=np.float64)
@@ -308,3 +318,8 @@ def splitmix_stream(seed: int, tag: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.uint64)
     lib().orc_splitmix_stream(seed, tag, n, out)
     return out
+
+
+def threads() -> int:
+    """Host threads the oracle's per-limb loops use."""
+    return int(lib().orc_threads())

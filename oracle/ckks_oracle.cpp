@@ -36,6 +36,9 @@
 #include <stdexcept>
 #include <string>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef uint64_t u64;
 typedef int64_t i64;
@@ -45,6 +48,11 @@ typedef std::vector<u64> Limb;
 typedef std::vector<Limb> Poly;  // [limb][coefficient]
 
 static thread_local std::string g_err;
+
+// Loops over independent RNS limbs may run on several host threads (OpenMP,
+// when the compiler provides it); every limb is computed exactly as in the
+// serial loop, so results do not depend on the thread count.
+#define PER_LIMB _Pragma("omp parallel for schedule(dynamic)")
 
 // ---------------------------------------------------------------- arithmetic
 static u64 mulmod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
@@ -309,6 +317,7 @@ static KeyDigit make_key_digit(const Ctx& C, const Poly& sp, u64 g, int j) {
   Stream se(C.seed, tag_evk_e(g, j));
   std::vector<i64> e(C.N); for (size_t i = 0; i < C.N; ++i) e[i] = sample_cbd(se);
   int lo = j * C.alpha, hi = std::min(lo + C.alpha, C.n_q);
+  PER_LIMB
   for (int t = 0; t < total; ++t) {
     u64 qt = C.q[t];
     Limb et = residues_of(C, e, t); ntt_forward(C, et, t);
@@ -344,6 +353,7 @@ static void gen_key(Ctx& C, u64 g) {
   if (C.keys.count(g)) return;
   int total = C.n_q + C.n_p;
   Poly sp(total);
+  PER_LIMB
   for (int t = 0; t < total; ++t) {
     if (g == 0) {  // relinearisation: s^2
       sp[t].resize(C.N);
@@ -370,6 +380,7 @@ static Ctx* ctx_create(int log_n, const std::vector<int>& qb, const std::vector<
   C->q = prime_chain(log_n, all);
   int total = (int)C->q.size();
   C->psi.resize(total); C->psi_rev.resize(total); C->ipsi_rev.resize(total); C->n_inv.resize(total);
+  PER_LIMB
   for (int t = 0; t < total; ++t) {
     u64 q = C->q[t], psi = find_psi(q, log_n), ipsi = invmod(psi, q);
     C->psi[t] = psi;
@@ -384,6 +395,7 @@ static Ctx* ctx_create(int log_n, const std::vector<int>& qb, const std::vector<
   Stream ss(seed, TAG_SK);
   C->s = sample_ternary(ss, log_n, hw);
   C->s_ntt.resize(total);
+  PER_LIMB
   for (int t = 0; t < total; ++t) { C->s_ntt[t] = residues_of(*C, C->s, t); ntt_forward(*C, C->s_ntt[t], t); }
   gen_key(*C, 0);
   return C.release();
@@ -404,6 +416,7 @@ static std::vector<double> encode_coeffs(const Ctx& C, const std::vector<cd>& z,
 }
 static Poly coeffs_to_ntt(const Ctx& C, const std::vector<double>& m, int level) {
   Poly p(level + 1, Limb(C.N));
+  PER_LIMB
   for (int i = 0; i <= level; ++i) {
     for (size_t k = 0; k < C.N; ++k) p[i][k] = double_to_mod(m[k], C.q[i]);
     ntt_forward(C, p[i], i);
@@ -449,6 +462,7 @@ static Ct encrypt(const Ctx& C, const std::vector<cd>& z, int level, u64 seed) {
   for (int i = 0; i <= level; ++i) for (size_t k = 0; k < C.N; ++k) ct.c[1][i][k] = sample_uniform(sa, C.q[i]);
   Stream se(seed, TAG_ENC_E);
   std::vector<i64> e(C.N); for (size_t k = 0; k < C.N; ++k) e[k] = sample_cbd(se);
+  PER_LIMB
   for (int i = 0; i <= level; ++i) {
     u64 q = C.q[i];
     Limb mi(C.N);
@@ -460,6 +474,7 @@ static Ct encrypt(const Ctx& C, const std::vector<cd>& z, int level, u64 seed) {
 }
 static std::vector<double> decrypt_coeffs(const Ctx& C, const Ct& ct) {
   Poly m(ct.level + 1, Limb(C.N));
+  PER_LIMB
   for (int i = 0; i <= ct.level; ++i) {
     u64 q = C.q[i];
     for (size_t k = 0; k < C.N; ++k) m[i][k] = addmod(ct.c[0][i][k], mulmod(ct.c[1][i][k], C.s_ntt[i][k], q), q);
@@ -492,6 +507,7 @@ static Poly rescale_poly(const Ctx& C, const Poly& p, int l) {
   u64 ql = C.q[l], h = ql >> 1;
   Limb last = p[l]; ntt_inverse(C, last, l);
   Poly out(l, Limb(C.N));
+  PER_LIMB
   for (int i = 0; i < l; ++i) {
     u64 qi = C.q[i], inv = invmod(ql % qi, qi);
     Limb r(C.N);
@@ -524,6 +540,7 @@ static Poly modup_coeff(const Ctx& C, const Poly& dcoef, int l, int j) {
     qhat_inv[i - lo] = invmod(h, C.q[i]);
   }
   Poly out(ext.size(), Limb(C.N));
+  PER_LIMB
   for (size_t e = 0; e < ext.size(); ++e) {
     int t = ext[e]; u64 qt = C.q[t];
     if (t >= lo && t < hi) { out[e] = dcoef[t]; continue; }
@@ -559,6 +576,7 @@ static Poly moddown_coeff(const Ctx& C, const Poly& x, int l) {
   };
   std::vector<u64> half_p(K); for (int k = 0; k < K; ++k) half_p[k] = half_mod(C.q[C.n_q + k]);
   Poly out(l + 1, Limb(C.N));
+  PER_LIMB
   for (int i = 0; i <= l; ++i) {
     u64 qi = C.q[i], hq = half_mod(qi);
     u64 Pm = 1 % qi; for (int k = 0; k < K; ++k) Pm = mulmod(Pm, C.q[C.n_q + k] % qi, qi);
@@ -585,12 +603,15 @@ static void key_switch(const Ctx& C, const Poly& d, int l, u64 g, Poly& o0, Poly
   auto it = C.keys.find(g);
   if (it == C.keys.end()) throw std::runtime_error("missing switching key");
   const std::vector<KeyDigit>& key = it->second;
-  Poly dcoef = d; for (int i = 0; i <= l; ++i) ntt_inverse(C, dcoef[i], i);
+  Poly dcoef = d;
+  PER_LIMB
+  for (int i = 0; i <= l; ++i) ntt_inverse(C, dcoef[i], i);
   std::vector<int> ext; for (int i = 0; i <= l; ++i) ext.push_back(i);
   for (int k = 0; k < C.n_p; ++k) ext.push_back(C.n_q + k);
   Poly acc0(ext.size(), Limb(C.N, 0)), acc1(ext.size(), Limb(C.N, 0));
   for (int j = 0; j < n_digits(C, l); ++j) {
     Poly y = modup_coeff(C, dcoef, l, j);
+    PER_LIMB
     for (size_t e = 0; e < ext.size(); ++e) {
       int t = ext[e]; u64 qt = C.q[t];
       ntt_forward(C, y[e], t);
@@ -600,8 +621,10 @@ static void key_switch(const Ctx& C, const Poly& d, int l, u64 g, Poly& o0, Poly
       }
     }
   }
+  PER_LIMB
   for (size_t e = 0; e < ext.size(); ++e) { ntt_inverse(C, acc0[e], ext[e]); ntt_inverse(C, acc1[e], ext[e]); }
   o0 = moddown_coeff(C, acc0, l); o1 = moddown_coeff(C, acc1, l);
+  PER_LIMB
   for (int i = 0; i <= l; ++i) { ntt_forward(C, o0[i], i); ntt_forward(C, o1[i], i); }
 }
 // tensor product + relinearisation (no rescale); both inputs at the same level
@@ -609,6 +632,7 @@ static Ct mul_relin(const Ctx& C, const Ct& a0, const Ct& b0) {
   int l = std::min(a0.level, b0.level);
   Ct a = drop_to(a0, l), b = drop_to(b0, l);
   Poly d0(l + 1, Limb(C.N)), d1(l + 1, Limb(C.N)), d2(l + 1, Limb(C.N));
+  PER_LIMB
   for (int i = 0; i <= l; ++i) {
     u64 q = C.q[i];
     for (size_t k = 0; k < C.N; ++k) {
@@ -633,6 +657,7 @@ static Ct apply_galois(Ctx& C, const Ct& a, u64 g) {
   gen_key(C, g);
   int l = a.level;
   Poly p0(l + 1), p1(l + 1);
+  PER_LIMB
   for (int i = 0; i <= l; ++i) {
     Limb x0 = a.c[0][i], x1 = a.c[1][i];
     ntt_inverse(C, x0, i); ntt_inverse(C, x1, i);
@@ -1036,4 +1061,28 @@ API int orc_plain_invsqrt(const double* a, uint64_t n, double lo, double hi, dou
 // raw PRNG / sampler access for pins
 API uint64_t orc_splitmix_stream(uint64_t seed, uint64_t tag, uint64_t n, uint64_t* out) {
   Stream s(seed, tag); for (uint64_t i = 0; i < n; ++i) out[i] = s.next(); return n;
+}
+
+// hybrid key switch of an NTT-domain polynomial d (limbs 0..level) under the key for g
+API int orc_key_switch(void* c, const uint64_t* d, int level, uint64_t g, uint64_t* out) {
+  GUARD(
+    Ctx* C = (Ctx*)c; gen_key(*C, g);
+    Poly x(level + 1);
+    for (int i = 0; i <= level; ++i) x[i].assign(d + (size_t)i * C->N, d + (size_t)(i + 1) * C->N);
+    Poly o0, o1; key_switch(*C, x, level, g, o0, o1);
+    for (int i = 0; i <= level; ++i) {
+      std::memcpy(out + (size_t)i * C->N, o0[i].data(), C->N * 8);
+      std::memcpy(out + (size_t)(level + 1 + i) * C->N, o1[i].data(), C->N * 8);
+    }
+    return 0;
+  )
+  return -1;
+}
+
+API int orc_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

@@ -1,0 +1,310 @@
+// extern "C" entry points declared in include/hedap.h.  Every call catches
+// exceptions and turns them into a status code plus a thread-local message.
+#include <cstring>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+#include "profiler.cuh"
+
+struct hedap_ctx {
+  hedap::Ctx* c;
+};
+struct hedap_ct {
+  std::unique_ptr<hedap::Ct> c;
+};
+
+namespace {
+thread_local std::string g_last_error;
+
+template <class F>
+hedap_status guarded(F&& f) {
+  try {
+    f();
+    return HEDAP_OK;
+  } catch (const hedap::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc& e) {
+    g_last_error = e.what();
+    return HEDAP_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return HEDAP_ERR_ARG;
+  }
+}
+void need(bool ok, const char* what) {
+  if (!ok) throw hedap::Error(HEDAP_ERR_ARG, what);
+}
+hedap_ct* wrap(std::unique_ptr<hedap::Ct> c) {
+  hedap_ct* h = new hedap_ct;
+  h->c = std::move(c);
+  return h;
+}
+}  // namespace
+
+#define API extern "C" __attribute__((visibility("default")))
+
+API const char* hedap_status_str(hedap_status s) {
+  switch (s) {
+    case HEDAP_OK: return "ok";
+    case HEDAP_ERR_ARG: return "invalid argument";
+    case HEDAP_ERR_LEVEL: return "not enough levels";
+    case HEDAP_ERR_SCALE: return "scale mismatch";
+    case HEDAP_ERR_OOM: return "out of device memory";
+    case HEDAP_ERR_CUDA: return "CUDA error";
+    case HEDAP_ERR_TIMEOUT: return "device wait timed out";
+    case HEDAP_ERR_RANGE: return "input out of range";
+    case HEDAP_ERR_KEY: return "missing switching key";
+  }
+  return "unknown status";
+}
+API const char* hedap_last_error(void) { return g_last_error.c_str(); }
+
+API hedap_status hedap_ctx_create(const hedap_params* params, uint64_t seed, void* cuda_stream, hedap_ctx** out) {
+  return guarded([&] {
+    need(params && out, "null argument");
+    *out = nullptr;
+    hedap::Ctx* c = hedap::ctx_create(*params, seed, (cudaStream_t)cuda_stream);
+    *out = new hedap_ctx{c};
+  });
+}
+API void hedap_ctx_destroy(hedap_ctx* ctx) {
+  if (!ctx) return;
+  cudaStream_t s = ctx->c->stream;
+  delete ctx->c;
+  cudaStreamSynchronize(s);
+  delete ctx;
+}
+API hedap_status hedap_ctx_primes(const hedap_ctx* ctx, uint64_t* out, size_t cap) {
+  return guarded([&] {
+    need(ctx && out, "null argument");
+    need(cap >= ctx->c->primes.size(), "capacity too small");
+    std::memcpy(out, ctx->c->primes.data(), ctx->c->primes.size() * 8);
+  });
+}
+API hedap_status hedap_sync(hedap_ctx* ctx) {
+  return guarded([&] {
+    need(ctx, "null argument");
+    HEDAP_CUDA(cudaStreamSynchronize(ctx->c->stream));
+  });
+}
+API hedap_status hedap_gen_galois_key(hedap_ctx* ctx, uint64_t g) {
+  return guarded([&] {
+    need(ctx, "null argument");
+    hedap::gen_galois_key(*ctx->c, g);
+  });
+}
+API hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t g, uint32_t digit, uint64_t* b, uint64_t* a) {
+  return guarded([&] {
+    need(ctx && b && a, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    hedap::gen_galois_key(C, g);
+    need((int)digit < C.dnum(C.L()), "digit out of range");
+    const size_t part = (size_t)C.total_primes() * C.N;
+    const uint64_t* base = C.keys.at(g).p + (size_t)digit * 2 * part;
+    HEDAP_CUDA(cudaMemcpyAsync(b, base, part * 8, cudaMemcpyDeviceToHost, C.stream));
+    HEDAP_CUDA(cudaMemcpyAsync(a, base + part, part * 8, cudaMemcpyDeviceToHost, C.stream));
+    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}
+API hedap_status hedap_encrypt(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, int level,
+                               uint64_t seed, hedap_ct** out) {
+  return guarded([&] {
+    need(ctx && re && out, "null argument");
+    *out = nullptr;
+    std::vector<double> r(re, re + n_slots), i;
+    if (im) i.assign(im, im + n_slots);
+    *out = wrap(hedap::encrypt(*ctx->c, r, i, level, seed));
+  });
+}
+API hedap_status hedap_decrypt(hedap_ctx* ctx, const hedap_ct* ct, double* re, double* im, size_t n_slots) {
+  return guarded([&] {
+    need(ctx && ct && re, "null argument");
+    need(n_slots == ctx->c->N / 2, "n_slots must equal N/2");
+    std::vector<double> r, i;
+    hedap::decrypt(*ctx->c, *ct->c, r, i);
+    std::memcpy(re, r.data(), n_slots * 8);
+    if (im) std::memcpy(im, i.data(), n_slots * 8);
+  });
+}
+API hedap_status hedap_ct_import(hedap_ctx* ctx, const uint64_t* limbs, int level, double scale, int on_device,
+                                 hedap_ct** out) {
+  return guarded([&] {
+    need(ctx && limbs && out, "null argument");
+    *out = nullptr;
+    hedap::Ctx& C = *ctx->c;
+    need(level >= 0 && level <= C.L(), "level out of range");
+    need(scale > 0, "scale must be positive");
+    const size_t per = (size_t)(level + 1) * C.N;
+    if (!on_device) {
+      for (int p = 0; p < 2; ++p)
+        for (int i = 0; i <= level; ++i) {
+          const uint64_t* src = limbs + (p * (size_t)(level + 1) + i) * C.N;
+          for (size_t k = 0; k < C.N; ++k)
+            if (src[k] >= C.primes[i]) throw hedap::Error(HEDAP_ERR_RANGE, "residue not below its prime");
+        }
+    }
+    auto c = hedap::ct_alloc(C, level);
+    c->scale = scale;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    HEDAP_CUDA(cudaMemcpyAsync(c->part(0), limbs, per * 8, kind, C.stream));
+    HEDAP_CUDA(cudaMemcpyAsync(c->part(1), limbs + per, per * 8, kind, C.stream));
+    if (!on_device) HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+    *out = wrap(std::move(c));
+  });
+}
+API hedap_status hedap_ct_export(hedap_ctx* ctx, const hedap_ct* ct, uint64_t* out, size_t cap, int on_device) {
+  return guarded([&] {
+    need(ctx && ct && out, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    const size_t per = (size_t)(ct->c->level + 1) * C.N;
+    need(cap >= 2 * per, "capacity too small");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    HEDAP_CUDA(cudaMemcpyAsync(out, ct->c->part(0), per * 8, kind, C.stream));
+    HEDAP_CUDA(cudaMemcpyAsync(out + per, ct->c->part(1), per * 8, kind, C.stream));
+    if (!on_device) HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}
+API hedap_status hedap_ct_info(const hedap_ct* ct, int* level, double* scale) {
+  return guarded([&] {
+    need(ct, "null argument");
+    if (level) *level = ct->c->level;
+    if (scale) *scale = ct->c->scale;
+  });
+}
+API void hedap_ct_free(hedap_ct* ct) { delete ct; }
+
+#define CT_OP(...)                                  \
+  return guarded([&] {                              \
+    need(ctx && out, "null argument");             \
+    *out = nullptr;                                 \
+    *out = wrap(__VA_ARGS__);                       \
+  })
+
+API hedap_status hedap_add(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_add(*ctx->c, *a->c, *b->c, false)));
+}
+API hedap_status hedap_sub(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_add(*ctx->c, *a->c, *b->c, true)));
+}
+API hedap_status hedap_mul_relin(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_mul_relin(*ctx->c, *a->c, *b->c)));
+}
+API hedap_status hedap_mul(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_mul(*ctx->c, *a->c, *b->c)));
+}
+API hedap_status hedap_rescale(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::ev_rescale(*ctx->c, *a->c)));
+}
+API hedap_status hedap_rotate(hedap_ctx* ctx, const hedap_ct* a, int64_t steps, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, *a->c, hedap::galois_for_rotation(*ctx->c, steps))));
+}
+API hedap_status hedap_conjugate(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, *a->c, 2 * ctx->c->N - 1)));
+}
+API hedap_status hedap_mul_const(hedap_ctx* ctx, const hedap_ct* a, double c, double target_scale, hedap_ct** out) {
+  CT_OP((need(a && target_scale > 0, "bad argument"), hedap::ev_mul_const(*ctx->c, *a->c, c, target_scale)));
+}
+API hedap_status hedap_add_const(hedap_ctx* ctx, const hedap_ct* a, double c, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::ev_add_const(*ctx->c, *a->c, c)));
+}
+API hedap_status hedap_mul_int(hedap_ctx* ctx, const hedap_ct* a, int64_t m, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::ev_mul_int(*ctx->c, *a->c, m)));
+}
+API hedap_status hedap_drop_level(hedap_ctx* ctx, const hedap_ct* a, int level, hedap_ct** out) {
+  CT_OP((need(a && level >= 0 && level <= a->c->level, "bad level"), hedap::ev_drop(*ctx->c, *a->c, level)));
+}
+API hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_invsqrt_cfg* cfg, hedap_ct** out) {
+  CT_OP((need(in && cfg, "null argument"), hedap::invsqrt(*ctx->c, *in->c, *cfg)));
+}
+API hedap_status hedap_ntt(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, uint32_t first_prime, int inverse,
+                           int on_device) {
+  return guarded([&] {
+    need(ctx && limbs, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    need(first_prime + n_limbs <= (size_t)C.total_primes(), "prime index out of range");
+    if (n_limbs == 0) return;
+    const size_t words = n_limbs * C.N;
+    hedap::DevBuf tmp;
+    uint64_t* d = limbs;
+    if (!on_device) {
+      tmp = hedap::DevBuf(words, C.stream);
+      HEDAP_CUDA(cudaMemcpyAsync(tmp.p, limbs, words * 8, cudaMemcpyHostToDevice, C.stream));
+      d = tmp.p;
+    }
+    hedap::LimbSet S{d, 0, 1, 0, (int)n_limbs, INT_MAX, (int)first_prime, 0};
+    if (inverse) hedap::ntt_inverse(C.tab, S, C.stream);
+    else hedap::ntt_forward(C.tab, S, C.stream);
+    if (!on_device) {
+      HEDAP_CUDA(cudaMemcpyAsync(limbs, tmp.p, words * 8, cudaMemcpyDeviceToHost, C.stream));
+      HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+    }
+  });
+}
+
+API hedap_status hedap_profile_enable(int on) {
+  return guarded([&] {
+    if (on) hedap::prof_reset();
+    hedap::prof_enable(on != 0);
+  });
+}
+API hedap_status hedap_profile_read(const char* cls, uint64_t* scopes, double* ms, double* bytes) {
+  return guarded([&] {
+    need(cls != nullptr, "null argument");
+    const int c = hedap::prof_class_of(cls);
+    need(c >= 0, "unknown kernel class");
+    hedap::prof_read(c, scopes, ms, bytes);
+  });
+}
+API hedap_status hedap_launch_count(uint64_t* out) {
+  return guarded([&] {
+    need(out != nullptr, "null argument");
+    *out = hedap::prof_launches();
+  });
+}
+
+// ---------------------------------------------------------------- key-switching steps (test ABI)
+API hedap_status hedap_modup(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out) {
+  return guarded([&] {
+    need(ctx && in && out, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    need(level >= 0 && level <= C.L(), "level out of range");
+    const size_t N = C.N, ext = (size_t)level + 1 + C.n_p, dn = (size_t)C.dnum(level);
+    hedap::DevBuf x((level + 1) * N, C.stream), y(dn * ext * N, C.stream);
+    HEDAP_CUDA(cudaMemcpyAsync(x.p, in, (level + 1) * N * 8, cudaMemcpyHostToDevice, C.stream));
+    hedap::k_modup(C, x.p, y.p, level, hedap::level_consts(C, level).modup.p);
+    HEDAP_CUDA(cudaMemcpyAsync(out, y.p, dn * ext * N * 8, cudaMemcpyDeviceToHost, C.stream));
+    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}
+API hedap_status hedap_moddown(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out) {
+  return guarded([&] {
+    need(ctx && in && out, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    need(level >= 0 && level <= C.L(), "level out of range");
+    const size_t N = C.N, ext = (size_t)level + 1 + C.n_p, nl = (size_t)level + 1;
+    hedap::DevBuf acc(2 * ext * N, C.stream), v(2 * nl * N, C.stream), o(2 * nl * N, C.stream);
+    HEDAP_CUDA(cudaMemcpyAsync(acc.p, in, 2 * ext * N * 8, cudaMemcpyHostToDevice, C.stream));
+    hedap::LimbSet qs{acc.p, ext * N, 2, 0, (int)nl, INT_MAX, 0, 0};
+    hedap::ntt_forward(C.tab, qs, C.stream);  // Q limbs enter ModDown in the NTT domain
+    hedap::k_moddown_spread(C, acc.p, v.p, level);
+    hedap::ntt_forward(C.tab, hedap::LimbSet{v.p, nl * N, 2, 0, (int)nl, INT_MAX, 0, 0}, C.stream);
+    hedap::k_moddown_finish(C, acc.p, v.p, o.p, o.p + nl * N, level, false, false);
+    hedap::ntt_inverse(C.tab, hedap::LimbSet{o.p, nl * N, 2, 0, (int)nl, INT_MAX, 0, 0}, C.stream);
+    HEDAP_CUDA(cudaMemcpyAsync(out, o.p, 2 * nl * N * 8, cudaMemcpyDeviceToHost, C.stream));
+    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}
+API hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint64_t galois, uint64_t* out) {
+  return guarded([&] {
+    need(ctx && d && out, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    need(level >= 0 && level <= C.L(), "level out of range");
+    const size_t N = C.N, nl = (size_t)level + 1;
+    hedap::DevBuf x(nl * N, C.stream), o(2 * nl * N, C.stream);
+    HEDAP_CUDA(cudaMemcpyAsync(x.p, d, nl * N * 8, cudaMemcpyHostToDevice, C.stream));
+    hedap::key_switch(C, x.p, level, galois, o.p, o.p + nl * N, false, false);
+    HEDAP_CUDA(cudaMemcpyAsync(out, o.p, 2 * nl * N * 8, cudaMemcpyDeviceToHost, C.stream));
+    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}

@@ -1,0 +1,199 @@
+// Internal declarations of the GB300 RNS-CKKS library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "hedap.h"
+#include "modarith.cuh"
+
+namespace hedap {
+
+typedef int64_t i64;
+
+struct Error : std::runtime_error {
+  hedap_status code;
+  Error(hedap_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define HEDAP_CUDA(x)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (x);                                                                    \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::hedap::Error(e_ == cudaErrorMemoryAllocation ? HEDAP_ERR_OOM : HEDAP_ERR_CUDA,  \
+                           std::string(#x) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+#define HEDAP_LAUNCH_CHECK() HEDAP_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------------ host math (params.cu)
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_invmod(u64 a, u64 q);
+bool h_is_prime(u64 n);
+std::vector<u64> h_prime_chain(int log_n, const std::vector<int>& bits);
+u64 h_find_psi(u64 q, int log_n);
+u64 h_shoup(u64 w, u64 q);  // floor(w * 2^64 / q)
+PrimeDev h_prime_dev(u64 q);
+uint32_t h_bitrev(uint32_t x, int bits);
+u64 h_smod(i64 v, u64 q);
+u64 h_double_to_mod(double x, u64 q);  // exact residue of an integer-valued double
+
+// SplitMix64 streams (Steele, Lea, Flood 2014); a stream for (seed, tag)
+// starts at mix(seed) ^ mix(tag ^ 0x5851F42D4C957F2D).
+struct SplitMix {
+  u64 state;
+  SplitMix(u64 seed, u64 tag);
+  u64 next();
+};
+namespace tags {
+inline u64 evk_a(u64 g, u64 j) { return (2ull << 56) | (g << 8) | j; }
+inline u64 evk_e(u64 g, u64 j) { return (3ull << 56) | (g << 8) | j; }
+const u64 sk = 1, enc_a = 4ull << 56, enc_e = 5ull << 56;
+}  // namespace tags
+u64 draw_uniform(SplitMix& s, u64 q);
+i64 draw_cbd21(SplitMix& s);
+std::vector<i64> draw_ternary(SplitMix& s, int log_n, int hw);
+
+// ------------------------------------------------------------------ device memory
+// Stream-ordered allocation from the device's default memory pool (kept
+// cached: the pool's release threshold is raised at context creation).
+struct DevBuf {
+  u64* p = nullptr;
+  size_t words = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t n, cudaStream_t st);
+  ~DevBuf();
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), words(o.words), s(o.s) { o.p = nullptr; o.words = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept;
+};
+
+// ------------------------------------------------------------------ tables and limb sets
+struct Tables {
+  const PrimeDev* pr;     // [n_primes]
+  const u64* psi;         // [n_primes][N] psi^bitrev(i)
+  const u64* psi_sh;      // Shoup companions
+  const u64* ipsi;        // [n_primes][N] psi^-bitrev(i)
+  const u64* ipsi_sh;
+  const u64* ninv;        // [n_primes] N^-1
+  const u64* ninv_sh;
+  int log_n;
+};
+
+// A set of limbs: parts p in [0, n_parts), limbs li in [limb_begin, limb_begin+n_limbs)
+// at base + p*part_stride + li*N.  Limb li < q_count uses prime prime_offset+li,
+// otherwise prime p_first + (li - q_count).
+struct LimbSet {
+  u64* base;
+  size_t part_stride;
+  int n_parts;
+  int limb_begin;
+  int n_limbs;
+  int q_count;
+  int prime_offset;
+  int p_first;
+  __host__ __device__ int prime(int li) const {
+    return li < q_count ? prime_offset + li : p_first + (li - q_count);
+  }
+  __host__ __device__ u64* limb(int part, int li, size_t N) const {
+    return base + part * part_stride + (size_t)li * N;
+  }
+};
+
+void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st);
+void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st);
+
+// ------------------------------------------------------------------ context and ciphertexts
+struct Ct {
+  DevBuf buf;
+  int cap = 0;     // limbs allocated per part
+  int level = 0;
+  double scale = 1;
+  size_t N = 0;
+  u64* part(int p) const { return buf.p + (size_t)p * cap * N; }
+  size_t part_stride() const { return (size_t)cap * N; }
+};
+
+constexpr int kMaxLimbs = 64;
+// one constant per Q limb, passed to kernels by value (w and its Shoup companion)
+struct LimbConsts {
+  u64 w[kMaxLimbs];
+  u64 wsh[kMaxLimbs];
+};
+// rescale by q_l: per i < l, q_l mod q_i and q_l^-1 mod q_i (+ Shoup)
+struct RescaleConsts {
+  u64 ql_mod[kMaxLimbs];
+  u64 inv[kMaxLimbs];
+  u64 inv_sh[kMaxLimbs];
+};
+
+struct LevelConsts {  // device constants for one level (see keyswitch.cu / evaluator.cu)
+  DevBuf modup;       // qhat_inv (+shoup) per Q prime, qhat mod target per digit
+  RescaleConsts rescale;
+};
+
+struct Ctx {
+  int log_n = 0;
+  size_t N = 0;
+  int n_q = 0, n_p = 0, alpha = 1, hw = 0;
+  double scale = 1;
+  u64 seed = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<u64> primes;
+  std::vector<PrimeDev> pdev;
+  DevBuf d_primes, d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_ninv, d_ninv_sh;
+  DevBuf d_moddown;   // level-independent ModDown constants
+  DevBuf d_r64;       // per prime: 2^64 mod q and its Shoup companion
+  DevBuf d_pmod;      // per prime: P mod q_t (key generation)
+  Tables tab{};
+  std::vector<i64> sk;
+  DevBuf d_sk;        // [n_q+n_p][N] NTT domain
+  std::map<u64, DevBuf> keys;  // galois (0 = relinearisation) -> [dnum][2][n_q+n_p][N]
+  std::map<int, std::unique_ptr<LevelConsts>> lc;
+  int L() const { return n_q - 1; }
+  int total_primes() const { return n_q + n_p; }
+  int dnum(int level) const { return (level + 1 + alpha - 1) / alpha; }
+};
+
+// ------------------------------------------------------------------ evaluator (evaluator.cu)
+std::unique_ptr<Ct> ct_alloc(Ctx& C, int level);
+std::unique_ptr<Ct> ct_copy(Ctx& C, const Ct& a, int level);
+std::unique_ptr<Ct> ev_add(Ctx& C, const Ct& a, const Ct& b, bool sub);
+std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b);
+std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a);
+std::unique_ptr<Ct> ev_mul(Ctx& C, const Ct& a, const Ct& b);
+std::unique_ptr<Ct> ev_galois(Ctx& C, const Ct& a, u64 g);
+std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level);
+std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target_scale);
+std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c);
+std::unique_ptr<Ct> ev_mul_int(Ctx& C, const Ct& a, i64 m);
+u64 galois_for_rotation(const Ctx& C, i64 steps);
+void key_switch(Ctx& C, const u64* d_ntt, int level, u64 galois, u64* out0, u64* out1, bool acc0, bool acc1);
+void gen_galois_key(Ctx& C, u64 g);
+const LevelConsts& level_consts(Ctx& C, int level);
+
+// ------------------------------------------------------------------ context (context.cu)
+Ctx* ctx_create(const hedap_params& p, u64 seed, cudaStream_t st);
+std::unique_ptr<Ct> encrypt(Ctx& C, const std::vector<double>& re, const std::vector<double>& im, int level,
+                            u64 seed);
+void decrypt(Ctx& C, const Ct& ct, std::vector<double>& re, std::vector<double>& im);
+
+// ------------------------------------------------------------------ CryptoInvSqrt (invsqrt.cu)
+std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg);
+
+// ------------------------------------------------------------------ launch helpers
+inline int grid_for(size_t work, int threads) {
+  size_t g = (work + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g ? g : 1);
+}
+
+}  // namespace hedap

@@ -1,0 +1,169 @@
+// CryptoInvSqrt (Alg. 1) with the pre-normalisation of Sec. 2.3:
+//   t   = affine map of a/B onto [-1, 1]            (one level)
+//   x   = 0.5 * a / B                                (ct_x, one level)
+//   y0  = sum_j c_j T_j(t), c_j the Chebyshev interpolant of 1/sqrt on [lo/B, hi/B]
+//   y  <- 1.5 y - x y^3   (Newton, Sec. 2.2; two levels per step)
+//   out = y / sqrt(B)
+//
+// The Chebyshev sum is evaluated in the Chebyshev basis with baby steps
+// T_1..T_k (k = 2^ceil(m/2), m = ceil(log2(d+1))) and giant steps T_k, T_2k, ...
+// (Paterson-Stockmeyer in the form of Bossuat et al. 2021): a polynomial of
+// degree D >= G is split as p = q T_G + r with
+//   q_0 = c_G, q_i = 2 c_{G+i},  r_i = c_i - c_{2G-i} (when 2G-i <= D),
+// from 2 T_G T_{j-G} = T_j + T_{2G-j}.  Each partial result is produced at a
+// prescribed (level, scale) so that additions never need a correction.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace hedap {
+
+typedef std::unique_ptr<Ct> CtP;
+
+static CtP mul_const_at(Ctx& C, const Ct& a, int level, double c, double target) {
+  if (level == a.level) return ev_mul_const(C, a, c, target);
+  auto d = ev_drop(C, a, level);
+  return ev_mul_const(C, *d, c, target);
+}
+
+// Chebyshev interpolation coefficients of 1/sqrt(x) at the d+1 first-kind nodes on [lo, hi]
+static std::vector<double> cheb_interp(double lo, double hi, int d) {
+  const int n = d + 1;
+  std::vector<double> f(n), c(n);
+  for (int k = 0; k < n; ++k) {
+    const double node = 0.5 * (lo + hi) + 0.5 * (hi - lo) * std::cos(M_PI * (k + 0.5) / n);
+    f[k] = 1.0 / std::sqrt(node);
+  }
+  for (int j = 0; j < n; ++j) {
+    double acc = 0;
+    for (int k = 0; k < n; ++k) acc += f[k] * std::cos(M_PI * j * (k + 0.5) / n);
+    c[j] = (j == 0 ? 1.0 : 2.0) / n * acc;
+  }
+  return c;
+}
+
+struct ChebPS {
+  Ctx& C;
+  std::map<int, CtP> T;
+  std::vector<int> giants;
+  int k = 2;
+  explicit ChebPS(Ctx& c) : C(c) {}
+
+  static int degree(const std::vector<double>& p) { return (int)p.size() - 1; }
+  int giant(int D) const {
+    int g = 0;
+    for (int v : giants)
+      if (v <= D) g = v;
+    return g;
+  }
+  static void divide(const std::vector<double>& p, int G, std::vector<double>& qt, std::vector<double>& rm) {
+    const int D = degree(p);
+    qt.assign(D - G + 1, 0.0);
+    qt[0] = p[G];
+    for (int i = 1; i <= D - G; ++i) qt[i] = 2.0 * p[G + i];
+    rm.assign(p.begin(), p.begin() + G);
+    for (int i = 0; i < G; ++i)
+      if (2 * G - i <= D) rm[i] -= p[2 * G - i];
+  }
+  int top_level(const std::vector<double>& p) const {
+    const int D = degree(p);
+    if (D < k) {
+      int lv = INT_MAX;
+      for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j)->level - 1);
+      return lv;
+    }
+    const int G = giant(D);
+    std::vector<double> qt, rm;
+    divide(p, G, qt, rm);
+    const int lq = degree(qt) == 0 ? INT_MAX : top_level(qt);
+    return std::min(std::min(lq, T.at(G)->level) - 1, top_level(rm));
+  }
+  CtP eval(const std::vector<double>& p, int level, double scale) {
+    const int D = degree(p);
+    if (D < k) {
+      CtP acc;
+      for (int j = 1; j <= D; ++j) {
+        CtP term = mul_const_at(C, *T.at(j), level + 1, p[j], scale);
+        acc = acc ? ev_add(C, *acc, *term, false) : std::move(term);
+      }
+      return ev_add_const(C, *acc, p[0]);
+    }
+    const int G = giant(D);
+    std::vector<double> qt, rm;
+    divide(p, G, qt, rm);
+    const Ct& tg = *T.at(G);
+    CtP prod;
+    if (degree(qt) == 0) {
+      prod = mul_const_at(C, tg, level + 1, qt[0], scale);
+    } else {
+      const double sq = scale * (double)C.primes[level + 1] / tg.scale;
+      CtP qv = eval(qt, level + 1, sq);
+      prod = ev_rescale(C, *ev_mul_relin(C, *qv, tg));  // at min level = level + 1
+      prod->scale = scale;
+    }
+    CtP rv = eval(rm, level, scale);
+    return ev_add(C, *prod, *rv, false);
+  }
+  // 2 T_a T_b - T_c, with T_c the constant 1 when c == 0
+  CtP product(const Ct& ta, const Ct& tb, int c) {
+    CtP prod = ev_mul(C, ta, tb);
+    CtP diff;
+    if (c == 0) {
+      diff = ev_add_const(C, *prod, -0.5);
+    } else {
+      CtP half = mul_const_at(C, *T.at(c), prod->level + 1, 0.5, prod->scale);
+      diff = ev_add(C, *prod, *half, true);
+    }
+    return ev_mul_int(C, *diff, 2);
+  }
+  CtP run(const Ct& t, const std::vector<double>& coeffs) {
+    const int d = degree(coeffs);
+    int m = 0;
+    while ((1 << m) < d + 1) ++m;
+    const int lb = std::max(1, (m + 1) / 2);
+    k = 1 << lb;
+    T.clear();
+    T[1] = ct_copy(C, t, t.level);
+    for (int j = 2; j <= k; ++j) T[j] = (j % 2 == 0) ? product(*T.at(j / 2), *T.at(j / 2), 0)
+                                                     : product(*T.at(j / 2), *T.at(j / 2 + 1), 1);
+    giants.clear();
+    for (int g = k; g < (1 << m); g *= 2) {
+      giants.push_back(g);
+      if (!T.count(g)) T[g] = product(*T.at(g / 2), *T.at(g / 2), 0);
+    }
+    const int lvl = top_level(coeffs);
+    if (lvl < 0) throw Error(HEDAP_ERR_LEVEL, "Chebyshev evaluation: not enough levels");
+    return eval(coeffs, lvl, C.scale);
+  }
+};
+
+// One Newton step in Alg. 1's loop order; tmp_alpha = 1.5 y is produced last so
+// that its scale equals tmp_beta's exactly.
+static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
+  CtP yy = ev_mul(C, y, y);
+  CtP xy = ev_mul(C, x, y);
+  CtP tb = ev_mul(C, *xy, *yy);
+  CtP ta = mul_const_at(C, y, tb->level + 1, 1.5, tb->scale);
+  return ev_add(C, *ta, *tb, true);
+}
+
+std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) {
+  if (!(cfg.B > 0) || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.degree > 4096)
+    throw Error(HEDAP_ERR_ARG, "invsqrt: invalid configuration");
+  if (cfg.pre_bts || cfg.bts_mask) throw Error(HEDAP_ERR_ARG, "invsqrt: bootstrapping not available in this context");
+  if (in.level < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
+  const double lo = cfg.lo / cfg.B, hi = cfg.hi / cfg.B;
+  const double alpha = 2.0 / (cfg.B * (hi - lo)), beta = -(hi + lo) / (hi - lo);
+  CtP t = ev_add_const(C, *ev_mul_const(C, in, alpha, C.scale), beta);
+  CtP x = ev_mul_const(C, in, 0.5 / cfg.B, C.scale);
+  ChebPS ps(C);
+  CtP y = ps.run(*t, cheb_interp(lo, hi, (int)cfg.degree));
+  for (uint32_t i = 0; i < cfg.newton_iters; ++i) {
+    if (std::min(y->level, x->level) < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: level exhausted in Newton loop");
+    y = newton_step(C, *x, *y);
+  }
+  if (cfg.B != 1.0) y = ev_mul_const(C, *y, 1.0 / std::sqrt(cfg.B), y->scale);
+  return y;
+}
+
+}  // namespace hedap

@@ -1,0 +1,77 @@
+// Device modular arithmetic on 64-bit words, primes 2^32 < q < 2^61.
+//
+//  * Shoup multiplication by a fixed operand w with companion
+//    w' = floor(w * 2^64 / q): result in [0, 2q) for any 64-bit input
+//    (Shoup; bound as in Harvey, "Faster arithmetic for number-theoretic
+//    transforms", 2014).
+//  * Barrett reduction of a product x < q^2 with mu = floor(2^(2b) / q),
+//    b = bit length of q (Barrett 1986): quotient estimate
+//    floor(floor(x / 2^(b-1)) * mu / 2^(b+1)), remainder in [0, 3q).
+#pragma once
+#include <cstdint>
+
+namespace hedap {
+
+typedef uint64_t u64;
+
+struct PrimeDev {  // per-prime constants used by the kernels
+  u64 q;
+  u64 mu;       // floor(2^(2b) / q)
+  int b;        // bit length of q
+  int pad;
+};
+
+__device__ __forceinline__ u64 shoup_mul_lazy(u64 x, u64 w, u64 wp, u64 q) {
+  u64 qh = __umul64hi(x, wp);
+  return x * w - qh * q;  // in [0, 2q)
+}
+__device__ __forceinline__ u64 shoup_mul(u64 x, u64 w, u64 wp, u64 q) {
+  u64 r = shoup_mul_lazy(x, w, wp, q);
+  return r >= q ? r - q : r;
+}
+__device__ __forceinline__ u64 barrett_reduce(u64 lo, u64 hi, const PrimeDev& p) {
+  // t = floor(x / 2^(b-1)) (< 2^(b+1)), qhat = floor(t * mu / 2^(b+1))
+  int s = p.b - 1;
+  u64 t = (lo >> s) | (hi << (64 - s));
+  u64 plo = t * p.mu, phi = __umul64hi(t, p.mu);
+  int s2 = p.b + 1;
+  u64 qhat = (plo >> s2) | (phi << (64 - s2));
+  u64 r = lo - qhat * p.q;
+  if (r >= p.q) r -= p.q;
+  if (r >= p.q) r -= p.q;
+  return r;
+}
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeDev& p) {
+  return barrett_reduce(a * b, __umul64hi(a, b), p);
+}
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+  u64 s = a + b;
+  return s >= q ? s - q : s;
+}
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) {
+  return a >= b ? a - b : a + q - b;
+}
+// 128-bit accumulator helpers for lazy sums of products
+struct Acc128 {
+  u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(Acc128& acc, u64 a, u64 b) {
+  u64 plo = a * b, phi = __umul64hi(a, b);
+  u64 nlo = acc.lo + plo;
+  acc.hi += phi + (nlo < plo ? 1 : 0);
+  acc.lo = nlo;
+}
+// reduce an arbitrary 128-bit value: hi is first brought below q, then the
+// value hi'*2^64 + lo < q*2^64 < q^2 * 2^(64-b) ... is reduced in two Barrett
+// steps on 2^64-aligned halves: x = hi' * 2^64 + lo = (hi' * r64 + lo) mod q,
+// with r64 = 2^64 mod q.
+__device__ __forceinline__ u64 reduce128(Acc128 x, const PrimeDev& p, u64 r64, u64 r64p) {
+  u64 hi = x.hi;
+  if (hi >= p.q) hi = barrett_reduce(hi, 0, p);           // hi < 2^64 <= q^2 for b >= 32
+  u64 a = shoup_mul(hi, r64, r64p, p.q);                  // hi * 2^64 mod q
+  u64 lo = x.lo;
+  u64 lr = barrett_reduce(lo, 0, p);                      // lo < 2^64 <= q^2
+  return add_mod(a, lr, p.q);
+}
+
+}  // namespace hedap

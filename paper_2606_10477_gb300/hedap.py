@@ -1,0 +1,326 @@
+"""ctypes binding of the GB300 RNS-CKKS library (``include/hedap.h``).
+
+Argument marshalling only: every operation runs in the CUDA library.  Importing
+this module does not load the library; the first ``Context`` does, and fails
+loudly when ``_build/libhedap.so`` is missing (run ``build()`` first) or no
+CUDA device is present.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhedap.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "not enough levels", -3: "scale mismatch", -4: "out of device memory",
+          -5: "CUDA error", -6: "device wait timed out", -7: "input out of range", -8: "missing switching key"}
+
+EXPORTED = [
+    "hedap_status_str", "hedap_last_error", "hedap_ctx_create", "hedap_ctx_destroy", "hedap_ctx_primes", "hedap_sync",
+    "hedap_gen_galois_key", "hedap_export_key", "hedap_encrypt", "hedap_decrypt", "hedap_ct_import",
+    "hedap_ct_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
+    "hedap_rescale", "hedap_rotate", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
+    "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
+    "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch",
+]
+
+
+class HedapError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("log_n", C.c_uint32), ("n_q", C.c_uint32), ("q_bits", C.POINTER(C.c_uint32)),
+                ("n_p", C.c_uint32), ("p_bits", C.POINTER(C.c_uint32)), ("alpha", C.c_uint32),
+                ("log_scale", C.c_double), ("secret_hw", C.c_uint32)]
+
+
+class InvSqrtCfg(C.Structure):
+    _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("B", C.c_double), ("degree", C.c_uint32),
+                ("newton_iters", C.c_uint32), ("pre_bts", C.c_uint32), ("bts_mask", C.c_uint64)]
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+            L = C.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, pp = C.c_void_p, C.POINTER(C.c_void_p)
+    u64p = C.POINTER(C.c_uint64)
+    dp = C.POINTER(C.c_double)
+    st = C.c_int
+    sig = {
+        "hedap_status_str": (C.c_char_p, [C.c_int]),
+        "hedap_last_error": (C.c_char_p, []),
+        "hedap_ctx_create": (st, [C.POINTER(Params), C.c_uint64, vp, pp]),
+        "hedap_ctx_destroy": (None, [vp]),
+        "hedap_ctx_primes": (st, [vp, u64p, C.c_size_t]),
+        "hedap_sync": (st, [vp]),
+        "hedap_gen_galois_key": (st, [vp, C.c_uint64]),
+        "hedap_export_key": (st, [vp, C.c_uint64, C.c_uint32, u64p, u64p]),
+        "hedap_encrypt": (st, [vp, dp, dp, C.c_size_t, C.c_int, C.c_uint64, pp]),
+        "hedap_decrypt": (st, [vp, vp, dp, dp, C.c_size_t]),
+        "hedap_ct_import": (st, [vp, u64p, C.c_int, C.c_double, C.c_int, pp]),
+        "hedap_ct_export": (st, [vp, vp, u64p, C.c_size_t, C.c_int]),
+        "hedap_ct_info": (st, [vp, C.POINTER(C.c_int), dp]),
+        "hedap_ct_free": (None, [vp]),
+        "hedap_add": (st, [vp, vp, vp, pp]),
+        "hedap_sub": (st, [vp, vp, vp, pp]),
+        "hedap_mul_relin": (st, [vp, vp, vp, pp]),
+        "hedap_mul": (st, [vp, vp, vp, pp]),
+        "hedap_rescale": (st, [vp, vp, pp]),
+        "hedap_rotate": (st, [vp, vp, C.c_int64, pp]),
+        "hedap_conjugate": (st, [vp, vp, pp]),
+        "hedap_mul_const": (st, [vp, vp, C.c_double, C.c_double, pp]),
+        "hedap_add_const": (st, [vp, vp, C.c_double, pp]),
+        "hedap_mul_int": (st, [vp, vp, C.c_int64, pp]),
+        "hedap_drop_level": (st, [vp, vp, C.c_int, pp]),
+        "hedap_invsqrt": (st, [vp, vp, C.POINTER(InvSqrtCfg), pp]),
+        "hedap_ntt": (st, [vp, u64p, C.c_size_t, C.c_uint32, C.c_int, C.c_int]),
+        "hedap_profile_enable": (st, [C.c_int]),
+        "hedap_profile_read": (st, [C.c_char_p, u64p, dp, dp]),
+        "hedap_launch_count": (st, [u64p]),
+        "hedap_modup": (st, [vp, u64p, C.c_int, u64p]),
+        "hedap_moddown": (st, [vp, u64p, C.c_int, u64p]),
+        "hedap_key_switch": (st, [vp, u64p, C.c_int, C.c_uint64, u64p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _check(rc):
+    if rc != 0:
+        raise HedapError(rc, load().hedap_last_error().decode())
+
+
+def _u64ptr(arr):
+    """Pointer and on_device flag for a numpy array or a CUDA torch tensor of uint64/int64."""
+    if isinstance(arr, np.ndarray):
+        assert arr.dtype == np.uint64 and arr.flags.c_contiguous
+        return arr.ctypes.data_as(C.POINTER(C.c_uint64)), 0
+    if hasattr(arr, "data_ptr"):  # torch tensor
+        assert arr.is_contiguous() and arr.element_size() == 8
+        return C.cast(C.c_void_p(arr.data_ptr()), C.POINTER(C.c_uint64)), 1 if arr.is_cuda else 0
+    raise TypeError("expected a numpy uint64 array or a torch tensor")
+
+
+class Ciphertext:
+    def __init__(self, ctx: "Context", handle: C.c_void_p):
+        self.ctx = ctx
+        self.h = handle
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and _lib is not None:
+            _lib.hedap_ct_free(h)
+            self.h = None
+
+    def _info(self):
+        lv, sc = C.c_int(), C.c_double()
+        _check(load().hedap_ct_info(self.h, C.byref(lv), C.byref(sc)))
+        return lv.value, sc.value
+
+    @property
+    def level(self) -> int:
+        return self._info()[0]
+
+    @property
+    def scale(self) -> float:
+        return self._info()[1]
+
+    def limbs(self) -> np.ndarray:
+        out = np.empty((2, self.level + 1, self.ctx.N), dtype=np.uint64)
+        p, _ = _u64ptr(out)
+        _check(load().hedap_ct_export(self.ctx.h, self.h, p, out.size, 0))
+        return out
+
+    def export_to(self, dst) -> None:
+        """Copy [2][level+1][N] words into dst (numpy array, host or CUDA torch tensor)."""
+        p, dev = _u64ptr(dst)
+        cap = dst.size if isinstance(dst, np.ndarray) else dst.numel()
+        _check(load().hedap_ct_export(self.ctx.h, self.h, p, cap, dev))
+
+
+class Context:
+    """A CKKS context on the current CUDA device (keys generated from ``seed``)."""
+
+    def __init__(self, log_n, q_bits, p_bits, alpha, log_scale, hw=0, seed=1, stream=None):
+        L = load()
+        self._qb = (C.c_uint32 * len(q_bits))(*q_bits)
+        self._pb = (C.c_uint32 * len(p_bits))(*p_bits)
+        prm = Params(log_n, len(q_bits), self._qb, len(p_bits), self._pb, alpha, float(log_scale), hw)
+        h = C.c_void_p()
+        _check(L.hedap_ctx_create(C.byref(prm), seed, C.c_void_p(stream or 0), C.byref(h)))
+        self.h = h
+        self.log_n, self.N = log_n, 1 << log_n
+        self.n_q, self.n_p, self.alpha = len(q_bits), len(p_bits), alpha
+        self.scale = 2.0 ** log_scale
+        self.seed = seed
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hedap_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+    def _ct(self, fn, *args) -> Ciphertext:
+        out = C.c_void_p()
+        _check(fn(self.h, *args, C.byref(out)))
+        return Ciphertext(self, out)
+
+    # ---- parameters and keys
+    def primes(self) -> np.ndarray:
+        out = np.empty(self.n_q + self.n_p, dtype=np.uint64)
+        _check(load().hedap_ctx_primes(self.h, out.ctypes.data_as(C.POINTER(C.c_uint64)), out.size))
+        return out
+
+    def gen_galois_key(self, g: int):
+        _check(load().hedap_gen_galois_key(self.h, g))
+
+    def galois_of_rotation(self, r: int) -> int:
+        return pow(5, r % (self.N // 2), 2 * self.N)
+
+    def key_digit(self, g: int, j: int):
+        tot = self.n_q + self.n_p
+        b = np.empty((tot, self.N), dtype=np.uint64)
+        a = np.empty((tot, self.N), dtype=np.uint64)
+        _check(load().hedap_export_key(self.h, g, j, _u64ptr(b)[0], _u64ptr(a)[0]))
+        return b, a
+
+    def sync(self):
+        _check(load().hedap_sync(self.h))
+
+    # ---- ring helpers
+    def ntt(self, limbs, first_prime: int, inverse=False):
+        """In-place NTT of consecutive limbs (numpy: returns a transformed copy)."""
+        if isinstance(limbs, np.ndarray):
+            x = np.ascontiguousarray(limbs, dtype=np.uint64).copy()
+            n = x.size // self.N
+            _check(load().hedap_ntt(self.h, _u64ptr(x)[0], n, first_prime, int(inverse), 0))
+            return x
+        p, dev = _u64ptr(limbs)
+        _check(load().hedap_ntt(self.h, p, limbs.numel() // self.N, first_prime, int(inverse), dev))
+        return limbs
+
+    # ---- key-switching steps
+    def modup_coeff(self, limbs: np.ndarray, level: int) -> np.ndarray:
+        x = np.ascontiguousarray(limbs, dtype=np.uint64)
+        dn = -(-(level + 1) // self.alpha)
+        out = np.empty((dn, level + 1 + self.n_p, self.N), dtype=np.uint64)
+        _check(load().hedap_modup(self.h, _u64ptr(x)[0], level, _u64ptr(out)[0]))
+        return out
+
+    def moddown_coeff(self, limbs: np.ndarray, level: int) -> np.ndarray:
+        x = np.ascontiguousarray(limbs, dtype=np.uint64)
+        out = np.empty((2, level + 1, self.N), dtype=np.uint64)
+        _check(load().hedap_moddown(self.h, _u64ptr(x)[0], level, _u64ptr(out)[0]))
+        return out
+
+    def key_switch(self, d: np.ndarray, level: int, galois: int) -> np.ndarray:
+        x = np.ascontiguousarray(d, dtype=np.uint64)
+        out = np.empty((2, level + 1, self.N), dtype=np.uint64)
+        _check(load().hedap_key_switch(self.h, _u64ptr(x)[0], level, galois, _u64ptr(out)[0]))
+        return out
+
+    # ---- ciphertexts
+    def encrypt(self, values, level: int, seed: int) -> Ciphertext:
+        v = np.asarray(values)
+        re = np.ascontiguousarray(v.real, dtype=np.float64)
+        im = np.ascontiguousarray(v.imag if np.iscomplexobj(v) else np.zeros_like(re), dtype=np.float64)
+        dp = C.POINTER(C.c_double)
+        return self._ct(load().hedap_encrypt, re.ctypes.data_as(dp), im.ctypes.data_as(dp), len(re), level, seed)
+
+    def decrypt(self, ct: Ciphertext) -> np.ndarray:
+        n = self.N // 2
+        re, im = np.empty(n), np.empty(n)
+        dp = C.POINTER(C.c_double)
+        _check(load().hedap_decrypt(self.h, ct.h, re.ctypes.data_as(dp), im.ctypes.data_as(dp), n))
+        return re + 1j * im
+
+    def ct_import(self, limbs, level: int, scale: float) -> Ciphertext:
+        if isinstance(limbs, np.ndarray):
+            limbs = np.ascontiguousarray(limbs, dtype=np.uint64)
+        p, dev = _u64ptr(limbs)
+        return self._ct(load().hedap_ct_import, p, level, float(scale), dev)
+
+    def add(self, a, b):
+        return self._ct(load().hedap_add, a.h, b.h)
+
+    def sub(self, a, b):
+        return self._ct(load().hedap_sub, a.h, b.h)
+
+    def mul_relin(self, a, b):
+        return self._ct(load().hedap_mul_relin, a.h, b.h)
+
+    def mul(self, a, b):
+        return self._ct(load().hedap_mul, a.h, b.h)
+
+    def rescale(self, a):
+        return self._ct(load().hedap_rescale, a.h)
+
+    def rotate(self, a, steps: int):
+        return self._ct(load().hedap_rotate, a.h, steps)
+
+    def conjugate(self, a):
+        return self._ct(load().hedap_conjugate, a.h)
+
+    def mul_const(self, a, c: float, target_scale: float):
+        return self._ct(load().hedap_mul_const, a.h, c, target_scale)
+
+    def add_const(self, a, c: float):
+        return self._ct(load().hedap_add_const, a.h, c)
+
+    def mul_int(self, a, m: int):
+        return self._ct(load().hedap_mul_int, a.h, m)
+
+    def drop(self, a, level: int):
+        return self._ct(load().hedap_drop_level, a.h, level)
+
+    def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0):
+        cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask)
+        return self._ct(load().hedap_invsqrt, a.h, C.byref(cfg))
+
+
+PROFILE_CLASSES = ("ntt", "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph", "elementwise")
+
+
+def profile_enable(on: bool) -> None:
+    _check(load().hedap_profile_enable(int(on)))
+
+
+def profile_read() -> dict:
+    """{class: (timed launch groups, total ms, algorithmic bytes)} since profile_enable(True)."""
+    out = {}
+    for c in PROFILE_CLASSES:
+        n, ms, by = C.c_uint64(), C.c_double(), C.c_double()
+        _check(load().hedap_profile_read(c.encode(), C.byref(n), C.byref(ms), C.byref(by)))
+        out[c] = (n.value, ms.value, by.value)
+    return out
+
+
+def launch_count() -> int:
+    n = C.c_uint64()
+    _check(load().hedap_launch_count(C.byref(n)))
+    return n.value

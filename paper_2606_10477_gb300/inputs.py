@@ -1,0 +1,53 @@
+"""Seeded synthetic inputs and CKKS parameter presets.
+
+This module holds no arithmetic of the method: it draws input values and
+random residues with numpy and names the parameter sets.  Both the CUDA path
+and the CPU oracle take their inputs from here.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# CKKS parameter presets (bit sizes of the Q primes q_0.., of the special primes,
+# primes per key-switching digit, log2 of the scale, secret Hamming weight (0 = dense)).
+PRESETS = {
+    # toy, correctness only: N = 2^12, 12 primes of ~40 bits + one 60-bit special prime
+    "toy": dict(log_n=12, q_bits=[40] * 12, p_bits=[60], alpha=1, log_scale=40, hw=0),
+    # N = 2^16, 24 primes of ~50 bits + 2 special primes of ~60 bits, 2 primes per digit
+    "n16": dict(log_n=16, q_bits=[50] * 24, p_bits=[60, 60], alpha=2, log_scale=50, hw=0),
+    # small rings with the same prime shapes, for fast parity checks
+    "n13": dict(log_n=13, q_bits=[50] * 8, p_bits=[60, 60], alpha=2, log_scale=50, hw=0),
+    "n10": dict(log_n=10, q_bits=[45, 36, 36, 36, 36, 36], p_bits=[50, 50], alpha=2, log_scale=36, hw=0),
+}
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def uniform_values(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    """n values uniform in [lo, hi]."""
+    return rng(seed).uniform(lo, hi, n)
+
+
+def log_uniform_values(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    """n values with log10 uniform in [log10 lo, log10 hi]."""
+    return 10.0 ** rng(seed).uniform(np.log10(lo), np.log10(hi), n)
+
+
+def linspace_values(n: int, lo: float, hi: float) -> np.ndarray:
+    """The paper's provisioning input: n evenly spaced points in [lo, hi]."""
+    return np.linspace(lo, hi, n)
+
+
+def random_limbs(seed: int, primes, n_coeffs: int) -> np.ndarray:
+    """Uniform residues: one row of n_coeffs words per prime, row i below primes[i]."""
+    g = rng(seed)
+    return np.stack([g.integers(0, int(q), n_coeffs, dtype=np.uint64) for q in primes])
+
+
+def random_ciphertext_limbs(seed: int, primes, level: int, n_coeffs: int) -> np.ndarray:
+    """[2][level+1][N] uniform residues (a valid-shaped NTT-domain ciphertext)."""
+    g = rng(seed)
+    return np.stack([np.stack([g.integers(0, int(primes[i]), n_coeffs, dtype=np.uint64) for i in range(level + 1)])
+                     for _ in range(2)])
