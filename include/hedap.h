@@ -159,6 +159,26 @@ hedap_status hedap_modup(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t
 hedap_status hedap_moddown(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
 hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint64_t galois, uint64_t* out);
 
+/* Rescale without device allocation.  No counterpart in the paper: this entry
+ * point exists for callers that cannot allocate device memory during an
+ * operation -- a serving loop that admitted its requests against a fixed HBM
+ * budget, a host framework whose allocator owns the device memory, or code
+ * that must not let a cudaMalloc/cudaFree synchronise the device.
+ * in:  device pointer, [2][level+1][N] words (NTT domain, as hedap_ct_export).
+ * out: device pointer, [2][level][N] words; must not overlap `in`.
+ * Same result as hedap_rescale (scale divided by q_level is the caller's to
+ * track).  Work is issued on the context's stream; the call returns without
+ * synchronising.  Scratch is one library-wide device array of 4 Mi words
+ * (32 MiB) that every GPU loading the library holds until the process exits;
+ * (2 + 2*level) * N must not exceed 4 Mi words (level <= 31 at N = 2^16),
+ * otherwise HEDAP_ERR_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU (other streams, other threads, other
+ * contexts on the same device) race on it.  It calls no cudaMalloc, cudaFree
+ * or allocating routine (with profiling off, the default). */
+hedap_status hedap_rescale_noalloc(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
+
 /* Profiling (process-wide, not part of the paper's interface).
  * hedap_profile_enable(1) resets the counters and, until disabled, records a
  * CUDA event pair around every launch group of these kernel classes:

@@ -6,13 +6,6 @@
 #include "kernels.cuh"
 #include "profiler.cuh"
 
-struct hedap_ctx {
-  hedap::Ctx* c;
-};
-struct hedap_ct {
-  std::unique_ptr<hedap::Ct> c;
-};
-
 namespace {
 thread_local std::string g_last_error;
 
@@ -41,6 +34,10 @@ hedap_ct* wrap(std::unique_ptr<hedap::Ct> c) {
   return h;
 }
 }  // namespace
+
+namespace hedap {
+void set_last_error(const std::string& m) { g_last_error = m; }
+}  // namespace hedap
 
 #define API extern "C" __attribute__((visibility("default")))
 

@@ -189,6 +189,9 @@ void decrypt(Ctx& C, const Ct& ct, std::vector<double>& re, std::vector<double>&
 // ------------------------------------------------------------------ CryptoInvSqrt (invsqrt.cu)
 std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg);
 
+// thread-local message returned by hedap_last_error (capi.cu)
+void set_last_error(const std::string& m);
+
 // ------------------------------------------------------------------ launch helpers
 inline int grid_for(size_t work, int threads) {
   size_t g = (work + threads - 1) / threads;
@@ -197,3 +200,11 @@ inline int grid_for(size_t work, int threads) {
 }
 
 }  // namespace hedap
+
+// opaque ABI handles
+struct hedap_ctx {
+  hedap::Ctx* c;
+};
+struct hedap_ct {
+  std::unique_ptr<hedap::Ct> c;
+};

@@ -27,7 +27,7 @@ EXPORTED = [
     "hedap_ct_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
     "hedap_rescale", "hedap_rotate", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
-    "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch",
+    "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
 ]
 
 
@@ -100,6 +100,7 @@ def _declare(L):
         "hedap_modup": (st, [vp, u64p, C.c_int, u64p]),
         "hedap_moddown": (st, [vp, u64p, C.c_int, u64p]),
         "hedap_key_switch": (st, [vp, u64p, C.c_int, C.c_uint64, u64p]),
+        "hedap_rescale_noalloc": (st, [vp, u64p, C.c_int, u64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
