@@ -73,8 +73,11 @@ typedef struct {
  * inputs a lie in [lo, hi]; a/B lies in (0, 1]; the initial value is the
  * degree-`degree` Chebyshev interpolant of 1/sqrt(x) on [lo/B, hi/B];
  * `newton_iters` Newton steps y <- y (3 - (a/B) y^2) / 2 follow; the output is
- * y / sqrt(B).  pre_bts and bts_mask request bootstrapping and must be 0 on a
- * context without bootstrapping keys. */
+ * y / sqrt(B) (applied to the scale label).  pre_bts = 1 bootstraps a/B
+ * before everything (the paper's Pre-BTS indicator c); bit j < 63 of bts_mask
+ * bootstraps y before Newton step j (bit 0 = right after the Chebyshev step,
+ * Alg. 1); bit 63 bootstraps y lazily whenever the next step would run out of
+ * levels.  Both need hedap_bootstrap_setup on the context. */
 typedef struct {
   double lo, hi, B;
   uint32_t degree;
@@ -146,6 +149,51 @@ hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_invsq
  * (global index over Q then P). */
 hedap_status hedap_ntt(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, uint32_t first_prime, int inverse,
                        int on_device);
+
+/* Bootstrapping (BTS, Sec. 2.1; the paper uses it as a library primitive).
+ * Full-slot CKKS bootstrapping: ModRaise, CoeffToSlot (cts_levels grouped
+ * special-FFT factors, baby-step/giant-step diagonals), EvalMod (Chebyshev
+ * interpolant of degree mod_degree of cos(2 pi (K u - 1/4) / 2^double_angles)
+ * then double_angles squarings), SlotToCoeff (stc_levels groups).  The top
+ * cts_levels primes are consumed by CoeffToSlot, the next ones by EvalMod and
+ * SlotToCoeff; *level_after receives the level of a bootstrapped ciphertext
+ * (l_afterBTS).  K must exceed the ModRaise overflow |I| (about 7 sigma of a
+ * sum of secret_hw uniform terms; 28 suits secret_hw = 192).
+ * hedap_bootstrap: input at level 0 with values in [-1, 1] and scale at most
+ * q_0 / 2^10; output at level_after with the context scale.
+ * hedap_bootstrap_scaled: input at level >= 1 with values in [-Y, Y]; it is
+ * scaled into [-1, 1] (one level, landing at scale q_0 / 2^12), bootstrapped
+ * and multiplied back by the integer Y (l_BTS = 1). */
+typedef struct {
+  uint32_t K;
+  uint32_t double_angles;
+  uint32_t mod_degree;
+  uint32_t cts_levels;
+  uint32_t stc_levels;
+} hedap_bts_params;
+hedap_status hedap_bootstrap_setup(hedap_ctx* ctx, const hedap_bts_params* p, int* level_after);
+hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
+hedap_status hedap_bootstrap_scaled(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, hedap_ct** out);
+/* Single steps of bootstrapping, for parity tests.  hedap_mod_raise: level-0
+ * input -> top level (centred lift).  hedap_mul_monomial: times X^e for
+ * e in {N/2 (= i in every slot), 3N/2 (= -i)}.  hedap_bts_linear_transform:
+ * group `group` of CoeffToSlot (inverse = 1) or SlotToCoeff (inverse = 0),
+ * rescaled to target_scale.  hedap_eval_mod: the EvalMod polynomial and double
+ * angles.  hedap_set_scale relabels a ciphertext's scale in place. */
+hedap_status hedap_mod_raise(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
+hedap_status hedap_mul_monomial(hedap_ctx* ctx, const hedap_ct* a, uint64_t e, hedap_ct** out);
+hedap_status hedap_bts_linear_transform(hedap_ctx* ctx, const hedap_ct* a, int inverse, int group,
+                                        double target_scale, hedap_ct** out);
+hedap_status hedap_eval_mod(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
+hedap_status hedap_set_scale(hedap_ctx* ctx, hedap_ct* a, double scale);
+/* Host-side helpers for parity tests.  hedap_encode: the canonical-embedding
+ * encoding of N/2 slots at `scale`, out[N] integer coefficients (|c| < 2^63).
+ * hedap_bts_diagonal: diagonal `offset` (rotation offset mod N/2) of group
+ * `group` of CoeffToSlot (inverse = 1) or SlotToCoeff (inverse = 0), N/2
+ * complex values into re/im; HEDAP_ERR_ARG when that offset is absent. */
+hedap_status hedap_encode(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, double scale,
+                          int64_t* out);
+hedap_status hedap_bts_diagonal(hedap_ctx* ctx, int inverse, int group, int64_t offset, double* re, double* im);
 
 /* Steps of hybrid key switching, for parity tests (host arrays, [limb][N]).
  * hedap_modup: coefficient-domain input over q_0..q_level -> for every digit j

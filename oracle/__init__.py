@@ -97,6 +97,16 @@ def _declare(L):
                                         C.c_uint32, f64p]),
         "orc_key_switch": (C.c_int, [vp, u64p, C.c_int, C.c_uint64, u64p]),
         "orc_threads": (C.c_int, []),
+        "orc_bts_setup": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "orc_bootstrap": (vp, [vp, vp]),
+        "orc_bootstrap_scaled": (vp, [vp, vp, C.c_int64]),
+        "orc_mod_raise": (vp, [vp, vp]),
+        "orc_linear_transform_group": (vp, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_double]),
+        "orc_eval_mod": (vp, [vp, vp]),
+        "orc_set_scale": (vp, [vp, vp, C.c_double]),
+        "orc_mul_monomial": (vp, [vp, vp, C.c_uint64]),
+        "orc_fft_group_offsets": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, i64p, C.c_int]),
+        "orc_fft_group_diag": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int64, f64p, f64p]),
         "orc_splitmix_stream": (C.c_uint64, [C.c_uint64, C.c_uint64, C.c_uint64, u64p]),
     }
     for name, (res, args) in sig.items():
@@ -291,6 +301,42 @@ class Context:
 
     def drop(self, a, level: int):
         return Ciphertext(self, lib().orc_drop(self.h, a.h, level))
+
+    def bts_setup(self, K=28, r=4, deg=31, cts=3, stc=3) -> int:
+        """Enable bootstrapping; returns the level of a bootstrapped ciphertext."""
+        return _check(lib().orc_bts_setup(self.h, K, r, deg, cts, stc))
+
+    def bootstrap(self, a):
+        return Ciphertext(self, lib().orc_bootstrap(self.h, a.h))
+
+    def bootstrap_scaled(self, a, Y: int):
+        return Ciphertext(self, lib().orc_bootstrap_scaled(self.h, a.h, Y))
+
+    def linear_transform_group(self, a, groups: int, inverse: bool, g: int, target: float):
+        return Ciphertext(self, lib().orc_linear_transform_group(self.h, a.h, groups, int(inverse), g, target))
+
+    def eval_mod(self, a):
+        return Ciphertext(self, lib().orc_eval_mod(self.h, a.h))
+
+    def with_scale(self, a, scale: float):
+        return Ciphertext(self, lib().orc_set_scale(self.h, a.h, scale))
+
+    def mod_raise(self, a):
+        return Ciphertext(self, lib().orc_mod_raise(self.h, a.h))
+
+    def mul_monomial(self, a, e: int):
+        return Ciphertext(self, lib().orc_mul_monomial(self.h, a.h, e))
+
+    def fft_group(self, groups: int, inverse: bool, g: int) -> dict:
+        """{offset: complex diagonal} of group g of the grouped special-FFT factors."""
+        offs = np.empty(4096, dtype=np.int64)
+        k = _check(lib().orc_fft_group_offsets(self.h, groups, int(inverse), g, offs, len(offs)))
+        out = {}
+        for o in offs[:k]:
+            re, im = np.empty(self.N // 2), np.empty(self.N // 2)
+            _check(lib().orc_fft_group_diag(self.h, groups, int(inverse), g, int(o), re, im))
+            out[int(o)] = re + 1j * im
+        return out
 
     def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0):
         return Ciphertext(self, lib().orc_invsqrt(self.h, a.h, lo, hi, B, degree, iters, pre_bts, bts_mask))

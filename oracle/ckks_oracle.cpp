@@ -267,6 +267,10 @@ struct Ctx {
   std::vector<i64> s;                    // secret coefficients
   Poly s_ntt;                            // per prime
   std::map<u64, std::vector<KeyDigit>> keys;  // galois element (0 = relinearisation) -> digits
+  // bootstrapping: off unless configured; K bounds the ModRaise overflow |I| < K,
+  // r double-angle steps, degree of the cosine interpolant, levels of CtS / StC
+  bool bts_on = false;
+  int bts_K = 28, bts_r = 4, bts_deg = 31, bts_cts = 3, bts_stc = 3;
   int L() const { return n_q - 1; }
 };
 struct Ct { Poly c[2]; int level = 0; double scale = 1; };
@@ -811,7 +815,8 @@ struct ChebEval {
     }
     return mul_int(C, diff, 2);
   }
-  Ct run(const Ct& t, const std::vector<double>& coeffs) {
+  Ct run(const Ct& t, const std::vector<double>& coeffs) { return run(t, coeffs, C.scale); }
+  Ct run(const Ct& t, const std::vector<double>& coeffs, double target) {
     int d = deg_of(coeffs);
     int m = 0; while ((1 << m) < d + 1) ++m;
     int lb = (m + 1) / 2; if (lb < 1) lb = 1;
@@ -828,9 +833,223 @@ struct ChebEval {
     }
     int lvl = best_level(coeffs);
     if (lvl < 0) throw std::runtime_error("Chebyshev evaluation: level exhausted");
-    return eval(coeffs, lvl, C.scale);
+    return eval(coeffs, lvl, target);
   }
 };
+
+
+// ---------------------------------------------------------------- bootstrapping
+// The paper uses BTS as a black box (Sec. 2.1): it needs level >= l_BTS, takes
+// inputs in [-1, 1] and returns a ciphertext at l_afterBTS.  This is the
+// textbook full-slot CKKS bootstrapping (Cheon et al. 2018 with the
+// CoeffToSlot / EvalMod / SlotToCoeff structure of Chen-Chillotti-Song 2019 and
+// the cosine + double-angle EvalMod of Bossuat et al. 2021):
+//   ModRaise   level-0 coefficients (centred mod q_0) lifted to every prime:
+//              plaintext t = m + q_0 I, |I| < K
+//   CoeffToSlot slots <- V^-1 slots, V the decoding matrix z = V w, factored into
+//              the radix-2 stages of the special FFT and grouped into bts_cts
+//              sparse matrices, each applied as baby-step / giant-step sums of
+//              diagonals times rotations; real and imaginary parts split by
+//              conjugation
+//   EvalMod    u = t / (q_0 K) -> sin(2 pi K u) = sin(2 pi m / q_0): Chebyshev
+//              interpolant of cos(2 pi (K u - 1/4) / 2^r), then r double angles
+//   SlotToCoeff slots <- V slots (bts_stc groups)
+// Constant factors are carried by the scale labels: ModRaise labels t with
+// scale 2 q_0 K; after EvalMod the label is multiplied by 2 pi s_in / q_0.
+typedef std::map<long, std::vector<cd>> DiagMap;  // rotation offset (mod n) -> diagonal
+
+static std::vector<cd> rot_vec(const std::vector<cd>& v, long k) {  // out[s] = v[s + k]
+  long n = (long)v.size();
+  std::vector<cd> r(n);
+  for (long s = 0; s < n; ++s) r[s] = v[(((s + k) % n) + n) % n];
+  return r;
+}
+// one radix-2 stage (sub-transform length len) of the decoding FFT over
+// bit-reversed input, or its inverse, as diagonals
+static DiagMap fft_stage(size_t n, size_t len, bool inverse) {
+  size_t h = len / 2; u64 M = 4 * len;
+  std::vector<cd> d0(n), dp(n), dm(n);
+  for (size_t s = 0; s < n; ++s) {
+    size_t j = s % len;
+    size_t jj = j < h ? j : j - h;
+    cd z = std::polar(1.0, 2.0 * M_PI * (double)powmod(5, jj, M) / (double)M);
+    if (!inverse) {
+      if (j < h) { d0[s] = 1.0; dp[s] = z; } else { d0[s] = -z; dm[s] = 1.0; }
+    } else {
+      if (j < h) { d0[s] = 0.5; dp[s] = 0.5; } else { d0[s] = -std::conj(z) * 0.5; dm[s] = std::conj(z) * 0.5; }
+    }
+  }
+  DiagMap D;  // offsets +h and -h coincide modulo n when h = n/2: add
+  D[0] = d0;
+  D[(long)h] = dp;
+  std::vector<cd>& m = D[(long)(n - h)];
+  if (m.empty()) m = dm; else for (size_t s = 0; s < n; ++s) m[s] += dm[s];
+  return D;
+}
+// (A B) v = sum_{a,b} (A_a o rot(B_b, a)) o rot(v, a + b)
+static DiagMap diag_compose(const DiagMap& A, const DiagMap& B, size_t n) {
+  DiagMap R;
+  for (auto& a : A) for (auto& b : B) {
+    long o = (long)((a.first + b.first) % (long)n);
+    std::vector<cd> rb = rot_vec(b.second, a.first);
+    std::vector<cd>& dst = R[o];
+    if (dst.empty()) dst.assign(n, cd(0, 0));
+    for (size_t s = 0; s < n; ++s) dst[s] += a.second[s] * rb[s];
+  }
+  return R;
+}
+// the bts_cts (inverse) or bts_stc (forward) grouped factors, in application order
+static std::vector<DiagMap> fft_groups(size_t n, int groups, bool inverse) {
+  int logn = 0; while ((1ull << logn) < n) ++logn;
+  std::vector<int> sizes(groups, logn / groups);
+  for (int g = 0; g < logn % groups; ++g) sizes[g] += 1;
+  std::vector<size_t> lens;  // stage lengths in application order
+  if (!inverse) for (int i = 1; i <= logn; ++i) lens.push_back(1ull << i);
+  else for (int i = logn; i >= 1; --i) lens.push_back(1ull << i);
+  std::vector<DiagMap> out; size_t pos = 0;
+  for (int g = 0; g < groups; ++g) {
+    DiagMap M = fft_stage(n, lens[pos++], inverse);
+    for (int k = 1; k < sizes[g]; ++k) M = diag_compose(fft_stage(n, lens[pos++], inverse), M, n);
+    out.push_back(M);
+  }
+  return out;
+}
+static Poly encode_at(const Ctx& C, const std::vector<cd>& z, double scale, int level) {
+  return coeffs_to_ntt(C, encode_coeffs(C, z, scale), level);
+}
+static Ct mul_plain(const Ctx& C, const Ct& a, const Poly& pt) {
+  Ct r = a;
+  PER_LIMB
+  for (int i = 0; i <= a.level; ++i)
+    for (int p = 0; p < 2; ++p) for (size_t k = 0; k < C.N; ++k) r.c[p][i][k] = mulmod(a.c[p][i][k], pt[i][k], C.q[i]);
+  return r;
+}
+// sum_o diag_o o rot(v, o) as sum_g rot( sum_b rot(diag_{k}, -G_g) o rot(v, b h0), G_g ),
+// offsets o = k h0, k = k_min + g n1 + b; one rescale at the end, result scale = target
+static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target) {
+  long n = (long)(C.N / 2);
+  long h0 = 0, kmin = 0, kmax = 0;
+  std::map<long, const std::vector<cd>*> byk;
+  for (auto& e : M) { long o = e.first <= n / 2 ? e.first : e.first - n; if (o) h0 = h0 ? std::__gcd(h0, std::labs(o)) : std::labs(o); }
+  if (!h0) h0 = 1;
+  for (auto& e : M) {
+    long o = e.first <= n / 2 ? e.first : e.first - n;
+    long k = o / h0; byk[k] = &e.second; kmin = std::min(kmin, k); kmax = std::max(kmax, k);
+  }
+  long span = kmax - kmin + 1, n1 = 1;
+  while (n1 * n1 < span) n1 <<= 1;
+  long giants = (span + n1 - 1) / n1;
+  double sp = target * (double)C.q[v.level] / v.scale;
+  std::vector<Ct> baby(n1);
+  std::vector<bool> have(n1, false);
+  Ct acc; bool acc_set = false;
+  for (long g = 0; g < giants; ++g) {
+    long G = h0 * (kmin + g * n1);
+    Ct inner; bool inner_set = false;
+    for (long b = 0; b < n1; ++b) {
+      long k = kmin + g * n1 + b;
+      auto it = byk.find(k);
+      if (it == byk.end()) continue;
+      if (!have[b]) { baby[b] = b == 0 ? v : rotate(C, v, b * h0); have[b] = true; }
+      Poly pt = encode_at(C, rot_vec(*it->second, -G), sp, v.level);
+      Ct term = mul_plain(C, baby[b], pt);
+      term.scale = v.scale * sp;
+      inner = inner_set ? add_sub(C, inner, term, false) : term; inner_set = true;
+    }
+    if (!inner_set) continue;
+    long Gm = ((G % n) + n) % n;
+    Ct r = Gm ? rotate(C, inner, G) : inner;
+    acc = acc_set ? add_sub(C, acc, r, false) : r; acc_set = true;
+  }
+  Ct out = rescale(C, acc);
+  out.scale = target;
+  return out;
+}
+static Ct mod_raise(const Ctx& C, const Ct& a) {
+  if (a.level != 0) throw std::runtime_error("mod_raise: input must be at level 0");
+  Ct r; r.level = C.L(); r.scale = a.scale;
+  u64 q0 = C.q[0], h = q0 >> 1;
+  for (int p = 0; p < 2; ++p) {
+    Limb x = a.c[p][0]; ntt_inverse(C, x, 0);
+    r.c[p].assign(C.L() + 1, Limb(C.N));
+    PER_LIMB
+    for (int i = 0; i <= C.L(); ++i) {
+      u64 qi = C.q[i];
+      for (size_t k = 0; k < C.N; ++k) r.c[p][i][k] = x[k] <= h ? x[k] % qi : submod(x[k] % qi, q0 % qi, qi);
+      ntt_forward(C, r.c[p][i], i);
+    }
+  }
+  return r;
+}
+// multiplication by the monomial X^e (0 <= e < 2N): negacyclic shift of the coefficients
+static Ct mul_monomial(const Ctx& C, const Ct& a, u64 e) {
+  Ct r = a; u64 M = 2 * C.N;
+  for (int p = 0; p < 2; ++p) {
+    PER_LIMB
+    for (int i = 0; i <= a.level; ++i) {
+      Limb x = a.c[p][i]; ntt_inverse(C, x, i);
+      Limb y(C.N, 0);
+      for (size_t k = 0; k < C.N; ++k) {
+        u64 t = (k + e) % M;
+        if (t < C.N) y[t] = x[k]; else y[t - C.N] = x[k] ? C.q[i] - x[k] : 0;
+      }
+      ntt_forward(C, y, i);
+      r.c[p][i] = y;
+    }
+  }
+  return r;
+}
+// Chebyshev interpolant of an arbitrary function on [lo, hi] (same closed form as cheb_coeffs)
+template <class F>
+static std::vector<double> cheb_interp_fn(F f, double lo, double hi, int d) {
+  int n = d + 1;
+  std::vector<double> fx(n), c(n, 0.0);
+  for (int k = 0; k < n; ++k) fx[k] = f(0.5 * (lo + hi) + 0.5 * (hi - lo) * std::cos(M_PI * (k + 0.5) / n));
+  for (int j = 0; j < n; ++j) {
+    double s = 0;
+    for (int k = 0; k < n; ++k) s += fx[k] * std::cos(M_PI * j * (k + 0.5) / n);
+    c[j] = (j == 0 ? 1.0 : 2.0) / n * s;
+  }
+  return c;
+}
+static Ct eval_mod(Ctx& C, const Ct& u) {
+  const double K = C.bts_K, R = std::ldexp(1.0, C.bts_r);
+  std::vector<double> coeffs = cheb_interp_fn([&](double x) { return std::cos(2.0 * M_PI * (K * x - 0.25) / R); },
+                                              -1.0, 1.0, C.bts_deg);
+  ChebEval ev(C);
+  Ct c = ev.run(u, coeffs, u.scale);
+  for (int i = 0; i < C.bts_r; ++i) c = mul_int(C, add_const(C, mul(C, c, c), -0.5), 2);  // cos 2x = 2 cos^2 x - 1
+  return c;
+}
+static int bts_levels(const Ctx& C) { return C.bts_cts + C.bts_r + C.bts_stc + 1 + [&] { int m = 0; while ((1 << m) < C.bts_deg + 1) ++m; return m; }(); }
+static Ct bootstrap_core(Ctx& C, const Ct& a) {
+  if (!C.bts_on) throw std::runtime_error("bootstrapping is not configured");
+  if (a.level != 0) throw std::runtime_error("bootstrap: input must be at level 0");
+  const size_t n = C.N / 2;
+  const double s_in = a.scale, q0 = (double)C.q[0];
+  Ct t = mod_raise(C, a);
+  t.scale = 2.0 * q0 * C.bts_K;
+  for (const DiagMap& M : fft_groups(n, C.bts_cts, true)) t = linear_transform(C, t, M, (double)C.q[t.level - 1]);
+  Ct cj = conjugate(C, t);
+  Ct re = add_sub(C, t, cj, false);
+  Ct im = mul_monomial(C, add_sub(C, t, cj, true), 3 * C.N / 2);  // times -i
+  re = eval_mod(C, re);
+  im = eval_mod(C, im);
+  Ct w = add_sub(C, re, mul_monomial(C, im, C.N / 2), false);  // re + i im
+  w.scale = w.scale * 2.0 * M_PI * s_in / q0;
+  std::vector<DiagMap> G = fft_groups(n, C.bts_stc, false);
+  for (size_t g = 0; g < G.size(); ++g)
+    w = linear_transform(C, w, G[g], g + 1 == G.size() ? C.scale : (double)C.q[w.level - 1]);
+  return w;
+}
+// values of y in [-Y, Y]: scale by 1/Y into [-1, 1] (one level, landing at level 0
+// with scale q_0 / 2^12), bootstrap, multiply back by the integer Y
+static Ct bootstrap_scaled(Ctx& C, const Ct& y, i64 Y) {
+  if (y.level < 1) throw std::runtime_error("bootstrap: input needs level >= 1");
+  Ct a = mul_const_to(C, drop_to(y, 1), 1.0 / (double)Y, (double)C.q[0] / 4096.0);
+  Ct b = bootstrap_core(C, a);
+  return Y == 1 ? b : mul_int(C, b, Y);
+}
 
 // ---------------------------------------------------------------- CryptoInvSqrt (Alg. 1)
 struct InvSqrtCfg { double lo, hi, B; int degree, iters, pre_bts; u64 bts_mask; };
@@ -847,25 +1066,44 @@ static Ct newton_step(Ctx& C, const Ct& x, const Ct& y) {
   return add_sub(C, ta, tb, true);
 }
 
+// Bootstrapping placement (the paper's Pre-BTS indicator c, Sec. 4.1, and BTS
+// during the Newton loop, Sec. 4.3): pre_bts bootstraps the input a/B first;
+// bit j (< 63) of bts_mask bootstraps y before Newton step j (bit 0: right
+// after the Chebyshev step, as in Alg. 1); bit 63 bootstraps lazily, before a
+// step whose y lacks the two levels it consumes (or would leave y at level 0
+// with further steps to go).  ct_x is never bootstrapped.  Y, the power of two
+// that bounds y = 1/sqrt(a/B), scales y into [-1, 1] around each BTS.
 static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   if (cfg.B <= 0 || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.iters < 0)
     throw std::runtime_error("invsqrt: bad configuration");
-  if (cfg.pre_bts || cfg.bts_mask) throw std::runtime_error("invsqrt: bootstrapping not available in this context");
+  if ((cfg.pre_bts || cfg.bts_mask) && !C.bts_on) throw std::runtime_error("invsqrt: bootstrapping not configured");
   double lo = cfg.lo / cfg.B, hi = cfg.hi / cfg.B;
+  i64 Y = 1; while ((double)Y < 1.0 / std::sqrt(lo)) Y *= 2;
+  Ct a = in; double Bf = cfg.B;
+  if (cfg.pre_bts) {  // a -> BTS(a / B): values in (0, 1]
+    if (in.level < 1) throw std::runtime_error("invsqrt: level exhausted");
+    a = bootstrap_core(C, mul_const_to(C, drop_to(in, 1), 1.0 / cfg.B, (double)C.q[0] / 4096.0));
+    Bf = 1.0;
+  }
   // pre-normalisation (Sec. 2.3): a -> a/B, then the affine map onto [-1, 1]
   // for the Chebyshev basis, folded into one constant multiplication
-  double alpha = 2.0 / (cfg.B * (hi - lo)), beta = -(hi + lo) / (hi - lo);
-  if (in.level < 2) throw std::runtime_error("invsqrt: level exhausted");
-  Ct t = add_const(C, mul_const_to(C, in, alpha, C.scale), beta);
-  Ct x = mul_const_to(C, in, 0.5 / cfg.B, C.scale);  // ct_x = 0.5 * a/B
+  double alpha = 2.0 / (Bf * (hi - lo)), beta = -(hi + lo) / (hi - lo);
+  if (a.level < 2) throw std::runtime_error("invsqrt: level exhausted");
+  Ct t = add_const(C, mul_const_to(C, a, alpha, C.scale), beta);
+  Ct x = mul_const_to(C, a, 0.5 / Bf, C.scale);  // ct_x = 0.5 * a/B
   std::vector<double> coeffs = cheb_coeffs(lo, hi, cfg.degree);
   ChebEval ev(C);
   Ct y = ev.run(t, coeffs);
+  const bool lazy = (cfg.bts_mask >> 63) & 1;
   for (int i = 0; i < cfg.iters; ++i) {
+    bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
+    bool need = lazy && (y.level < 2 || (y.level == 2 && cfg.iters - i >= 2));
+    if (force || need) y = bootstrap_scaled(C, y, Y);
     if (std::min(y.level, x.level) < 2) throw std::runtime_error("invsqrt: level exhausted in Newton loop");
     y = newton_step(C, x, y);
   }
-  if (cfg.B != 1.0) y = mul_const_to(C, y, 1.0 / std::sqrt(cfg.B), y.scale);
+  if (cfg.iters == 0 && (cfg.bts_mask & 1)) y = bootstrap_scaled(C, y, Y);
+  if (cfg.B != 1.0) y.scale *= std::sqrt(cfg.B);  // y / sqrt(B): relabelled, no level used
   return y;
 }
 
@@ -1086,3 +1324,43 @@ API int orc_threads() {
   return 1;
 #endif
 }
+
+API int orc_bts_setup(void* c, int K, int r, int deg, int cts, int stc) {
+  GUARD(
+    Ctx* C = (Ctx*)c;
+    C->bts_K = K; C->bts_r = r; C->bts_deg = deg; C->bts_cts = cts; C->bts_stc = stc;
+    if (C->L() - bts_levels(*C) < 1) throw std::runtime_error("prime chain too short for bootstrapping");
+    C->bts_on = true;
+    return C->L() - bts_levels(*C);
+  )
+  return -1;
+}
+API void* orc_bootstrap(void* c, void* a) { CT_OP(bootstrap_core(*(Ctx*)c, *(Ct*)a)) }
+API void* orc_bootstrap_scaled(void* c, void* a, int64_t Y) { CT_OP(bootstrap_scaled(*(Ctx*)c, *(Ct*)a, Y)) }
+API void* orc_mod_raise(void* c, void* a) { CT_OP(mod_raise(*(Ctx*)c, *(Ct*)a)) }
+API void* orc_mul_monomial(void* c, void* a, uint64_t e) { CT_OP(mul_monomial(*(Ctx*)c, *(Ct*)a, e)) }
+// diagonals of the grouped special-FFT factors: writes the offsets of group g into
+// offsets[cap] and returns how many (diagonals themselves via orc_fft_group_diag)
+API int orc_fft_group_offsets(void* c, int groups, int inverse, int g, int64_t* offsets, int cap) {
+  GUARD(
+    Ctx* C = (Ctx*)c; std::vector<DiagMap> G = fft_groups(C->N / 2, groups, inverse != 0);
+    int k = 0; for (auto& e : G.at(g)) { if (k < cap) offsets[k] = e.first; ++k; }
+    return k;
+  )
+  return -1;
+}
+API int orc_fft_group_diag(void* c, int groups, int inverse, int g, int64_t offset, double* re, double* im) {
+  GUARD(
+    Ctx* C = (Ctx*)c; std::vector<DiagMap> G = fft_groups(C->N / 2, groups, inverse != 0);
+    const std::vector<cd>& d = G.at(g).at(offset);
+    for (size_t s = 0; s < d.size(); ++s) { re[s] = d[s].real(); im[s] = d[s].imag(); }
+    return 0;
+  )
+  return -1;
+}
+// single steps of bootstrapping, for tests
+API void* orc_linear_transform_group(void* c, void* a, int groups, int inverse, int g, double target) {
+  CT_OP(linear_transform(*(Ctx*)c, *(Ct*)a, fft_groups(((Ctx*)c)->N / 2, groups, inverse != 0).at(g), target))
+}
+API void* orc_eval_mod(void* c, void* a) { CT_OP(eval_mod(*(Ctx*)c, *(Ct*)a)) }
+API void* orc_set_scale(void* c, void* a, double scale) { (void)c; Ct r = *(Ct*)a; r.scale = scale; return new Ct(r); }

@@ -305,3 +305,61 @@ API hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, 
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   });
 }
+
+// ---------------------------------------------------------------- bootstrapping
+API hedap_status hedap_bootstrap_setup(hedap_ctx* ctx, const hedap_bts_params* p, int* level_after) {
+  return guarded([&] {
+    need(ctx && p, "null argument");
+    const int l = hedap::bts_setup(*ctx->c, (int)p->K, (int)p->double_angles, (int)p->mod_degree,
+                                   (int)p->cts_levels, (int)p->stc_levels);
+    if (level_after) *level_after = l;
+  });
+}
+API hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::bootstrap_core(*ctx->c, *a->c)));
+}
+API hedap_status hedap_bootstrap_scaled(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, hedap_ct** out) {
+  CT_OP((need(a && Y >= 1, "bad argument"), hedap::bootstrap_scaled(*ctx->c, *a->c, Y)));
+}
+API hedap_status hedap_mod_raise(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::mod_raise(*ctx->c, *a->c)));
+}
+API hedap_status hedap_mul_monomial(hedap_ctx* ctx, const hedap_ct* a, uint64_t e, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::mul_monomial(*ctx->c, *a->c, e)));
+}
+API hedap_status hedap_bts_linear_transform(hedap_ctx* ctx, const hedap_ct* a, int inverse, int group,
+                                            double target_scale, hedap_ct** out) {
+  CT_OP((need(a && target_scale > 0, "bad argument"),
+         hedap::bts_linear_transform(*ctx->c, *a->c, inverse != 0, group, target_scale)));
+}
+API hedap_status hedap_eval_mod(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
+  CT_OP((need(a, "null ciphertext"), hedap::eval_mod(*ctx->c, *a->c)));
+}
+API hedap_status hedap_set_scale(hedap_ctx* ctx, hedap_ct* a, double scale) {
+  return guarded([&] {
+    need(ctx && a && scale > 0, "bad argument");
+    a->c->scale = scale;
+  });
+}
+API hedap_status hedap_encode(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, double scale,
+                              int64_t* out) {
+  return guarded([&] {
+    need(ctx && re && out, "null argument");
+    need(n_slots == ctx->c->N / 2, "n_slots must equal N/2");
+    std::vector<std::complex<double>> z(n_slots);
+    for (size_t j = 0; j < n_slots; ++j) z[j] = {re[j], im ? im[j] : 0.0};
+    std::vector<double> m = hedap::encode_slots(*ctx->c, z, scale);
+    for (size_t k = 0; k < m.size(); ++k) {
+      need(std::fabs(m[k]) < 9.2e18, "coefficient exceeds 63 bits");
+      out[k] = (int64_t)m[k];
+    }
+  });
+}
+API hedap_status hedap_bts_diagonal(hedap_ctx* ctx, int inverse, int group, int64_t offset, double* re, double* im) {
+  return guarded([&] {
+    need(ctx && re && im, "null argument");
+    std::vector<std::complex<double>> d;
+    need(hedap::bts_diagonal(*ctx->c, inverse != 0, group, (long)offset, d), "no such diagonal");
+    for (size_t s = 0; s < d.size(); ++s) { re[s] = d[s].real(); im[s] = d[s].imag(); }
+  });
+}

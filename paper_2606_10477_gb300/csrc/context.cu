@@ -232,7 +232,7 @@ struct SpecialFFT {
           const cplx r = root[(g % M) * stride];
           const cplx x = v[b + j], y = v[b + j + len / 2];
           v[b + j] = (x + y) * 0.5;
-          v[b + j + len / 2] = (x - y) * std::conj(r) * 0.5;
+          v[b + j + len / 2] = (x - y) * 0.5 / r;
           g = (g * 5) % M;
         }
       }
@@ -241,11 +241,10 @@ struct SpecialFFT {
   }
 };
 
-static std::vector<double> encode(const Ctx& C, const std::vector<double>& re, const std::vector<double>& im,
-                                  double scale) {
+std::vector<double> encode_slots(const Ctx& C, const std::vector<std::complex<double>>& z, double scale) {
   const size_t n = C.N / 2;
-  std::vector<cplx> v(n);
-  for (size_t j = 0; j < n; ++j) v[j] = cplx(re[j], im.empty() ? 0.0 : im[j]);
+  if (z.size() != n) throw Error(HEDAP_ERR_ARG, "encode: n_slots must equal N/2");
+  std::vector<cplx> v(z);
   SpecialFFT(C.log_n).inverse(v);
   std::vector<double> m(C.N);
   for (size_t k = 0; k < n; ++k) {
@@ -253,6 +252,13 @@ static std::vector<double> encode(const Ctx& C, const std::vector<double>& re, c
     m[k + n] = std::round(v[k].imag() * scale);
   }
   return m;
+}
+
+static std::vector<double> encode(const Ctx& C, const std::vector<double>& re, const std::vector<double>& im,
+                                  double scale) {
+  std::vector<cplx> v(C.N / 2);
+  for (size_t j = 0; j < v.size(); ++j) v[j] = cplx(re[j], im.empty() ? 0.0 : im[j]);
+  return encode_slots(C, v, scale);
 }
 
 std::unique_ptr<Ct> encrypt(Ctx& C, const std::vector<double>& re, const std::vector<double>& im, int level,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <complex>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -140,6 +141,11 @@ struct LevelConsts {  // device constants for one level (see keyswitch.cu / eval
   RescaleConsts rescale;
 };
 
+struct BtsState;  // bootstrapping state (bootstrap.cu)
+struct BtsStateDeleter {
+  void operator()(BtsState* p) const;
+};
+
 struct Ctx {
   int log_n = 0;
   size_t N = 0;
@@ -158,6 +164,7 @@ struct Ctx {
   DevBuf d_sk;        // [n_q+n_p][N] NTT domain
   std::map<u64, DevBuf> keys;  // galois (0 = relinearisation) -> [dnum][2][n_q+n_p][N]
   std::map<int, std::unique_ptr<LevelConsts>> lc;
+  std::unique_ptr<BtsState, BtsStateDeleter> bts;
   int L() const { return n_q - 1; }
   int total_primes() const { return n_q + n_p; }
   int dnum(int level) const { return (level + 1 + alpha - 1) / alpha; }
@@ -186,8 +193,21 @@ std::unique_ptr<Ct> encrypt(Ctx& C, const std::vector<double>& re, const std::ve
                             u64 seed);
 void decrypt(Ctx& C, const Ct& ct, std::vector<double>& re, std::vector<double>& im);
 
+std::vector<double> encode_slots(const Ctx& C, const std::vector<std::complex<double>>& z, double scale);
+
 // ------------------------------------------------------------------ CryptoInvSqrt (invsqrt.cu)
 std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg);
+std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target);
+
+// ------------------------------------------------------------------ bootstrapping (bootstrap.cu)
+int bts_setup(Ctx& C, int K, int r, int deg, int cts, int stc);
+std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a);
+std::unique_ptr<Ct> bootstrap_scaled(Ctx& C, const Ct& y, i64 Y);
+std::unique_ptr<Ct> mod_raise(Ctx& C, const Ct& a);
+std::unique_ptr<Ct> mul_monomial(Ctx& C, const Ct& a, u64 e);
+std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& a, bool inverse, int g, double target);
+std::unique_ptr<Ct> eval_mod(Ctx& C, const Ct& a);
+bool bts_diagonal(Ctx& C, bool inverse, int g, long offset, std::vector<std::complex<double>>& out);
 
 // thread-local message returned by hedap_last_error (capi.cu)
 void set_last_error(const std::string& m);

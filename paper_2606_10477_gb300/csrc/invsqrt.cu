@@ -116,7 +116,7 @@ struct ChebPS {
     }
     return ev_mul_int(C, *diff, 2);
   }
-  CtP run(const Ct& t, const std::vector<double>& coeffs) {
+  CtP run(const Ct& t, const std::vector<double>& coeffs, double target) {
     const int d = degree(coeffs);
     int m = 0;
     while ((1 << m) < d + 1) ++m;
@@ -133,9 +133,14 @@ struct ChebPS {
     }
     const int lvl = top_level(coeffs);
     if (lvl < 0) throw Error(HEDAP_ERR_LEVEL, "Chebyshev evaluation: not enough levels");
-    return eval(coeffs, lvl, C.scale);
+    return eval(coeffs, lvl, target);
   }
 };
+
+std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target) {
+  ChebPS ps(C);
+  return ps.run(t, coeffs, target);
+}
 
 // One Newton step in Alg. 1's loop order; tmp_alpha = 1.5 y is produced last so
 // that its scale equals tmp_beta's exactly.
@@ -147,22 +152,47 @@ static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
   return ev_add(C, *ta, *tb, true);
 }
 
+// Bootstrapping placement (the Pre-BTS indicator c of Sec. 4.1 and BTS during
+// the Newton loop, Sec. 4.3): pre_bts bootstraps a/B first; bit j (< 63) of
+// bts_mask bootstraps y before Newton step j (bit 0: right after the Chebyshev
+// step, as in Alg. 1); bit 63 bootstraps lazily, before a step whose y lacks
+// the two levels the step consumes or would be left at level 0 with steps to
+// go.  ct_x is never bootstrapped.  Y, the power of two bounding y, scales y
+// into [-1, 1] around each BTS.  The final 1/sqrt(B) is applied to the scale
+// label (no level is used).
 std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) {
   if (!(cfg.B > 0) || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.degree > 4096)
     throw Error(HEDAP_ERR_ARG, "invsqrt: invalid configuration");
-  if (cfg.pre_bts || cfg.bts_mask) throw Error(HEDAP_ERR_ARG, "invsqrt: bootstrapping not available in this context");
-  if (in.level < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
+  if ((cfg.pre_bts || cfg.bts_mask) && !C.bts)
+    throw Error(HEDAP_ERR_ARG, "invsqrt: bootstrapping not configured on this context");
   const double lo = cfg.lo / cfg.B, hi = cfg.hi / cfg.B;
-  const double alpha = 2.0 / (cfg.B * (hi - lo)), beta = -(hi + lo) / (hi - lo);
-  CtP t = ev_add_const(C, *ev_mul_const(C, in, alpha, C.scale), beta);
-  CtP x = ev_mul_const(C, in, 0.5 / cfg.B, C.scale);
-  ChebPS ps(C);
-  CtP y = ps.run(*t, cheb_interp(lo, hi, (int)cfg.degree));
-  for (uint32_t i = 0; i < cfg.newton_iters; ++i) {
+  i64 Y = 1;
+  while ((double)Y < 1.0 / std::sqrt(lo)) Y *= 2;
+  CtP pre;
+  double Bf = cfg.B;
+  if (cfg.pre_bts) {  // a -> BTS(a / B), values in (0, 1]
+    if (in.level < 1) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
+    CtP d = in.level > 1 ? ev_drop(C, in, 1) : nullptr;
+    pre = bootstrap_core(C, *ev_mul_const(C, d ? *d : in, 1.0 / cfg.B, (double)C.primes[0] / 4096.0));
+    Bf = 1.0;
+  }
+  const Ct& a = pre ? *pre : in;
+  if (a.level < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
+  const double alpha = 2.0 / (Bf * (hi - lo)), beta = -(hi + lo) / (hi - lo);
+  CtP t = ev_add_const(C, *ev_mul_const(C, a, alpha, C.scale), beta);
+  CtP x = ev_mul_const(C, a, 0.5 / Bf, C.scale);
+  CtP y = cheb_eval(C, *t, cheb_interp(lo, hi, (int)cfg.degree), C.scale);
+  const bool lazy = (cfg.bts_mask >> 63) & 1;
+  const int n = (int)cfg.newton_iters;
+  for (int i = 0; i < n; ++i) {
+    const bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
+    const bool need = lazy && (y->level < 2 || (y->level == 2 && n - i >= 2));
+    if (force || need) y = bootstrap_scaled(C, *y, Y);
     if (std::min(y->level, x->level) < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: level exhausted in Newton loop");
     y = newton_step(C, *x, *y);
   }
-  if (cfg.B != 1.0) y = ev_mul_const(C, *y, 1.0 / std::sqrt(cfg.B), y->scale);
+  if (n == 0 && (cfg.bts_mask & 1)) y = bootstrap_scaled(C, *y, Y);
+  if (cfg.B != 1.0) y->scale *= std::sqrt(cfg.B);
   return y;
 }
 

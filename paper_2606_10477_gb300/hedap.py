@@ -28,7 +28,14 @@ EXPORTED = [
     "hedap_rescale", "hedap_rotate", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
+    "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
+    "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
 ]
+
+
+class BtsParams(C.Structure):
+    _fields_ = [("K", C.c_uint32), ("double_angles", C.c_uint32), ("mod_degree", C.c_uint32),
+                ("cts_levels", C.c_uint32), ("stc_levels", C.c_uint32)]
 
 
 class HedapError(RuntimeError):
@@ -101,6 +108,16 @@ def _declare(L):
         "hedap_moddown": (st, [vp, u64p, C.c_int, u64p]),
         "hedap_key_switch": (st, [vp, u64p, C.c_int, C.c_uint64, u64p]),
         "hedap_rescale_noalloc": (st, [vp, u64p, C.c_int, u64p]),
+        "hedap_bootstrap_setup": (st, [vp, C.POINTER(BtsParams), C.POINTER(C.c_int)]),
+        "hedap_bootstrap": (st, [vp, vp, pp]),
+        "hedap_bootstrap_scaled": (st, [vp, vp, C.c_int64, pp]),
+        "hedap_mod_raise": (st, [vp, vp, pp]),
+        "hedap_mul_monomial": (st, [vp, vp, C.c_uint64, pp]),
+        "hedap_bts_linear_transform": (st, [vp, vp, C.c_int, C.c_int, C.c_double, pp]),
+        "hedap_eval_mod": (st, [vp, vp, pp]),
+        "hedap_set_scale": (st, [vp, vp, C.c_double]),
+        "hedap_encode": (st, [vp, dp, dp, C.c_size_t, C.c_double, C.POINTER(C.c_int64)]),
+        "hedap_bts_diagonal": (st, [vp, C.c_int, C.c_int, C.c_int64, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -298,6 +315,53 @@ class Context:
 
     def drop(self, a, level: int):
         return self._ct(load().hedap_drop_level, a.h, level)
+
+    # ---- bootstrapping
+    def bts_setup(self, K=28, r=4, deg=31, cts=3, stc=3) -> int:
+        """Enable bootstrapping; returns the level of a bootstrapped ciphertext."""
+        lv = C.c_int()
+        _check(load().hedap_bootstrap_setup(self.h, C.byref(BtsParams(K, r, deg, cts, stc)), C.byref(lv)))
+        return lv.value
+
+    def bootstrap(self, a):
+        return self._ct(load().hedap_bootstrap, a.h)
+
+    def bootstrap_scaled(self, a, Y: int):
+        return self._ct(load().hedap_bootstrap_scaled, a.h, Y)
+
+    def mod_raise(self, a):
+        return self._ct(load().hedap_mod_raise, a.h)
+
+    def mul_monomial(self, a, e: int):
+        return self._ct(load().hedap_mul_monomial, a.h, e)
+
+    def linear_transform_group(self, a, groups_unused: int, inverse: bool, g: int, target: float):
+        return self._ct(load().hedap_bts_linear_transform, a.h, int(inverse), g, target)
+
+    def eval_mod(self, a):
+        return self._ct(load().hedap_eval_mod, a.h)
+
+    def encode_coeffs(self, re, im=None, scale=None) -> np.ndarray:
+        re = np.ascontiguousarray(re, dtype=np.float64)
+        im = np.zeros_like(re) if im is None else np.ascontiguousarray(im, dtype=np.float64)
+        out = np.empty(self.N, dtype=np.int64)
+        dp = C.POINTER(C.c_double)
+        _check(load().hedap_encode(self.h, re.ctypes.data_as(dp), im.ctypes.data_as(dp), len(re),
+                                   float(scale or self.scale), out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def bts_diagonal(self, inverse: bool, g: int, offset: int):
+        n = self.N // 2
+        re, im = np.empty(n), np.empty(n)
+        dp = C.POINTER(C.c_double)
+        _check(load().hedap_bts_diagonal(self.h, int(inverse), g, offset, re.ctypes.data_as(dp),
+                                         im.ctypes.data_as(dp)))
+        return re + 1j * im
+
+    def with_scale(self, a, scale: float):
+        b = self.drop(a, a.level)
+        _check(load().hedap_set_scale(self.h, b.h, scale))
+        return b
 
     def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0):
         cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask)

@@ -18,7 +18,18 @@ PRESETS = {
     # small rings with the same prime shapes, for fast parity checks
     "n13": dict(log_n=13, q_bits=[50] * 8, p_bits=[60, 60], alpha=2, log_scale=50, hw=0),
     "n10": dict(log_n=10, q_bits=[45, 36, 36, 36, 36, 36], p_bits=[50, 50], alpha=2, log_scale=36, hw=0),
+    # N = 2^16 with bootstrapping: q_0 (60 bits), 10 compute primes (45), SlotToCoeff 3 x 45,
+    # EvalMod 10 x 55, CoeffToSlot 3 x 60, P = 3 x 60; log2(QP) = 1555; sparse ternary secret h = 192
+    "bts16": dict(log_n=16, q_bits=[60] + [45] * 10 + [45] * 3 + [55] * 10 + [60] * 3, p_bits=[60] * 3, alpha=3,
+                  log_scale=45, hw=192),
+    # the same chain shape at N = 2^12, for parity with the CPU oracle
+    "bts12": dict(log_n=12, q_bits=[60] + [45] * 8 + [45] * 3 + [55] * 10 + [60] * 3, p_bits=[60] * 3, alpha=3,
+                  log_scale=45, hw=192),
 }
+
+# bootstrapping parameters: ModRaise overflow bound K, double angles r, EvalMod
+# Chebyshev degree, CoeffToSlot and SlotToCoeff levels
+BTS = dict(K=28, r=4, deg=31, cts=3, stc=3)
 
 
 def rng(seed: int) -> np.random.Generator:

@@ -1,0 +1,125 @@
+"""Bootstrapping on the GPU (through the C ABI) against the CPU oracle.
+
+ModRaise, the monomial products, EvalMod, the grouped CoeffToSlot /
+SlotToCoeff transforms and the whole bootstrap are compared bit for bit at
+N = 2^12 (the plaintext diagonals come from two independently written FP64
+encoders that perform the same operations in the same order); at N = 2^16 by
+the decrypted error and CryptoInvSqrt's MRE.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_10477_gb300 import hedap, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def make(name, cls, seed=1):
+    p = inputs.PRESETS[name]
+    c = cls(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], seed)
+    b = inputs.BTS
+    lvl = c.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    return c, lvl
+
+
+@pytest.fixture(scope="module")
+def pair12():
+    g, lg = make("bts12", hedap.Context)
+    o, lo = make("bts12", oracle.Context)
+    return g, o
+
+
+def same(gc, oc):
+    assert gc.level == oc.level and gc.scale == oc.scale
+    assert np.array_equal(gc.limbs(), oc.limbs())
+
+
+def level0_pair(g, o, seed, values):
+    """Oracle-encrypted ciphertext at level 0 with scale q_0 / 2^12, imported into the library."""
+    q0 = float(o.primes()[0])
+    oc = o.mul_const(o.encrypt(values, 1, seed), 1.0, q0 / 4096)
+    return g.ct_import(oc.limbs(), 0, oc.scale), oc
+
+
+def test_mod_raise_and_monomials_bit_exact(pair12):
+    g, o = pair12
+    gc, oc = level0_pair(g, o, 3, inputs.uniform_values(3, o.N // 2, -1, 1))
+    same(g.mod_raise(gc), o.mod_raise(oc))
+    L = o.n_q - 1
+    limbs = inputs.random_ciphertext_limbs(4, o.primes(), L, o.N)
+    ga, oa = g.ct_import(limbs, L, o.scale), o.ct_import(limbs, L, o.scale)
+    for e in (o.N // 2, 3 * o.N // 2):
+        same(g.mul_monomial(ga, e), o.mul_monomial(oa, e))
+
+
+def test_eval_mod_bit_exact(pair12):
+    g, o = pair12
+    lvl = o.n_q - 1 - 3
+    u = inputs.uniform_values(5, o.N // 2, -1, 1)
+    scale = float(o.primes()[lvl])
+    oc = o.mul_const(o.encrypt(u, lvl + 1, 6), 1.0, scale)
+    gc = g.ct_import(oc.limbs(), oc.level, oc.scale)
+    gm, om = g.eval_mod(gc), o.eval_mod(oc)
+    same(gm, om)
+    K = inputs.BTS["K"]
+    assert np.max(np.abs(o.decrypt(om).real - np.sin(2 * np.pi * K * u))) < 1e-6
+
+
+@pytest.mark.parametrize("inverse", [True, False])
+def test_linear_transform_groups_match_oracle(pair12, inverse):
+    g, o = pair12
+    L = o.n_q - 1
+    z = inputs.uniform_values(7, o.N // 2, -1, 1) + 1j * inputs.uniform_values(8, o.N // 2, -1, 1)
+    oc = o.encrypt(z, L, 9)
+    gc = g.ct_import(oc.limbs(), L, oc.scale)
+    for grp in range(inputs.BTS["cts" if inverse else "stc"]):
+        target = oc.scale / 16  # plaintext scale q_l / 16 keeps the encoded diagonals below 2^63
+        oc = o.linear_transform_group(oc, 3, inverse, grp, target)
+        gc = g.linear_transform_group(gc, 3, inverse, grp, target)
+        same(gc, oc)
+
+
+def test_bootstrap_matches_oracle_and_input(pair12):
+    g, o = pair12
+    z = inputs.uniform_values(10, o.N // 2, -1, 1) + 1j * inputs.uniform_values(11, o.N // 2, -1, 1)
+    gc, oc = level0_pair(g, o, 12, z)
+    gb, ob = g.bootstrap(gc), o.bootstrap(oc)
+    assert gb.level == o.n_q - 1 - 16
+    same(gb, ob)
+    assert np.max(np.abs(g.decrypt(gb) - z)) < 1e-4
+
+
+def test_bootstrap_full_size():
+    """N = 2^16, 32768 complex slots, log2(QP) = 1555, h = 192."""
+    g, lvl = make("bts16", hedap.Context)
+    assert lvl == g.n_q - 1 - 16
+    z = inputs.uniform_values(13, g.N // 2, -1, 1) + 1j * inputs.uniform_values(14, g.N // 2, -1, 1)
+    ct = g.encrypt(z, 1, 15)
+    b = g.bootstrap_scaled(ct, 1)
+    assert b.level == lvl
+    err = np.abs(g.decrypt(b) - z)
+    assert np.max(err) < 1e-3 and np.mean(err) < 1e-4
+
+
+def test_invsqrt_with_bootstrapping_full_size():
+    """N = 2^16, inputs log-uniform in [1e-4, 1] at l_max, Chebyshev degree 63, 4 Newton steps,
+    lazy bootstrapping: decrypted MRE <= 1e-7."""
+    g, lvl = make("bts16", hedap.Context, seed=2)
+    a = inputs.log_uniform_values(16, g.N // 2, 1e-4, 1.0)
+    ct = g.encrypt(a, lvl, 17)
+    y = g.decrypt(g.invsqrt(ct, 1e-4, 1.0, 1.0, 63, 4, 0, 1 << 63)).real
+    ref = 1 / np.sqrt(a)
+    mre = float(np.mean(np.abs(y - ref) / ref))
+    assert mre <= 1e-7, mre
+
+
+def test_encoder_and_diagonals_match_oracle(pair12):
+    g, o = pair12
+    z = inputs.uniform_values(20, o.N // 2, -1, 1) + 1j * inputs.uniform_values(21, o.N // 2, -1, 1)
+    for sc in (2.0 ** 40, 2.0 ** 56):
+        assert np.array_equal(g.encode_coeffs(z.real, z.imag, sc), o.encode_coeffs(z.real, z.imag, sc).astype(np.int64))
+    for inverse in (True, False):
+        for grp in range(3):
+            for off, d in o.fft_group(3, inverse, grp).items():
+                assert np.array_equal(g.bts_diagonal(inverse, grp, off), d)

@@ -1,0 +1,101 @@
+"""Pins of the oracle's bootstrapping against facts outside the oracle.
+
+The grouped FFT factors multiply to the decoding matrix V (and its inverse,
+up to the bit-reversal permutation), checked against numpy's dense matrix
+algebra; X^(N/2) acts as i on every slot; ModRaise adds a multiple of q_0
+below K; EvalMod approximates sin(2 pi K u); the whole bootstrap returns its
+input within a stated error, and CryptoInvSqrt with bootstrapping inside the
+Newton loop reproduces its FP64 model.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_10477_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    p = inputs.PRESETS["bts12"]
+    b = inputs.BTS
+    o = oracle.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
+    o.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    return o
+
+
+def decoding_matrix(N):
+    n = N // 2
+    g5 = np.array([pow(5, j, 2 * N) for j in range(n)])
+    return np.exp(1j * np.pi * (np.outer(g5, np.arange(n)) % (2 * N)) / N)
+
+
+def bitrev_perm(n):
+    bits = int(np.log2(n))
+    return np.array([int(format(i, f"0{bits}b")[::-1], 2) for i in range(n)])
+
+
+def apply(D, x):
+    return sum(d * np.roll(x, -off) for off, d in D.items())
+
+
+def test_grouped_factors_are_the_decoding_matrix(ctx):
+    n = ctx.N // 2
+    V = decoding_matrix(ctx.N)
+    perm = bitrev_perm(n)
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=n) + 1j * rng.normal(size=n)
+    w = np.linalg.solve(V, v)
+    x = v.copy()
+    for g in range(3):
+        x = apply(ctx.fft_group(3, True, g), x)
+    assert np.max(np.abs(x - w[perm])) < 1e-12  # CoeffToSlot = bit-reversed V^-1
+    y = w[perm].copy()
+    for g in range(3):
+        y = apply(ctx.fft_group(3, False, g), y)
+    assert np.max(np.abs(y - v)) < 1e-11       # SlotToCoeff = V on bit-reversed input
+    # a group of r stages has at most 2^(r+1) - 1 diagonals
+    assert all(len(ctx.fft_group(3, inv, g)) <= 31 for inv in (True, False) for g in range(3))
+
+
+def test_monomial_half_n_is_i_in_every_slot(ctx):
+    z = inputs.uniform_values(2, ctx.N // 2, -1, 1) + 1j * inputs.uniform_values(3, ctx.N // 2, -1, 1)
+    ct = ctx.encrypt(z, 3, 4)
+    assert np.max(np.abs(ctx.decrypt(ctx.mul_monomial(ct, ctx.N // 2)) - 1j * z)) < 1e-8
+    assert np.max(np.abs(ctx.decrypt(ctx.mul_monomial(ct, 3 * ctx.N // 2)) + 1j * z)) < 1e-8
+
+
+def test_mod_raise_adds_small_multiple_of_q0(ctx):
+    q0 = int(ctx.primes()[0])
+    z = inputs.uniform_values(5, ctx.N // 2, -1, 1)
+    ct0 = ctx.mul_const(ctx.encrypt(z, 1, 6), 1.0, q0 / 4096)
+    m = ctx.decrypt_coeffs(ct0)
+    t = ctx.decrypt_coeffs(ctx.mod_raise(ct0))
+    I = np.round((t - m) / q0)
+    assert np.max(np.abs(t - m - q0 * I)) <= 4096  # FP64 resolution of values ~ K q_0 ~ 2^65
+    assert 0 < np.max(np.abs(I)) < inputs.BTS["K"]
+
+
+def test_eval_mod_approximates_scaled_sine(ctx):
+    K = inputs.BTS["K"]
+    lvl = ctx.n_q - 1 - 3
+    u = inputs.uniform_values(7, ctx.N // 2, -1, 1)
+    ct = ctx.mul_const(ctx.encrypt(u, lvl + 1, 8), 1.0, float(ctx.primes()[lvl]))
+    out = ctx.decrypt(ctx.eval_mod(ct)).real
+    assert np.max(np.abs(out - np.sin(2 * np.pi * K * u))) < 1e-8
+
+
+def test_bootstrap_returns_its_input(ctx):
+    q0 = float(ctx.primes()[0])
+    z = inputs.uniform_values(9, ctx.N // 2, -1, 1) + 1j * inputs.uniform_values(10, ctx.N // 2, -1, 1)
+    ct0 = ctx.mul_const(ctx.encrypt(z, 1, 11), 1.0, q0 / 4096)
+    b = ctx.bootstrap(ct0)
+    assert b.level == ctx.n_q - 1 - 16
+    assert np.max(np.abs(ctx.decrypt(b) - z)) < 1e-4
+
+
+def test_invsqrt_with_lazy_bootstrapping_reproduces_fp64_model(ctx):
+    a = inputs.log_uniform_values(16, ctx.N // 2, 1e-4, 1.0)
+    L_after = ctx.n_q - 1 - 16
+    y = ctx.decrypt(ctx.invsqrt(ctx.encrypt(a, L_after, 17), 1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63)).real
+    plain = oracle.plain_invsqrt(a, 1e-4, 1.0, 1.0, 15, 5)
+    assert np.max(np.abs(y - plain) / plain) < 1e-4
