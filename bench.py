@@ -1,10 +1,14 @@
 """Benchmark: CryptoInvSqrt ciphertexts per second at N = 2^16 on one GB300.
 
 One step = CryptoInvSqrt (Alg. 1: Chebyshev initial value + Newton) on a batch
-of resident ciphertexts (N = 2^16, 32768 slots, 24 x 50-bit Q primes + 2 x
+of 8 resident ciphertexts (N = 2^16, 32768 slots, 24 x 50-bit Q primes + 2 x
 60-bit P primes, two primes per key-switching digit, scale 2^50, inputs
 uniform in [1e-3, 1]) with a (degree, Newton steps) pair whose decrypted MRE
-is at most 1e-7.  Prints one JSON line.
+is at most 1e-7.  `value` is the batched path (the 8 ciphertexts packed into
+one batch, one launch sequence); `plain` is the same work one ciphertext per
+call sequence.  `bootstrapped` times CryptoInvSqrt with bootstrapping inside
+the Newton loop (N = 2^16, log2(QP) = 1555, inputs log-uniform in [1e-4, 1]).
+Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -46,6 +50,7 @@ def parse():
     ap.add_argument("--degree", type=int, default=31)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bts", action="store_true", help="skip the bootstrapped workload")
     return ap.parse_args()
 
 
@@ -178,7 +183,12 @@ def run_ours(args):
     vals = [inputs.uniform_values(1000 * rank + i, ctx.N // 2, LO, HI) for i in range(batch)]
     cts = [ctx.encrypt(v, L, 7 + i) for i, v in enumerate(vals)]
 
-    def step():
+    packed = ctx.pack(cts)
+
+    def step():  # batched: the whole batch through one launch sequence
+        return ctx.invsqrt(packed, LO, HI, B, args.degree, args.iters)
+
+    def step_plain():  # one ciphertext per call sequence
         return [ctx.invsqrt(c, LO, HI, B, args.degree, args.iters) for c in cts]
 
     def barrier():
@@ -186,14 +196,14 @@ def run_ours(args):
             torch.distributed.barrier()
 
     # accuracy of this configuration on the batch (untimed)
-    outs = step()
+    out_b = step()
     mres = []
-    for v, o in zip(vals, outs):
-        y = ctx.decrypt(o).real
+    for k, v in enumerate(vals):
+        y = ctx.decrypt(ctx.unpack(out_b, k)).real
         ref = 1 / np.sqrt(v)
         mres.append(float(np.mean(np.abs(y - ref) / ref)))
-    out_level = outs[0].level
-    del outs
+    out_level = out_b.level
+    del out_b
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -218,6 +228,17 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     value = ws * batch * args.steps / (elapsed_ms / 1e3)
+
+    # ---- the plain path, same work and timing
+    step_plain()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(max(1, min(args.steps, 3))):
+        step_plain()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_value = batch * max(1, min(args.steps, 3)) / (p0.elapsed_time(p1) / 1e3)
 
     # ---- per-ciphertext latency (plain path: one ciphertext per call sequence)
     lat = []
@@ -253,9 +274,9 @@ def run_ours(args):
     d2h = sum(h.numel() * 8 for h in host_out)
 
     def e2e_step():
-        for hi, ho in zip(host_in, host_out):
-            ci = ctx.ct_import(hi, L, ctx.scale)
-            co = ctx.invsqrt(ci, LO, HI, B, args.degree, args.iters)
+        ins = [ctx.ct_import(hi, L, ctx.scale) for hi in host_in]
+        outs = ctx.invsqrt_batch(ins, [(LO, HI, B, args.degree, args.iters, 0, 0)] * batch)
+        for co, ho in zip(outs, host_out):
             co.export_to(ho)
 
     e2e_step()
@@ -282,6 +303,9 @@ def run_ours(args):
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "one full oracle CryptoInvSqrt of one ciphertext on the same workload", "mre": omre}
 
+    bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
+                                                         stream=stream, rank=rank, batch=batch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -302,10 +326,59 @@ def run_ours(args):
             },
             "profile_share": {k: round(v[1] / total_prof_ms, 4) for k, v in prof.items()} if total_prof_ms else {},
             "cpu_baseline": cpu,
+            "plain": {"value": plain_value, "unit": UNIT, "ms_per_ct": 1e3 / plain_value,
+                      "speedup_batched_vs_plain": value / plain_value},
+            "bootstrapped": bts,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63, iters=4, steps=2):
+    """CryptoInvSqrt with lazy bootstrapping in the Newton loop: N = 2^16, bts16 chain
+    (log2 QP = 1555, h = 192), inputs log-uniform in [1e-4, 1] at l_max, batch of ciphertexts."""
+    p = inputs.PRESETS["bts16"]
+    b = inputs.BTS
+    t0 = time.perf_counter()
+    ctx = ctx_cls(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 11 + rank,
+                  stream=stream.cuda_stream)
+    lmax = ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    lo = 1e-4
+    vals = [inputs.log_uniform_values(2000 + i, ctx.N // 2, lo, 1.0) for i in range(batch)]
+    packed = ctx.pack([ctx.encrypt(v, lmax, 3000 + i) for i, v in enumerate(vals)])
+    mask = 1 << 63
+    out = ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, 0, mask)  # warm-up: keys and diagonals are built here
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    mres = []
+    for k, v in enumerate(vals):
+        y = ctx.decrypt(ctx.unpack(out, k)).real
+        mres.append(float(np.mean(np.abs(y - 1 / np.sqrt(v)) * np.sqrt(v))))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, 0, mask)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    single = ctx.encrypt(vals[0], lmax, 4000)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.invsqrt(single, lo, 1.0, 1.0, degree, iters, 0, mask)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    bts_ct = ctx.encrypt(vals[0] / 2, 1, 5000)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    ctx.bootstrap_scaled(bts_ct, 1)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    return {"workload": f"CryptoInvSqrt with lazy bootstrapping, N=2^16, log2(QP)=1555, h=192, inputs log-U[{lo},1] "
+                        f"at level {lmax}, degree {degree}, {iters} Newton steps, batch {batch}",
+            "value": batch * 1e3 / ms, "unit": UNIT, "ms_per_batch": ms, "mre": max(mres),
+            "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s}
 
 
 def main():

@@ -144,6 +144,25 @@ hedap_status hedap_drop_level(hedap_ctx* ctx, const hedap_ct* a, int level, heda
 /* CryptoInvSqrt (Alg. 1). */
 hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_invsqrt_cfg* cfg, hedap_ct** out);
 
+/* Batches (the paper has none; many ciphertexts through one launch sequence).
+ * A batch handle holds up to 16 ciphertexts at one level and scale; every
+ * operation above accepts batch handles (both operands with the same batch
+ * size) and applies to each ciphertext, each kernel launch covering the whole
+ * batch and each switching-key word read once per batch.  hedap_decrypt,
+ * hedap_ct_export/import take single ciphertexts.
+ * hedap_batch_pack copies n single or batch handles (same level and scale,
+ * n <= 16 ciphertexts in total) into one batch; hedap_batch_unpack copies
+ * ciphertext `index` out; hedap_ct_batch_size reports the count.
+ * hedap_invsqrt_batch runs CryptoInvSqrt on n single ciphertexts with their
+ * own configurations: inputs with equal level, scale and configuration are
+ * packed (up to 16 per batch, in input order) and run together; out[i]
+ * receives input i's result.  On error every out[i] is NULL. */
+hedap_status hedap_batch_pack(hedap_ctx* ctx, const hedap_ct* const* cts, size_t n, hedap_ct** out);
+hedap_status hedap_batch_unpack(hedap_ctx* ctx, const hedap_ct* batch, size_t index, hedap_ct** out);
+hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n);
+hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
+                                 hedap_ct** out);
+
 /* Negacyclic NTT (inverse=0) or inverse NTT with N^-1 (inverse=1) of n_limbs
  * consecutive length-N limbs in place; limb i uses prime index first_prime+i
  * (global index over Q then P). */

@@ -135,8 +135,8 @@ void BtsStateDeleter::operator()(BtsState* p) const { delete p; }
 // ModRaise: from limb 0 in the coefficient domain (both parts, stride N) to every
 // limb 0..L of out: the centred representative of x mod q_0, reduced mod q_i.
 __global__ void k_mod_raise_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ x, u64* __restrict__ out,
-                                   size_t os, int limbs, int log_n) {
-  const size_t N = (size_t)1 << log_n, per = (size_t)limbs << log_n, total = 2 * per;
+                                   size_t os, int n_parts, int limbs, int log_n) {
+  const size_t N = (size_t)1 << log_n, per = (size_t)limbs << log_n, total = n_parts * per;
   const u64 q0 = pr[0].q, h = q0 >> 1;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / per);
@@ -153,8 +153,8 @@ __global__ void k_mod_raise_kernel(const PrimeDev* __restrict__ pr, const u64* _
 // the evaluation at psi^(2 bitrev(j) + 1) picks up iota^(2 bitrev(j)+1) = iota (-1)^bitrev(j),
 // and bitrev(j) is odd exactly when j >= N/2.
 __global__ void k_monomial_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ in, size_t is,
-                                  u64* __restrict__ out, size_t os, int limbs, int log_n, LimbConsts F) {
-  const size_t N = (size_t)1 << log_n, per = (size_t)limbs << log_n, total = 2 * per;
+                                  u64* __restrict__ out, size_t os, int n_parts, int limbs, int log_n, LimbConsts F) {
+  const size_t N = (size_t)1 << log_n, per = (size_t)limbs << log_n, total = n_parts * per;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / per);
     const size_t r = e - p * per;
@@ -184,8 +184,8 @@ struct PtMacArgs {
   int count;
 };
 __global__ void k_pt_mac_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s, PtMacArgs A,
-                                u64* __restrict__ out, size_t os, int limbs, int log_n) {
-  const size_t per = (size_t)limbs << log_n, total = 2 * per;
+                                u64* __restrict__ out, size_t os, int n_parts, int limbs, int log_n) {
+  const size_t per = (size_t)limbs << log_n, total = n_parts * per;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / per);
     const size_t r = e - p * per;
@@ -200,22 +200,22 @@ __global__ void k_pt_mac_kernel(const PrimeDev* __restrict__ pr, const u64* __re
 std::unique_ptr<Ct> mod_raise(Ctx& C, const Ct& a) {
   if (a.level != 0) throw Error(HEDAP_ERR_LEVEL, "ModRaise needs a level-0 ciphertext");
   const size_t N = C.N;
-  const int L = C.L();
-  DevBuf x(2 * N, C.stream);
-  for (int p = 0; p < 2; ++p)
-    HEDAP_CUDA(cudaMemcpyAsync(x.p + p * N, a.part(p), N * 8, cudaMemcpyDeviceToDevice, C.stream));
-  ntt_inverse(C.tab, LimbSet{x.p, N, 2, 0, 1, INT_MAX, 0, 0}, C.stream);
-  auto o = ct_alloc(C, L);
+  const int L = C.L(), P = a.parts();
+  DevBuf x((size_t)P * N, C.stream);
+  HEDAP_CUDA(cudaMemcpy2DAsync(x.p, N * 8, a.part(0), a.part_stride() * 8, N * 8, P, cudaMemcpyDeviceToDevice,
+                               C.stream));
+  ntt_inverse(C.tab, LimbSet{x.p, N, P, 0, 1, INT_MAX, 0, 0}, C.stream);
+  auto o = ct_alloc(C, L, a.batch);
   o->scale = a.scale;
   {
-    ProfScope prof_(PROF_ELEMENTWISE, C.stream, (2.0 + 2.0 * (L + 1)) * N * 8);
+    ProfScope prof_(PROF_ELEMENTWISE, C.stream, (1.0 + (L + 1.0)) * P * N * 8);
     prof_count_launches(1);
-    k_mod_raise_kernel<<<grid_for(2 * (size_t)(L + 1) * N, 256), 256, 0, C.stream>>>(C.tab.pr, x.p, o->part(0),
-                                                                                      o->part_stride(), L + 1,
+    k_mod_raise_kernel<<<grid_for((size_t)P * (L + 1) * N, 256), 256, 0, C.stream>>>(C.tab.pr, x.p, o->part(0),
+                                                                                      o->part_stride(), P, L + 1,
                                                                                       C.log_n);
     HEDAP_LAUNCH_CHECK();
   }
-  ntt_forward(C.tab, LimbSet{o->part(0), o->part_stride(), 2, 0, L + 1, INT_MAX, 0, 0}, C.stream);
+  ntt_forward(C.tab, LimbSet{o->part(0), o->part_stride(), P, 0, L + 1, INT_MAX, 0, 0}, C.stream);
   return o;
 }
 
@@ -229,12 +229,12 @@ std::unique_ptr<Ct> mul_monomial(Ctx& C, const Ct& a, u64 e) {
     F.w[i] = e == n2 ? iota : q - iota;
     F.wsh[i] = h_shoup(F.w[i], q);
   }
-  auto o = ct_alloc(C, a.level);
+  auto o = ct_alloc(C, a.level, a.batch);
   o->scale = a.scale;
-  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 4.0 * (a.level + 1) * C.N * 8);
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 2.0 * a.parts() * (a.level + 1) * C.N * 8);
   prof_count_launches(1);
-  k_monomial_kernel<<<grid_for(2 * (size_t)(a.level + 1) * C.N, 256), 256, 0, C.stream>>>(
-      C.tab.pr, a.part(0), a.part_stride(), o->part(0), o->part_stride(), a.level + 1, C.log_n, F);
+  k_monomial_kernel<<<grid_for((size_t)a.parts() * (a.level + 1) * C.N, 256), 256, 0, C.stream>>>(
+      C.tab.pr, a.part(0), a.part_stride(), o->part(0), o->part_stride(), a.parts(), a.level + 1, C.log_n, F);
   HEDAP_LAUNCH_CHECK();
   return o;
 }
@@ -302,13 +302,13 @@ std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int 
       ++A.count;
     }
     if (!A.count) continue;
-    auto inner = ct_alloc(C, l);
+    auto inner = ct_alloc(C, l, v.batch);
     inner->scale = v.scale * sp;
     {
-      ProfScope prof_(PROF_ELEMENTWISE, C.stream, (3.0 * A.count + 2.0) * (l + 1) * C.N * 8);
+      ProfScope prof_(PROF_ELEMENTWISE, C.stream, (1.5 * A.count + 1.0) * v.parts() * (l + 1) * C.N * 8);
       prof_count_launches(1);
-      k_pt_mac_kernel<<<grid_for(2 * (size_t)(l + 1) * C.N, 256), 256, 0, C.stream>>>(
-          C.tab.pr, C.d_r64.p, A, inner->part(0), inner->part_stride(), l + 1, C.log_n);
+      k_pt_mac_kernel<<<grid_for((size_t)v.parts() * (l + 1) * C.N, 256), 256, 0, C.stream>>>(
+          C.tab.pr, C.d_r64.p, A, inner->part(0), inner->part_stride(), v.parts(), l + 1, C.log_n);
       HEDAP_LAUNCH_CHECK();
     }
     const long Gs = G.h0 * (G.kmin + g * G.n1);

@@ -269,7 +269,7 @@ API hedap_status hedap_modup(hedap_ctx* ctx, const uint64_t* in, int level, uint
     const size_t N = C.N, ext = (size_t)level + 1 + C.n_p, dn = (size_t)C.dnum(level);
     hedap::DevBuf x((level + 1) * N, C.stream), y(dn * ext * N, C.stream);
     HEDAP_CUDA(cudaMemcpyAsync(x.p, in, (level + 1) * N * 8, cudaMemcpyHostToDevice, C.stream));
-    hedap::k_modup(C, x.p, y.p, level, hedap::level_consts(C, level).modup.p);
+    hedap::k_modup(C, x.p, y.p, 1, level, hedap::level_consts(C, level).modup.p);
     HEDAP_CUDA(cudaMemcpyAsync(out, y.p, dn * ext * N * 8, cudaMemcpyDeviceToHost, C.stream));
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   });
@@ -284,9 +284,9 @@ API hedap_status hedap_moddown(hedap_ctx* ctx, const uint64_t* in, int level, ui
     HEDAP_CUDA(cudaMemcpyAsync(acc.p, in, 2 * ext * N * 8, cudaMemcpyHostToDevice, C.stream));
     hedap::LimbSet qs{acc.p, ext * N, 2, 0, (int)nl, INT_MAX, 0, 0};
     hedap::ntt_forward(C.tab, qs, C.stream);  // Q limbs enter ModDown in the NTT domain
-    hedap::k_moddown_spread(C, acc.p, v.p, level);
+    hedap::k_moddown_spread(C, acc.p, v.p, 2, level);
     hedap::ntt_forward(C.tab, hedap::LimbSet{v.p, nl * N, 2, 0, (int)nl, INT_MAX, 0, 0}, C.stream);
-    hedap::k_moddown_finish(C, acc.p, v.p, o.p, o.p + nl * N, level, false, false);
+    hedap::k_moddown_finish(C, acc.p, v.p, o.p, nl * N, 2, level, false, false);
     hedap::ntt_inverse(C.tab, hedap::LimbSet{o.p, nl * N, 2, 0, (int)nl, INT_MAX, 0, 0}, C.stream);
     HEDAP_CUDA(cudaMemcpyAsync(out, o.p, 2 * nl * N * 8, cudaMemcpyDeviceToHost, C.stream));
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));
@@ -300,7 +300,7 @@ API hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, 
     const size_t N = C.N, nl = (size_t)level + 1;
     hedap::DevBuf x(nl * N, C.stream), o(2 * nl * N, C.stream);
     HEDAP_CUDA(cudaMemcpyAsync(x.p, d, nl * N * 8, cudaMemcpyHostToDevice, C.stream));
-    hedap::key_switch(C, x.p, level, galois, o.p, o.p + nl * N, false, false);
+    hedap::key_switch(C, x.p, nl * N, 1, level, galois, o.p, nl * N, false, false);
     HEDAP_CUDA(cudaMemcpyAsync(out, o.p, 2 * nl * N * 8, cudaMemcpyDeviceToHost, C.stream));
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   });
@@ -361,5 +361,66 @@ API hedap_status hedap_bts_diagonal(hedap_ctx* ctx, int inverse, int group, int6
     std::vector<std::complex<double>> d;
     need(hedap::bts_diagonal(*ctx->c, inverse != 0, group, (long)offset, d), "no such diagonal");
     for (size_t s = 0; s < d.size(); ++s) { re[s] = d[s].real(); im[s] = d[s].imag(); }
+  });
+}
+
+// ---------------------------------------------------------------- batches
+API hedap_status hedap_batch_pack(hedap_ctx* ctx, const hedap_ct* const* cts, size_t n, hedap_ct** out) {
+  return guarded([&] {
+    need(ctx && cts && out && n >= 1 && n <= 16, "bad argument");
+    *out = nullptr;
+    std::vector<const hedap::Ct*> v;
+    for (size_t i = 0; i < n; ++i) {
+      need(cts[i] != nullptr, "null ciphertext");
+      v.push_back(cts[i]->c.get());
+    }
+    *out = wrap(hedap::batch_pack(*ctx->c, v));
+  });
+}
+API hedap_status hedap_batch_unpack(hedap_ctx* ctx, const hedap_ct* batch, size_t index, hedap_ct** out) {
+  CT_OP((need(batch != nullptr, "null ciphertext"), hedap::batch_unpack(*ctx->c, *batch->c, (int)index)));
+}
+API hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n) {
+  return guarded([&] {
+    need(ct && n, "null argument");
+    *n = ct->c->batch;
+  });
+}
+API hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs,
+                                     size_t n, hedap_ct** out) {
+  return guarded([&] {
+    need(ctx && in && cfgs && out, "null argument");
+    for (size_t i = 0; i < n; ++i) out[i] = nullptr;
+    hedap::Ctx& C = *ctx->c;
+    std::vector<bool> done(n, false);
+    try {
+      for (size_t i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        need(in[i] != nullptr && in[i]->c->batch == 1, "inputs must be single ciphertexts");
+        // group: same level, scale and configuration, up to 16 ciphertexts, in input order
+        std::vector<size_t> g{i};
+        for (size_t j = i + 1; j < n && g.size() < 16; ++j) {
+          if (done[j] || !in[j]) continue;
+          const hedap::Ct &a = *in[i]->c, &b = *in[j]->c;
+          if (b.batch == 1 && a.level == b.level && a.scale == b.scale &&
+              memcmp(&cfgs[i], &cfgs[j], sizeof(hedap_invsqrt_cfg)) == 0)
+            g.push_back(j);
+        }
+        std::vector<const hedap::Ct*> v;
+        for (size_t j : g) v.push_back(in[j]->c.get());
+        auto packed = hedap::batch_pack(C, v);
+        auto res = hedap::invsqrt(C, *packed, cfgs[i]);
+        for (size_t k = 0; k < g.size(); ++k) {
+          out[g[k]] = wrap(hedap::batch_unpack(C, *res, (int)k));
+          done[g[k]] = true;
+        }
+      }
+    } catch (...) {
+      for (size_t i = 0; i < n; ++i) {
+        delete out[i];
+        out[i] = nullptr;
+      }
+      throw;
+    }
   });
 }

@@ -296,6 +296,7 @@ std::unique_ptr<Ct> encrypt(Ctx& C, const std::vector<double>& re, const std::ve
 // A decrypted coefficient is far below q_0 q_1 ... q_{k-1} / 2 for k = min(l+1, 8).
 void decrypt(Ctx& C, const Ct& ct, std::vector<double>& re, std::vector<double>& im) {
   const size_t N = C.N;
+  if (ct.batch != 1) throw Error(HEDAP_ERR_ARG, "decrypt takes one ciphertext (unpack the batch first)");
   const int l = ct.level, k = std::min(l + 1, 8);
   DevBuf m((size_t)(l + 1) * N, C.stream);
   k_fma(C, ct.part(0), ct.part(1), C.d_sk.p, m.p, l + 1, 1);  // c0 + c1 s

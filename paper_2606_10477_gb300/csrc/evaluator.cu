@@ -1,7 +1,9 @@
 // Host orchestration of the CKKS operations of Sec. 2.1 over the device
 // kernels: Add/Sub, Mul_C (tensor product + hybrid key switching), rescale,
 // Mul_P by constants, Galois automorphisms (rotation, conjugation).
-// Ciphertexts stay in the NTT domain; every temporary is stream-ordered on the
+// Every operation works on a batch of ciphertexts at one level and scale (a
+// single ciphertext is a batch of one); each launch covers the whole batch.
+// Ciphertexts stay in the NTT domain; temporaries are stream-ordered on the
 // context's stream.
 #include <cmath>
 
@@ -14,24 +16,26 @@ static LimbSet qset(u64* base, size_t part_stride, int n_parts, int first, int c
   return LimbSet{base, part_stride, n_parts, first, count, INT_MAX, prime_offset, 0};
 }
 
-std::unique_ptr<Ct> ct_alloc(Ctx& C, int level) {
+std::unique_ptr<Ct> ct_alloc(Ctx& C, int level, int batch) {
   if (level < 0 || level > C.L()) throw Error(HEDAP_ERR_LEVEL, "level out of range");
+  if (batch < 1 || batch > kMaxBatch) throw Error(HEDAP_ERR_ARG, "batch must lie in [1, 16]");
   auto c = std::make_unique<Ct>();
   c->N = C.N;
   c->cap = level + 1;
   c->level = level;
+  c->batch = batch;
   c->scale = C.scale;
-  c->buf = DevBuf(2 * (size_t)(level + 1) * C.N, C.stream);
+  c->buf = DevBuf(2 * (size_t)batch * (level + 1) * C.N, C.stream);
   return c;
 }
 
+// copy limbs 0..level of every part of a into a new (packed) batch
 std::unique_ptr<Ct> ct_copy(Ctx& C, const Ct& a, int level) {
   if (level > a.level) throw Error(HEDAP_ERR_LEVEL, "cannot raise the level by copying");
-  auto c = ct_alloc(C, level);
+  auto c = ct_alloc(C, level, a.batch);
   c->scale = a.scale;
-  for (int p = 0; p < 2; ++p)
-    HEDAP_CUDA(cudaMemcpyAsync(c->part(p), a.part(p), (size_t)(level + 1) * C.N * 8, cudaMemcpyDeviceToDevice,
-                               C.stream));
+  HEDAP_CUDA(cudaMemcpy2DAsync(c->part(0), c->part_stride() * 8, a.part(0), a.part_stride() * 8,
+                               (size_t)(level + 1) * C.N * 8, a.parts(), cudaMemcpyDeviceToDevice, C.stream));
   return c;
 }
 std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level) {
@@ -39,16 +43,48 @@ std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level) {
   return ct_copy(C, a, level);
 }
 
+std::unique_ptr<Ct> batch_pack(Ctx& C, const std::vector<const Ct*>& cts) {
+  if (cts.empty()) throw Error(HEDAP_ERR_ARG, "empty batch");
+  const Ct& f = *cts[0];
+  int total = 0;
+  for (const Ct* c : cts) {
+    if (c->level != f.level || c->scale != f.scale) throw Error(HEDAP_ERR_ARG, "batched ciphertexts differ in level or scale");
+    total += c->batch;
+  }
+  auto b = ct_alloc(C, f.level, total);
+  b->scale = f.scale;
+  int at = 0;
+  for (const Ct* c : cts) {
+    HEDAP_CUDA(cudaMemcpy2DAsync(b->part(2 * at), b->part_stride() * 8, c->part(0), c->part_stride() * 8,
+                                 (size_t)(f.level + 1) * C.N * 8, c->parts(), cudaMemcpyDeviceToDevice, C.stream));
+    at += c->batch;
+  }
+  return b;
+}
+std::unique_ptr<Ct> batch_unpack(Ctx& C, const Ct& b, int k) {
+  if (k < 0 || k >= b.batch) throw Error(HEDAP_ERR_ARG, "batch index out of range");
+  auto c = ct_alloc(C, b.level, 1);
+  c->scale = b.scale;
+  HEDAP_CUDA(cudaMemcpy2DAsync(c->part(0), c->part_stride() * 8, b.part(2 * k), b.part_stride() * 8,
+                               (size_t)(b.level + 1) * C.N * 8, 2, cudaMemcpyDeviceToDevice, C.stream));
+  return c;
+}
+
 static void check_scales(double a, double b) {
   if (std::fabs(a / b - 1.0) > 1e-12) throw Error(HEDAP_ERR_SCALE, "operand scales differ");
+}
+static void check_batches(const Ct& a, const Ct& b) {
+  if (a.batch != b.batch) throw Error(HEDAP_ERR_ARG, "operands have different batch sizes");
 }
 
 std::unique_ptr<Ct> ev_add(Ctx& C, const Ct& a, const Ct& b, bool sub) {
   const int l = std::min(a.level, b.level);
   check_scales(a.scale, b.scale);
-  auto o = ct_alloc(C, l);
+  check_batches(a, b);
+  auto o = ct_alloc(C, l, a.batch);
   o->scale = a.scale;
-  k_add_sub(C, a.part(0), a.part_stride(), b.part(0), b.part_stride(), o->part(0), o->part_stride(), l + 1, sub);
+  k_add_sub(C, a.part(0), a.part_stride(), b.part(0), b.part_stride(), o->part(0), o->part_stride(), a.parts(),
+            l + 1, sub);
   return o;
 }
 
@@ -96,40 +132,46 @@ const LevelConsts& level_consts(Ctx& C, int l) {
 }
 
 // ------------------------------------------------------------------ key switching
-// Hybrid key switching (Han-Ki 2020) of d (NTT domain, limbs 0..l) with the key
-// for `galois`: iNTT, ModUp of every digit to Q_l u P, NTT, inner product with
-// the key digits, iNTT of the P limbs, ModDown (rounded division by P), NTT.
-void key_switch(Ctx& C, const u64* d_ntt, int l, u64 galois, u64* out0, u64* out1, bool acc0, bool acc1) {
+// Hybrid key switching (Han-Ki 2020) of a batch of polynomials with the key for
+// `galois`: iNTT, ModUp of every digit to Q_l u P, NTT, inner product with the
+// key digits (each key word read once for the batch), iNTT of the P limbs,
+// ModDown (rounded division by P), NTT.
+void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
+                bool acc0, bool acc1) {
   auto it = C.keys.find(galois);
   if (it == C.keys.end()) {
     gen_galois_key(C, galois);
     it = C.keys.find(galois);
   }
-  const size_t N = C.N;
+  const size_t N = C.N, nl = (size_t)l + 1;
   const int K = C.n_p, ext = l + 1 + K, dn = C.dnum(l);
   const LevelConsts& LC = level_consts(C, l);
-  DevBuf dc((size_t)(l + 1) * N, C.stream);
-  HEDAP_CUDA(cudaMemcpyAsync(dc.p, d_ntt, (size_t)(l + 1) * N * 8, cudaMemcpyDeviceToDevice, C.stream));
-  ntt_inverse(C.tab, qset(dc.p, 0, 1, 0, l + 1), C.stream);
-  DevBuf y((size_t)dn * ext * N, C.stream);
-  k_modup(C, dc.p, y.p, l, LC.modup.p);
-  ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, dn, 0, ext, l + 1, 0, C.n_q}, C.stream);
-  DevBuf acc(2 * (size_t)ext * N, C.stream);
-  k_ksk_inner(C, y.p, it->second.p, acc.p, l);
-  ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2, l + 1, K, l + 1, 0, C.n_q}, C.stream);
-  DevBuf v(2 * (size_t)(l + 1) * N, C.stream);
-  k_moddown_spread(C, acc.p, v.p, l);
-  ntt_forward(C.tab, qset(v.p, (size_t)(l + 1) * N, 2, 0, l + 1), C.stream);
-  k_moddown_finish(C, acc.p, v.p, out0, out1, l, acc0, acc1);
+  DevBuf dc((size_t)batch * nl * N, C.stream);
+  HEDAP_CUDA(cudaMemcpy2DAsync(dc.p, nl * N * 8, d, d_stride * 8, nl * N * 8, batch, cudaMemcpyDeviceToDevice,
+                               C.stream));
+  ntt_inverse(C.tab, qset(dc.p, nl * N, batch, 0, l + 1), C.stream);
+  DevBuf y((size_t)batch * dn * ext * N, C.stream);
+  k_modup(C, dc.p, y.p, batch, l, LC.modup.p);
+  ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream);
+  DevBuf acc((size_t)batch * 2 * ext * N, C.stream);
+  k_ksk_inner(C, y.p, it->second.p, acc.p, batch, l);
+  ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream);
+  DevBuf v((size_t)batch * 2 * nl * N, C.stream);
+  k_moddown_spread(C, acc.p, v.p, 2 * batch, l);
+  ntt_forward(C.tab, qset(v.p, nl * N, 2 * batch, 0, l + 1), C.stream);
+  k_moddown_finish(C, acc.p, v.p, out, out_stride, 2 * batch, l, acc0, acc1);
 }
 
 std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b) {
   const int l = std::min(a.level, b.level);
-  auto o = ct_alloc(C, l);
+  check_batches(a, b);
+  auto o = ct_alloc(C, l, a.batch);
   o->scale = a.scale * b.scale;
-  DevBuf d2((size_t)(l + 1) * C.N, C.stream);
-  k_tensor(C, a.part(0), a.part(1), b.part(0), b.part(1), o->part(0), o->part(1), d2.p, l + 1);
-  key_switch(C, d2.p, l, 0, o->part(0), o->part(1), true, true);
+  const size_t per = (size_t)(l + 1) * C.N;
+  DevBuf d2(a.batch * per, C.stream);
+  k_tensor(C, a.part(0), a.part_stride(), b.part(0), b.part_stride(), o->part(0), o->part_stride(), d2.p, a.batch,
+           l + 1);
+  key_switch(C, d2.p, per, a.batch, l, 0, o->part(0), o->part_stride(), true, true);
   return o;
 }
 
@@ -138,17 +180,18 @@ std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a) {
   const int l = a.level;
   if (l < 1) throw Error(HEDAP_ERR_LEVEL, "rescale needs level >= 1");
   const size_t N = C.N;
+  const int P = a.parts();
   const LevelConsts& LC = level_consts(C, l);
-  auto o = ct_alloc(C, l - 1);
+  auto o = ct_alloc(C, l - 1, a.batch);
   o->scale = a.scale / (double)C.primes[l];
-  DevBuf last(2 * N, C.stream);
-  for (int p = 0; p < 2; ++p)
-    HEDAP_CUDA(cudaMemcpyAsync(last.p + p * N, a.part(p) + (size_t)l * N, N * 8, cudaMemcpyDeviceToDevice, C.stream));
-  ntt_inverse(C.tab, qset(last.p, N, 2, 0, 1, l), C.stream);
-  DevBuf tmp(2 * (size_t)l * N, C.stream);
-  k_rescale_spread(C, last.p, N, tmp.p, (size_t)l * N, l, LC.rescale);
-  ntt_forward(C.tab, qset(tmp.p, (size_t)l * N, 2, 0, l), C.stream);
-  k_rescale_finish(C, a.part(0), a.part_stride(), tmp.p, (size_t)l * N, o->part(0), o->part_stride(), l,
+  DevBuf last(P * N, C.stream);
+  HEDAP_CUDA(cudaMemcpy2DAsync(last.p, N * 8, a.part(0) + (size_t)l * N, a.part_stride() * 8, N * 8, P,
+                               cudaMemcpyDeviceToDevice, C.stream));
+  ntt_inverse(C.tab, qset(last.p, N, P, 0, 1, l), C.stream);
+  DevBuf tmp((size_t)P * l * N, C.stream);
+  k_rescale_spread(C, last.p, N, tmp.p, (size_t)l * N, P, l, LC.rescale);
+  ntt_forward(C.tab, qset(tmp.p, (size_t)l * N, P, 0, l), C.stream);
+  k_rescale_finish(C, a.part(0), a.part_stride(), tmp.p, (size_t)l * N, o->part(0), o->part_stride(), P, l,
                    LC.rescale);
   return o;
 }
@@ -163,10 +206,10 @@ u64 galois_for_rotation(const Ctx& C, i64 steps) {
 
 std::unique_ptr<Ct> ev_galois(Ctx& C, const Ct& a, u64 g) {
   const int l = a.level;
-  auto o = ct_alloc(C, l);
+  auto o = ct_alloc(C, l, a.batch);
   o->scale = a.scale;
-  k_automorph(C, a.part(0), a.part_stride(), o->part(0), o->part_stride(), 2, l + 1, g);
-  key_switch(C, o->part(1), l, g, o->part(0), o->part(1), true, false);
+  k_automorph(C, a.part(0), a.part_stride(), o->part(0), o->part_stride(), a.parts(), l + 1, g);
+  key_switch(C, o->part(1), 2 * o->part_stride(), a.batch, l, g, o->part(0), o->part_stride(), true, false);
   return o;
 }
 
@@ -182,9 +225,9 @@ std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target) {
     K.w[i] = h_double_to_mod(v, C.primes[i]);
     K.wsh[i] = h_shoup(K.w[i], C.primes[i]);
   }
-  auto t = ct_alloc(C, l);
+  auto t = ct_alloc(C, l, a.batch);
   t->scale = a.scale * sp;
-  k_mul_limbconst(C, a.part(0), a.part_stride(), t->part(0), t->part_stride(), 2, l + 1, K);
+  k_mul_limbconst(C, a.part(0), a.part_stride(), t->part(0), t->part_stride(), a.parts(), l + 1, K);
   auto o = ev_rescale(C, *t);
   o->scale = target;
   return o;
@@ -195,7 +238,7 @@ std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c) {
   LimbConsts K;
   for (int i = 0; i <= a.level; ++i) K.w[i] = h_double_to_mod(v, C.primes[i]);
   auto o = ct_copy(C, a, a.level);
-  k_add_limbconst(C, o->part(0), a.level + 1, K);
+  k_add_limbconst(C, o->part(0), 2 * o->part_stride(), a.batch, a.level + 1, K);
   return o;
 }
 
@@ -205,9 +248,9 @@ std::unique_ptr<Ct> ev_mul_int(Ctx& C, const Ct& a, i64 m) {
     K.w[i] = h_smod(m, C.primes[i]);
     K.wsh[i] = h_shoup(K.w[i], C.primes[i]);
   }
-  auto o = ct_alloc(C, a.level);
+  auto o = ct_alloc(C, a.level, a.batch);
   o->scale = a.scale;
-  k_mul_limbconst(C, a.part(0), a.part_stride(), o->part(0), o->part_stride(), 2, a.level + 1, K);
+  k_mul_limbconst(C, a.part(0), a.part_stride(), o->part(0), o->part_stride(), a.parts(), a.level + 1, K);
   return o;
 }
 

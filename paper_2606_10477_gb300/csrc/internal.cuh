@@ -113,14 +113,18 @@ void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st);
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st);
 
 // ------------------------------------------------------------------ context and ciphertexts
+// One ciphertext, or a batch of `batch` ciphertexts at one level and scale:
+// [batch][2][cap][N] words, ciphertext k owning parts 2k (c0) and 2k+1 (c1).
 struct Ct {
   DevBuf buf;
   int cap = 0;     // limbs allocated per part
   int level = 0;
+  int batch = 1;
   double scale = 1;
   size_t N = 0;
   u64* part(int p) const { return buf.p + (size_t)p * cap * N; }
   size_t part_stride() const { return (size_t)cap * N; }
+  int parts() const { return 2 * batch; }
 };
 
 constexpr int kMaxLimbs = 64;
@@ -171,7 +175,7 @@ struct Ctx {
 };
 
 // ------------------------------------------------------------------ evaluator (evaluator.cu)
-std::unique_ptr<Ct> ct_alloc(Ctx& C, int level);
+std::unique_ptr<Ct> ct_alloc(Ctx& C, int level, int batch = 1);
 std::unique_ptr<Ct> ct_copy(Ctx& C, const Ct& a, int level);
 std::unique_ptr<Ct> ev_add(Ctx& C, const Ct& a, const Ct& b, bool sub);
 std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b);
@@ -183,7 +187,13 @@ std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target_sc
 std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c);
 std::unique_ptr<Ct> ev_mul_int(Ctx& C, const Ct& a, i64 m);
 u64 galois_for_rotation(const Ctx& C, i64 steps);
-void key_switch(Ctx& C, const u64* d_ntt, int level, u64 galois, u64* out0, u64* out1, bool acc0, bool acc1);
+// key switch of `batch` NTT-domain polynomials (limbs 0..level, ciphertext k's at d + k*d_stride):
+// (ks0, ks1) of ciphertext k go to out + (2k)*out_stride and out + (2k+1)*out_stride,
+// added to what is there when acc0 / acc1
+void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int level, u64 galois, u64* out, size_t out_stride,
+                bool acc0, bool acc1);
+std::unique_ptr<Ct> batch_pack(Ctx& C, const std::vector<const Ct*>& cts);
+std::unique_ptr<Ct> batch_unpack(Ctx& C, const Ct& b, int k);
 void gen_galois_key(Ctx& C, u64 g);
 const LevelConsts& level_consts(Ctx& C, int level);
 

@@ -1,9 +1,10 @@
 // Element-wise RNS kernels, rescale, automorphism and the hybrid key-switching
-// steps (ModUp basis conversion, key inner product, ModDown).
+// steps (ModUp basis conversion, key inner product, ModDown), all batched.
 //
-// All arrays are limb-major: limb i of a part is N consecutive words.  Element
-// kernels walk the flattened (part, limb, coefficient) space two coefficients at
-// a time with 128-bit loads and stores.
+// Arrays are limb-major: limb i of a part is N consecutive words.  A batch of B
+// ciphertexts is 2B parts with one part stride (ciphertext k owns parts 2k, 2k+1).
+// Element kernels walk the flattened (part, limb, coefficient) space two
+// coefficients at a time with 128-bit loads and stores.
 #include "internal.cuh"
 #include "kernels.cuh"
 #include "profiler.cuh"
@@ -13,15 +14,17 @@ namespace hedap {
 __device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
 __device__ __forceinline__ void st2(u64* p, ulonglong2 v) { *reinterpret_cast<ulonglong2*>(p) = v; }
 
+#define GRID_LOOP(var, total) \
+  for (size_t var = blockIdx.x * (size_t)blockDim.x + threadIdx.x; var < (total); var += (size_t)gridDim.x * blockDim.x)
+
 // ---------------------------------------------------------------- add / sub
 __global__ void k_add_sub_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ a, size_t as,
-                                 const u64* __restrict__ b, size_t bs, u64* __restrict__ o, size_t os, int limbs,
-                                 int log_n, int sub) {
-  const size_t per_part = (size_t)limbs << log_n, total = 2 * per_part / 2;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+                                 const u64* __restrict__ b, size_t bs, u64* __restrict__ o, size_t os, int n_parts,
+                                 int limbs, int log_n, int sub) {
+  const size_t per_part = (size_t)limbs << log_n;
+  GRID_LOOP(t, n_parts * per_part / 2) {
     const size_t e = 2 * t;
-    const int p = (int)(e / per_part);
-    const size_t r = e - p * per_part;
+    const size_t p = e / per_part, r = e - p * per_part;
     const u64 q = pr[r >> log_n].q;
     ulonglong2 x = ld2(a + p * as + r), y = ld2(b + p * bs + r), z;
     z.x = sub ? sub_mod(x.x, y.x, q) : add_mod(x.x, y.x, q);
@@ -29,42 +32,47 @@ __global__ void k_add_sub_kernel(const PrimeDev* __restrict__ pr, const u64* __r
     st2(o + p * os + r, z);
   }
 }
-void k_add_sub(const Ctx& C, const u64* a, size_t as, const u64* b, size_t bs, u64* o, size_t os, int limbs,
-               bool sub) {
-  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 6.0 * limbs * C.N * 8);
+void k_add_sub(const Ctx& C, const u64* a, size_t as, const u64* b, size_t bs, u64* o, size_t os, int n_parts,
+               int limbs, bool sub) {
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 3.0 * n_parts * limbs * C.N * 8);
   prof_count_launches(1);
-  const size_t work = (size_t)limbs * C.N;
-  k_add_sub_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, a, as, b, bs, o, os, limbs, C.log_n, sub);
+  const size_t work = (size_t)n_parts * limbs * C.N / 2;
+  k_add_sub_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, a, as, b, bs, o, os, n_parts, limbs,
+                                                              C.log_n, sub);
   HEDAP_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------- tensor product
-__global__ void k_tensor_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ a0,
-                                const u64* __restrict__ a1, const u64* __restrict__ b0, const u64* __restrict__ b1,
-                                u64* __restrict__ d0, u64* __restrict__ d1, u64* __restrict__ d2, int limbs,
-                                int log_n) {
-  const size_t total = ((size_t)limbs << log_n) / 2;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+// ciphertext k: (a_2k, a_2k+1) x (b_2k, b_2k+1) -> d0 = o_2k, d1 = o_2k+1, d2 at d2 + k*limbs*N
+__global__ void k_tensor_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ a, size_t as,
+                                const u64* __restrict__ b, size_t bs, u64* __restrict__ o, size_t os,
+                                u64* __restrict__ d2, int batch, int limbs, int log_n) {
+  const size_t per = (size_t)limbs << log_n;
+  GRID_LOOP(t, batch * per / 2) {
     const size_t e = 2 * t;
-    const PrimeDev P = pr[e >> log_n];
-    ulonglong2 x0 = ld2(a0 + e), x1 = ld2(a1 + e), y0 = ld2(b0 + e), y1 = ld2(b1 + e), r0, r1, r2;
+    const size_t k = e / per, r = e - k * per;
+    const PrimeDev P = pr[r >> log_n];
+    const ulonglong2 x0 = ld2(a + 2 * k * as + r), x1 = ld2(a + (2 * k + 1) * as + r);
+    const ulonglong2 y0 = ld2(b + 2 * k * bs + r), y1 = ld2(b + (2 * k + 1) * bs + r);
+    ulonglong2 r0, r1, r2;
     r0.x = mul_mod(x0.x, y0.x, P);
     r0.y = mul_mod(x0.y, y0.y, P);
     r1.x = add_mod(mul_mod(x0.x, y1.x, P), mul_mod(x1.x, y0.x, P), P.q);
     r1.y = add_mod(mul_mod(x0.y, y1.y, P), mul_mod(x1.y, y0.y, P), P.q);
     r2.x = mul_mod(x1.x, y1.x, P);
     r2.y = mul_mod(x1.y, y1.y, P);
-    st2(d0 + e, r0);
-    st2(d1 + e, r1);
-    st2(d2 + e, r2);
+    st2(o + 2 * k * os + r, r0);
+    st2(o + (2 * k + 1) * os + r, r1);
+    st2(d2 + k * per + r, r2);
   }
 }
-void k_tensor(const Ctx& C, const u64* a0, const u64* a1, const u64* b0, const u64* b1, u64* d0, u64* d1, u64* d2,
+void k_tensor(const Ctx& C, const u64* a, size_t as, const u64* b, size_t bs, u64* o, size_t os, u64* d2, int batch,
               int limbs) {
-  ProfScope prof_(PROF_TENSOR, C.stream, 7.0 * limbs * C.N * 8);
+  ProfScope prof_(PROF_TENSOR, C.stream, 7.0 * batch * limbs * C.N * 8);
   prof_count_launches(1);
-  const size_t work = ((size_t)limbs * C.N) / 2;
-  k_tensor_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, a0, a1, b0, b1, d0, d1, d2, limbs, C.log_n);
+  const size_t work = (size_t)batch * limbs * C.N / 2;
+  k_tensor_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, a, as, b, bs, o, os, d2, batch, limbs,
+                                                             C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
 
@@ -72,11 +80,10 @@ void k_tensor(const Ctx& C, const u64* a0, const u64* a1, const u64* b0, const u
 __global__ void k_mul_limbconst_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ in, size_t is,
                                        u64* __restrict__ out, size_t os, int n_parts, int limbs, int log_n,
                                        LimbConsts K) {
-  const size_t per_part = (size_t)limbs << log_n, total = n_parts * per_part / 2;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+  const size_t per_part = (size_t)limbs << log_n;
+  GRID_LOOP(t, n_parts * per_part / 2) {
     const size_t e = 2 * t;
-    const int p = (int)(e / per_part);
-    const size_t r = e - p * per_part;
+    const size_t p = e / per_part, r = e - p * per_part;
     const int i = (int)(r >> log_n);
     const u64 q = pr[i].q, w = K.w[i], wp = K.wsh[i];
     ulonglong2 x = ld2(in + p * is + r);
@@ -95,63 +102,66 @@ void k_mul_limbconst(const Ctx& C, const u64* in, size_t is, u64* out, size_t os
   HEDAP_LAUNCH_CHECK();
 }
 
-__global__ void k_add_limbconst_kernel(const PrimeDev* __restrict__ pr, u64* __restrict__ io, int limbs, int log_n,
-                                       LimbConsts K) {
-  const size_t total = ((size_t)limbs << log_n) / 2;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+// add a per-limb constant to n_parts parts spaced `stride` apart (the c0 parts of a batch)
+__global__ void k_add_limbconst_kernel(const PrimeDev* __restrict__ pr, u64* __restrict__ io, size_t stride,
+                                       int n_parts, int limbs, int log_n, LimbConsts K) {
+  const size_t per_part = (size_t)limbs << log_n;
+  GRID_LOOP(t, n_parts * per_part / 2) {
     const size_t e = 2 * t;
-    const int i = (int)(e >> log_n);
+    const size_t p = e / per_part, r = e - p * per_part;
+    const int i = (int)(r >> log_n);
     const u64 q = pr[i].q, w = K.w[i];
-    ulonglong2 x = ld2(io + e);
+    u64* at = io + p * stride + r;
+    ulonglong2 x = ld2(at);
     x.x = add_mod(x.x, w, q);
     x.y = add_mod(x.y, w, q);
-    st2(io + e, x);
+    st2(at, x);
   }
 }
-void k_add_limbconst(const Ctx& C, u64* io, int limbs, const LimbConsts& K) {
-  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 2.0 * limbs * C.N * 8);
+void k_add_limbconst(const Ctx& C, u64* io, size_t stride, int n_parts, int limbs, const LimbConsts& K) {
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 2.0 * n_parts * limbs * C.N * 8);
   prof_count_launches(1);
-  const size_t work = (size_t)limbs * C.N / 2;
-  k_add_limbconst_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, io, limbs, C.log_n, K);
+  const size_t work = (size_t)n_parts * limbs * C.N / 2;
+  k_add_limbconst_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, io, stride, n_parts, limbs, C.log_n,
+                                                                   K);
   HEDAP_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------- rescale
-// last: coefficient-domain limb l of each part (part stride ls).  For i < l the
+// last: the coefficient-domain limb l of each part (part stride ls).  For i < l the
 // centred representative of last mod q_l is reduced mod q_i:
 //   v <= (q_l-1)/2 -> v mod q_i,  else (v mod q_i) - (q_l mod q_i)
 __global__ void k_rescale_spread_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ last, size_t ls,
-                                        u64* __restrict__ tmp, size_t ts, int l, int log_n, RescaleConsts R) {
-  const size_t N = (size_t)1 << log_n, per_part = (size_t)l << log_n, total = 2 * per_part;
-  const u64 ql = pr[l].q, half = ql >> 1;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(e / per_part);
-    const size_t r = e - p * per_part;
+                                        u64* __restrict__ tmp, size_t ts, int n_parts, int l, int log_n,
+                                        RescaleConsts R) {
+  const size_t N = (size_t)1 << log_n, per_part = (size_t)l << log_n;
+  const u64 half = pr[l].q >> 1;
+  GRID_LOOP(e, n_parts * per_part) {
+    const size_t p = e / per_part, r = e - p * per_part;
     const int i = (int)(r >> log_n);
-    const size_t n = r & (N - 1);
-    const u64 v = last[p * ls + n];
+    const u64 v = last[p * ls + (r & (N - 1))];
     const PrimeDev P = pr[i];
     u64 m = barrett_reduce(v, 0, P);
     if (v > half) m = sub_mod(m, R.ql_mod[i], P.q);
     tmp[p * ts + r] = m;
   }
-  (void)ql;
 }
-void k_rescale_spread(const Ctx& C, const u64* last, size_t ls, u64* tmp, size_t ts, int l, const RescaleConsts& R) {
-  ProfScope prof_(PROF_RESCALE, C.stream, (2.0 + 2.0 * l) * C.N * 8);
+void k_rescale_spread(const Ctx& C, const u64* last, size_t ls, u64* tmp, size_t ts, int n_parts, int l,
+                      const RescaleConsts& R) {
+  ProfScope prof_(PROF_RESCALE, C.stream, (1.0 + l) * n_parts * C.N * 8);
   prof_count_launches(1);
-  const size_t work = 2 * (size_t)l * C.N;
-  k_rescale_spread_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, last, ls, tmp, ts, l, C.log_n, R);
+  const size_t work = (size_t)n_parts * l * C.N;
+  k_rescale_spread_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, last, ls, tmp, ts, n_parts, l,
+                                                                     C.log_n, R);
   HEDAP_LAUNCH_CHECK();
 }
 __global__ void k_rescale_finish_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ in, size_t is,
                                         const u64* __restrict__ tmp, size_t ts, u64* __restrict__ out, size_t os,
-                                        int l, int log_n, RescaleConsts R) {
-  const size_t per_part = (size_t)l << log_n, total = 2 * per_part / 2;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+                                        int n_parts, int l, int log_n, RescaleConsts R) {
+  const size_t per_part = (size_t)l << log_n;
+  GRID_LOOP(t, n_parts * per_part / 2) {
     const size_t e = 2 * t;
-    const int p = (int)(e / per_part);
-    const size_t r = e - p * per_part;
+    const size_t p = e / per_part, r = e - p * per_part;
     const int i = (int)(r >> log_n);
     const u64 q = pr[i].q, w = R.inv[i], wp = R.inv_sh[i];
     ulonglong2 x = ld2(in + p * is + r), y = ld2(tmp + p * ts + r);
@@ -160,13 +170,13 @@ __global__ void k_rescale_finish_kernel(const PrimeDev* __restrict__ pr, const u
     st2(out + p * os + r, x);
   }
 }
-void k_rescale_finish(const Ctx& C, const u64* in, size_t is, const u64* tmp, size_t ts, u64* out, size_t os, int l,
-                      const RescaleConsts& R) {
-  ProfScope prof_(PROF_RESCALE, C.stream, 6.0 * l * C.N * 8);
+void k_rescale_finish(const Ctx& C, const u64* in, size_t is, const u64* tmp, size_t ts, u64* out, size_t os,
+                      int n_parts, int l, const RescaleConsts& R) {
+  ProfScope prof_(PROF_RESCALE, C.stream, 3.0 * n_parts * l * C.N * 8);
   prof_count_launches(1);
-  const size_t work = (size_t)l * C.N;
-  k_rescale_finish_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, in, is, tmp, ts, out, os, l, C.log_n,
-                                                                     R);
+  const size_t work = (size_t)n_parts * l * C.N / 2;
+  k_rescale_finish_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, in, is, tmp, ts, out, os, n_parts, l,
+                                                                     C.log_n, R);
   HEDAP_LAUNCH_CHECK();
 }
 
@@ -175,11 +185,10 @@ void k_rescale_finish(const Ctx& C, const u64* in, size_t is, const u64* tmp, si
 // psi^(g (2 bitrev(j) + 1)), i.e. input index bitrev(((g e_j mod 2N) - 1) / 2).
 __global__ void k_automorph_kernel(const u64* __restrict__ in, size_t is, u64* __restrict__ out, size_t os,
                                    int n_parts, int limbs, int log_n, u64 g) {
-  const size_t N = (size_t)1 << log_n, per_part = (size_t)limbs << log_n, total = n_parts * per_part;
+  const size_t N = (size_t)1 << log_n, per_part = (size_t)limbs << log_n;
   const u64 mask2n = 2 * N - 1;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(e / per_part);
-    const size_t r = e - p * per_part;
+  GRID_LOOP(e, n_parts * per_part) {
+    const size_t p = e / per_part, r = e - p * per_part;
     const size_t base = r & ~(N - 1);
     const uint32_t j = (uint32_t)(r & (N - 1));
     const u64 ej = 2 * (u64)(__brev(j) >> (32 - log_n)) + 1;
@@ -198,31 +207,33 @@ void k_automorph(const Ctx& C, const u64* in, size_t is, u64* out, size_t os, in
 
 // ---------------------------------------------------------------- key switching
 // ModUp (fast basis conversion, no correction) of every digit of the
-// coefficient-domain input at level l into the extended basis Q_l u P:
+// coefficient-domain inputs at level l into the extended basis Q_l u P:
 //   y_j,t = sum_{i in digit j} [x_i * qhat_i^-1]_{q_i} * (qhat_i mod t)  mod t
-// The digit's own limbs receive x itself.  Output y: [dnum][l+1+K][N].
+// The digit's own limbs receive x itself.  dcoef: [B][l+1][N]; y: [B][dnum][l+1+K][N].
 // Constants (per level): qinv[l+1], qinv_sh[l+1], then qhat[dnum][alpha][ext].
 __global__ void k_modup_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s,
                                const u64* __restrict__ dcoef, u64* __restrict__ y, const u64* __restrict__ cst, int l,
-                               int alpha, int n_q, int K, int log_n) {
+                               int alpha, int n_q, int K, int batch, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int ext = l + 1 + K, dn = (l + 1 + alpha - 1) / alpha;
   const u64* qinv = cst;
   const u64* qinv_sh = cst + (l + 1);
   const u64* qhat = cst + 2 * (l + 1);
-  const size_t total = (size_t)dn << log_n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e >> log_n);
-    const size_t n = e & (N - 1);
+  GRID_LOOP(e, (size_t)batch * dn * N) {
+    const size_t kj = e >> log_n, n = e & (N - 1);
+    const int j = (int)(kj % dn);
+    const size_t k = kj / dn;
+    const u64* xin = dcoef + k * (size_t)(l + 1) * N;
+    u64* yo = y + kj * (size_t)ext * N;
     const int lo = j * alpha, hi = min(lo + alpha, l + 1);
     u64 z[8];
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       if (a < hi - lo) {
         const int i = lo + a;
-        const u64 x = dcoef[(size_t)i * N + n];
+        const u64 x = xin[(size_t)i * N + n];
         z[a] = shoup_mul(x, qinv[i], qinv_sh[i], pr[i].q);
-        y[((size_t)j * ext + i) * N + n] = x;
+        yo[(size_t)i * N + n] = x;
       }
     }
     const u64* qh = qhat + (size_t)j * alpha * ext;
@@ -233,54 +244,82 @@ __global__ void k_modup_kernel(const PrimeDev* __restrict__ pr, const u64* __res
 #pragma unroll
       for (int a = 0; a < 8; ++a)
         if (a < hi - lo) mac128(acc, z[a], qh[(size_t)a * ext + t]);
-      y[((size_t)j * ext + t) * N + n] = reduce128(acc, pr[pt], r64s[2 * pt], r64s[2 * pt + 1]);
+      yo[(size_t)t * N + n] = reduce128(acc, pr[pt], r64s[2 * pt], r64s[2 * pt + 1]);
     }
   }
 }
-void k_modup(const Ctx& C, const u64* dcoef, u64* y, int level, const u64* d_consts) {
-  ProfScope prof_(PROF_MODUP, C.stream, ((level + 1.0) + (double)C.dnum(level) * (level + 1 + C.n_p)) * C.N * 8);
-  prof_count_launches(1);
+void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const u64* d_consts) {
   if (C.alpha > 8) throw Error(HEDAP_ERR_ARG, "alpha > 8 not supported");
-  const size_t work = (size_t)C.dnum(level) * C.N;
+  const int dn = C.dnum(level), ext = level + 1 + C.n_p;
+  ProfScope prof_(PROF_MODUP, C.stream, ((level + 1.0) + (double)dn * ext) * batch * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)batch * dn * C.N;
   k_modup_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, C.d_r64.p, dcoef, y, d_consts, level, C.alpha,
-                                                            C.n_q, C.n_p, C.log_n);
+                                                            C.n_q, C.n_p, batch, C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
 
-// inner product with the switching key: acc_{0,1}[t] = sum_j y_j[t] * key_j[{b,a}][t]
-// key layout: [dnum_max][2][n_q + n_p][N]
+// inner product with the switching key, reading each key word once for the whole batch:
+//   acc[k][0|1][t] = sum_j y[k][j][t] * key_j[b|a][t]
+// key layout: [dnum_max][2][n_q + n_p][N]; y: [B][dn][ext][N]; acc: [B][2][ext][N]
+template <int MAXB>
 __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s,
                                    const u64* __restrict__ y, const u64* __restrict__ key, u64* __restrict__ acc,
-                                   int l, int dn, int n_q, int K, int log_n) {
+                                   int l, int dn, int n_q, int K, int batch, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int ext = l + 1 + K, total_primes = n_q + K;
-  const size_t total = (size_t)ext << log_n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+  GRID_LOOP(e, (size_t)ext << log_n) {
     const int t = (int)(e >> log_n);
     const size_t n = e & (N - 1);
     const int pt = t <= l ? t : n_q + (t - l - 1);
-    Acc128 s0{0, 0}, s1{0, 0};
+    Acc128 s0[MAXB], s1[MAXB];
+#pragma unroll
+    for (int k = 0; k < MAXB; ++k) s0[k] = s1[k] = Acc128{0, 0};
     for (int j = 0; j < dn; ++j) {
-      const u64 v = y[((size_t)j * ext + t) * N + n];
       const u64* kj = key + (size_t)j * 2 * total_primes * N;
-      mac128(s0, v, kj[(size_t)pt * N + n]);
-      mac128(s1, v, kj[((size_t)total_primes + pt) * N + n]);
+      const u64 kb = kj[(size_t)pt * N + n], ka = kj[((size_t)total_primes + pt) * N + n];
+#pragma unroll
+      for (int k = 0; k < MAXB; ++k) {
+        if (k < batch) {
+          const u64 v = y[(((size_t)k * dn + j) * ext + t) * N + n];
+          mac128(s0[k], v, kb);
+          mac128(s1[k], v, ka);
+        }
+      }
     }
     const PrimeDev P = pr[pt];
-    acc[(size_t)t * N + n] = reduce128(s0, P, r64s[2 * pt], r64s[2 * pt + 1]);
-    acc[((size_t)ext + t) * N + n] = reduce128(s1, P, r64s[2 * pt], r64s[2 * pt + 1]);
+    const u64 r64 = r64s[2 * pt], r64p = r64s[2 * pt + 1];
+#pragma unroll
+    for (int k = 0; k < MAXB; ++k) {
+      if (k < batch) {
+        acc[(((size_t)k * 2) * ext + t) * N + n] = reduce128(s0[k], P, r64, r64p);
+        acc[(((size_t)k * 2 + 1) * ext + t) * N + n] = reduce128(s1[k], P, r64, r64p);
+      }
+    }
   }
 }
-void k_ksk_inner(const Ctx& C, const u64* y, const u64* key, u64* acc, int level) {
-  ProfScope prof_(PROF_KSK_INNER, C.stream, (3.0 * C.dnum(level) + 2.0) * (level + 1 + C.n_p) * C.N * 8);
+void k_ksk_inner(const Ctx& C, const u64* y, const u64* key, u64* acc, int batch, int level) {
+  if (batch < 1 || batch > kMaxBatch) throw Error(HEDAP_ERR_ARG, "batch must lie in [1, 16]");
+  const int dn = C.dnum(level), ext = level + 1 + C.n_p;
+  ProfScope prof_(PROF_KSK_INNER, C.stream, ((double)batch * dn + 2.0 * dn + 2.0 * batch) * ext * C.N * 8);
   prof_count_launches(1);
-  const size_t work = (size_t)(level + 1 + C.n_p) * C.N;
-  k_ksk_inner_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level,
-                                                                C.dnum(level), C.n_q, C.n_p, C.log_n);
+  const size_t work = (size_t)ext * C.N;
+  if (batch == 1)
+    k_ksk_inner_kernel<1><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level, dn,
+                                                                     C.n_q, C.n_p, batch, C.log_n);
+  else if (batch <= 4)
+    k_ksk_inner_kernel<4><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level, dn,
+                                                                     C.n_q, C.n_p, batch, C.log_n);
+  else if (batch <= 8)
+    k_ksk_inner_kernel<8><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level, dn,
+                                                                     C.n_q, C.n_p, batch, C.log_n);
+  else
+    k_ksk_inner_kernel<kMaxBatch><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level,
+                                                                             dn, C.n_q, C.n_p, batch, C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
 
-// ModDown, first half: from the coefficient-domain P limbs of acc (both parts)
+// ModDown, first half: from the coefficient-domain P limbs of acc (n_parts parts, stride ext*N)
 //   r_k = [(x_k + floor(P/2)) * phat_k^-1]_{p_k},
 //   v_i = sum_k r_k * (phat_k mod q_i) - floor(P/2)  mod q_i   (coefficient domain)
 // so that, after an NTT of v, x - v = x + floor(P/2) - BConv(...) on every coefficient.
@@ -288,7 +327,7 @@ void k_ksk_inner(const Ctx& C, const u64* y, const u64* key, u64* acc, int level
 // phat_q[K][n_q], Pinv[n_q], Pinv_sh[n_q], halfP_q[n_q].
 __global__ void k_moddown_spread_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s,
                                         const u64* __restrict__ acc, u64* __restrict__ v,
-                                        const u64* __restrict__ cst, int l, int n_q, int K, int log_n) {
+                                        const u64* __restrict__ cst, int n_parts, int l, int n_q, int K, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int ext = l + 1 + K;
   const u64* halfP_p = cst;
@@ -296,16 +335,14 @@ __global__ void k_moddown_spread_kernel(const PrimeDev* __restrict__ pr, const u
   const u64* phinv_sh = cst + 2 * K;
   const u64* phat_q = cst + 3 * K;
   const u64* halfP_q = cst + 3 * K + (size_t)K * n_q + 2 * (size_t)n_q;
-  const size_t total = (size_t)2 << log_n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(e >> log_n);
-    const size_t n = e & (N - 1);
+  GRID_LOOP(e, (size_t)n_parts << log_n) {
+    const size_t p = e >> log_n, n = e & (N - 1);
     u64 r[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       if (k < K) {
         const u64 pk = pr[n_q + k].q;
-        const u64 x = acc[((size_t)p * ext + l + 1 + k) * N + n];
+        const u64 x = acc[(p * ext + l + 1 + k) * N + n];
         r[k] = shoup_mul(add_mod(x, halfP_p[k], pk), phinv[k], phinv_sh[k], pk);
       }
     }
@@ -315,41 +352,41 @@ __global__ void k_moddown_spread_kernel(const PrimeDev* __restrict__ pr, const u
       for (int k = 0; k < 8; ++k)
         if (k < K) mac128(s, r[k], phat_q[(size_t)k * n_q + i]);
       const u64 conv = reduce128(s, pr[i], r64s[2 * i], r64s[2 * i + 1]);
-      v[((size_t)p * (l + 1) + i) * N + n] = sub_mod(conv, halfP_q[i], pr[i].q);
+      v[(p * (l + 1) + i) * N + n] = sub_mod(conv, halfP_q[i], pr[i].q);
     }
   }
 }
-void k_moddown_spread(const Ctx& C, const u64* acc, u64* v, int level) {
-  ProfScope prof_(PROF_MODDOWN, C.stream, (2.0 * C.n_p + 2.0 * (level + 1)) * C.N * 8);
-  prof_count_launches(1);
+void k_moddown_spread(const Ctx& C, const u64* acc, u64* v, int n_parts, int level) {
   if (C.n_p > 8) throw Error(HEDAP_ERR_ARG, "more than 8 special primes not supported");
-  const size_t work = 2 * C.N;
+  ProfScope prof_(PROF_MODDOWN, C.stream, (double)n_parts * (C.n_p + level + 1.0) * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)n_parts * C.N;
   k_moddown_spread_kernel<<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, acc, v, C.d_moddown.p,
-                                                                     level, C.n_q, C.n_p, C.log_n);
+                                                                     n_parts, level, C.n_q, C.n_p, C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
-// ModDown, second half (NTT domain): out = (acc - v) * P^-1 mod q_i
+// ModDown, second half (NTT domain): out_p = (acc_p - v_p) * P^-1 mod q_i, part p of the
+// output at out + p * os; even parts add into the output when acc_even, odd when acc_odd
 __global__ void k_moddown_finish_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ acc,
-                                        const u64* __restrict__ v, u64* __restrict__ out0, u64* __restrict__ out1,
-                                        const u64* __restrict__ cst, int l, int n_q, int K, int log_n, int acc0,
-                                        int acc1) {
-  const size_t per_part = (size_t)(l + 1) << log_n, total = 2 * per_part / 2;
-  const int ext = l + 1 + K;
+                                        const u64* __restrict__ v, u64* __restrict__ out, size_t os,
+                                        const u64* __restrict__ cst, int n_parts, int l, int n_q, int K, int log_n,
+                                        int acc_even, int acc_odd) {
+  const size_t per_part = (size_t)(l + 1) << log_n;
+  const size_t ext_stride = (size_t)(l + 1 + K) << log_n;
   const u64* Pinv = cst + 3 * K + (size_t)K * n_q;
   const u64* Pinv_sh = Pinv + n_q;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+  GRID_LOOP(t, n_parts * per_part / 2) {
     const size_t e = 2 * t;
-    const int p = (int)(e / per_part);
-    const size_t r = e - p * per_part;
+    const size_t p = e / per_part, r = e - p * per_part;
     const int i = (int)(r >> log_n);
     const u64 q = pr[i].q;
-    const ulonglong2 x = ld2(acc + (size_t)p * ext * ((size_t)1 << log_n) + r);
+    const ulonglong2 x = ld2(acc + p * ext_stride + r);
     const ulonglong2 w = ld2(v + p * per_part + r);
     ulonglong2 z;
     z.x = shoup_mul(sub_mod(x.x, w.x, q), Pinv[i], Pinv_sh[i], q);
     z.y = shoup_mul(sub_mod(x.y, w.y, q), Pinv[i], Pinv_sh[i], q);
-    u64* o = (p == 0 ? out0 : out1) + r;
-    if (p == 0 ? acc0 : acc1) {
+    u64* o = out + p * os + r;
+    if ((p & 1) ? acc_odd : acc_even) {
       const ulonglong2 c = ld2(o);
       z.x = add_mod(z.x, c.x, q);
       z.y = add_mod(z.y, c.y, q);
@@ -357,13 +394,14 @@ __global__ void k_moddown_finish_kernel(const PrimeDev* __restrict__ pr, const u
     st2(o, z);
   }
 }
-void k_moddown_finish(const Ctx& C, const u64* acc, const u64* v, u64* out0, u64* out1, int level, bool acc0,
-                      bool acc1) {
-  ProfScope prof_(PROF_MODDOWN, C.stream, (6.0 + 2.0 * (acc0 + acc1)) * (level + 1) * C.N * 8 / 2);
+void k_moddown_finish(const Ctx& C, const u64* acc, const u64* v, u64* out, size_t os, int n_parts, int level,
+                      bool acc_even, bool acc_odd) {
+  ProfScope prof_(PROF_MODDOWN, C.stream, (3.0 + (acc_even + acc_odd) / 2.0) * n_parts * (level + 1) * C.N * 8);
   prof_count_launches(1);
-  const size_t work = (size_t)(level + 1) * C.N;
-  k_moddown_finish_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, acc, v, out0, out1, C.d_moddown.p,
-                                                                     level, C.n_q, C.n_p, C.log_n, acc0, acc1);
+  const size_t work = (size_t)n_parts * (level + 1) * C.N / 2;
+  k_moddown_finish_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, acc, v, out, os, C.d_moddown.p,
+                                                                     n_parts, level, C.n_q, C.n_p, C.log_n, acc_even,
+                                                                     acc_odd);
   HEDAP_LAUNCH_CHECK();
 }
 
@@ -373,8 +411,7 @@ __global__ void k_keygen_combine_kernel(const PrimeDev* __restrict__ pr, u64* __
                                         const u64* __restrict__ a, const u64* __restrict__ s,
                                         const u64* __restrict__ sp, const u64* __restrict__ pmod, int lo, int hi,
                                         int total_primes, int log_n) {
-  const size_t total = (size_t)total_primes << log_n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+  GRID_LOOP(e, (size_t)total_primes << log_n) {
     const int t = (int)(e >> log_n);
     const PrimeDev P = pr[t];
     u64 v = sub_mod(b[e], mul_mod(a[e], s[e], P), P.q);
@@ -394,8 +431,7 @@ void k_keygen_combine(const Ctx& C, u64* b, const u64* a, const u64* s, const u6
 // out = x (op) y*z elementwise over `limbs` limbs (prime = limb index): op 0: x - y*z, 1: x + y*z, 2: y*z
 __global__ void k_fma_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ x, const u64* __restrict__ y,
                              const u64* __restrict__ z, u64* __restrict__ out, int limbs, int log_n, int op) {
-  const size_t total = (size_t)limbs << log_n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+  GRID_LOOP(e, (size_t)limbs << log_n) {
     const PrimeDev P = pr[e >> log_n];
     const u64 m = mul_mod(y[e], z[e], P);
     out[e] = op == 2 ? m : (op == 0 ? sub_mod(x[e], m, P.q) : add_mod(x[e], m, P.q));

@@ -76,9 +76,9 @@ extern "C" __attribute__((visibility("default"))) hedap_status hedap_rescale_noa
       R.inv[i] = hedap::h_invmod(ql % qi, qi);
       R.inv_sh[i] = hedap::h_shoup(R.inv[i], qi);
     }
-    hedap::k_rescale_spread(C, last, N, tmp, l * N, level, R);
+    hedap::k_rescale_spread(C, last, N, tmp, l * N, 2, level, R);
     hedap::ntt_forward(C.tab, hedap::LimbSet{tmp, l * N, 2, 0, level, INT_MAX, 0, 0}, C.stream);
-    hedap::k_rescale_finish(C, in, (l + 1) * N, tmp, l * N, out, l * N, level, R);
+    hedap::k_rescale_finish(C, in, (l + 1) * N, tmp, l * N, out, l * N, 2, level, R);
     return HEDAP_OK;
   } catch (const hedap::Error& e) {
     hedap::set_last_error(e.what());

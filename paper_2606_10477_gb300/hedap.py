@@ -30,6 +30,7 @@ EXPORTED = [
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
+    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch",
 ]
 
 
@@ -118,6 +119,10 @@ def _declare(L):
         "hedap_set_scale": (st, [vp, vp, C.c_double]),
         "hedap_encode": (st, [vp, dp, dp, C.c_size_t, C.c_double, C.POINTER(C.c_int64)]),
         "hedap_bts_diagonal": (st, [vp, C.c_int, C.c_int, C.c_int64, dp, dp]),
+        "hedap_batch_pack": (st, [vp, pp, C.c_size_t, pp]),
+        "hedap_batch_unpack": (st, [vp, vp, C.c_size_t, pp]),
+        "hedap_ct_batch_size": (st, [vp, C.POINTER(C.c_int)]),
+        "hedap_invsqrt_batch": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, pp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -164,6 +169,12 @@ class Ciphertext:
     @property
     def scale(self) -> float:
         return self._info()[1]
+
+    @property
+    def batch(self) -> int:
+        n = C.c_int()
+        _check(load().hedap_ct_batch_size(self.h, C.byref(n)))
+        return n.value
 
     def limbs(self) -> np.ndarray:
         out = np.empty((2, self.level + 1, self.ctx.N), dtype=np.uint64)
@@ -366,6 +377,23 @@ class Context:
     def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0):
         cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask)
         return self._ct(load().hedap_invsqrt, a.h, C.byref(cfg))
+
+    # ---- batches
+    def pack(self, cts) -> Ciphertext:
+        arr = (C.c_void_p * len(cts))(*[c.h for c in cts])
+        return self._ct(load().hedap_batch_pack, arr, len(cts))
+
+    def unpack(self, b: Ciphertext, k: int) -> Ciphertext:
+        return self._ct(load().hedap_batch_unpack, b.h, k)
+
+    def invsqrt_batch(self, cts, cfgs):
+        """cfgs: list of (lo, hi, B, degree, iters, pre_bts, bts_mask), one per ciphertext."""
+        n = len(cts)
+        arr = (C.c_void_p * n)(*[c.h for c in cts])
+        cf = (InvSqrtCfg * n)(*[InvSqrtCfg(*c) for c in cfgs])
+        outs = (C.c_void_p * n)()
+        _check(load().hedap_invsqrt_batch(self.h, arr, cf, n, outs))
+        return [Ciphertext(self, C.c_void_p(o)) for o in outs]
 
 
 PROFILE_CLASSES = ("ntt", "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph", "elementwise")

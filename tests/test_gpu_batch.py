@@ -1,0 +1,66 @@
+"""Batched ciphertexts: every operation on a packed batch equals the same
+operation on each ciphertext alone, bit for bit (CUDA library through its C ABI)."""
+import numpy as np
+import pytest
+
+from paper_2606_10477_gb300 import hedap, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def ctx(name, seed=1):
+    p = inputs.PRESETS[name]
+    return hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], seed)
+
+
+def imported(g, seed, level, n):
+    pr = g.primes()
+    return [g.ct_import(inputs.random_ciphertext_limbs(seed + i, pr, level, g.N), level, g.scale) for i in range(n)]
+
+
+def check(g, batch_out, singles):
+    assert batch_out.batch == len(singles)
+    for k, s in enumerate(singles):
+        u = g.unpack(batch_out, k)
+        assert u.level == s.level and u.scale == s.scale
+        assert np.array_equal(u.limbs(), s.limbs()), f"ciphertext {k}"
+
+
+@pytest.mark.parametrize("name,n", [("n13", 3), ("toy", 16)])
+def test_batched_ring_ops_equal_single_ops(name, n):
+    g = ctx(name)
+    L = g.n_q - 1
+    a, b = imported(g, 100, L, n), imported(g, 200, L, n)
+    A, B = g.pack(a), g.pack(b)
+    assert A.batch == n
+    check(g, g.add(A, B), [g.add(x, y) for x, y in zip(a, b)])
+    check(g, g.sub(A, B), [g.sub(x, y) for x, y in zip(a, b)])
+    check(g, g.mul(A, B), [g.mul(x, y) for x, y in zip(a, b)])
+    check(g, g.rescale(A), [g.rescale(x) for x in a])
+    check(g, g.rotate(A, 3), [g.rotate(x, 3) for x in a])
+    check(g, g.conjugate(A), [g.conjugate(x) for x in a])
+    check(g, g.mul_const(A, 0.75, g.scale), [g.mul_const(x, 0.75, g.scale) for x in a])
+    check(g, g.add_const(A, -0.25), [g.add_const(x, -0.25) for x in a])
+    check(g, g.mul_int(A, 3), [g.mul_int(x, 3) for x in a])
+
+
+def test_invsqrt_batch_groups_and_matches_single():
+    g = ctx("toy")
+    L = g.n_q - 1
+    vals = [inputs.uniform_values(300 + i, g.N // 2, 0.01, 1.0) for i in range(5)]
+    cts = [g.encrypt(v, L if i != 2 else L - 1, 400 + i) for i, v in enumerate(vals)]
+    cfgs = [(0.01, 1.0, 1.0, 15, 2, 0, 0)] * 5
+    cfgs[4] = (0.01, 1.0, 1.0, 7, 2, 0, 0)  # a different configuration forms its own group
+    outs = g.invsqrt_batch(cts, cfgs)
+    for ct, cfg, o in zip(cts, cfgs, outs):
+        s = g.invsqrt(ct, *cfg)
+        assert o.level == s.level and np.array_equal(o.limbs(), s.limbs())
+
+
+def test_bootstrap_batch_equals_single():
+    p = inputs.PRESETS["bts12"]
+    g = ctx("bts12")
+    b = inputs.BTS
+    g.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    cts = [g.encrypt(inputs.uniform_values(500 + i, g.N // 2, -1, 1), 1, 600 + i) for i in range(3)]
+    check(g, g.bootstrap_scaled(g.pack(cts), 1), [g.bootstrap_scaled(c, 1) for c in cts])
