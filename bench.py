@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bts", action="store_true", help="skip the bootstrapped workload")
+    ap.add_argument("--only", choices=["ntt"], help="time only the batched NTT (for kernel profiling)")
+    ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     return ap.parse_args()
 
 
@@ -303,6 +305,7 @@ def run_ours(args):
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "one full oracle CryptoInvSqrt of one ciphertext on the same workload", "mre": omre}
 
+    ntt = measure_ntt(ctx, inputs, torch, stream, 384)
     bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
                                                          stream=stream, rank=rank, batch=batch)
 
@@ -315,6 +318,7 @@ def run_ours(args):
             "mre": max(mres), "mre_target": MRE_TARGET,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "ntt_gbs": ntt_gbs,
+            "ntt_batched": ntt,
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -381,9 +385,57 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
             "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s}
 
 
+def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5):
+    """Batched forward and inverse NTT over `limbs` limbs of N = 2^16 words resident in HBM
+    (polynomials of n_q limbs, one launch per phase): algorithmic GB/s = limbs * N * 16 B
+    (each word read and written once) per transform."""
+    primes = ctx.primes()[:ctx.n_q]
+    polys = max(1, limbs // len(primes))
+    host = np.concatenate([inputs.random_limbs(9000 + i, primes, ctx.N) for i in range(polys)])
+    buf = torch.from_numpy(host.view(np.int64)).cuda()
+    limbs = polys * len(primes)
+
+    def run(inverse):
+        ctx.ntt_batch(buf, len(primes), 0, inverse=inverse)
+
+    run(False)
+    run(True)
+    torch.cuda.synchronize()
+    assert np.array_equal(buf.cpu().numpy().view(np.uint64), host), "NTT round trip failed"
+    out = {}
+    for name, inv in (("forward", False), ("inverse", True)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run(inv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "gbs": limbs * ctx.N * 16 / (ms / 1e3) / 1e9, "us_per_limb": 1e3 * ms / limbs}
+    out["limbs"] = limbs
+    return out
+
+
+def run_ntt_only(args):
+    import torch
+    from paper_2606_10477_gb300 import hedap, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    p = inputs.PRESETS[PRESET]
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1,
+                        stream=stream.cuda_stream)
+    fwd, inv, fv, iv = ctx.ntt_tune(args.ntt_limbs, 3)
+    r = measure_ntt(ctx, inputs, torch, stream, args.ntt_limbs, reps=max(1, args.steps))
+    print(json.dumps({"metric": "NTT GB/s (N=2^16, 64-bit limbs, batched)", "value": r["forward"]["gbs"],
+                      "unit": "GB/s", "ntt": r, "tune": {"forward_ms": fwd, "inverse_ms": inv,
+                                                         "chosen": [fv, iv]}}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.only == "ntt":
+        run_ntt_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -163,11 +163,63 @@ hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n);
 hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
                                  hedap_ct** out);
 
+/* HE-DAP provisioning (Sec. 4.2): Alg. 2 GetOptIter and Alg. 3, run on this
+ * library with CUDA-event costs.  For every profiled level l (l_BTS + 1 up to
+ * the level of a bootstrapped ciphertext; l_BTS = 1 here) and degree
+ * d = 2^d_e - 2, d_e_min <= d_e <= d_e_max, a ciphertext of
+ * linspace(A, B_max, N/2) is encrypted at level l and CryptoInvSqrt (inputs
+ * in [A, B_max], pre-normalisation by B, lazy BTS) runs for up to i_max
+ * Newton steps with c = 0 (when l >= l_BTS + 3) and c = 1 (Pre-BTS; when
+ * bootstrapping is configured and l < l_afterBTS - 1), decrypting after each
+ * step: M[i] = MRE, T[i] = accumulated HE time (ms, Dec excluded; the Pre-BTS
+ * included for c = 1).  Alg. 2's rule picks I per (l, d, c) -> a D entry;
+ * Alg. 3's rule picks per level u1 (fastest with m <= (floor(alpha)+theta)
+ * 10^l), u2 (fastest) and, if mre_target > 0, u3 (fastest with
+ * m <= mre_target).  Ties: smaller t, smaller d, c = 0, smaller i.
+ * Outputs: D entries (kind 0), R entries (kind 1, 2, 3 per level), and the
+ * trace of every (l, d, c, i, M[i], T[i]); counts in *n_D, *n_R, *n_trace
+ * (arrays may be NULL to query counts; HEDAP_ERR_ARG if a capacity is short). */
+typedef struct {
+  double A, B_max, B;
+  uint32_t d_e_min, d_e_max;
+  uint32_t i_max;
+  double theta, delta;
+  double mre_target;
+  int32_t level_min, level_max; /* 0 = the full range */
+  uint64_t seed;                /* encryption randomness of the provisioning ciphertexts */
+} hedap_select_cfg;
+typedef struct {
+  int32_t level;
+  uint32_t degree, c, iters;
+  double mre, ms;
+  uint32_t kind; /* 0: D entry, 1: u1 (theta rule), 2: u2 (fastest), 3: u3 (MRE target) */
+} hedap_select_entry;
+typedef struct {
+  int32_t level;
+  uint32_t degree, c, iter;
+  double mre, ms;
+} hedap_select_trace;
+hedap_status hedap_select(hedap_ctx* ctx, const hedap_select_cfg* cfg, hedap_select_entry* D, size_t D_cap,
+                          size_t* n_D, hedap_select_entry* R, size_t R_cap, size_t* n_R, hedap_select_trace* trace,
+                          size_t trace_cap, size_t* n_trace);
+/* The two selection rules alone (host only, no context needed).
+ * hedap_getoptiter_rule: *I = smallest 0-based i with M[i] <= MRE_delta, or -1;
+ * *threshold = MRE_delta.  hedap_select_level_rule: u1, u2, u3 of one level's
+ * D entries; *has_u3 = 1 when some entry meets mre_target. */
+hedap_status hedap_getoptiter_rule(const double* M, size_t n, double delta, int* I, double* threshold);
+hedap_status hedap_select_level_rule(const hedap_select_entry* D, size_t n, double theta, double mre_target,
+                                     hedap_select_entry* u1, hedap_select_entry* u2, hedap_select_entry* u3,
+                                     int* has_u3);
+
 /* Negacyclic NTT (inverse=0) or inverse NTT with N^-1 (inverse=1) of n_limbs
  * consecutive length-N limbs in place; limb i uses prime index first_prime+i
  * (global index over Q then P). */
 hedap_status hedap_ntt(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, uint32_t first_prime, int inverse,
                        int on_device);
+/* The same over n_polys consecutive polynomials of n_limbs limbs each (limb i
+ * of every polynomial uses prime first_prime+i), in one launch per phase. */
+hedap_status hedap_ntt_batch(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, size_t n_polys, uint32_t first_prime,
+                             int inverse, int on_device);
 
 /* Bootstrapping (BTS, Sec. 2.1; the paper uses it as a library primitive).
  * Full-slot CKKS bootstrapping: ModRaise, CoeffToSlot (cts_levels grouped
@@ -245,6 +297,17 @@ hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint
  * contexts on the same device) race on it.  It calls no cudaMalloc, cudaFree
  * or allocating routine (with profiling off, the default). */
 hedap_status hedap_rescale_noalloc(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
+
+/* NTT autotuner: times every NTT launch shape (words staged per CTA, CTAs per
+ * SM) on `limbs` limbs of scratch, forward and inverse separately (best of
+ * `reps`), and makes the fastest the context's shape.  Per-variant times go
+ * to fwd_ms / inv_ms (capacity cap, may be NULL); the chosen variant indices
+ * to *fwd_variant / *inv_variant. */
+hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
+                            int* fwd_variant, int* inv_variant);
+/* Select NTT launch shapes directly (0 <= variant < 6); every shape computes
+ * the same transform.  Context creation runs the autotuner once. */
+hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant);
 
 /* Profiling (process-wide, not part of the paper's interface).
  * hedap_profile_enable(1) resets the counters and, until disabled, records a

@@ -1070,8 +1070,9 @@ static Ct newton_step(Ctx& C, const Ct& x, const Ct& y) {
 // during the Newton loop, Sec. 4.3): pre_bts bootstraps the input a/B first;
 // bit j (< 63) of bts_mask bootstraps y before Newton step j (bit 0: right
 // after the Chebyshev step, as in Alg. 1); bit 63 bootstraps lazily, before a
-// step whose y lacks the two levels it consumes (or would leave y at level 0
-// with further steps to go).  ct_x is never bootstrapped.  Y, the power of two
+// step that would leave y below level 1 (fewer than 3 levels), so that later
+// bootstraps stay possible whatever number of steps follows.  ct_x is never
+// bootstrapped.  Y, the power of two
 // that bounds y = 1/sqrt(a/B), scales y into [-1, 1] around each BTS.
 static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   if (cfg.B <= 0 || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.iters < 0)
@@ -1097,7 +1098,7 @@ static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   const bool lazy = (cfg.bts_mask >> 63) & 1;
   for (int i = 0; i < cfg.iters; ++i) {
     bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
-    bool need = lazy && (y.level < 2 || (y.level == 2 && cfg.iters - i >= 2));
+    bool need = lazy && y.level < 3;  // the step would leave y below level 1
     if (force || need) y = bootstrap_scaled(C, y, Y);
     if (std::min(y.level, x.level) < 2) throw std::runtime_error("invsqrt: level exhausted in Newton loop");
     y = newton_step(C, x, y);

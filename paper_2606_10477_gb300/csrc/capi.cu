@@ -424,3 +424,88 @@ API hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, 
     }
   });
 }
+API hedap_status hedap_ntt_batch(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, size_t n_polys, uint32_t first_prime,
+                                 int inverse, int on_device) {
+  return guarded([&] {
+    need(ctx && limbs, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    need(first_prime + n_limbs <= (size_t)C.total_primes(), "prime index out of range");
+    need(n_polys * n_limbs <= 65535, "too many limbs in one batch");
+    if (n_limbs == 0 || n_polys == 0) return;
+    const size_t words = n_polys * n_limbs * C.N;
+    hedap::DevBuf tmp;
+    uint64_t* d = limbs;
+    if (!on_device) {
+      tmp = hedap::DevBuf(words, C.stream);
+      HEDAP_CUDA(cudaMemcpyAsync(tmp.p, limbs, words * 8, cudaMemcpyHostToDevice, C.stream));
+      d = tmp.p;
+    }
+    hedap::LimbSet S{d, n_limbs * C.N, (int)n_polys, 0, (int)n_limbs, INT_MAX, (int)first_prime, 0};
+    if (inverse) hedap::ntt_inverse(C.tab, S, C.stream);
+    else hedap::ntt_forward(C.tab, S, C.stream);
+    if (!on_device) {
+      HEDAP_CUDA(cudaMemcpyAsync(limbs, tmp.p, words * 8, cudaMemcpyDeviceToHost, C.stream));
+      HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+    }
+  });
+}
+
+API hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
+                                int* fwd_variant, int* inv_variant) {
+  return guarded([&] {
+    need(ctx != nullptr && limbs > 0 && reps > 0, "bad argument");
+    std::vector<float> f, i;
+    hedap::ntt_tune(*ctx->c, limbs, reps, &f, &i);
+    for (int k = 0; k < cap && k < (int)f.size(); ++k) {
+      if (fwd_ms) fwd_ms[k] = f[k];
+      if (inv_ms) inv_ms[k] = i[k];
+    }
+    if (fwd_variant) *fwd_variant = ctx->c->tab.ntt_fwd_variant;
+    if (inv_variant) *inv_variant = ctx->c->tab.ntt_inv_variant;
+  });
+}
+API hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant) {
+  return guarded([&] {
+    need(ctx && fwd_variant >= 0 && fwd_variant < hedap::kNttVariants && inv_variant >= 0 &&
+             inv_variant < hedap::kNttVariants,
+         "variant out of range");
+    ctx->c->tab.ntt_fwd_variant = fwd_variant;
+    ctx->c->tab.ntt_inv_variant = inv_variant;
+  });
+}
+
+// ---------------------------------------------------------------- selector
+API hedap_status hedap_select(hedap_ctx* ctx, const hedap_select_cfg* cfg, hedap_select_entry* D, size_t D_cap,
+                              size_t* n_D, hedap_select_entry* R, size_t R_cap, size_t* n_R,
+                              hedap_select_trace* trace, size_t trace_cap, size_t* n_trace) {
+  return guarded([&] {
+    need(ctx && cfg, "null argument");
+    std::vector<hedap_select_entry> d, r;
+    std::vector<hedap_select_trace> t;
+    hedap::select(*ctx->c, *cfg, d, r, t);
+    if (n_D) *n_D = d.size();
+    if (n_R) *n_R = r.size();
+    if (n_trace) *n_trace = t.size();
+    need(!D || D_cap >= d.size(), "D capacity too small");
+    need(!R || R_cap >= r.size(), "R capacity too small");
+    need(!trace || trace_cap >= t.size(), "trace capacity too small");
+    if (D) std::copy(d.begin(), d.end(), D);
+    if (R) std::copy(r.begin(), r.end(), R);
+    if (trace) std::copy(t.begin(), t.end(), trace);
+  });
+}
+API hedap_status hedap_getoptiter_rule(const double* M, size_t n, double delta, int* I, double* threshold) {
+  return guarded([&] {
+    need(M && I, "null argument");
+    *I = hedap::getoptiter_rule(M, n, delta, threshold);
+  });
+}
+API hedap_status hedap_select_level_rule(const hedap_select_entry* D, size_t n, double theta, double mre_target,
+                                         hedap_select_entry* u1, hedap_select_entry* u2, hedap_select_entry* u3,
+                                         int* has_u3) {
+  return guarded([&] {
+    need(D && u1 && u2 && u3 && n > 0, "bad argument");
+    const int r = hedap::level_rule(D, n, theta, mre_target, u1, u2, u3);
+    if (has_u3) *has_u3 = r == 1;
+  });
+}

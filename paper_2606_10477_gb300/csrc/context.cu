@@ -55,7 +55,7 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   const size_t N = C->N;
 
   // NTT tables: psi^bitrev(i), psi^-bitrev(i) and Shoup companions
-  std::vector<u64> psi(T * N), psi_sh(T * N), ipsi(T * N), ipsi_sh(T * N), ninv(T), ninv_sh(T), r64(2 * T);
+  std::vector<u64> psi2(2 * T * N), ipsi2(2 * T * N), ninv(T), ninv_sh(T), r64(2 * T);
   std::vector<u64> pw(N), ipw(N);
   for (int t = 0; t < T; ++t) {
     const u64 q = C->primes[t];
@@ -68,10 +68,10 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
     }
     for (size_t i = 0; i < N; ++i) {
       const uint32_t r = h_bitrev((uint32_t)i, C->log_n);
-      psi[t * N + i] = pw[r];
-      psi_sh[t * N + i] = h_shoup(pw[r], q);
-      ipsi[t * N + i] = ipw[r];
-      ipsi_sh[t * N + i] = h_shoup(ipw[r], q);
+      psi2[2 * (t * N + i)] = pw[r];
+      psi2[2 * (t * N + i) + 1] = h_shoup(pw[r], q);
+      ipsi2[2 * (t * N + i)] = ipw[r];
+      ipsi2[2 * (t * N + i) + 1] = h_shoup(ipw[r], q);
     }
     ninv[t] = h_invmod(N % q, q);
     ninv_sh[t] = h_shoup(ninv[t], q);
@@ -83,15 +83,13 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
     memcpy(pd.data(), C->pdev.data(), T * sizeof(PrimeDev));
     upload(*C, C->d_primes, pd);
   }
-  upload(*C, C->d_psi, psi);
-  upload(*C, C->d_psi_sh, psi_sh);
-  upload(*C, C->d_ipsi, ipsi);
-  upload(*C, C->d_ipsi_sh, ipsi_sh);
+  upload(*C, C->d_psi2, psi2);
+  upload(*C, C->d_ipsi2, ipsi2);
   upload(*C, C->d_ninv, ninv);
   upload(*C, C->d_ninv_sh, ninv_sh);
   upload(*C, C->d_r64, r64);
-  C->tab = Tables{(const PrimeDev*)C->d_primes.p, C->d_psi.p, C->d_psi_sh.p, C->d_ipsi.p, C->d_ipsi_sh.p,
-                  C->d_ninv.p, C->d_ninv_sh.p, C->log_n};
+  C->tab = Tables{(const PrimeDev*)C->d_primes.p, (const ulonglong2*)C->d_psi2.p, (const ulonglong2*)C->d_ipsi2.p,
+                  C->d_ninv.p, C->d_ninv_sh.p, C->log_n, 3, 3};
 
   // P = prod p_k; ModDown constants and P mod q_t
   const int K = C->n_p, nq = C->n_q;
@@ -148,6 +146,7 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   upload(*C, C->d_sk, skr);
   ntt_forward(C->tab, LimbSet{C->d_sk.p, 0, 1, 0, T, nq, 0, nq}, C->stream);
   gen_galois_key(*C, 0);
+  ntt_tune(*C, 8 * C->n_q, 2, nullptr, nullptr);  // pick the NTT launch shape for this ring
   HEDAP_CUDA(cudaStreamSynchronize(C->stream));
   return C.release();
 }

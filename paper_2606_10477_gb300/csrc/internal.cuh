@@ -79,15 +79,16 @@ struct DevBuf {
 
 // ------------------------------------------------------------------ tables and limb sets
 struct Tables {
-  const PrimeDev* pr;     // [n_primes]
-  const u64* psi;         // [n_primes][N] psi^bitrev(i)
-  const u64* psi_sh;      // Shoup companions
-  const u64* ipsi;        // [n_primes][N] psi^-bitrev(i)
-  const u64* ipsi_sh;
-  const u64* ninv;        // [n_primes] N^-1
+  const PrimeDev* pr;        // [n_primes]
+  const ulonglong2* psi2;    // [n_primes][N] (psi^bitrev(i), Shoup companion)
+  const ulonglong2* ipsi2;   // [n_primes][N] (psi^-bitrev(i), Shoup companion)
+  const u64* ninv;           // [n_primes] N^-1
   const u64* ninv_sh;
   int log_n;
+  int ntt_fwd_variant;       // NTT launch shape (see ntt.cu), chosen by ntt_tune
+  int ntt_inv_variant;
 };
+constexpr int kNttVariants = 6;
 
 // A set of limbs: parts p in [0, n_parts), limbs li in [limb_begin, limb_begin+n_limbs)
 // at base + p*part_stride + li*N.  Limb li < q_count uses prime prime_offset+li,
@@ -111,6 +112,8 @@ struct LimbSet {
 
 void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st);
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st);
+struct Ctx;
+void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vector<float>* inv_ms);
 
 // ------------------------------------------------------------------ context and ciphertexts
 // One ciphertext, or a batch of `batch` ciphertexts at one level and scale:
@@ -159,7 +162,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   std::vector<u64> primes;
   std::vector<PrimeDev> pdev;
-  DevBuf d_primes, d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_ninv, d_ninv_sh;
+  DevBuf d_primes, d_psi2, d_ipsi2, d_ninv, d_ninv_sh;
   DevBuf d_moddown;   // level-independent ModDown constants
   DevBuf d_r64;       // per prime: 2^64 mod q and its Shoup companion
   DevBuf d_pmod;      // per prime: P mod q_t (key generation)
@@ -207,7 +210,27 @@ std::vector<double> encode_slots(const Ctx& C, const std::vector<std::complex<do
 
 // ------------------------------------------------------------------ CryptoInvSqrt (invsqrt.cu)
 std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg);
+// CryptoInvSqrt in steps (construction = pre-BTS and pre-normalisation; then
+// chebyshev(); then newton(i) for i = 0, 1, ...), used by invsqrt and the selector
+struct InvSqrtRun {
+  Ctx& C;
+  hedap_invsqrt_cfg cfg;
+  double lo, hi;
+  i64 Y;
+  std::unique_ptr<Ct> t, x, y;
+  InvSqrtRun(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg);
+  void chebyshev();
+  void newton(int i);
+  std::unique_ptr<Ct> result() const;  // y / sqrt(B)
+};
 std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target);
+
+// ------------------------------------------------------------------ selector (selector.cu)
+int getoptiter_rule(const double* M, size_t n, double delta, double* thr_out);
+int level_rule(const hedap_select_entry* D, size_t n, double theta, double target, hedap_select_entry* u1,
+               hedap_select_entry* u2, hedap_select_entry* u3);
+void select(Ctx& C, const hedap_select_cfg& sc, std::vector<hedap_select_entry>& D,
+            std::vector<hedap_select_entry>& R, std::vector<hedap_select_trace>& trace);
 
 // ------------------------------------------------------------------ bootstrapping (bootstrap.cu)
 int bts_setup(Ctx& C, int K, int r, int deg, int cts, int stc);

@@ -155,21 +155,23 @@ static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
 // Bootstrapping placement (the Pre-BTS indicator c of Sec. 4.1 and BTS during
 // the Newton loop, Sec. 4.3): pre_bts bootstraps a/B first; bit j (< 63) of
 // bts_mask bootstraps y before Newton step j (bit 0: right after the Chebyshev
-// step, as in Alg. 1); bit 63 bootstraps lazily, before a step whose y lacks
-// the two levels the step consumes or would be left at level 0 with steps to
-// go.  ct_x is never bootstrapped.  Y, the power of two bounding y, scales y
-// into [-1, 1] around each BTS.  The final 1/sqrt(B) is applied to the scale
+// step, as in Alg. 1); bit 63 bootstraps lazily, before any step that would
+// leave y below level 1 (y has fewer than 3 levels), so that a later bootstrap
+// stays possible and the state after i steps does not depend on how many steps
+// follow.  ct_x is never bootstrapped.  Y, the power of two bounding y, scales
+// y into [-1, 1] around each BTS.  The final 1/sqrt(B) is applied to the scale
 // label (no level is used).
-std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) {
+InvSqrtRun::InvSqrtRun(Ctx& C_, const Ct& in, const hedap_invsqrt_cfg& c) : C(C_), cfg(c) {
   if (!(cfg.B > 0) || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.degree > 4096)
     throw Error(HEDAP_ERR_ARG, "invsqrt: invalid configuration");
   if ((cfg.pre_bts || cfg.bts_mask) && !C.bts)
     throw Error(HEDAP_ERR_ARG, "invsqrt: bootstrapping not configured on this context");
-  const double lo = cfg.lo / cfg.B, hi = cfg.hi / cfg.B;
-  i64 Y = 1;
+  lo = cfg.lo / cfg.B;
+  hi = cfg.hi / cfg.B;
+  Y = 1;
   while ((double)Y < 1.0 / std::sqrt(lo)) Y *= 2;
-  CtP pre;
   double Bf = cfg.B;
+  CtP pre;
   if (cfg.pre_bts) {  // a -> BTS(a / B), values in (0, 1]
     if (in.level < 1) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
     CtP d = in.level > 1 ? ev_drop(C, in, 1) : nullptr;
@@ -179,21 +181,31 @@ std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) 
   const Ct& a = pre ? *pre : in;
   if (a.level < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
   const double alpha = 2.0 / (Bf * (hi - lo)), beta = -(hi + lo) / (hi - lo);
-  CtP t = ev_add_const(C, *ev_mul_const(C, a, alpha, C.scale), beta);
-  CtP x = ev_mul_const(C, a, 0.5 / Bf, C.scale);
-  CtP y = cheb_eval(C, *t, cheb_interp(lo, hi, (int)cfg.degree), C.scale);
-  const bool lazy = (cfg.bts_mask >> 63) & 1;
+  t = ev_add_const(C, *ev_mul_const(C, a, alpha, C.scale), beta);
+  x = ev_mul_const(C, a, 0.5 / Bf, C.scale);
+}
+void InvSqrtRun::chebyshev() { y = cheb_eval(C, *t, cheb_interp(lo, hi, (int)cfg.degree), C.scale); }
+void InvSqrtRun::newton(int i) {
+  const bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
+  const bool lazy = ((cfg.bts_mask >> 63) & 1) && y->level < 3;
+  if (force || lazy) y = bootstrap_scaled(C, *y, Y);
+  if (std::min(y->level, x->level) < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: level exhausted in Newton loop");
+  y = newton_step(C, *x, *y);
+}
+std::unique_ptr<Ct> InvSqrtRun::result() const {
+  auto r = ct_copy(C, *y, y->level);
+  if (cfg.B != 1.0) r->scale *= std::sqrt(cfg.B);
+  return r;
+}
+
+std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) {
+  InvSqrtRun run(C, in, cfg);
+  run.chebyshev();
   const int n = (int)cfg.newton_iters;
-  for (int i = 0; i < n; ++i) {
-    const bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
-    const bool need = lazy && (y->level < 2 || (y->level == 2 && n - i >= 2));
-    if (force || need) y = bootstrap_scaled(C, *y, Y);
-    if (std::min(y->level, x->level) < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: level exhausted in Newton loop");
-    y = newton_step(C, *x, *y);
-  }
-  if (n == 0 && (cfg.bts_mask & 1)) y = bootstrap_scaled(C, *y, Y);
-  if (cfg.B != 1.0) y->scale *= std::sqrt(cfg.B);
-  return y;
+  for (int i = 0; i < n; ++i) run.newton(i);
+  if (n == 0 && (cfg.bts_mask & 1)) run.y = bootstrap_scaled(C, *run.y, run.Y);
+  if (cfg.B != 1.0) run.y->scale *= std::sqrt(cfg.B);
+  return std::move(run.y);
 }
 
 }  // namespace hedap

@@ -30,8 +30,32 @@ EXPORTED = [
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
-    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch",
+    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_ntt_batch",
+    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
 ]
+
+
+class SelectCfg(C.Structure):
+    _fields_ = [("A", C.c_double), ("B_max", C.c_double), ("B", C.c_double), ("d_e_min", C.c_uint32),
+                ("d_e_max", C.c_uint32), ("i_max", C.c_uint32), ("theta", C.c_double), ("delta", C.c_double),
+                ("mre_target", C.c_double), ("level_min", C.c_int32), ("level_max", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class SelectEntry(C.Structure):
+    _fields_ = [("level", C.c_int32), ("degree", C.c_uint32), ("c", C.c_uint32), ("iters", C.c_uint32),
+                ("mre", C.c_double), ("ms", C.c_double), ("kind", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SelectTrace(C.Structure):
+    _fields_ = [("level", C.c_int32), ("degree", C.c_uint32), ("c", C.c_uint32), ("iter", C.c_uint32),
+                ("mre", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BtsParams(C.Structure):
@@ -123,6 +147,17 @@ def _declare(L):
         "hedap_batch_unpack": (st, [vp, vp, C.c_size_t, pp]),
         "hedap_ct_batch_size": (st, [vp, C.POINTER(C.c_int)]),
         "hedap_invsqrt_batch": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, pp]),
+        "hedap_ntt_batch": (st, [vp, u64p, C.c_size_t, C.c_size_t, C.c_uint32, C.c_int, C.c_int]),
+        "hedap_ntt_tune": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
+                                C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "hedap_ntt_set_variant": (st, [vp, C.c_int, C.c_int]),
+        "hedap_select": (st, [vp, C.POINTER(SelectCfg), C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t),
+                              C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t), C.POINTER(SelectTrace),
+                              C.c_size_t, C.POINTER(C.c_size_t)]),
+        "hedap_getoptiter_rule": (st, [dp, C.c_size_t, C.c_double, C.POINTER(C.c_int), dp]),
+        "hedap_select_level_rule": (st, [C.POINTER(SelectEntry), C.c_size_t, C.c_double, C.c_double,
+                                         C.POINTER(SelectEntry), C.POINTER(SelectEntry), C.POINTER(SelectEntry),
+                                         C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -251,6 +286,24 @@ class Context:
             return x
         p, dev = _u64ptr(limbs)
         _check(load().hedap_ntt(self.h, p, limbs.numel() // self.N, first_prime, int(inverse), dev))
+        return limbs
+
+    def ntt_tune(self, limbs=384, reps=3):
+        """Autotune the NTT launch shape; returns (fwd ms per variant, inv ms per variant, chosen fwd, chosen inv)."""
+        f, i = (C.c_float * 16)(), (C.c_float * 16)()
+        fv, iv = C.c_int(), C.c_int()
+        _check(load().hedap_ntt_tune(self.h, limbs, reps, f, i, 16, C.byref(fv), C.byref(iv)))
+        n = 6
+        return list(f[:n]), list(i[:n]), fv.value, iv.value
+
+    def ntt_set_variant(self, fwd: int, inv: int):
+        _check(load().hedap_ntt_set_variant(self.h, fwd, inv))
+
+    def ntt_batch(self, limbs, n_limbs: int, first_prime: int, inverse=False):
+        """In-place NTT of a CUDA tensor holding polynomials of n_limbs limbs each."""
+        p, dev = _u64ptr(limbs)
+        _check(load().hedap_ntt_batch(self.h, p, n_limbs, limbs.numel() // (n_limbs * self.N), first_prime,
+                                      int(inverse), dev))
         return limbs
 
     # ---- key-switching steps
@@ -386,6 +439,18 @@ class Context:
     def unpack(self, b: Ciphertext, k: int) -> Ciphertext:
         return self._ct(load().hedap_batch_unpack, b.h, k)
 
+    def select(self, A, B_max, B, d_e_min, d_e_max, i_max, theta=1.0, delta=1.0, mre_target=0.0,
+               level_min=0, level_max=0, seed=7):
+        """Run HE-DAP provisioning (Alg. 2 + Alg. 3); returns (D, R, trace) as lists of dicts."""
+        cfg = SelectCfg(A, B_max, B, d_e_min, d_e_max, i_max, theta, delta, mre_target, level_min, level_max, seed)
+        cap_d = 64 * (d_e_max - d_e_min + 1) * 2
+        D, R, T = (SelectEntry * cap_d)(), (SelectEntry * (64 * 3))(), (SelectTrace * (cap_d * i_max))()
+        nd, nr, nt = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        _check(load().hedap_select(self.h, C.byref(cfg), D, len(D), C.byref(nd), R, len(R), C.byref(nr), T, len(T),
+                                   C.byref(nt)))
+        return ([D[i].as_dict() for i in range(nd.value)], [R[i].as_dict() for i in range(nr.value)],
+                [T[i].as_dict() for i in range(nt.value)])
+
     def invsqrt_batch(self, cts, cfgs):
         """cfgs: list of (lo, hi, B, degree, iters, pre_bts, bts_mask), one per ciphertext."""
         n = len(cts)
@@ -417,3 +482,22 @@ def launch_count() -> int:
     n = C.c_uint64()
     _check(load().hedap_launch_count(C.byref(n)))
     return n.value
+
+
+def getoptiter_rule(M, delta: float):
+    """Alg. 2's threshold rule (host code of the library): (I 0-based or -1, MRE_delta)."""
+    m = np.ascontiguousarray(M, dtype=np.float64)
+    I, thr = C.c_int(), C.c_double()
+    _check(load().hedap_getoptiter_rule(m.ctypes.data_as(C.POINTER(C.c_double)), len(m), delta, C.byref(I),
+                                        C.byref(thr)))
+    return I.value, thr.value
+
+
+def select_level_rule(entries, theta: float, mre_target: float = 0.0):
+    """Alg. 3's per-level rule: entries are dicts (level, degree, c, iters, mre, ms); returns (u1, u2, u3 or None)."""
+    arr = (SelectEntry * len(entries))(*[SelectEntry(e["level"], e["degree"], e["c"], e["iters"], e["mre"], e["ms"], 0)
+                                         for e in entries])
+    u1, u2, u3, h = SelectEntry(), SelectEntry(), SelectEntry(), C.c_int()
+    _check(load().hedap_select_level_rule(arr, len(entries), theta, mre_target, C.byref(u1), C.byref(u2),
+                                          C.byref(u3), C.byref(h)))
+    return u1.as_dict(), u2.as_dict(), (u3.as_dict() if h.value else None)

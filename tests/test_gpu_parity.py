@@ -97,6 +97,22 @@ def test_ntt_bit_exact_every_prime(name, request):
     assert np.array_equal(g.ntt(fwd, 0, inverse=True), x)
 
 
+@pytest.mark.parametrize("name", ["n10", "n13"])
+def test_every_ntt_launch_shape_is_bit_exact(name, request):
+    g, o = request.getfixturevalue(name)
+    primes = o.primes()
+    x = inputs.random_limbs(17, primes, o.N)
+    ref_f = np.stack([o.ntt(x[i], i) for i in range(len(primes))])
+    ref_i = np.stack([o.ntt(x[i], i, inverse=True) for i in range(len(primes))])
+    try:
+        for v in range(6):
+            g.ntt_set_variant(v, v)
+            assert np.array_equal(g.ntt(x, 0), ref_f), f"forward variant {v}"
+            assert np.array_equal(g.ntt(x, 0, inverse=True), ref_i), f"inverse variant {v}"
+    finally:
+        g.ntt_tune(4 * g.n_q, 1)
+
+
 def test_ntt_ragged_batch_offset_primes(n13):
     g, o = n13
     primes = o.primes()
