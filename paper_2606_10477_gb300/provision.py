@@ -1,0 +1,110 @@
+"""HE-DAP provisioning on this GPU (Sec. 4: run once at installation).
+
+Runs Alg. 2 / Alg. 3 (``hedap_select``) for a parameter preset and writes the
+per-level table R[l] = [u1 (accuracy), u2 (speed), u3 (absolute MRE target)]
+with the full D set and per-iteration trace, keyed by device name, preset and
+git revision, plus this GPU's analogue of the paper's Table 1 (Chebyshev
+evaluation time per degree against the BTS time) and Table 10 (exploration
+time).
+
+  python -m paper_2606_10477_gb300.provision --preset bts16 --out provisioning.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import time
+
+import numpy as np
+
+from . import hedap, inputs
+
+
+def git_revision() -> str:
+    try:
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        return subprocess.run(["git", "-C", root, "rev-parse", "HEAD"], capture_output=True, text=True,
+                              timeout=10).stdout.strip() or "unknown"
+    except (OSError, subprocess.SubprocessError):
+        return "unknown"
+
+
+def device_name() -> str:
+    try:
+        return subprocess.run(["nvidia-smi", "--query-gpu=name", "--format=csv,noheader", "-i", "0"],
+                              capture_output=True, text=True, timeout=10).stdout.strip()
+    except (OSError, subprocess.SubprocessError):
+        return "unknown"
+
+
+def chebyshev_vs_bts(ctx, lmax, A, B_max, B, degrees, reps=3):
+    """Table 1 analogue: pre-normalisation + Chebyshev evaluation at l_max, against one BTS."""
+    import torch
+    vals = np.linspace(A, B_max, ctx.N // 2)
+    ct = ctx.encrypt(vals, lmax, 1)
+    rows = []
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            ctx.sync()
+            best = min(best, time.perf_counter() - t0)
+        return 1e3 * best
+
+    y = ctx.encrypt(vals / B_max, 1, 2)
+    bts_ms = timed(lambda: ctx.bootstrap_scaled(y, 1))
+    for d in degrees:
+        try:
+            ms = timed(lambda: ctx.invsqrt(ct, A, B_max, B, d, 0))
+        except hedap.HedapError:
+            continue
+        rows.append({"degree": d, "cheb_ms": ms, "bts_ms": bts_ms, "ratio": ms / bts_ms})
+    return rows
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--preset", default="bts16")
+    ap.add_argument("--A", type=float, default=0.001)
+    ap.add_argument("--B-max", type=float, default=100.0)
+    ap.add_argument("--B", type=float, default=100.0)
+    ap.add_argument("--de-min", type=int, default=4)
+    ap.add_argument("--de-max", type=int, default=7)
+    ap.add_argument("--i-max", type=int, default=15)
+    ap.add_argument("--theta", type=float, default=1.0)
+    ap.add_argument("--delta", type=float, default=1.0)
+    ap.add_argument("--mre-target", type=float, default=1e-7)
+    ap.add_argument("--out", default="provisioning.json")
+    args = ap.parse_args(argv)
+
+    p = inputs.PRESETS[args.preset]
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
+    lmax = ctx.n_q - 1
+    if p["hw"]:
+        b = inputs.BTS
+        lmax = ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    t0 = time.perf_counter()
+    D, R, T = ctx.select(args.A, args.B_max, args.B, args.de_min, args.de_max, args.i_max, args.theta, args.delta,
+                         args.mre_target)
+    explore_s = time.perf_counter() - t0
+    table1 = chebyshev_vs_bts(ctx, lmax, args.A, args.B_max, args.B,
+                              [(1 << e) - 2 for e in range(args.de_min, args.de_max + 1)]) if p["hw"] else []
+    out = {
+        "key": {"device": device_name(), "preset": args.preset, "params": p, "git": git_revision()},
+        "config": vars(args), "l_max": lmax, "exploration_s": explore_s,
+        "R": R, "D": D, "trace": T, "table1": table1,
+    }
+    with open(args.out, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({"exploration_s": explore_s, "levels": sorted({r["level"] for r in R}),
+                      "R": [(r["level"], r["kind"], r["degree"], r["c"], r["iters"], r["mre"], round(r["ms"], 2))
+                            for r in R], "table1": table1}))
+
+
+if __name__ == "__main__":
+    main()
