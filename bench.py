@@ -170,7 +170,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU path
 def run_ours(args):
     import torch
-    from paper_2606_10477_gb300 import hedap, inputs
+    from paper_2606_10477_gb300 import hedap, inputs, replicas
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
@@ -178,8 +178,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     p = inputs.PRESETS[PRESET]
-    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1 + rank,
-                        stream=stream.cuda_stream)
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"],
+                        replicas.rank_seed(1, rank), stream=stream.cuda_stream)
     L = ctx.n_q - 1
     batch = args.batch
     vals = [inputs.uniform_values(1000 * rank + i, ctx.N // 2, LO, HI) for i in range(batch)]
@@ -225,11 +225,9 @@ def run_ours(args):
     elapsed_ms = e0.elapsed_time(e1)
     launches = hedap.launch_count() - launches0
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = ws * batch * args.steps / (elapsed_ms / 1e3)
+    value, tmax_s, _ = replicas.aggregate(batch * args.steps, elapsed_ms / 1e3,
+                                          torch.distributed if ws > 1 else None)
+    elapsed_ms = tmax_s * 1e3
 
     # ---- the plain path, same work and timing
     step_plain()
@@ -290,11 +288,7 @@ def run_ours(args):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * batch * k_e2e / e2e_s
+    e2e_value, e2e_s, _ = replicas.aggregate(batch * k_e2e, e2e_s, torch.distributed if ws > 1 else None)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
