@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bts", action="store_true", help="skip the bootstrapped workload")
-    ap.add_argument("--only", choices=["ntt"], help="time only the batched NTT (for kernel profiling)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
+    ap.add_argument("--only", choices=["ntt", "serving"],
+                    help="time only the batched NTT (for kernel profiling) or only the serving workload")
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     return ap.parse_args()
 
@@ -302,6 +305,7 @@ def run_ours(args):
     ntt = measure_ntt(ctx, inputs, torch, stream, 384)
     bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
                                                          stream=stream, rank=rank, batch=batch)
+    serving = None if args.no_serving else serving_workload(hedap, inputs, torch, stream, rank, args.serve_queries)
 
     if rank == 0:
         line = {
@@ -327,6 +331,7 @@ def run_ours(args):
             "plain": {"value": plain_value, "unit": UNIT, "ms_per_ct": 1e3 / plain_value,
                       "speedup_batched_vs_plain": value / plain_value},
             "bootstrapped": bts,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -379,6 +384,100 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
             "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s}
 
 
+SERVE_RECORDS = [1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20]
+SERVE_ZCFG = (1e-3, 1.0, 1.0, 31, 4, 0, 1 << 63)  # variance of the records (sd 0.1): [1e-3, 1]
+SERVE_PCFG = (1e-5, 1e-2, 1e-2, 31, 5, 0, 1 << 63)  # product of two variances: [1e-5, 1e-2]
+
+
+def serving_workload(hedap, inputs, torch, stream, rank, n_queries, max_batch=8):
+    """Poisson arrivals of encrypted z-score / correlation queries (half each) over 2^10..2^20
+    Gaussian records (mean 50, sd 10, in units of 100) packed into N=2^16 ciphertexts at the
+    bootstrapped level; InvSqrt of the variance with lazy bootstrapping; keys resident."""
+    p = inputs.PRESETS["bts16"]
+    b = inputs.BTS
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 21 + rank,
+                        stream=stream.cuda_stream)
+    lvl = ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"]) + 3  # 3 levels above a bootstrapped one
+    slots = ctx.N // 2
+    pool = []
+    for k, n in enumerate(SERVE_RECORDS):
+        x = inputs.gaussian_records(500 + k, n)
+        y = inputs.correlated_records(600 + k, x, 0.5)
+        gx = [ctx.encrypt(v, lvl, 7000 + 100 * k + i) for i, v in enumerate(inputs.pack_slots(x, slots))]
+        gy = [ctx.encrypt(v, lvl, 8000 + 100 * k + i) for i, v in enumerate(inputs.pack_slots(y, slots))]
+        pool.append((n, x, y, gx, gy))
+    rng = np.random.default_rng(99 + rank)
+
+    def submit(srv, kind, k):
+        n, _, _, gx, gy = pool[k]
+        if kind == hedap.QUERY_ZSCORE:
+            return srv.submit(kind, gx, n, SERVE_ZCFG)
+        return srv.submit(kind, gx, n, SERVE_PCFG, ys=gy)
+
+    def plan(m):
+        return [(hedap.QUERY_ZSCORE if i % 2 == 0 else hedap.QUERY_PCC, int(rng.integers(len(pool))))
+                for i in range(m)]
+
+    # warm-up (bootstrapping diagonals, key-switching buffers) and accuracy of one query of each kind
+    srv = hedap.Server(ctx, max_batch=max_batch)
+    kz, kp = len(pool) - 1, 3
+    _, zs, _ = srv.poll(submit(srv, hedap.QUERY_ZSCORE, kz))
+    _, rs, _ = srv.poll(submit(srv, hedap.QUERY_PCC, kp))
+    n, x, _, _, _ = pool[kz]
+    z = np.concatenate([ctx.decrypt(c).real for c in zs])[:n]
+    z_err = float(np.max(np.abs(z - (x - x.mean()) / x.std())))
+    n, x, y, _, _ = pool[kp]
+    r_err = float(np.max(np.abs(ctx.decrypt(rs[0]).real - np.corrcoef(x, y)[0, 1])))
+    srv.close()
+
+    # capacity: a burst released at once
+    burst = plan(2 * max_batch)
+    srv = hedap.Server(ctx, max_batch=max_batch, paused=True)
+    ids = [submit(srv, kind, k) for kind, k in burst]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    srv.resume()
+    for i in ids:
+        srv.poll(i)
+    capacity = len(ids) / (time.perf_counter() - t0)
+    srv.close()
+
+    # Poisson arrivals at 70% of that capacity
+    rate = 0.7 * capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_queries))
+    queries = plan(n_queries)
+    srv = hedap.Server(ctx, max_batch=max_batch)
+    t0 = time.perf_counter()
+    ids = []
+    for (kind, k), t in zip(queries, arrivals):
+        wait = t0 + t - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(submit(srv, kind, k))
+    groups = [srv.poll(i)[2]["group_size"] for i in ids]
+    st = srv.stats()
+    srv.close()
+    records = sum(pool[k][0] for _, k in queries)
+    ctx.close()
+    return {"workload": f"Poisson arrivals, {n_queries} queries (z-score / PCC alternating) over "
+                        f"{SERVE_RECORDS[0]}..{SERVE_RECORDS[-1]} Gaussian records (mean 50, sd 10, /100), "
+                        f"N=2^16 bts16 chain, inputs at level {lvl} (3 above a bootstrapped ciphertext), InvSqrt degree 31 "
+                        f"with lazy bootstrapping, "
+                        f"max_batch {max_batch}",
+            "qps": st["qps"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "arrival_rate_qps": rate,
+            "burst_capacity_qps": capacity, "records_per_s": records * st["qps"] / n_queries,
+            "mean_group_size": float(np.mean(groups)), "zscore_max_abs_err": z_err, "pcc_abs_err": r_err}
+
+
+def run_serving_only(args):
+    import torch
+    from paper_2606_10477_gb300 import hedap, inputs
+    stream = torch.cuda.current_stream()
+    r = serving_workload(hedap, inputs, torch, stream, 0, args.serve_queries)
+    print(json.dumps({"metric": "queries/s (serving, Poisson arrivals)", "value": r["qps"], "unit": "queries/s",
+                      "higher_is_better": True, "serving": r}), flush=True)
+
+
 def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5):
     """Batched forward and inverse NTT over `limbs` limbs of N = 2^16 words resident in HBM
     (polynomials of n_q limbs, one launch per phase): algorithmic GB/s = limbs * N * 16 B
@@ -429,6 +528,8 @@ def main():
     args = parse()
     if args.only == "ntt":
         run_ntt_only(args)
+    elif args.only == "serving":
+        run_serving_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -298,6 +298,66 @@ hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint
  * or allocating routine (with profiling off, the default). */
 hedap_status hedap_rescale_noalloc(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
 
+/* Serving (the statistical workloads of Sec. 5.3: Z-score normalisation and
+ * the Pearson correlation coefficient, each needing InvSqrt of an encrypted
+ * variance).  A server owns a worker thread that drives the context: the
+ * oldest waiting query is admitted with the later ones that can share its
+ * group (one kind, input level, input scale and InvSqrt configuration; up to
+ * max_batch) while the estimated device memory of the admitted queries stays
+ * within hbm_budget_bytes; each group is
+ * advanced step by step, interleaved with the other groups in flight, each
+ * step one batched operation over the group.  A query's result is bit for
+ * bit the same whatever other queries share its group.
+ *   z-score: x = n_ct ciphertexts holding the records in their slots (unused
+ *     slots zero); result: n_ct ciphertexts z = (x - mean) * InvSqrt(var).
+ *   PCC: x and y as above, record k of x paired with record k of y;
+ *     result: one ciphertext with r = cov * InvSqrt(var_x * var_y) in every slot.
+ * mean, var and cov are over n_records records (population moments).  All
+ * inputs are single ciphertexts at one level >= 4 and one scale, and are
+ * BORROWED: the caller keeps them alive and unchanged until the query is
+ * done.  The InvSqrt configuration must cover the variance (z-score) or the
+ * product of variances (PCC); a lazy-bootstrap mask (bit 63) needs
+ * hedap_bootstrap_setup on the context, and when InvSqrt leaves the result at
+ * level 0 the server bootstraps it once more for the final product.
+ * hedap_server_create generates the rotation keys by 1, 2, 4, .., N/4 (kept
+ * resident) and starts the worker; max_batch in [1, 16]; with start_paused
+ * the worker admits nothing until hedap_server_resume (a burst submitted
+ * meanwhile is grouped in arrival order).  While a server runs,
+ * other calls on its context are serialised with the worker's steps.
+ * hedap_server_submit returns HEDAP_ERR_OOM for a query whose own estimate
+ * exceeds the budget.  hedap_server_poll: *done = 1 once finished (wait != 0
+ * blocks until then); with out != NULL it hands over the result ciphertexts
+ * (caller frees them with hedap_ct_free) and forgets the query; a failed query
+ * reports its error once and is forgotten; *group_size = the number of queries
+ * the query was grouped with (itself included).  hedap_server_estimate: the
+ * admission estimate in bytes for a query of that kind, n_ct and input level.  hedap_server_stats: completion
+ * latency percentiles (submit to GPU completion, ms) over all completed
+ * queries and queries per second from the first submission to the last
+ * completion.  hedap_server_destroy finishes every submitted query first. */
+typedef struct hedap_server hedap_server;
+enum { HEDAP_QUERY_ZSCORE = 1, HEDAP_QUERY_PCC = 2 };
+typedef struct {
+  uint32_t max_batch;
+  uint32_t start_paused;
+  uint64_t hbm_budget_bytes;
+} hedap_server_cfg;
+typedef struct {
+  uint32_t kind;                 /* HEDAP_QUERY_ZSCORE or HEDAP_QUERY_PCC */
+  const hedap_ct* const* x;      /* n_ct ciphertexts */
+  const hedap_ct* const* y;      /* n_ct ciphertexts (PCC), else NULL */
+  uint32_t n_ct;
+  uint64_t n_records;            /* <= n_ct * N/2 */
+  hedap_invsqrt_cfg invsqrt;
+} hedap_query;
+hedap_status hedap_server_create(hedap_ctx* ctx, const hedap_server_cfg* cfg, hedap_server** out);
+hedap_status hedap_server_submit(hedap_server* s, const hedap_query* q, uint64_t* id);
+hedap_status hedap_server_poll(hedap_server* s, uint64_t id, int wait, int* done, hedap_ct** out, size_t cap,
+                               size_t* n_out, double* latency_ms, uint32_t* group_size);
+hedap_status hedap_server_resume(hedap_server* s);
+hedap_status hedap_server_estimate(const hedap_server* s, uint32_t kind, uint32_t n_ct, int level, uint64_t* bytes);
+hedap_status hedap_server_stats(hedap_server* s, double* p50_ms, double* p99_ms, double* qps, uint64_t* completed);
+void hedap_server_destroy(hedap_server* s);
+
 /* NTT autotuner: times every NTT launch shape (words staged per CTA, CTAs per
  * SM) on `limbs` limbs of scratch, forward and inverse separately (best of
  * `reps`), and makes the fastest the context's shape.  Per-variant times go

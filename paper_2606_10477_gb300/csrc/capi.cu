@@ -25,6 +25,15 @@ hedap_status guarded(F&& f) {
     return HEDAP_ERR_ARG;
   }
 }
+// Every entry point that takes a context runs under the context's lock, so
+// calls from several host threads (a user thread beside a server's worker)
+// see its lazily built keys and constants consistently.
+template <class F>
+hedap_status guarded_on(const hedap_ctx* ctx, F&& f) {
+  if (!ctx) return guarded(std::forward<F>(f));
+  std::lock_guard<std::mutex> lk(ctx->c->mu);
+  return guarded(std::forward<F>(f));
+}
 void need(bool ok, const char* what) {
   if (!ok) throw hedap::Error(HEDAP_ERR_ARG, what);
 }
@@ -73,26 +82,26 @@ API void hedap_ctx_destroy(hedap_ctx* ctx) {
   delete ctx;
 }
 API hedap_status hedap_ctx_primes(const hedap_ctx* ctx, uint64_t* out, size_t cap) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && out, "null argument");
     need(cap >= ctx->c->primes.size(), "capacity too small");
     std::memcpy(out, ctx->c->primes.data(), ctx->c->primes.size() * 8);
   });
 }
 API hedap_status hedap_sync(hedap_ctx* ctx) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx, "null argument");
     HEDAP_CUDA(cudaStreamSynchronize(ctx->c->stream));
   });
 }
 API hedap_status hedap_gen_galois_key(hedap_ctx* ctx, uint64_t g) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx, "null argument");
     hedap::gen_galois_key(*ctx->c, g);
   });
 }
 API hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t g, uint32_t digit, uint64_t* b, uint64_t* a) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && b && a, "null argument");
     hedap::Ctx& C = *ctx->c;
     hedap::gen_galois_key(C, g);
@@ -106,7 +115,7 @@ API hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t g, uint32_t digit, ui
 }
 API hedap_status hedap_encrypt(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, int level,
                                uint64_t seed, hedap_ct** out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && re && out, "null argument");
     *out = nullptr;
     std::vector<double> r(re, re + n_slots), i;
@@ -115,7 +124,7 @@ API hedap_status hedap_encrypt(hedap_ctx* ctx, const double* re, const double* i
   });
 }
 API hedap_status hedap_decrypt(hedap_ctx* ctx, const hedap_ct* ct, double* re, double* im, size_t n_slots) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && ct && re, "null argument");
     need(n_slots == ctx->c->N / 2, "n_slots must equal N/2");
     std::vector<double> r, i;
@@ -126,7 +135,7 @@ API hedap_status hedap_decrypt(hedap_ctx* ctx, const hedap_ct* ct, double* re, d
 }
 API hedap_status hedap_ct_import(hedap_ctx* ctx, const uint64_t* limbs, int level, double scale, int on_device,
                                  hedap_ct** out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && limbs && out, "null argument");
     *out = nullptr;
     hedap::Ctx& C = *ctx->c;
@@ -151,7 +160,7 @@ API hedap_status hedap_ct_import(hedap_ctx* ctx, const uint64_t* limbs, int leve
   });
 }
 API hedap_status hedap_ct_export(hedap_ctx* ctx, const hedap_ct* ct, uint64_t* out, size_t cap, int on_device) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && ct && out, "null argument");
     hedap::Ctx& C = *ctx->c;
     const size_t per = (size_t)(ct->c->level + 1) * C.N;
@@ -172,7 +181,7 @@ API hedap_status hedap_ct_info(const hedap_ct* ct, int* level, double* scale) {
 API void hedap_ct_free(hedap_ct* ct) { delete ct; }
 
 #define CT_OP(...)                                  \
-  return guarded([&] {                              \
+  return guarded_on(ctx, [&] {                      \
     need(ctx && out, "null argument");             \
     *out = nullptr;                                 \
     *out = wrap(__VA_ARGS__);                       \
@@ -216,7 +225,7 @@ API hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_i
 }
 API hedap_status hedap_ntt(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, uint32_t first_prime, int inverse,
                            int on_device) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && limbs, "null argument");
     hedap::Ctx& C = *ctx->c;
     need(first_prime + n_limbs <= (size_t)C.total_primes(), "prime index out of range");
@@ -262,7 +271,7 @@ API hedap_status hedap_launch_count(uint64_t* out) {
 
 // ---------------------------------------------------------------- key-switching steps (test ABI)
 API hedap_status hedap_modup(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && in && out, "null argument");
     hedap::Ctx& C = *ctx->c;
     need(level >= 0 && level <= C.L(), "level out of range");
@@ -275,7 +284,7 @@ API hedap_status hedap_modup(hedap_ctx* ctx, const uint64_t* in, int level, uint
   });
 }
 API hedap_status hedap_moddown(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && in && out, "null argument");
     hedap::Ctx& C = *ctx->c;
     need(level >= 0 && level <= C.L(), "level out of range");
@@ -293,7 +302,7 @@ API hedap_status hedap_moddown(hedap_ctx* ctx, const uint64_t* in, int level, ui
   });
 }
 API hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint64_t galois, uint64_t* out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && d && out, "null argument");
     hedap::Ctx& C = *ctx->c;
     need(level >= 0 && level <= C.L(), "level out of range");
@@ -308,7 +317,7 @@ API hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, 
 
 // ---------------------------------------------------------------- bootstrapping
 API hedap_status hedap_bootstrap_setup(hedap_ctx* ctx, const hedap_bts_params* p, int* level_after) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && p, "null argument");
     const int l = hedap::bts_setup(*ctx->c, (int)p->K, (int)p->double_angles, (int)p->mod_degree,
                                    (int)p->cts_levels, (int)p->stc_levels);
@@ -336,14 +345,14 @@ API hedap_status hedap_eval_mod(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** ou
   CT_OP((need(a, "null ciphertext"), hedap::eval_mod(*ctx->c, *a->c)));
 }
 API hedap_status hedap_set_scale(hedap_ctx* ctx, hedap_ct* a, double scale) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && a && scale > 0, "bad argument");
     a->c->scale = scale;
   });
 }
 API hedap_status hedap_encode(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, double scale,
                               int64_t* out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && re && out, "null argument");
     need(n_slots == ctx->c->N / 2, "n_slots must equal N/2");
     std::vector<std::complex<double>> z(n_slots);
@@ -356,7 +365,7 @@ API hedap_status hedap_encode(hedap_ctx* ctx, const double* re, const double* im
   });
 }
 API hedap_status hedap_bts_diagonal(hedap_ctx* ctx, int inverse, int group, int64_t offset, double* re, double* im) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && re && im, "null argument");
     std::vector<std::complex<double>> d;
     need(hedap::bts_diagonal(*ctx->c, inverse != 0, group, (long)offset, d), "no such diagonal");
@@ -366,7 +375,7 @@ API hedap_status hedap_bts_diagonal(hedap_ctx* ctx, int inverse, int group, int6
 
 // ---------------------------------------------------------------- batches
 API hedap_status hedap_batch_pack(hedap_ctx* ctx, const hedap_ct* const* cts, size_t n, hedap_ct** out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && cts && out && n >= 1 && n <= 16, "bad argument");
     *out = nullptr;
     std::vector<const hedap::Ct*> v;
@@ -388,7 +397,7 @@ API hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n) {
 }
 API hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs,
                                      size_t n, hedap_ct** out) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && in && cfgs && out, "null argument");
     for (size_t i = 0; i < n; ++i) out[i] = nullptr;
     hedap::Ctx& C = *ctx->c;
@@ -426,7 +435,7 @@ API hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, 
 }
 API hedap_status hedap_ntt_batch(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, size_t n_polys, uint32_t first_prime,
                                  int inverse, int on_device) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && limbs, "null argument");
     hedap::Ctx& C = *ctx->c;
     need(first_prime + n_limbs <= (size_t)C.total_primes(), "prime index out of range");
@@ -452,7 +461,7 @@ API hedap_status hedap_ntt_batch(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs
 
 API hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
                                 int* fwd_variant, int* inv_variant) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx != nullptr && limbs > 0 && reps > 0, "bad argument");
     std::vector<float> f, i;
     hedap::ntt_tune(*ctx->c, limbs, reps, &f, &i);
@@ -465,7 +474,7 @@ API hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_
   });
 }
 API hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && fwd_variant >= 0 && fwd_variant < hedap::kNttVariants && inv_variant >= 0 &&
              inv_variant < hedap::kNttVariants,
          "variant out of range");
@@ -478,7 +487,7 @@ API hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_
 API hedap_status hedap_select(hedap_ctx* ctx, const hedap_select_cfg* cfg, hedap_select_entry* D, size_t D_cap,
                               size_t* n_D, hedap_select_entry* R, size_t R_cap, size_t* n_R,
                               hedap_select_trace* trace, size_t trace_cap, size_t* n_trace) {
-  return guarded([&] {
+  return guarded_on(ctx, [&] {
     need(ctx && cfg, "null argument");
     std::vector<hedap_select_entry> d, r;
     std::vector<hedap_select_trace> t;

@@ -42,6 +42,7 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
 
   int dev = 0;
   HEDAP_CUDA(cudaGetDevice(&dev));
+  C->device = dev;
   cudaMemPool_t pool;
   HEDAP_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
   uint64_t thr = UINT64_MAX;

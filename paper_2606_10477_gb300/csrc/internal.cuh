@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -172,6 +173,8 @@ struct Ctx {
   std::map<u64, DevBuf> keys;  // galois (0 = relinearisation) -> [dnum][2][n_q+n_p][N]
   std::map<int, std::unique_ptr<LevelConsts>> lc;
   std::unique_ptr<BtsState, BtsStateDeleter> bts;
+  int device = 0;             // the CUDA device current at creation
+  mutable std::mutex mu;      // held by every C-ABI call on this context and by a server's worker per step
   int L() const { return n_q - 1; }
   int total_primes() const { return n_q + n_p; }
   int dnum(int level) const { return (level + 1 + alpha - 1) / alpha; }

@@ -32,6 +32,8 @@ EXPORTED = [
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_ntt_batch",
     "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
+    "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
+    "hedap_server_resume", "hedap_server_estimate",
 ]
 
 
@@ -78,6 +80,18 @@ class Params(C.Structure):
 class InvSqrtCfg(C.Structure):
     _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("B", C.c_double), ("degree", C.c_uint32),
                 ("newton_iters", C.c_uint32), ("pre_bts", C.c_uint32), ("bts_mask", C.c_uint64)]
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("max_batch", C.c_uint32), ("start_paused", C.c_uint32), ("hbm_budget_bytes", C.c_uint64)]
+
+
+class Query(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("x", C.POINTER(C.c_void_p)), ("y", C.POINTER(C.c_void_p)),
+                ("n_ct", C.c_uint32), ("n_records", C.c_uint64), ("invsqrt", InvSqrtCfg)]
+
+
+QUERY_ZSCORE, QUERY_PCC = 1, 2
 
 
 def load(path: str = LIB_PATH):
@@ -158,6 +172,14 @@ def _declare(L):
         "hedap_select_level_rule": (st, [C.POINTER(SelectEntry), C.c_size_t, C.c_double, C.c_double,
                                          C.POINTER(SelectEntry), C.POINTER(SelectEntry), C.POINTER(SelectEntry),
                                          C.POINTER(C.c_int)]),
+        "hedap_server_create": (st, [vp, C.POINTER(ServerCfg), pp]),
+        "hedap_server_submit": (st, [vp, C.POINTER(Query), u64p]),
+        "hedap_server_poll": (st, [vp, C.c_uint64, C.c_int, C.POINTER(C.c_int), pp, C.c_size_t,
+                                   C.POINTER(C.c_size_t), dp, C.POINTER(C.c_uint32)]),
+        "hedap_server_resume": (st, [vp]),
+        "hedap_server_estimate": (st, [vp, C.c_uint32, C.c_uint32, C.c_int, u64p]),
+        "hedap_server_stats": (st, [vp, dp, dp, dp, u64p]),
+        "hedap_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -462,6 +484,73 @@ class Context:
 
 
 PROFILE_CLASSES = ("ntt", "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph", "elementwise")
+
+
+class Server:
+    """Continuous-batching server for z-score / correlation queries on one context.
+
+    Inputs are borrowed by the library until a query is done; this wrapper
+    keeps references to them until then."""
+
+    def __init__(self, ctx: Context, max_batch: int = 8, hbm_budget_bytes: int = 64 << 30, paused: bool = False):
+        self.ctx = ctx
+        self._held = {}
+        h = C.c_void_p()
+        cfg = ServerCfg(max_batch, 1 if paused else 0, hbm_budget_bytes)
+        _check(load().hedap_server_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+
+    def submit(self, kind: int, xs, n_records: int, cfg, ys=None) -> int:
+        """Submit a query; cfg = (lo, hi, B, degree, iters, pre_bts, bts_mask). Returns its id."""
+        xa = (C.c_void_p * len(xs))(*[c.h for c in xs])
+        ya = (C.c_void_p * len(ys))(*[c.h for c in ys]) if ys is not None else None
+        q = Query(kind, C.cast(xa, C.POINTER(C.c_void_p)),
+                  C.cast(ya, C.POINTER(C.c_void_p)) if ya is not None else None,
+                  len(xs), n_records, InvSqrtCfg(*cfg))
+        qid = C.c_uint64()
+        _check(load().hedap_server_submit(self.h, C.byref(q), C.byref(qid)))
+        self._held[qid.value] = (list(xs), list(ys or []))
+        return qid.value
+
+    def poll(self, qid: int, wait: bool = True):
+        """(done, results, info); results are handed over once done; info = {latency_ms, group_size}."""
+        done, n, lat, gs = C.c_int(), C.c_size_t(), C.c_double(), C.c_uint32()
+        try:
+            _check(load().hedap_server_poll(self.h, qid, 1 if wait else 0, C.byref(done), None, 0, C.byref(n),
+                                            C.byref(lat), C.byref(gs)))
+        except HedapError:
+            self._held.pop(qid, None)
+            raise
+        if not done.value:
+            return False, None, None
+        out = (C.c_void_p * n.value)()
+        _check(load().hedap_server_poll(self.h, qid, 0, C.byref(done), out, n.value, None, None, None))
+        self._held.pop(qid, None)
+        return True, [Ciphertext(self.ctx, C.c_void_p(v)) for v in out], {"latency_ms": lat.value,
+                                                                          "group_size": gs.value}
+
+    def resume(self) -> None:
+        _check(load().hedap_server_resume(self.h))
+
+    def estimate(self, kind: int, n_ct: int, level: int) -> int:
+        b = C.c_uint64()
+        _check(load().hedap_server_estimate(self.h, kind, n_ct, level, C.byref(b)))
+        return b.value
+
+    def stats(self) -> dict:
+        p50, p99, qps, n = C.c_double(), C.c_double(), C.c_double(), C.c_uint64()
+        _check(load().hedap_server_stats(self.h, C.byref(p50), C.byref(p99), C.byref(qps), C.byref(n)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "qps": qps.value, "completed": n.value}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().hedap_server_destroy(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
 
 
 def profile_enable(on: bool) -> None:

@@ -62,3 +62,24 @@ def random_ciphertext_limbs(seed: int, primes, level: int, n_coeffs: int) -> np.
     g = rng(seed)
     return np.stack([np.stack([g.integers(0, int(primes[i]), n_coeffs, dtype=np.uint64) for i in range(level + 1)])
                      for _ in range(2)])
+
+
+def gaussian_records(seed: int, n: int, mean: float = 50.0, sd: float = 10.0, unit: float = 0.01) -> np.ndarray:
+    """n records drawn from N(mean, sd^2), expressed in `unit`s of 100 (0.5 +- 0.1 by default)."""
+    return rng(seed).normal(mean, sd, n) * unit
+
+
+def correlated_records(seed: int, x: np.ndarray, rho: float, mean: float = 50.0, sd: float = 10.0,
+                       unit: float = 0.01) -> np.ndarray:
+    """Records paired with x (same distribution) with correlation about rho."""
+    z = (x / unit - mean) / sd
+    e = rng(seed).normal(0.0, 1.0, x.size)
+    return (mean + sd * (rho * z + np.sqrt(1.0 - rho * rho) * e)) * unit
+
+
+def pack_slots(values: np.ndarray, slots: int) -> list:
+    """Split records into ceil(n / slots) slot vectors, the last one zero-padded."""
+    n_ct = max(1, -(-values.size // slots))
+    buf = np.zeros(n_ct * slots)
+    buf[:values.size] = values
+    return [buf[k * slots:(k + 1) * slots].copy() for k in range(n_ct)]
