@@ -255,7 +255,8 @@ def run_ours(args):
 
     # ---- same steps with the per-kernel-class event profiler on
     hedap.profile_enable(True)
-    for _ in range(max(1, min(args.steps, 2))):
+    n_prof_steps = max(1, min(args.steps, 2))
+    for _ in range(n_prof_steps):
         step()
     torch.cuda.synchronize()
     prof = hedap.profile_read()
@@ -327,6 +328,9 @@ def run_ours(args):
                 "launch_groups": n_dom, "avg_group_us": 1e3 * ms_dom / max(1, n_dom),
             },
             "profile_share": {k: round(v[1] / total_prof_ms, 4) for k, v in prof.items()} if total_prof_ms else {},
+            "profile_classes": {k: {"groups_per_step": v[0] / n_prof_steps, "ms_per_step": v[1] / n_prof_steps,
+                                    "us_per_group": 1e3 * v[1] / v[0], "algorithmic_gbs": v[2] / (v[1] / 1e3) / 1e9}
+                                for k, v in prof.items() if v[0] > 0},
             "cpu_baseline": cpu,
             "plain": {"value": plain_value, "unit": UNIT, "ms_per_ct": 1e3 / plain_value,
                       "speedup_batched_vs_plain": value / plain_value},

@@ -359,13 +359,13 @@ hedap_status hedap_server_stats(hedap_server* s, double* p50_ms, double* p99_ms,
 void hedap_server_destroy(hedap_server* s);
 
 /* NTT autotuner: times every NTT launch shape (words staged per CTA, CTAs per
- * SM) on `limbs` limbs of scratch, forward and inverse separately (best of
+ * SM, radix 16 or 8 register passes) on `limbs` limbs of scratch, forward and inverse separately (best of
  * `reps`), and makes the fastest the context's shape.  Per-variant times go
  * to fwd_ms / inv_ms (capacity cap, may be NULL); the chosen variant indices
  * to *fwd_variant / *inv_variant. */
 hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
                             int* fwd_variant, int* inv_variant);
-/* Select NTT launch shapes directly (0 <= variant < 6); every shape computes
+/* Select NTT launch shapes directly (0 <= variant < 8); every shape computes
  * the same transform.  Context creation runs the autotuner once. */
 hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant);
 

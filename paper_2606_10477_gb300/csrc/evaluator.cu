@@ -96,7 +96,8 @@ const LevelConsts& level_consts(Ctx& C, int l) {
   const int a = C.alpha, dn = C.dnum(l), K = C.n_p, ext = l + 1 + K;
   const u64* q = C.primes.data();
   auto prime_of_ext = [&](int t) { return t <= l ? q[t] : q[C.n_q + (t - l - 1)]; };
-  std::vector<u64> v(2 * (l + 1) + (size_t)dn * a * ext, 0);
+  const size_t nb = (size_t)dn * a * ext;  // qhat table size; its Shoup companions follow it
+  std::vector<u64> v(2 * (l + 1) + 2 * nb, 0);
   for (int j = 0; j < dn; ++j) {
     const int lo = j * a, hi = std::min(lo + a, l + 1);
     for (int i = lo; i < hi; ++i) {
@@ -112,11 +113,21 @@ const LevelConsts& level_consts(Ctx& C, int l) {
         for (int m = lo; m < hi; ++m)
           if (m != i) hm = h_mulmod(hm, q[m] % pt, pt);
         v[2 * (l + 1) + ((size_t)j * a + (i - lo)) * ext + t] = hm;
+        v[2 * (l + 1) + nb + ((size_t)j * a + (i - lo)) * ext + t] = h_shoup(hm, pt);
       }
     }
   }
   L->modup = DevBuf(v.size(), C.stream);
   HEDAP_CUDA(cudaMemcpyAsync(L->modup.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  // the key switch's inverse NTT ends with N^-1 qhat_i^-1 instead of N^-1, so that its output is the
+  // first factor [x_i qhat_i^-1]_{q_i} of the fast basis conversion
+  std::vector<u64> post(2 * (l + 1));
+  for (int i = 0; i <= l; ++i) {
+    post[2 * i] = h_mulmod(h_invmod(C.N % q[i], q[i]), v[i], q[i]);
+    post[2 * i + 1] = h_shoup(post[2 * i], q[i]);
+  }
+  L->intt_post = DevBuf(post.size(), C.stream);
+  HEDAP_CUDA(cudaMemcpyAsync(L->intt_post.p, post.data(), post.size() * 8, cudaMemcpyHostToDevice, C.stream));
   HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   if (l >= 1) {
     const u64 ql = q[l];
@@ -135,7 +146,10 @@ const LevelConsts& level_consts(Ctx& C, int l) {
 // Hybrid key switching (Han-Ki 2020) of a batch of polynomials with the key for
 // `galois`: iNTT, ModUp of every digit to Q_l u P, NTT, inner product with the
 // key digits (each key word read once for the batch), iNTT of the P limbs,
-// ModDown (rounded division by P), NTT.
+// ModDown (rounded division by P), NTT.  The ModUp is fused into the transforms:
+// the inverse NTT reads d out of place and ends with N^-1 qhat_i^-1, the forward
+// NTT of each extended limb loads the basis conversion directly, and a digit's
+// own limbs (whose NTT is d itself) are neither converted nor transformed.
 void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
                 bool acc0, bool acc1) {
   auto it = C.keys.find(galois);
@@ -146,15 +160,25 @@ void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 gal
   const size_t N = C.N, nl = (size_t)l + 1;
   const int K = C.n_p, ext = l + 1 + K, dn = C.dnum(l);
   const LevelConsts& LC = level_consts(C, l);
-  DevBuf dc((size_t)batch * nl * N, C.stream);
-  HEDAP_CUDA(cudaMemcpy2DAsync(dc.p, nl * N * 8, d, d_stride * 8, nl * N * 8, batch, cudaMemcpyDeviceToDevice,
-                               C.stream));
-  ntt_inverse(C.tab, qset(dc.p, nl * N, batch, 0, l + 1), C.stream);
+  DevBuf dc((size_t)batch * nl * N, C.stream);  // z_i = [x_i qhat_i^-1]_{q_i}, coefficient domain
+  NttAux inv{};
+  inv.src = d;
+  inv.src_stride = d_stride;
+  inv.post = LC.intt_post.p;
+  ntt_inverse(C.tab, qset(dc.p, nl * N, batch, 0, l + 1), C.stream, &inv);
   DevBuf y((size_t)batch * dn * ext * N, C.stream);
-  k_modup(C, dc.p, y.p, batch, l, LC.modup.p);
-  ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream);
+  NttAux up{};
+  up.own_alpha = C.alpha;
+  up.own_dn = dn;
+  up.own_limit = l + 1;
+  up.z = dc.p;
+  up.z_stride = nl * N;
+  up.bconv = LC.modup.p + 2 * nl;
+  up.bconv_sh_offset = (size_t)dn * C.alpha * ext;
+  up.ext = ext;
+  ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream, &up);
   DevBuf acc((size_t)batch * 2 * ext * N, C.stream);
-  k_ksk_inner(C, y.p, it->second.p, acc.p, batch, l);
+  k_ksk_inner(C, y.p, d, d_stride, it->second.p, acc.p, batch, l);
   ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream);
   DevBuf v((size_t)batch * 2 * nl * N, C.stream);
   k_moddown_spread(C, acc.p, v.p, 2 * batch, l);

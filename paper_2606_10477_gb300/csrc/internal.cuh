@@ -89,7 +89,7 @@ struct Tables {
   int ntt_fwd_variant;       // NTT launch shape (see ntt.cu), chosen by ntt_tune
   int ntt_inv_variant;
 };
-constexpr int kNttVariants = 6;
+constexpr int kNttVariants = 8;
 
 // A set of limbs: parts p in [0, n_parts), limbs li in [limb_begin, limb_begin+n_limbs)
 // at base + p*part_stride + li*N.  Limb li < q_count uses prime prime_offset+li,
@@ -111,8 +111,29 @@ struct LimbSet {
   }
 };
 
-void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st);
-void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st);
+// Optional fusions of one batched transform (value-initialised: a plain in-place transform).
+struct NttAux {
+  // out of place: the first phase reads limb li of part p at src + p * src_stride + li * N
+  const u64* src = nullptr;
+  size_t src_stride = 0;
+  // inverse only: the final factor of limb li is the pair post[2 li], post[2 li + 1] (value, Shoup
+  // companion) instead of N^-1
+  const u64* post = nullptr;
+  // skip the limbs li of digit j = part % own_dn, li in [j own_alpha, min((j + 1) own_alpha, own_limit))
+  int own_alpha = 0;
+  int own_dn = 1;
+  int own_limit = 0;
+  // forward only: the first phase loads the fast basis conversion of digit j into the prime of limb li,
+  //   sum_a z[k][j alpha + a] * bconv[j][a][li]  mod prime(li),  k = part / own_dn, alpha = own_alpha,
+  // from z (limb stride N, member stride z_stride) instead of reading limb li
+  const u64* z = nullptr;
+  size_t z_stride = 0;
+  const u64* bconv = nullptr;  // [dn][alpha][ext]; their Shoup companions at bconv + bconv_sh_offset
+  size_t bconv_sh_offset = 0;
+  int ext = 0;
+};
+void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
+void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
 struct Ctx;
 void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vector<float>* inv_ms);
 
@@ -144,8 +165,9 @@ struct RescaleConsts {
   u64 inv_sh[kMaxLimbs];
 };
 
-struct LevelConsts {  // device constants for one level (see keyswitch.cu / evaluator.cu)
-  DevBuf modup;       // qhat_inv (+shoup) per Q prime, qhat mod target per digit
+struct LevelConsts {  // device constants for one level (evaluator.cu)
+  DevBuf modup;       // qhat_inv (+shoup) per Q prime, qhat mod target per digit (+shoup)
+  DevBuf intt_post;   // per Q prime i <= l: N^-1 qhat_i^-1 mod q_i and its Shoup companion
   RescaleConsts rescale;
 };
 

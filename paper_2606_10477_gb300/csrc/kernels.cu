@@ -5,6 +5,8 @@
 // ciphertexts is 2B parts with one part stride (ciphertext k owns parts 2k, 2k+1).
 // Element kernels walk the flattened (part, limb, coefficient) space two
 // coefficients at a time with 128-bit loads and stores.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "kernels.cuh"
 #include "profiler.cuh"
@@ -259,63 +261,50 @@ void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const
   HEDAP_LAUNCH_CHECK();
 }
 
-// inner product with the switching key, reading each key word once for the whole batch:
+// inner product with the switching key:
 //   acc[k][0|1][t] = sum_j y[k][j][t] * key_j[b|a][t]
-// key layout: [dnum_max][2][n_q + n_p][N]; y: [B][dn][ext][N]; acc: [B][2][ext][N]
-template <int MAXB>
+// key layout: [dnum_max][2][n_q + n_p][N]; y: [B][dn][ext][N]; acc: [B][2][ext][N].
+// A digit's own limbs (t in digit j) are not in y: there the extended digit equals
+// the NTT-domain input itself, read from d ([B] members of stride ds, limbs of N).
+// One thread per (k, t, n): a CTA holds the batch members of the same coefficients
+// (threadIdx.y = k), so each key word comes from DRAM once and from L1 for the
+// other members; few registers per thread keep many loads in flight.
 __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s,
-                                   const u64* __restrict__ y, const u64* __restrict__ key, u64* __restrict__ acc,
-                                   int l, int dn, int n_q, int K, int batch, int log_n) {
+                                   const u64* __restrict__ y, const u64* __restrict__ d, size_t ds,
+                                   const u64* __restrict__ key, u64* __restrict__ acc, int l, int dn, int alpha,
+                                   int n_q, int K, int log_n) {
   const size_t N = (size_t)1 << log_n;
   const int ext = l + 1 + K, total_primes = n_q + K;
-  GRID_LOOP(e, (size_t)ext << log_n) {
-    const int t = (int)(e >> log_n);
-    const size_t n = e & (N - 1);
-    const int pt = t <= l ? t : n_q + (t - l - 1);
-    Acc128 s0[MAXB], s1[MAXB];
-#pragma unroll
-    for (int k = 0; k < MAXB; ++k) s0[k] = s1[k] = Acc128{0, 0};
-    for (int j = 0; j < dn; ++j) {
-      const u64* kj = key + (size_t)j * 2 * total_primes * N;
-      const u64 kb = kj[(size_t)pt * N + n], ka = kj[((size_t)total_primes + pt) * N + n];
-#pragma unroll
-      for (int k = 0; k < MAXB; ++k) {
-        if (k < batch) {
-          const u64 v = y[(((size_t)k * dn + j) * ext + t) * N + n];
-          mac128(s0[k], v, kb);
-          mac128(s1[k], v, ka);
-        }
-      }
-    }
-    const PrimeDev P = pr[pt];
-    const u64 r64 = r64s[2 * pt], r64p = r64s[2 * pt + 1];
-#pragma unroll
-    for (int k = 0; k < MAXB; ++k) {
-      if (k < batch) {
-        acc[(((size_t)k * 2) * ext + t) * N + n] = reduce128(s0[k], P, r64, r64p);
-        acc[(((size_t)k * 2 + 1) * ext + t) * N + n] = reduce128(s1[k], P, r64, r64p);
-      }
-    }
+  const int t = blockIdx.y, k = threadIdx.y;
+  const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int pt = t <= l ? t : n_q + (t - l - 1);
+  const int own = t <= l ? t / alpha : -1;
+  const u64* kb = key + (size_t)pt * N + n;
+  const u64* ka = key + ((size_t)total_primes + pt) * N + n;
+  const u64* yk = y + ((size_t)k * dn * ext + t) * N + n;
+  const size_t key_step = (size_t)2 * total_primes * N, y_step = (size_t)ext * N;
+  Acc128 s0{0, 0}, s1{0, 0};
+#pragma unroll 4
+  for (int j = 0; j < dn; ++j) {
+    const u64 v = j == own ? d[k * ds + (size_t)t * N + n] : yk[j * y_step];
+    mac128(s0, v, __ldg(kb + j * key_step));
+    mac128(s1, v, __ldg(ka + j * key_step));
   }
+  const PrimeDev P = pr[pt];
+  const u64 r64 = r64s[2 * pt], r64p = r64s[2 * pt + 1];
+  acc[(((size_t)k * 2) * ext + t) * N + n] = reduce128(s0, P, r64, r64p);
+  acc[(((size_t)k * 2 + 1) * ext + t) * N + n] = reduce128(s1, P, r64, r64p);
 }
-void k_ksk_inner(const Ctx& C, const u64* y, const u64* key, u64* acc, int batch, int level) {
+void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
+                 int level) {
   if (batch < 1 || batch > kMaxBatch) throw Error(HEDAP_ERR_ARG, "batch must lie in [1, 16]");
   const int dn = C.dnum(level), ext = level + 1 + C.n_p;
   ProfScope prof_(PROF_KSK_INNER, C.stream, ((double)batch * dn + 2.0 * dn + 2.0 * batch) * ext * C.N * 8);
   prof_count_launches(1);
-  const size_t work = (size_t)ext * C.N;
-  if (batch == 1)
-    k_ksk_inner_kernel<1><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level, dn,
-                                                                     C.n_q, C.n_p, batch, C.log_n);
-  else if (batch <= 4)
-    k_ksk_inner_kernel<4><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level, dn,
-                                                                     C.n_q, C.n_p, batch, C.log_n);
-  else if (batch <= 8)
-    k_ksk_inner_kernel<8><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level, dn,
-                                                                     C.n_q, C.n_p, batch, C.log_n);
-  else
-    k_ksk_inner_kernel<kMaxBatch><<<grid_for(work, 128), 128, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, key, acc, level,
-                                                                             dn, C.n_q, C.n_p, batch, C.log_n);
+  const unsigned tx = 32u * (unsigned)std::max(1, 8 / batch);  // about 256 threads per CTA
+  const dim3 block(tx, (unsigned)batch), grid((unsigned)(C.N / tx), (unsigned)ext);
+  k_ksk_inner_kernel<<<grid, block, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, d, d_stride, key, acc, level, dn, C.alpha,
+                                                   C.n_q, C.n_p, C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
 

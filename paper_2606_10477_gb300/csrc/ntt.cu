@@ -10,13 +10,18 @@
 // "columns" (rows of C consecutive words, coalesced) into shared memory and
 // runs those stages there; the last L2 stages couple only elements inside
 // blocks of 2^L2 consecutive words, so the second launch stages whole blocks.
-// Inside a launch every thread takes groups of 16 elements through four stages
-// in registers between shared-memory exchanges (two passes per 256-point
-// phase).  For a group with elements at c = high*2^(S+K) + m*2^S + low (or the
+// Inside a launch every thread takes groups of 2^RL elements through RL stages
+// in registers between shared-memory exchanges (RL = 4: two passes per
+// 256-point phase; RL = 3: three).  For a group with elements at c = high*2^(S+K) + m*2^S + low (or the
 // mirrored forward form), the twiddle of every butterfly has a closed-form index
 // in (high, m, u), so no per-element index arithmetic is needed.  Twiddles are
-// (w, floor(w 2^64 / q)) pairs read with one 16-byte load; the column phase's
-// 2^L1 distinct twiddles are staged in shared memory.  Butterflies keep residues
+// (w, floor(w 2^64 / q)) pairs read with one 16-byte load; every CTA stages the
+// twiddles it uses in shared memory with its data (the column phase's 2^L1, the
+// row phase's contiguous per-stage ranges for its blocks).  Optional fusions (NttAux):
+// the first phase may read another buffer (out of place) or compute its input as
+// the fast basis conversion of a key-switching digit (ModUp fused into the load),
+// the inverse may end with a per-limb factor other than N^-1, and a digit's own
+// limbs may be skipped.  Butterflies keep residues
 // lazily in [0, 4q) (forward) or [0, 2q) (inverse) following Harvey (2014);
 // the final launch writes canonical residues.
 #include "internal.cuh"
@@ -47,7 +52,18 @@ __device__ __forceinline__ u64 reduce4q(u64 x, u64 q) {
 }
 __device__ __forceinline__ ulonglong2 ldg2(const ulonglong2* p) { return __ldg(p); }
 
-constexpr int kRadixLog = 4;  // stages per register pass
+// RL: stages per register pass (radix 2^RL), a template parameter of every kernel
+
+// true when limb li of `part` is one of its digit's own limbs (skipped, see NttAux)
+__device__ __forceinline__ bool own_limb(const NttAux& A, int part, int li) {
+  if (!A.own_alpha) return false;
+  const int lo = (part % A.own_dn) * A.own_alpha;
+  return li >= lo && li < min(lo + A.own_alpha, A.own_limit);
+}
+// source of limb li of `part` for the first phase (in place unless A.src)
+__device__ __forceinline__ const u64* first_src(const NttAux& A, const LimbSet& S, int part, int li, size_t N) {
+  return A.src ? A.src + part * A.src_stride + (size_t)li * N : S.limb(part, li, N);
+}
 
 // shared-memory index of element x of a row block: one pad word every 16
 __device__ __forceinline__ uint32_t padx(uint32_t x) { return x + (x >> 4); }
@@ -55,10 +71,10 @@ __device__ __forceinline__ uint32_t padx(uint32_t x) { return x + (x >> 4); }
 // ---------------------------------------------------------------- forward, column phase
 // element (c, col) at sm[c * C + col]; global index j = r0 + col + c * 2^L2;
 // stage s couples c and c + 2^(L1-s-1); twiddle index 2^s + (c >> (L1 - s)).
-template <int L1, int C, int S0>
+template <int L1, int C, int RL, int S0>
 __device__ __forceinline__ void fwd_cols_passes(u64* sm, const ulonglong2* tw, u64 q) {
   if constexpr (S0 < L1) {
-    constexpr int K = (L1 - S0) < kRadixLog ? (L1 - S0) : kRadixLog;
+    constexpr int K = (L1 - S0) < RL ? (L1 - S0) : RL;
     constexpr int TL = 1 << (L1 - S0 - K);
     constexpr int GROUPS = C << (L1 - K);
     for (int g = threadIdx.x; g < GROUPS; g += blockDim.x) {
@@ -82,29 +98,62 @@ __device__ __forceinline__ void fwd_cols_passes(u64* sm, const ulonglong2* tw, u
       for (int m = 0; m < (1 << K); ++m) sm[(base + m * TL) * C + col] = v[m];
     }
     __syncthreads();
-    fwd_cols_passes<L1, C, S0 + K>(sm, tw, q);
+    fwd_cols_passes<L1, C, RL, S0 + K>(sm, tw, q);
   }
 }
 
-template <int L1, int L2, int C, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S) {
+template <int L1, int L2, int C, int TPB, int MINB, int RL>
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S, NttAux A) {
   extern __shared__ u64 sm[];
   constexpr size_t N = (size_t)1 << (L1 + L2);
   ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + (C << L1));
   const int y = blockIdx.y, part = y / S.n_limbs, li = S.limb_begin + y % S.n_limbs;
+  if (own_limb(A, part, li)) return;
   const int pi = S.prime(li);
   const u64 q = T.pr[pi].q;
   u64* a = S.limb(part, li, N);
   const ulonglong2* W = T.psi2 + (size_t)pi * N;
-  for (int i = threadIdx.x; i < (1 << L1); i += blockDim.x) tw[i] = ldg2(W + i);
+#pragma unroll
+  for (int i = threadIdx.x; i < (1 << L1); i += TPB) tw[i] = ldg2(W + i);
   const int r0 = blockIdx.x * C;
-  for (int idx = threadIdx.x; idx < (C << L1); idx += blockDim.x) {
-    const int c = idx / C, col = idx % C;
-    sm[idx] = a[((size_t)c << L2) + r0 + col];
+  if (A.z) {  // fused ModUp: fast basis conversion of digit j into this limb's prime
+    // sum of na <= 8 Shoup products, each in [0, 2q), brought into [0, 4q): the
+    // first butterflies accept any input below 4q
+    const int j = part % A.own_dn, lo = j * A.own_alpha, na = min(A.own_alpha, A.own_limit - lo);
+    const u64* zk = A.z + (size_t)(part / A.own_dn) * A.z_stride + (size_t)lo * N;
+    const u64* bc = A.bconv + (size_t)j * A.own_alpha * A.ext + li;
+    const u64* bcs = bc + A.bconv_sh_offset;
+    u64 f[8], fs[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      f[t] = t < na ? bc[(size_t)t * A.ext] : 0;
+      fs[t] = t < na ? bcs[(size_t)t * A.ext] : 0;
+    }
+    const u64 q4 = q << 2, q8 = q << 3;
+#pragma unroll
+    for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
+      const int c = idx / C, col = idx % C;
+      const size_t n = ((size_t)c << L2) + r0 + col;
+      u64 v = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < na) v += shoup_mul_lazy(zk[(size_t)t * N + n], f[t], fs[t], q);
+      if (v >= q8) v -= q8;
+      if (v >= q4) v -= q4;
+      sm[idx] = v;
+    }
+  } else {
+    const u64* src = first_src(A, S, part, li, N);
+#pragma unroll
+    for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
+      const int c = idx / C, col = idx % C;
+      sm[idx] = src[((size_t)c << L2) + r0 + col];
+    }
   }
   __syncthreads();
-  fwd_cols_passes<L1, C, 0>(sm, tw, q);
-  for (int idx = threadIdx.x; idx < (C << L1); idx += blockDim.x) {
+  fwd_cols_passes<L1, C, RL, 0>(sm, tw, q);
+#pragma unroll
+  for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
     const int c = idx / C, col = idx % C;
     a[((size_t)c << L2) + r0 + col] = sm[idx];
   }
@@ -113,10 +162,23 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S)
 // ---------------------------------------------------------------- forward, block phase
 // block b, local x at sm[b * R + padx(x)]; j = (B0 + b) * 2^L2 + x; local stage s'
 // couples x and x + 2^(L2-s'-1); twiddle index 2^(L1+s') + ((B0+b) << s') + (x >> (L2 - s')).
-template <int L1, int L2, int BPC, int S0>
-__device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* W, u64 q, uint32_t B0) {
+// For the CTA's blocks B0 .. B0+BPC-1 the twiddles of stage s' are the contiguous
+// range starting at 2^(L1+s') + (B0 << s') of BPC 2^s' entries; they are staged in
+// shared memory one stage after another (stage s' at offset BPC (2^s' - 1)), so
+// twiddle (b, s', r) sits at tw[BPC (2^s' - 1) + (b << s') + r].
+template <int L1, int L2, int BPC, int TPB>
+__device__ __forceinline__ void fwd_rows_stage_twiddles(ulonglong2* tw, const ulonglong2* W, uint32_t B0) {
+#pragma unroll
+  for (int sl = 0; sl < L2; ++sl) {
+    const ulonglong2* src = W + (1u << (L1 + sl)) + (B0 << sl);
+    ulonglong2* dst = tw + BPC * ((1 << sl) - 1);
+    for (int i = threadIdx.x; i < (BPC << sl); i += TPB) dst[i] = ldg2(src + i);
+  }
+}
+template <int L1, int L2, int BPC, int RL, int S0>
+__device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* tw, u64 q) {
   if constexpr (S0 < L2) {
-    constexpr int K = (L2 - S0) < kRadixLog ? (L2 - S0) : kRadixLog;
+    constexpr int K = (L2 - S0) < RL ? (L2 - S0) : RL;
     constexpr int TL = 1 << (L2 - S0 - K);
     constexpr int GPB = 1 << (L2 - K);
     constexpr int R = (1 << L2) + (1 << (L2 - 4));
@@ -125,7 +187,6 @@ __device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* W, u6
       const uint32_t low = gg & (TL - 1), high = gg >> (L2 - S0 - K);
       const uint32_t base = (high << (L2 - S0)) | low;
       u64* blk = sm + b * R;
-      const uint32_t bb = B0 + b;
       u64 v[1 << K];
 #pragma unroll
       for (int m = 0; m < (1 << K); ++m) v[m] = blk[padx(base + m * TL)];
@@ -135,43 +196,58 @@ __device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* W, u6
 #pragma unroll
         for (int m1 = 0; m1 < (1 << K); ++m1) {
           if (m1 & half) continue;
-          const uint32_t wi = (1u << (L1 + sl)) + (bb << sl) + (high << u) + (m1 >> (K - u));
-          ct_bfly(v[m1], v[m1 + half], ldg2(W + wi), q);
+          const uint32_t wi = BPC * ((1u << sl) - 1) + (b << sl) + (high << u) + (m1 >> (K - u));
+          ct_bfly(v[m1], v[m1 + half], tw[wi], q);
         }
       }
 #pragma unroll
       for (int m = 0; m < (1 << K); ++m) blk[padx(base + m * TL)] = v[m];
     }
     __syncthreads();
-    fwd_rows_passes<L1, L2, BPC, S0 + K>(sm, W, q, B0);
+    fwd_rows_passes<L1, L2, BPC, RL, S0 + K>(sm, tw, q);
   }
 }
 
-template <int L1, int L2, int BPC, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S) {
+template <int L1, int L2, int BPC, int TPB, int MINB, int RL>
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S, NttAux A) {
   extern __shared__ u64 sm[];
   constexpr size_t N = (size_t)1 << (L1 + L2);
   constexpr int E = BPC << L2, R = (1 << L2) + (1 << (L2 - 4));
   const int y = blockIdx.y, part = y / S.n_limbs, li = S.limb_begin + y % S.n_limbs;
+  if (own_limb(A, part, li)) return;
   const int pi = S.prime(li);
   const u64 q = T.pr[pi].q;
   u64* a = S.limb(part, li, N);
+  ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + BPC * R);
   const size_t j0 = (size_t)blockIdx.x * E;
-  for (int idx = threadIdx.x; idx < E; idx += blockDim.x) sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))] = a[j0 + idx];
+#pragma unroll
+  for (int idx = threadIdx.x; idx < E; idx += TPB) sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))] = a[j0 + idx];
+  fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
   __syncthreads();
-  fwd_rows_passes<L1, L2, BPC, 0>(sm, T.psi2 + (size_t)pi * N, q, (uint32_t)(blockIdx.x * BPC));
-  for (int idx = threadIdx.x; idx < E; idx += blockDim.x)
+  fwd_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
+#pragma unroll
+  for (int idx = threadIdx.x; idx < E; idx += TPB)
     a[j0 + idx] = reduce4q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
 }
 
 // ---------------------------------------------------------------- inverse, block phase
 // GS stage with pair distance 2^lt (lt < L2): twiddle index 2^(LOGN-lt-1) + (j >> (lt+1)),
 // j >> (lt+1) = ((B0+b) << (L2-lt-1)) + (x >> (lt+1)); groups x = high*2^(LT0+K) + m*2^LT0 + low.
-template <int L1, int L2, int BPC, int LT0>
-__device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* W, u64 q, uint32_t B0) {
+// Staged like the forward phase: stage lt's range starts at 2^(LOGN-lt-1) + (B0 << (L2-lt-1))
+// with BPC 2^(L2-lt-1) entries, at offset BPC (2^L2 - 2^(L2-lt)) in shared memory.
+template <int L1, int L2, int BPC, int TPB>
+__device__ __forceinline__ void inv_rows_stage_twiddles(ulonglong2* tw, const ulonglong2* W, uint32_t B0) {
+#pragma unroll
+  for (int lt = 0; lt < L2; ++lt) {
+    const ulonglong2* src = W + (1u << (L1 + L2 - lt - 1)) + (B0 << (L2 - lt - 1));
+    ulonglong2* dst = tw + BPC * ((1 << L2) - (1 << (L2 - lt)));
+    for (int i = threadIdx.x; i < (BPC << (L2 - lt - 1)); i += TPB) dst[i] = ldg2(src + i);
+  }
+}
+template <int L1, int L2, int BPC, int RL, int LT0>
+__device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* tw, u64 q) {
   if constexpr (LT0 < L2) {
-    constexpr int K = (L2 - LT0) < kRadixLog ? (L2 - LT0) : kRadixLog;
-    constexpr int LOGN = L1 + L2;
+    constexpr int K = (L2 - LT0) < RL ? (L2 - LT0) : RL;
     constexpr int GPB = 1 << (L2 - K);
     constexpr int R = (1 << L2) + (1 << (L2 - 4));
     for (int g = threadIdx.x; g < BPC * GPB; g += blockDim.x) {
@@ -179,7 +255,6 @@ __device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* W, u6
       const uint32_t low = gg & ((1u << LT0) - 1), high = gg >> LT0;
       const uint32_t base = (high << (LT0 + K)) | low;
       u64* blk = sm + b * R;
-      const uint32_t bb = B0 + b;
       u64 v[1 << K];
 #pragma unroll
       for (int m = 0; m < (1 << K); ++m) v[m] = blk[padx(base + (m << LT0))];
@@ -189,41 +264,48 @@ __device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* W, u6
 #pragma unroll
         for (int m1 = 0; m1 < (1 << K); ++m1) {
           if (m1 & half) continue;
-          const uint32_t wi = (1u << (LOGN - lt - 1)) + (bb << (L2 - lt - 1)) + (high << (K - u - 1)) + (m1 >> (u + 1));
-          gs_bfly(v[m1], v[m1 + half], ldg2(W + wi), q);
+          const uint32_t wi = BPC * ((1u << L2) - (1u << (L2 - lt))) + (b << (L2 - lt - 1)) + (high << (K - u - 1)) +
+                              (m1 >> (u + 1));
+          gs_bfly(v[m1], v[m1 + half], tw[wi], q);
         }
       }
 #pragma unroll
       for (int m = 0; m < (1 << K); ++m) blk[padx(base + (m << LT0))] = v[m];
     }
     __syncthreads();
-    inv_rows_passes<L1, L2, BPC, LT0 + K>(sm, W, q, B0);
+    inv_rows_passes<L1, L2, BPC, RL, LT0 + K>(sm, tw, q);
   }
 }
 
-template <int L1, int L2, int BPC, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_rows(Tables T, LimbSet S) {
+template <int L1, int L2, int BPC, int TPB, int MINB, int RL>
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_rows(Tables T, LimbSet S, NttAux A) {
   extern __shared__ u64 sm[];
   constexpr size_t N = (size_t)1 << (L1 + L2);
   constexpr int E = BPC << L2, R = (1 << L2) + (1 << (L2 - 4));
   const int y = blockIdx.y, part = y / S.n_limbs, li = S.limb_begin + y % S.n_limbs;
+  if (own_limb(A, part, li)) return;
   const int pi = S.prime(li);
   const u64 q = T.pr[pi].q;
   u64* a = S.limb(part, li, N);
+  const u64* src = first_src(A, S, part, li, N);
+  ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + BPC * R);
   const size_t j0 = (size_t)blockIdx.x * E;
-  for (int idx = threadIdx.x; idx < E; idx += blockDim.x) sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))] = a[j0 + idx];
+#pragma unroll
+  for (int idx = threadIdx.x; idx < E; idx += TPB) sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))] = src[j0 + idx];
+  inv_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.ipsi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
   __syncthreads();
-  inv_rows_passes<L1, L2, BPC, 0>(sm, T.ipsi2 + (size_t)pi * N, q, (uint32_t)(blockIdx.x * BPC));
-  for (int idx = threadIdx.x; idx < E; idx += blockDim.x)
+  inv_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
+#pragma unroll
+  for (int idx = threadIdx.x; idx < E; idx += TPB)
     a[j0 + idx] = sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))];  // [0, 2q)
 }
 
 // ---------------------------------------------------------------- inverse, column phase (+ N^-1)
 // column distance 2^lc (lt = L2 + lc): twiddle index 2^(L1-lc-1) + (c >> (lc+1)) < 2^L1
-template <int L1, int C, int LC0>
+template <int L1, int C, int RL, int LC0>
 __device__ __forceinline__ void inv_cols_passes(u64* sm, const ulonglong2* tw, u64 q) {
   if constexpr (LC0 < L1) {
-    constexpr int K = (L1 - LC0) < kRadixLog ? (L1 - LC0) : kRadixLog;
+    constexpr int K = (L1 - LC0) < RL ? (L1 - LC0) : RL;
     constexpr int GROUPS = C << (L1 - K);
     for (int g = threadIdx.x; g < GROUPS; g += blockDim.x) {
       const uint32_t col = g % C, gg = g / C;
@@ -246,106 +328,129 @@ __device__ __forceinline__ void inv_cols_passes(u64* sm, const ulonglong2* tw, u
       for (int m = 0; m < (1 << K); ++m) sm[(base + (m << LC0)) * C + col] = v[m];
     }
     __syncthreads();
-    inv_cols_passes<L1, C, LC0 + K>(sm, tw, q);
+    inv_cols_passes<L1, C, RL, LC0 + K>(sm, tw, q);
   }
 }
 
-template <int L1, int L2, int C, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S) {
+template <int L1, int L2, int C, int TPB, int MINB, int RL>
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S, NttAux A) {
   extern __shared__ u64 sm[];
   constexpr size_t N = (size_t)1 << (L1 + L2);
   ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + (C << L1));
   const int y = blockIdx.y, part = y / S.n_limbs, li = S.limb_begin + y % S.n_limbs;
+  if (own_limb(A, part, li)) return;
   const int pi = S.prime(li);
   const u64 q = T.pr[pi].q;
   u64* a = S.limb(part, li, N);
   const ulonglong2* W = T.ipsi2 + (size_t)pi * N;
-  for (int i = threadIdx.x; i < (1 << L1); i += blockDim.x) tw[i] = ldg2(W + i);
+#pragma unroll
+  for (int i = threadIdx.x; i < (1 << L1); i += TPB) tw[i] = ldg2(W + i);
   const int r0 = blockIdx.x * C;
-  for (int idx = threadIdx.x; idx < (C << L1); idx += blockDim.x) {
+#pragma unroll
+  for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
     const int c = idx / C, col = idx % C;
     sm[idx] = a[((size_t)c << L2) + r0 + col];
   }
   __syncthreads();
-  inv_cols_passes<L1, C, 0>(sm, tw, q);
-  const u64 ni = T.ninv[pi], nip = T.ninv_sh[pi];
-  for (int idx = threadIdx.x; idx < (C << L1); idx += blockDim.x) {
+  inv_cols_passes<L1, C, RL, 0>(sm, tw, q);
+  const u64 ni = A.post ? A.post[2 * li] : T.ninv[pi], nip = A.post ? A.post[2 * li + 1] : T.ninv_sh[pi];
+#pragma unroll
+  for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
     const int c = idx / C, col = idx % C;
     a[((size_t)c << L2) + r0 + col] = shoup_mul(sm[idx], ni, nip, q);
   }
 }
 
 // ---------------------------------------------------------------- dispatch
-// A variant fixes the words staged per CTA (E) and the CTAs per SM the register
-// allocation must allow (MINB); threads per CTA = E / 16.  The autotuner in
+// A variant fixes the words staged per CTA (E), the CTAs per SM the register
+// allocation must allow (MINB) and the stages per register pass (RL: radix 16 or
+// radix 8, the latter with half the registers per thread); threads per CTA = E / 2^RL.  The autotuner in
 // ntt_tune() times every variant and keeps the fastest per direction.
-template <int L1, int L2, int E, int MINB>
-static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse) {
+template <int L1, int L2, int E, int MINB, int RL>
+static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse, const NttAux& A) {
   constexpr int LOGN = L1 + L2;
   constexpr int EE = E <= (1 << LOGN) ? E : (1 << LOGN);
-  constexpr int C = EE >> L1, BPC = EE >> L2, TPB = EE / 16;
+  constexpr int C = EE >> L1, BPC = EE >> L2, TPB = EE >> RL;
   const dim3 grid((unsigned)(((size_t)1 << LOGN) / EE), (unsigned)(S.n_parts * S.n_limbs));
   const size_t smem_cols = (size_t)EE * sizeof(u64) + ((size_t)1 << L1) * sizeof(ulonglong2);
-  const size_t smem_rows = (size_t)BPC * ((1 << L2) + (1 << (L2 - 4))) * sizeof(u64);
+  const size_t smem_rows =
+      (size_t)BPC * ((1 << L2) + (1 << (L2 - 4))) * sizeof(u64) + (size_t)BPC * (1 << L2) * sizeof(ulonglong2);
   if (grid.y == 0) return;
   static const bool attrs = [&] {  // opt in to more than 48 KB of dynamic shared memory, once per shape
     if (smem_cols > 48 * 1024) {
-      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols<L1, L2, C, TPB, MINB>,
+      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols));
-      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_inv_cols<L1, L2, C, TPB, MINB>,
+      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_inv_cols<L1, L2, C, TPB, MINB, RL>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols));
     }
     if (smem_rows > 48 * 1024) {
-      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB>,
+      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows));
-      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_inv_rows<L1, L2, BPC, TPB, MINB>,
+      HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_inv_rows<L1, L2, BPC, TPB, MINB, RL>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows));
     }
     return true;
   }();
   (void)attrs;
+  // the first phase applies src / z; the second runs in place on S
+  NttAux A2 = A;
+  A2.src = nullptr;
+  A2.z = nullptr;
   if (!inverse) {
-    k_ntt_fwd_cols<L1, L2, C, TPB, MINB><<<grid, TPB, smem_cols, st>>>(T, S);
-    k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB><<<grid, TPB, smem_rows, st>>>(T, S);
+    k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
+    k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A2);
   } else {
-    k_ntt_inv_rows<L1, L2, BPC, TPB, MINB><<<grid, TPB, smem_rows, st>>>(T, S);
-    k_ntt_inv_cols<L1, L2, C, TPB, MINB><<<grid, TPB, smem_cols, st>>>(T, S);
+    k_ntt_inv_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A);
+    k_ntt_inv_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A2);
   }
   HEDAP_LAUNCH_CHECK();
 }
 
 template <int L1, int L2>
-static void launch_variant(int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse) {
+static void launch_variant(int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
+                           const NttAux& A) {
   switch (v) {
-    case 0: launch_pair<L1, L2, 4096, 1>(S, T, st, inverse); break;
-    case 1: launch_pair<L1, L2, 4096, 3>(S, T, st, inverse); break;
-    case 2: launch_pair<L1, L2, 2048, 4>(S, T, st, inverse); break;
-    case 3: launch_pair<L1, L2, 2048, 6>(S, T, st, inverse); break;
-    case 4: launch_pair<L1, L2, 8192, 1>(S, T, st, inverse); break;
-    default: launch_pair<L1, L2, 1024, 8>(S, T, st, inverse); break;
+    case 0: launch_pair<L1, L2, 4096, 1, 4>(S, T, st, inverse, A); break;
+    case 1: launch_pair<L1, L2, 4096, 3, 4>(S, T, st, inverse, A); break;
+    case 2: launch_pair<L1, L2, 2048, 4, 4>(S, T, st, inverse, A); break;
+    case 3: launch_pair<L1, L2, 2048, 6, 4>(S, T, st, inverse, A); break;
+    case 4: launch_pair<L1, L2, 8192, 1, 4>(S, T, st, inverse, A); break;
+    case 5: launch_pair<L1, L2, 1024, 8, 4>(S, T, st, inverse, A); break;
+    case 6: launch_pair<L1, L2, 2048, 4, 3>(S, T, st, inverse, A); break;
+    default: launch_pair<L1, L2, 1024, 8, 3>(S, T, st, inverse, A); break;
   }
 }
 
-static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool inverse) {
+static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool inverse, const NttAux* aux) {
   if (S.n_parts * S.n_limbs == 0) return;
+  const NttAux A = aux ? *aux : NttAux{};
+  if (A.own_alpha && (A.own_dn < 1 || A.own_alpha > 8)) throw Error(HEDAP_ERR_ARG, "NTT: bad digit layout");
+  if (A.z && (inverse || !A.own_alpha || !A.bconv || !A.bconv_sh_offset)) throw Error(HEDAP_ERR_ARG, "NTT: bad ModUp fusion");
+  if (A.post && !inverse) throw Error(HEDAP_ERR_ARG, "NTT: post factors apply to the inverse only");
   const int v = inverse ? T.ntt_inv_variant : T.ntt_fwd_variant;
-  ProfScope prof_(PROF_NTT, st, 16.0 * S.n_parts * S.n_limbs * ((size_t)1 << T.log_n));
+  // algorithmic bytes: each transformed limb read once and written once (a digit's own limbs are skipped)
+  const double limbs = (double)S.n_parts * S.n_limbs - (A.own_alpha ? (double)S.n_parts / A.own_dn * A.own_limit : 0.0);
+  ProfScope prof_(PROF_NTT, st, 16.0 * limbs * ((size_t)1 << T.log_n));
   prof_count_launches(2);
   switch (T.log_n) {
-    case 10: launch_variant<5, 5>(v, S, T, st, inverse); break;
-    case 11: launch_variant<5, 6>(v, S, T, st, inverse); break;
-    case 12: launch_variant<6, 6>(v, S, T, st, inverse); break;
-    case 13: launch_variant<6, 7>(v, S, T, st, inverse); break;
-    case 14: launch_variant<7, 7>(v, S, T, st, inverse); break;
-    case 15: launch_variant<7, 8>(v, S, T, st, inverse); break;
-    case 16: launch_variant<8, 8>(v, S, T, st, inverse); break;
-    case 17: launch_variant<8, 9>(v, S, T, st, inverse); break;
+    case 10: launch_variant<5, 5>(v, S, T, st, inverse, A); break;
+    case 11: launch_variant<5, 6>(v, S, T, st, inverse, A); break;
+    case 12: launch_variant<6, 6>(v, S, T, st, inverse, A); break;
+    case 13: launch_variant<6, 7>(v, S, T, st, inverse, A); break;
+    case 14: launch_variant<7, 7>(v, S, T, st, inverse, A); break;
+    case 15: launch_variant<7, 8>(v, S, T, st, inverse, A); break;
+    case 16: launch_variant<8, 8>(v, S, T, st, inverse, A); break;
+    case 17: launch_variant<8, 9>(v, S, T, st, inverse, A); break;
     default: throw Error(HEDAP_ERR_ARG, "log_n must lie in [10, 17]");
   }
 }
 
-void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st) { dispatch(T, S, st, false); }
-void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st) { dispatch(T, S, st, true); }
+void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux) {
+  dispatch(T, S, st, false, aux);
+}
+void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux) {
+  dispatch(T, S, st, true, aux);
+}
 
 // Time every variant on `limbs` limbs of scratch (forward and inverse separately,
 // best of `reps` after one warm-up) and keep the fastest in C.tab.
@@ -366,7 +471,7 @@ void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vect
       float ms = 1e30f;
       for (int r = 0; r <= reps; ++r) {
         HEDAP_CUDA(cudaEventRecord(a, C.stream));
-        dispatch(T, S, C.stream, dir == 1);
+        dispatch(T, S, C.stream, dir == 1, nullptr);
         HEDAP_CUDA(cudaEventRecord(b, C.stream));
         HEDAP_CUDA(cudaEventSynchronize(b));
         float t = 0;

@@ -315,7 +315,7 @@ class Context:
         f, i = (C.c_float * 16)(), (C.c_float * 16)()
         fv, iv = C.c_int(), C.c_int()
         _check(load().hedap_ntt_tune(self.h, limbs, reps, f, i, 16, C.byref(fv), C.byref(iv)))
-        n = 6
+        n = 8
         return list(f[:n]), list(i[:n]), fv.value, iv.value
 
     def ntt_set_variant(self, fwd: int, inv: int):
