@@ -21,9 +21,45 @@ struct PrimeDev {  // per-prime constants used by the kernels
   int pad;
 };
 
+// x * w - floor(x * wp / 2^64) * q  mod 2^64, in [0, 2q), from 32-bit pieces:
+// the high half of x * wp in four wide multiply-adds (every partial sum fits in
+// 64 bits, so it is exact), then x * w + qh * (2^64 - q) mod 2^64 in two wide
+// and four low multiply-adds.
 __device__ __forceinline__ u64 shoup_mul_lazy(u64 x, u64 w, u64 wp, u64 q) {
-  u64 qh = __umul64hi(x, wp);
-  return x * w - qh * q;  // in [0, 2q)
+  const u64 nq = 0 - q;
+  u64 r;
+  asm("{\n\t"
+      ".reg .u32 x0, x1, a0, a1, b0, b1, n0, n1, h0, h1, r0, r1;\n\t"
+      ".reg .u64 p, t, u, v, qh;\n\t"
+      "mov.b64 {x0, x1}, %1;\n\t"
+      "mov.b64 {b0, b1}, %3;\n\t"
+      "mul.wide.u32 p, x0, b0;\n\t"
+      "mov.b64 {h0, h1}, p;\n\t"
+      "cvt.u64.u32 t, h1;\n\t"
+      "mad.wide.u32 t, x0, b1, t;\n\t"
+      "mov.b64 {h0, h1}, t;\n\t"
+      "cvt.u64.u32 u, h0;\n\t"
+      "mad.wide.u32 u, x1, b0, u;\n\t"
+      "cvt.u64.u32 v, h1;\n\t"
+      "mad.wide.u32 v, x1, b1, v;\n\t"
+      "mov.b64 {h0, h1}, u;\n\t"
+      "cvt.u64.u32 qh, h1;\n\t"
+      "add.u64 qh, v, qh;\n\t"
+      "mov.b64 {a0, a1}, %2;\n\t"
+      "mov.b64 {n0, n1}, %4;\n\t"
+      "mov.b64 {h0, h1}, qh;\n\t"
+      "mul.wide.u32 p, a0, x0;\n\t"
+      "mad.wide.u32 p, h0, n0, p;\n\t"
+      "mov.b64 {r0, r1}, p;\n\t"
+      "mad.lo.u32 r1, a0, x1, r1;\n\t"
+      "mad.lo.u32 r1, a1, x0, r1;\n\t"
+      "mad.lo.u32 r1, h0, n1, r1;\n\t"
+      "mad.lo.u32 r1, h1, n0, r1;\n\t"
+      "mov.b64 %0, {r0, r1};\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(x), "l"(w), "l"(wp), "l"(nq));
+  return r;
 }
 __device__ __forceinline__ u64 shoup_mul(u64 x, u64 w, u64 wp, u64 q) {
   u64 r = shoup_mul_lazy(x, w, wp, q);
