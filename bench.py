@@ -5,10 +5,12 @@ of 8 resident ciphertexts (N = 2^16, 32768 slots, 24 x 50-bit Q primes + 2 x
 60-bit P primes, two primes per key-switching digit, scale 2^50, inputs
 uniform in [1e-3, 1]) with a (degree, Newton steps) pair whose decrypted MRE
 is at most 1e-7.  `value` is the batched path (the 8 ciphertexts packed into
-one batch, one launch sequence); `plain` is the same work one ciphertext per
-call sequence.  `bootstrapped` times CryptoInvSqrt with bootstrapping inside
-the Newton loop (N = 2^16, log2(QP) = 1555, inputs log-uniform in [1e-4, 1]).
-Prints one JSON line.
+one batch, one launch sequence, replayed from a CUDA graph; `eager` is the same
+sequence launched kernel by kernel); `plain` is the same work one ciphertext
+per call sequence.  `bootstrapped` times CryptoInvSqrt with bootstrapping
+inside the Newton loop (N = 2^16, log2(QP) = 1555, inputs log-uniform in
+[1e-4, 1]); `serving` runs Poisson arrivals of encrypted z-score / correlation
+queries through the serving loop.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -213,24 +215,41 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps on resident inputs
+    # ---- timed region: K steps on resident inputs, each one replay of the batched step captured
+    # as a CUDA graph (the same launch sequence as step(), bit for bit)
+    graph_b = ctx.invsqrt_graph(packed, LO, HI, B, args.degree, args.iters)
+    for _ in range(args.warmup):
+        graph_b.run(want_output=False)
+    torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    launches0 = hedap.launch_count()
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        graph_b.run(want_output=False)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     elapsed_ms = e0.elapsed_time(e1)
-    launches = hedap.launch_count() - launches0
+    launches = graph_b.kernels * args.steps
     clk = clocks.stop()
     value, tmax_s, _ = replicas.aggregate(batch * args.steps, elapsed_ms / 1e3,
                                           torch.distributed if ws > 1 else None)
     elapsed_ms = tmax_s * 1e3
+    graph_kernels = graph_b.kernels
+    graph_b.close()
+
+    # ---- the same batched step launched kernel by kernel (no graph)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = hedap.launch_count()
+    t0e.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    eager_value = batch * args.steps / (t0e.elapsed_time(t1e) / 1e3)
+    eager_launches = (hedap.launch_count() - launches0) / args.steps
 
     # ---- the plain path, same work and timing
     step_plain()
@@ -242,6 +261,24 @@ def run_ours(args):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_value = batch * max(1, min(args.steps, 3)) / (p0.elapsed_time(p1) / 1e3)
+
+    # ---- one ciphertext per replay of a graph captured for a single ciphertext
+    graph_1 = ctx.invsqrt_graph(cts[0], LO, HI, B, args.degree, args.iters)
+    for _ in range(2):
+        graph_1.run(cts[0], want_output=False)
+    torch.cuda.synchronize()
+    g_lat = []
+    for c in cts:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph_1.run(c, want_output=False)
+        b.record(stream)
+        b.synchronize()
+        g_lat.append(a.elapsed_time(b))
+    graph_info = {"plain_ms_p50": float(np.percentile(g_lat, 50)), "plain_value": 1e3 / float(np.mean(g_lat)),
+                  "unit": UNIT, "kernels_per_replay_batched": graph_kernels,
+                  "kernels_per_replay_plain": graph_1.kernels}
+    graph_1.close()
 
     # ---- per-ciphertext latency (plain path: one ciphertext per call sequence)
     lat = []
@@ -332,8 +369,12 @@ def run_ours(args):
                                     "us_per_group": 1e3 * v[1] / v[0], "algorithmic_gbs": v[2] / (v[1] / 1e3) / 1e9}
                                 for k, v in prof.items() if v[0] > 0},
             "cpu_baseline": cpu,
+            "execution": "each timed step is one replay of the batched InvSqrt launch sequence captured as a "
+                         "CUDA graph (hedap_graph_run); eager = the same sequence launched kernel by kernel",
+            "eager": {"value": eager_value, "unit": UNIT, "kernels_per_step": eager_launches},
             "plain": {"value": plain_value, "unit": UNIT, "ms_per_ct": 1e3 / plain_value,
                       "speedup_batched_vs_plain": value / plain_value},
+            "graph": graph_info,
             "bootstrapped": bts,
             "serving": serving,
         }

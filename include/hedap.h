@@ -358,6 +358,24 @@ hedap_status hedap_server_estimate(const hedap_server* s, uint32_t kind, uint32_
 hedap_status hedap_server_stats(hedap_server* s, double* p50_ms, double* p99_ms, double* qps, uint64_t* completed);
 void hedap_server_destroy(hedap_server* s);
 
+/* CryptoInvSqrt as a CUDA graph (no counterpart in the paper: a launch-overhead
+ * optimisation).  hedap_invsqrt_graph_create runs InvSqrt once on a copy of
+ * `example` (building every table the sequence needs) and captures the launch
+ * sequence for that input level, batch and scale and that configuration; the
+ * graph owns its input and output buffers.  Profiling must be off.
+ * hedap_graph_run: copies `in` (if not NULL; same level, batch and scale as the
+ * example, else HEDAP_ERR_ARG) into the graph's input, replays the graph on the
+ * context's stream, and (if out is not NULL) returns a new ciphertext holding the
+ * result, the same as hedap_invsqrt bit for bit.  Calls on the graph serialise
+ * with other calls on its context.  hedap_graph_kernels: kernels one replay
+ * launches.  Destroy the graph before its context. */
+typedef struct hedap_graph hedap_graph;
+hedap_status hedap_invsqrt_graph_create(hedap_ctx* ctx, const hedap_ct* example, const hedap_invsqrt_cfg* cfg,
+                                        hedap_graph** out);
+hedap_status hedap_graph_run(hedap_graph* g, const hedap_ct* in, hedap_ct** out);
+hedap_status hedap_graph_kernels(const hedap_graph* g, uint64_t* n);
+void hedap_graph_destroy(hedap_graph* g);
+
 /* NTT autotuner: times every NTT launch shape (words staged per CTA, CTAs per
  * SM, radix 16 or 8 register passes) on `limbs` limbs of scratch, forward and inverse separately (best of
  * `reps`), and makes the fastest the context's shape.  Per-variant times go

@@ -51,6 +51,7 @@ void drain() {  // caller holds g_mu
 void prof_count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 uint64_t prof_launches() { return g_launches.load(); }
 void prof_enable(bool on) { g_on.store(on); }
+bool prof_enabled() { return g_on.load(); }
 void prof_reset() {
   std::lock_guard<std::mutex> lk(g_mu);
   drain();

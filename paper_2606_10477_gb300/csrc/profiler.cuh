@@ -14,6 +14,7 @@ enum ProfClass { PROF_NTT = 0, PROF_MODUP, PROF_KSK_INNER, PROF_MODDOWN, PROF_TE
 void prof_count_launches(int n);
 uint64_t prof_launches();
 void prof_enable(bool on);
+bool prof_enabled();
 void prof_reset();
 // sum of event-timed milliseconds, enclosed launches and algorithmic bytes of a class (synchronises)
 void prof_read(int cls, uint64_t* scopes, double* ms, double* bytes);

@@ -33,7 +33,8 @@ EXPORTED = [
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_ntt_batch",
     "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
-    "hedap_server_resume", "hedap_server_estimate",
+    "hedap_server_resume", "hedap_server_estimate", "hedap_invsqrt_graph_create", "hedap_graph_run",
+    "hedap_graph_kernels", "hedap_graph_destroy",
 ]
 
 
@@ -177,6 +178,10 @@ def _declare(L):
         "hedap_server_poll": (st, [vp, C.c_uint64, C.c_int, C.POINTER(C.c_int), pp, C.c_size_t,
                                    C.POINTER(C.c_size_t), dp, C.POINTER(C.c_uint32)]),
         "hedap_server_resume": (st, [vp]),
+        "hedap_invsqrt_graph_create": (st, [vp, vp, C.POINTER(InvSqrtCfg), pp]),
+        "hedap_graph_run": (st, [vp, vp, pp]),
+        "hedap_graph_kernels": (st, [vp, u64p]),
+        "hedap_graph_destroy": (None, [vp]),
         "hedap_server_estimate": (st, [vp, C.c_uint32, C.c_uint32, C.c_int, u64p]),
         "hedap_server_stats": (st, [vp, dp, dp, dp, u64p]),
         "hedap_server_destroy": (None, [vp]),
@@ -453,6 +458,13 @@ class Context:
         cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask)
         return self._ct(load().hedap_invsqrt, a.h, C.byref(cfg))
 
+    def invsqrt_graph(self, example, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0) -> "Graph":
+        """CryptoInvSqrt captured as a CUDA graph for the example's level, batch and scale."""
+        cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask)
+        h = C.c_void_p()
+        _check(load().hedap_invsqrt_graph_create(self.h, example.h, C.byref(cfg), C.byref(h)))
+        return Graph(self, h)
+
     # ---- batches
     def pack(self, cts) -> Ciphertext:
         arr = (C.c_void_p * len(cts))(*[c.h for c in cts])
@@ -484,6 +496,36 @@ class Context:
 
 
 PROFILE_CLASSES = ("ntt", "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph", "elementwise")
+
+
+class Graph:
+    """A captured CryptoInvSqrt (see Context.invsqrt_graph)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.h = handle
+
+    def run(self, a=None, want_output=True):
+        """Replay on `a` (or on the previous input); returns the result ciphertext or None."""
+        out = C.c_void_p()
+        _check(load().hedap_graph_run(self.h, a.h if a is not None else None,
+                                      C.byref(out) if want_output else None))
+        return Ciphertext(self.ctx, out) if want_output else None
+
+    @property
+    def kernels(self) -> int:
+        n = C.c_uint64()
+        _check(load().hedap_graph_kernels(self.h, C.byref(n)))
+        return n.value
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().hedap_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
 
 
 class Server:
