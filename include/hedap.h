@@ -131,6 +131,13 @@ hedap_status hedap_mul(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hed
 /* Divide by the last prime q_l with rounding; scale /= q_l, level -= 1. */
 hedap_status hedap_rescale(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
 hedap_status hedap_rotate(hedap_ctx* ctx, const hedap_ct* a, int64_t steps, hedap_ct** out);
+/* n rotations of one ciphertext (out[i] by steps[i]) sharing one ModUp of its
+ * second part (hoisting, as in the bootstrapping baby steps): the extended
+ * digits are formed once and each rotation permutes them by its automorphism
+ * before the key inner product.  Each result decrypts like hedap_rotate's
+ * (they differ by multiples of the digit moduli before ModDown).  out must
+ * hold n handles; on error none is returned. */
+hedap_status hedap_rotate_hoisted(hedap_ctx* ctx, const hedap_ct* a, const int64_t* steps, size_t n, hedap_ct** out);
 hedap_status hedap_conjugate(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
 /* Mul_P by a real constant c, rescaled so that the result has exactly
  * scale `target_scale` (the constant is encoded at target*q_l/scale). */

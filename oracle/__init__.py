@@ -84,6 +84,7 @@ def _declare(L):
         "orc_mul": (vp, [vp, vp, vp]),
         "orc_rescale": (vp, [vp, vp]),
         "orc_rotate": (vp, [vp, vp, C.c_int64]),
+        "orc_rotate_hoisted": (C.c_int, [vp, vp, C.POINTER(C.c_int64), C.c_int, C.POINTER(vp)]),
         "orc_conjugate": (vp, [vp, vp]),
         "orc_mul_const": (vp, [vp, vp, C.c_double, C.c_double]),
         "orc_add_const": (vp, [vp, vp, C.c_double]),
@@ -286,6 +287,14 @@ class Context:
 
     def rotate(self, a, steps: int):
         return Ciphertext(self, lib().orc_rotate(self.h, a.h, steps))
+
+    def rotate_hoisted(self, a, steps):
+        """Rotations of one ciphertext sharing one ModUp (hoisting), one per entry of steps."""
+        st = (C.c_int64 * len(steps))(*steps)
+        out = (C.c_void_p * len(steps))()
+        if lib().orc_rotate_hoisted(self.h, a.h, st, len(steps), out) != 0:
+            raise OracleError(lib().orc_last_error().decode())
+        return [Ciphertext(self, out[i]) for i in range(len(steps))]
 
     def conjugate(self, a):
         return Ciphertext(self, lib().orc_conjugate(self.h, a.h))

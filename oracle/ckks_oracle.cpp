@@ -674,6 +674,58 @@ static Ct apply_galois(Ctx& C, const Ct& a, u64 g) {
   return r;
 }
 static Ct rotate(Ctx& C, const Ct& a, i64 steps) { return apply_galois(C, a, galois_of_rotation(C, steps)); }
+// Several rotations of one ciphertext sharing the ModUp of its second part (hoisting): the
+// extended digits of c1 are formed once in the coefficient domain; each rotation applies its
+// automorphism to every extended limb, then takes the inner product with its key, ModDown, and
+// adds the rotated c0.
+static std::vector<Ct> rotate_hoisted(Ctx& C, const Ct& a, const std::vector<i64>& steps) {
+  const int l = a.level;
+  Poly x0 = a.c[0], x1 = a.c[1];
+  PER_LIMB
+  for (int i = 0; i <= l; ++i) { ntt_inverse(C, x0[i], i); ntt_inverse(C, x1[i], i); }
+  std::vector<int> ext;
+  for (int i = 0; i <= l; ++i) ext.push_back(i);
+  for (int k = 0; k < C.n_p; ++k) ext.push_back(C.n_q + k);
+  std::vector<Poly> ys;
+  for (int j = 0; j < n_digits(C, l); ++j) ys.push_back(modup_coeff(C, x1, l, j));
+  std::vector<Ct> out;
+  for (i64 st : steps) {
+    const u64 g = galois_of_rotation(C, st);
+    gen_key(C, g);
+    const std::vector<KeyDigit>& key = C.keys.find(g)->second;
+    Poly acc0(ext.size(), Limb(C.N, 0)), acc1(ext.size(), Limb(C.N, 0));
+    for (size_t j = 0; j < ys.size(); ++j) {
+      PER_LIMB
+      for (size_t e = 0; e < ext.size(); ++e) {
+        const int t = ext[e];
+        const u64 qt = C.q[t];
+        Limb yg = automorph_coeff(C, ys[j][e], g, qt);
+        ntt_forward(C, yg, t);
+        for (size_t n = 0; n < C.N; ++n) {
+          acc0[e][n] = addmod(acc0[e][n], mulmod(yg[n], key[j].b[t][n], qt), qt);
+          acc1[e][n] = addmod(acc1[e][n], mulmod(yg[n], key[j].a[t][n], qt), qt);
+        }
+      }
+    }
+    PER_LIMB
+    for (size_t e = 0; e < ext.size(); ++e) { ntt_inverse(C, acc0[e], ext[e]); ntt_inverse(C, acc1[e], ext[e]); }
+    Poly o0 = moddown_coeff(C, acc0, l), o1 = moddown_coeff(C, acc1, l);
+    Ct r; r.level = l; r.scale = a.scale;
+    r.c[0] = Poly(l + 1); r.c[1] = Poly(l + 1);
+    PER_LIMB
+    for (int i = 0; i <= l; ++i) {
+      Limb p0 = automorph_coeff(C, x0[i], g, C.q[i]);
+      ntt_forward(C, p0, i);
+      ntt_forward(C, o0[i], i);
+      ntt_forward(C, o1[i], i);
+      for (size_t k = 0; k < C.N; ++k) p0[k] = addmod(p0[k], o0[i][k], C.q[i]);
+      r.c[0][i] = p0;
+      r.c[1][i] = o1[i];
+    }
+    out.push_back(r);
+  }
+  return out;
+}
 static Ct conjugate(Ctx& C, const Ct& a) { return apply_galois(C, a, 2 * C.N - 1); }
 
 // multiply by a real constant c encoded at plaintext scale sp, then rescale
@@ -940,8 +992,18 @@ static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target)
   while (n1 * n1 < span) n1 <<= 1;
   long giants = (span + n1 - 1) / n1;
   double sp = target * (double)C.q[v.level] / v.scale;
+  // baby steps: every rotation of v used by some giant step, hoisted
   std::vector<Ct> baby(n1);
-  std::vector<bool> have(n1, false);
+  baby[0] = v;
+  {
+    std::vector<long> need;
+    std::vector<i64> steps;
+    for (long b = 1; b < n1; ++b)
+      for (long g = 0; g < giants; ++g)
+        if (byk.count(kmin + g * n1 + b)) { need.push_back(b); steps.push_back(b * h0); break; }
+    std::vector<Ct> rot = rotate_hoisted(C, v, steps);
+    for (size_t i = 0; i < need.size(); ++i) baby[need[i]] = rot[i];
+  }
   Ct acc; bool acc_set = false;
   for (long g = 0; g < giants; ++g) {
     long G = h0 * (kmin + g * n1);
@@ -950,7 +1012,6 @@ static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target)
       long k = kmin + g * n1 + b;
       auto it = byk.find(k);
       if (it == byk.end()) continue;
-      if (!have[b]) { baby[b] = b == 0 ? v : rotate(C, v, b * h0); have[b] = true; }
       Poly pt = encode_at(C, rot_vec(*it->second, -G), sp, v.level);
       Ct term = mul_plain(C, baby[b], pt);
       term.scale = v.scale * sp;
@@ -1276,6 +1337,16 @@ API void* orc_mul(void* c, void* a, void* b) { CT_OP(mul(*(Ctx*)c, *(Ct*)a, *(Ct
 API void* orc_rescale(void* c, void* a) { CT_OP(rescale(*(Ctx*)c, *(Ct*)a)) }
 API void* orc_rotate(void* c, void* a, int64_t steps) { CT_OP(rotate(*(Ctx*)c, *(Ct*)a, steps)) }
 API void* orc_conjugate(void* c, void* a) { CT_OP(conjugate(*(Ctx*)c, *(Ct*)a)) }
+// hoisted rotations: out[i] receives the rotation by steps[i]; returns 0 or -1
+API int orc_rotate_hoisted(void* c, void* a, const int64_t* steps, int n, void** out) {
+  GUARD(
+    std::vector<i64> st(steps, steps + n);
+    std::vector<Ct> r = rotate_hoisted(*(Ctx*)c, *(Ct*)a, st);
+    for (int i = 0; i < n; ++i) out[i] = new Ct(r[i]);
+    return 0;
+  )
+  return -1;
+}
 API void* orc_mul_const(void* c, void* a, double v, double target_scale) { CT_OP(mul_const_to(*(Ctx*)c, *(Ct*)a, v, target_scale)) }
 API void* orc_add_const(void* c, void* a, double v) { CT_OP(add_const(*(Ctx*)c, *(Ct*)a, v)) }
 API void* orc_mul_int(void* c, void* a, int64_t m) { CT_OP(mul_int(*(Ctx*)c, *(Ct*)a, m)) }

@@ -7,7 +7,9 @@
 //                radix-2 stages of the special FFT grouped into `cts` sparse
 //                factors, each applied as a baby-step / giant-step sum of
 //                plaintext diagonals times rotations (Halevi-Shoup, Chen-
-//                Chillotti-Song 2019); real / imaginary parts split by conjugation
+//                Chillotti-Song 2019), the baby-step rotations hoisted (one
+//                ModUp shared by all of them); real / imaginary parts split by
+//                conjugation and taken through EvalMod as one batch
 //   EvalMod      u = t / (q_0 K) -> sin(2 pi K u) = sin(2 pi m / q_0): Chebyshev
 //                interpolant of cos(2 pi (K u - 1/4) / 2^r) and r double angles
 //                (Bossuat et al. 2021)
@@ -284,7 +286,21 @@ std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int 
     P.level = l;
     P.sp = sp;
   }
+  // baby steps: every rotation of v any giant step uses, hoisted (one ModUp of v)
   std::vector<std::unique_ptr<Ct>> baby(G.n1);
+  {
+    std::vector<long> need;
+    for (long b = 1; b < G.n1; ++b)
+      for (long g = 0; g < G.giants; ++g)
+        if (P.pt.count({g, b})) {
+          need.push_back(b);
+          break;
+        }
+    std::vector<u64> gs;
+    for (long b : need) gs.push_back(galois_for_rotation(C, b * G.h0));
+    auto rot = ev_galois_hoisted(C, v, gs);
+    for (size_t i = 0; i < need.size(); ++i) baby[need[i]] = std::move(rot[i]);
+  }
   std::unique_ptr<Ct> acc;
   const long n = (long)(C.N / 2);
   for (long g = 0; g < G.giants; ++g) {
@@ -293,7 +309,6 @@ std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int 
     for (long b = 0; b < G.n1; ++b) {
       auto it = P.pt.find({g, b});
       if (it == P.pt.end()) continue;
-      if (b && !baby[b]) baby[b] = ev_galois(C, v, galois_for_rotation(C, b * G.h0));
       const Ct& src = b ? *baby[b] : v;
       if (A.count == 16) throw Error(HEDAP_ERR_ARG, "more than 16 baby steps");
       A.ct[A.count] = src.part(0);
@@ -352,8 +367,15 @@ std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a) {
   auto cj = ev_galois(C, *t, 2 * C.N - 1);
   auto re = ev_add(C, *t, *cj, false);
   auto im = mul_monomial(C, *ev_add(C, *t, *cj, true), 3 * C.N / 2);  // times -i
-  re = eval_mod(C, *re);
-  im = eval_mod(C, *im);
+  if (2 * re->batch <= 16) {  // both parts through one batched EvalMod
+    auto both = eval_mod(C, *batch_pack(C, {re.get(), im.get()}));
+    const int B = re->batch;
+    re = batch_slice(C, *both, 0, B);
+    im = batch_slice(C, *both, B, B);
+  } else {
+    re = eval_mod(C, *re);
+    im = eval_mod(C, *im);
+  }
   auto w = ev_add(C, *re, *mul_monomial(C, *im, C.N / 2), false);  // re + i im
   w->scale = w->scale * 2.0 * M_PI * s_in / q0;
   for (int g = 0; g < S.stc; ++g)

@@ -202,6 +202,16 @@ API hedap_status hedap_mul(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b,
 API hedap_status hedap_rescale(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
   CT_OP((need(a, "null ciphertext"), hedap::ev_rescale(*ctx->c, *a->c)));
 }
+API hedap_status hedap_rotate_hoisted(hedap_ctx* ctx, const hedap_ct* a, const int64_t* steps, size_t n,
+                                      hedap_ct** out) {
+  return guarded_on(ctx, [&] {
+    need(ctx && a && steps && out && n > 0, "null argument");
+    std::vector<uint64_t> gs;
+    for (size_t i = 0; i < n; ++i) gs.push_back(hedap::galois_for_rotation(*ctx->c, steps[i]));
+    auto r = hedap::ev_galois_hoisted(*ctx->c, *a->c, gs);
+    for (size_t i = 0; i < n; ++i) out[i] = wrap(std::move(r[i]));
+  });
+}
 API hedap_status hedap_rotate(hedap_ctx* ctx, const hedap_ct* a, int64_t steps, hedap_ct** out) {
   CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, *a->c, hedap::galois_for_rotation(*ctx->c, steps))));
 }

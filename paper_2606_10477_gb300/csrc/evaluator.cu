@@ -61,6 +61,14 @@ std::unique_ptr<Ct> batch_pack(Ctx& C, const std::vector<const Ct*>& cts) {
   }
   return b;
 }
+std::unique_ptr<Ct> batch_slice(Ctx& C, const Ct& b, int first, int count) {
+  if (first < 0 || count < 1 || first + count > b.batch) throw Error(HEDAP_ERR_ARG, "batch slice out of range");
+  auto c = ct_alloc(C, b.level, count);
+  c->scale = b.scale;
+  HEDAP_CUDA(cudaMemcpy2DAsync(c->part(0), c->part_stride() * 8, b.part(2 * first), b.part_stride() * 8,
+                               (size_t)(b.level + 1) * C.N * 8, 2 * count, cudaMemcpyDeviceToDevice, C.stream));
+  return c;
+}
 std::unique_ptr<Ct> batch_unpack(Ctx& C, const Ct& b, int k) {
   if (k < 0 || k >= b.batch) throw Error(HEDAP_ERR_ARG, "batch index out of range");
   auto c = ct_alloc(C, b.level, 1);
@@ -150,15 +158,11 @@ const LevelConsts& level_consts(Ctx& C, int l) {
 // the inverse NTT reads d out of place and ends with N^-1 qhat_i^-1, the forward
 // NTT of each extended limb loads the basis conversion directly, and a digit's
 // own limbs (whose NTT is d itself) are neither converted nor transformed.
-void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
-                bool acc0, bool acc1) {
-  auto it = C.keys.find(galois);
-  if (it == C.keys.end()) {
-    gen_galois_key(C, galois);
-    it = C.keys.find(galois);
-  }
+// ModUp of a batch of NTT-domain polynomials d (member stride d_stride) into NTT-domain extended
+// digits [B][dn][ext][N] (a digit's own limbs are left out: they are d itself)
+static DevBuf ks_modup(Ctx& C, const u64* d, size_t d_stride, int batch, int l) {
   const size_t N = C.N, nl = (size_t)l + 1;
-  const int K = C.n_p, ext = l + 1 + K, dn = C.dnum(l);
+  const int ext = l + 1 + C.n_p, dn = C.dnum(l);
   const LevelConsts& LC = level_consts(C, l);
   DevBuf dc((size_t)batch * nl * N, C.stream);  // z_i = [x_i qhat_i^-1]_{q_i}, coefficient domain
   NttAux inv{};
@@ -177,13 +181,59 @@ void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 gal
   up.bconv_sh_offset = (size_t)dn * C.alpha * ext;
   up.ext = ext;
   ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream, &up);
+  return y;
+}
+static const DevBuf& key_for(Ctx& C, u64 galois) {
+  auto it = C.keys.find(galois);
+  if (it == C.keys.end()) {
+    gen_galois_key(C, galois);
+    it = C.keys.find(galois);
+  }
+  return it->second;
+}
+// inner product of the extended digits (permuted by X -> X^perm when perm != 0) with the key for
+// `galois`, iNTT of the P limbs, ModDown, NTT, written to / added into out
+static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64 perm,
+                      u64* out, size_t out_stride, bool acc0, bool acc1) {
+  const DevBuf& key = key_for(C, galois);
+  const size_t N = C.N, nl = (size_t)l + 1;
+  const int K = C.n_p, ext = l + 1 + K;
   DevBuf acc((size_t)batch * 2 * ext * N, C.stream);
-  k_ksk_inner(C, y.p, d, d_stride, it->second.p, acc.p, batch, l);
+  k_ksk_inner(C, y.p, d, d_stride, key.p, acc.p, batch, l, perm);
   ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream);
   DevBuf v((size_t)batch * 2 * nl * N, C.stream);
   k_moddown_spread(C, acc.p, v.p, 2 * batch, l);
   ntt_forward(C.tab, qset(v.p, nl * N, 2 * batch, 0, l + 1), C.stream);
   k_moddown_finish(C, acc.p, v.p, out, out_stride, 2 * batch, l, acc0, acc1);
+}
+
+void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
+                bool acc0, bool acc1) {
+  key_for(C, galois);
+  DevBuf y = ks_modup(C, d, d_stride, batch, l);
+  ks_finish(C, y, d, d_stride, batch, l, galois, 0, out, out_stride, acc0, acc1);
+}
+
+// Rotations of one (batched) ciphertext by several Galois elements sharing one ModUp of its
+// second part (hoisting): the extended digits of c1 are formed once, and each rotation applies its
+// automorphism to them inside the inner product.  The result differs from ev_galois (which
+// converts the rotated c1) by multiples of the digit moduli in the extended basis, within the
+// same noise bound.
+std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const std::vector<u64>& gs) {
+  const int l = a.level;
+  for (u64 g : gs) key_for(C, g);
+  const u64* d = a.part(1);
+  const size_t ds = 2 * a.part_stride();
+  DevBuf y = ks_modup(C, d, ds, a.batch, l);
+  std::vector<std::unique_ptr<Ct>> out;
+  for (u64 g : gs) {
+    auto o = ct_alloc(C, l, a.batch);
+    o->scale = a.scale;
+    k_automorph(C, a.part(0), 2 * a.part_stride(), o->part(0), 2 * o->part_stride(), a.batch, l + 1, g);
+    ks_finish(C, y, d, ds, a.batch, l, g, g, o->part(0), o->part_stride(), true, false);
+    out.push_back(std::move(o));
+  }
+  return out;
 }
 
 std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b) {

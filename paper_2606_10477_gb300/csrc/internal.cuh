@@ -210,6 +210,7 @@ std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b);
 std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a);
 std::unique_ptr<Ct> ev_mul(Ctx& C, const Ct& a, const Ct& b);
 std::unique_ptr<Ct> ev_galois(Ctx& C, const Ct& a, u64 g);
+std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const std::vector<u64>& gs);
 std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level);
 std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target_scale);
 std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c);
@@ -222,6 +223,7 @@ void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int level, u64
                 bool acc0, bool acc1);
 std::unique_ptr<Ct> batch_pack(Ctx& C, const std::vector<const Ct*>& cts);
 std::unique_ptr<Ct> batch_unpack(Ctx& C, const Ct& b, int k);
+std::unique_ptr<Ct> batch_slice(Ctx& C, const Ct& b, int first, int count);  // members first .. first+count-1
 void gen_galois_key(Ctx& C, u64 g);
 const LevelConsts& level_consts(Ctx& C, int level);
 

@@ -269,24 +269,35 @@ void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const
 // One thread per (k, t, n): a CTA holds the batch members of the same coefficients
 // (threadIdx.y = k), so each key word comes from DRAM once and from L1 for the
 // other members; few registers per thread keep many loads in flight.
+// With g != 0 the extended digits enter permuted by the automorphism X -> X^g (a
+// hoisted rotation: the digits were converted once, before the automorphism): the
+// NTT-domain value at n is read at the index whose evaluation point is the g-th
+// power of n's; within 32 consecutive indices the permutation stays inside one
+// aligned group of 32, so the gather is coalesced.
+__device__ __forceinline__ uint32_t galois_index(uint32_t n, u64 g, int log_n) {
+  const u64 e = 2 * (u64)(__brev(n) >> (32 - log_n)) + 1;
+  const u64 eg = (g * e) & ((2ull << log_n) - 1);
+  return __brev((uint32_t)((eg - 1) >> 1)) >> (32 - log_n);
+}
 __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s,
                                    const u64* __restrict__ y, const u64* __restrict__ d, size_t ds,
                                    const u64* __restrict__ key, u64* __restrict__ acc, int l, int dn, int alpha,
-                                   int n_q, int K, int log_n) {
+                                   int n_q, int K, int log_n, u64 g) {
   const size_t N = (size_t)1 << log_n;
   const int ext = l + 1 + K, total_primes = n_q + K;
   const int t = blockIdx.y, k = threadIdx.y;
   const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t ns = g ? galois_index((uint32_t)n, g, log_n) : n;  // source index of the digits
   const int pt = t <= l ? t : n_q + (t - l - 1);
   const int own = t <= l ? t / alpha : -1;
   const u64* kb = key + (size_t)pt * N + n;
   const u64* ka = key + ((size_t)total_primes + pt) * N + n;
-  const u64* yk = y + ((size_t)k * dn * ext + t) * N + n;
+  const u64* yk = y + ((size_t)k * dn * ext + t) * N + ns;
   const size_t key_step = (size_t)2 * total_primes * N, y_step = (size_t)ext * N;
   Acc128 s0{0, 0}, s1{0, 0};
 #pragma unroll 4
   for (int j = 0; j < dn; ++j) {
-    const u64 v = j == own ? d[k * ds + (size_t)t * N + n] : yk[j * y_step];
+    const u64 v = j == own ? d[k * ds + (size_t)t * N + ns] : yk[j * y_step];
     mac128(s0, v, __ldg(kb + j * key_step));
     mac128(s1, v, __ldg(ka + j * key_step));
   }
@@ -296,7 +307,7 @@ __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* _
   acc[(((size_t)k * 2 + 1) * ext + t) * N + n] = reduce128(s1, P, r64, r64p);
 }
 void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
-                 int level) {
+                 int level, u64 galois_perm) {
   if (batch < 1 || batch > kMaxBatch) throw Error(HEDAP_ERR_ARG, "batch must lie in [1, 16]");
   const int dn = C.dnum(level), ext = level + 1 + C.n_p;
   ProfScope prof_(PROF_KSK_INNER, C.stream, ((double)batch * dn + 2.0 * dn + 2.0 * batch) * ext * C.N * 8);
@@ -304,7 +315,7 @@ void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, cons
   const unsigned tx = 32u * (unsigned)std::max(1, 8 / batch);  // about 256 threads per CTA
   const dim3 block(tx, (unsigned)batch), grid((unsigned)(C.N / tx), (unsigned)ext);
   k_ksk_inner_kernel<<<grid, block, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, d, d_stride, key, acc, level, dn, C.alpha,
-                                                   C.n_q, C.n_p, C.log_n);
+                                                   C.n_q, C.n_p, C.log_n, galois_perm);
   HEDAP_LAUNCH_CHECK();
 }
 

@@ -21,7 +21,7 @@ void k_rescale_finish(const Ctx& C, const u64* in, size_t is, const u64* tmp, si
 void k_automorph(const Ctx& C, const u64* in, size_t is, u64* out, size_t os, int n_parts, int limbs, u64 g);
 void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const u64* d_consts);
 void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
-                 int level);
+                 int level, u64 galois_perm = 0);
 void k_moddown_spread(const Ctx& C, const u64* acc, u64* v, int n_parts, int level);
 void k_moddown_finish(const Ctx& C, const u64* acc, const u64* v, u64* out, size_t os, int n_parts, int level,
                       bool acc_even, bool acc_odd);

@@ -25,7 +25,7 @@ EXPORTED = [
     "hedap_status_str", "hedap_last_error", "hedap_ctx_create", "hedap_ctx_destroy", "hedap_ctx_primes", "hedap_sync",
     "hedap_gen_galois_key", "hedap_export_key", "hedap_encrypt", "hedap_decrypt", "hedap_ct_import",
     "hedap_ct_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
-    "hedap_rescale", "hedap_rotate", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
+    "hedap_rescale", "hedap_rotate", "hedap_rotate_hoisted", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
@@ -134,6 +134,7 @@ def _declare(L):
         "hedap_mul": (st, [vp, vp, vp, pp]),
         "hedap_rescale": (st, [vp, vp, pp]),
         "hedap_rotate": (st, [vp, vp, C.c_int64, pp]),
+        "hedap_rotate_hoisted": (st, [vp, vp, C.POINTER(C.c_int64), C.c_size_t, pp]),
         "hedap_conjugate": (st, [vp, vp, pp]),
         "hedap_mul_const": (st, [vp, vp, C.c_double, C.c_double, pp]),
         "hedap_add_const": (st, [vp, vp, C.c_double, pp]),
@@ -391,6 +392,12 @@ class Context:
 
     def rotate(self, a, steps: int):
         return self._ct(load().hedap_rotate, a.h, steps)
+
+    def rotate_hoisted(self, a: Ciphertext, steps) -> list:
+        st = (C.c_int64 * len(steps))(*steps)
+        out = (C.c_void_p * len(steps))()
+        _check(load().hedap_rotate_hoisted(self.h, a.h, st, len(steps), out))
+        return [Ciphertext(self, C.c_void_p(out[i])) for i in range(len(steps))]
 
     def conjugate(self, a):
         return self._ct(load().hedap_conjugate, a.h)

@@ -183,6 +183,17 @@ def test_rotation_conjugation_bit_exact(name, request):
         same_ct(g.conjugate(ga), o.conjugate(oa))
 
 
+@pytest.mark.parametrize("name", ["n10", "toy"])
+def test_hoisted_rotations_bit_exact(name, request):
+    g, o = request.getfixturevalue(name)
+    L = o.n_q - 1
+    for level in (L, 1):
+        ga, oa = imported_pair(g, o, 31 + level, level)
+        steps = [1, -3, 7, 0]
+        for gc, oc in zip(g.rotate_hoisted(ga, steps), o.rotate_hoisted(oa, steps)):
+            same_ct(gc, oc)
+
+
 def test_ring_ops_bit_exact_at_full_size():
     """N = 2^16, 24 + 2 primes, two primes per digit: one HMult, one rotation, one rescale."""
     p = inputs.PRESETS["n16"]

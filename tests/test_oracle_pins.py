@@ -360,6 +360,23 @@ def test_rotation_and_conjugation_permute_slots(small):
     assert np.max(np.abs(ctx.decrypt(ctx.conjugate(ct)) - np.conj(z))) < 1e-6
 
 
+def test_hoisted_rotations_permute_slots(small):
+    """Hoisted rotations (one ModUp, automorphism applied to the extended digits) decrypt to the
+    rotated slots, like the ordinary rotation, though the ciphertexts differ (the conversion's
+    slack is rotated instead of recomputed)."""
+    ctx = small
+    rng = np.random.default_rng(12)
+    z = rng.uniform(-1, 1, ctx.N // 2) + 1j * rng.uniform(-1, 1, ctx.N // 2)
+    ct = ctx.encrypt(z, 4, 7)
+    steps = [1, 3, -2, 0]
+    outs = ctx.rotate_hoisted(ct, steps)
+    assert len(outs) == len(steps)
+    for r, o in zip(steps, outs):
+        assert o.level == ct.level and o.scale == ct.scale
+        assert np.max(np.abs(ctx.decrypt(o) - np.roll(z, -r))) < 1e-6
+    assert not np.array_equal(outs[0].limbs(), ctx.rotate(ct, 1).limbs())
+
+
 def test_scalar_ops_and_rescale(small):
     ctx = small
     rng = np.random.default_rng(11)
