@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bts", action="store_true", help="skip the bootstrapped workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-level batch workload")
     ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
-    ap.add_argument("--only", choices=["ntt", "serving"],
+    ap.add_argument("--only", choices=["ntt", "serving", "mixed"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     return ap.parse_args()
@@ -343,6 +344,7 @@ def run_ours(args):
     ntt = measure_ntt(ctx, inputs, torch, stream, 384)
     bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
                                                          stream=stream, rank=rank, batch=batch)
+    mixed = None if args.no_mixed else mixed_workload(hedap, inputs, torch, stream, rank)
     serving = None if args.no_serving else serving_workload(hedap, inputs, torch, stream, rank, args.serve_queries)
 
     if rank == 0:
@@ -376,6 +378,7 @@ def run_ours(args):
                       "speedup_batched_vs_plain": value / plain_value},
             "graph": graph_info,
             "bootstrapped": bts,
+            "mixed_levels": mixed,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -429,6 +432,56 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
             "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s}
 
 
+def mixed_workload(hedap, inputs, torch, stream, rank, n_cts=64, band=4):
+    """64 ciphertexts at N=2^16 (the n16 chain: 24 x 50-bit primes) at mixed levels and slot
+    counts: level ~ U{14..23} (15..24 limbs; CryptoInvSqrt with degree 31 and 3 Newton steps takes 13
+    levels and the result must keep one), 2^U{10..15} slots (sparse packing: the values repeated to
+    fill N/2 slots), inputs log-uniform in [1e-3, 1].  Three executions of the same work: one
+    ciphertext per call, batches of equal level, and batches of level bands (dropped to the band's
+    lowest level)."""
+    p = inputs.PRESETS["n16"]
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 31 + rank,
+                        stream=stream.cuda_stream)
+    rng = np.random.default_rng(41 + rank)
+    levels = rng.integers(14, 24, n_cts)
+    slots = 2 ** rng.integers(10, 16, n_cts)
+    half = ctx.N // 2
+    vals = [inputs.log_uniform_values(5000 + i, int(s), 1e-3, 1.0) for i, s in enumerate(slots)]
+    cts = [ctx.encrypt(np.tile(v, half // v.size), int(l), 6000 + i) for i, (v, l) in enumerate(zip(vals, levels))]
+    cfg = (1e-3, 1.0, 1.0, 31, 3, 0, 0)
+    cfgs = [cfg] * n_cts
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    def mre(outs):
+        worst = 0.0
+        for v, o in zip(vals, outs):
+            y = ctx.decrypt(o).real[:v.size]
+            worst = max(worst, float(np.mean(np.abs(y * np.sqrt(v) - 1))))
+        return worst
+
+    res = {}
+    ctx.invsqrt_many(cts, cfgs, band)  # warm-up: level constants of every level
+    ctx.invsqrt_many(cts, cfgs, 0)
+    for name, fn in (("plain", lambda: [ctx.invsqrt(c, *cfg) for c in cts]),
+                     ("batched_equal_levels", lambda: ctx.invsqrt_many(cts, cfgs, 0)),
+                     ("batched_level_bands", lambda: ctx.invsqrt_many(cts, cfgs, band))):
+        outs, sec = timed(fn)
+        res[name] = {"value": n_cts / sec, "unit": UNIT, "seconds": sec, "max_mre": mre(outs)}
+    ctx.close()
+    res["workload"] = (f"{n_cts} ciphertexts, N=2^16 n16 chain, levels U{{14..23}}, slots 2^U{{10..15}}, inputs "
+                       f"log-U[1e-3,1], CryptoInvSqrt degree 31, 3 Newton steps; level band {band}")
+    res["speedup_bands_vs_plain"] = res["batched_level_bands"]["value"] / res["plain"]["value"]
+    return res
+
+
 SERVE_RECORDS = [1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20]
 SERVE_ZCFG = (1e-3, 1.0, 1.0, 31, 4, 0, 1 << 63)  # variance of the records (sd 0.1): [1e-3, 1]
 SERVE_PCFG = (1e-5, 1e-2, 1e-2, 31, 5, 0, 1 << 63)  # product of two variances: [1e-5, 1e-2]
@@ -445,9 +498,10 @@ def serving_workload(hedap, inputs, torch, stream, rank, n_queries, max_batch=8)
     lvl = ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"]) + 3  # 3 levels above a bootstrapped one
     slots = ctx.N // 2
     pool = []
+    rhos = np.random.default_rng(77 + rank).uniform(-0.9, 0.9, len(SERVE_RECORDS))
     for k, n in enumerate(SERVE_RECORDS):
         x = inputs.gaussian_records(500 + k, n)
-        y = inputs.correlated_records(600 + k, x, 0.5)
+        y = inputs.correlated_records(600 + k, x, float(rhos[k]))
         gx = [ctx.encrypt(v, lvl, 7000 + 100 * k + i) for i, v in enumerate(inputs.pack_slots(x, slots))]
         gy = [ctx.encrypt(v, lvl, 8000 + 100 * k + i) for i, v in enumerate(inputs.pack_slots(y, slots))]
         pool.append((n, x, y, gx, gy))
@@ -487,31 +541,39 @@ def serving_workload(hedap, inputs, torch, stream, rank, n_queries, max_batch=8)
     capacity = len(ids) / (time.perf_counter() - t0)
     srv.close()
 
-    # Poisson arrivals at 70% of that capacity
-    rate = 0.7 * capacity
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_queries))
-    queries = plan(n_queries)
-    srv = hedap.Server(ctx, max_batch=max_batch)
-    t0 = time.perf_counter()
-    ids = []
-    for (kind, k), t in zip(queries, arrivals):
-        wait = t0 + t - time.perf_counter()
-        if wait > 0:
-            time.sleep(wait)
-        ids.append(submit(srv, kind, k))
-    groups = [srv.poll(i)[2]["group_size"] for i in ids]
-    st = srv.stats()
-    srv.close()
-    records = sum(pool[k][0] for _, k in queries)
+    # Poisson arrivals at fractions of that capacity
+    def poisson(frac, m):
+        rate = frac * capacity
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, m))
+        queries = plan(m)
+        srv = hedap.Server(ctx, max_batch=max_batch)
+        t0 = time.perf_counter()
+        ids = []
+        for (kind, k), t in zip(queries, arrivals):
+            wait = t0 + t - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(submit(srv, kind, k))
+        groups = [srv.poll(i)[2]["group_size"] for i in ids]
+        st = srv.stats()
+        srv.close()
+        records = sum(pool[k][0] for _, k in queries)
+        return {"load": frac, "arrival_rate_qps": rate, "queries": m, "qps": st["qps"], "p50_ms": st["p50_ms"],
+                "p99_ms": st["p99_ms"], "records_per_s": records * st["qps"] / m,
+                "mean_group_size": float(np.mean(groups))}
+
+    main = poisson(0.75, n_queries)
+    sweep = [poisson(f, n_queries) for f in (0.25, 0.5, 0.9)]
     ctx.close()
     return {"workload": f"Poisson arrivals, {n_queries} queries (z-score / PCC alternating) over "
-                        f"{SERVE_RECORDS[0]}..{SERVE_RECORDS[-1]} Gaussian records (mean 50, sd 10, /100), "
-                        f"N=2^16 bts16 chain, inputs at level {lvl} (3 above a bootstrapped ciphertext), InvSqrt degree 31 "
-                        f"with lazy bootstrapping, "
-                        f"max_batch {max_batch}",
-            "qps": st["qps"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "arrival_rate_qps": rate,
-            "burst_capacity_qps": capacity, "records_per_s": records * st["qps"] / n_queries,
-            "mean_group_size": float(np.mean(groups)), "zscore_max_abs_err": z_err, "pcc_abs_err": r_err}
+                        f"{SERVE_RECORDS[0]}..{SERVE_RECORDS[-1]} Gaussian records (mean 50, sd 10, /100; PCC pairs "
+                        f"with rho ~ U[-0.9, 0.9]), N=2^16 bts16 chain, inputs at level {lvl} (3 above a bootstrapped "
+                        f"ciphertext), InvSqrt degree 31 with lazy bootstrapping, max_batch {max_batch}, "
+                        f"arrival rate 0.75 x burst capacity",
+            "qps": main["qps"], "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "arrival_rate_qps": main["arrival_rate_qps"], "burst_capacity_qps": capacity,
+            "records_per_s": main["records_per_s"], "mean_group_size": main["mean_group_size"],
+            "load_sweep": sweep, "zscore_max_abs_err": z_err, "pcc_abs_err": r_err}
 
 
 def run_serving_only(args):
@@ -575,6 +637,10 @@ def main():
         run_ntt_only(args)
     elif args.only == "serving":
         run_serving_only(args)
+    elif args.only == "mixed":
+        import torch
+        from paper_2606_10477_gb300 import hedap, inputs
+        print(json.dumps({"mixed_levels": mixed_workload(hedap, inputs, torch, torch.cuda.current_stream(), 0)}))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -169,6 +169,14 @@ hedap_status hedap_batch_unpack(hedap_ctx* ctx, const hedap_ct* batch, size_t in
 hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n);
 hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
                                  hedap_ct** out);
+/* As hedap_invsqrt_batch, for inputs at mixed levels: with level_band = W > 0,
+ * inputs with equal scale and configuration whose levels fall in the same band
+ * [k W, (k+1) W) form one group (up to 16, input order) and are first dropped
+ * to the lowest level present in it (dropping limbs costs no precision, only
+ * levels: the configuration must be feasible at that level, as it is at each
+ * input's own level).  level_band = 0 is hedap_invsqrt_batch. */
+hedap_status hedap_invsqrt_many(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
+                                int level_band, hedap_ct** out);
 
 /* HE-DAP provisioning (Sec. 4.2): Alg. 2 GetOptIter and Alg. 3, run on this
  * library with CUDA-event costs.  For every profiled level l (l_BTS + 1 up to

@@ -405,43 +405,61 @@ API hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n) {
     *n = ct->c->batch;
   });
 }
+// groups of inputs run as one batch: equal scale and configuration, and equal level (band = 0)
+// or levels in the same band [k band, (k+1) band) dropped to the lowest level present there;
+// up to 16 per group, in input order
+static void invsqrt_grouped(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
+                            int band, hedap_ct** out) {
+  need(ctx && in && cfgs && out && band >= 0, "bad argument");
+  for (size_t i = 0; i < n; ++i) out[i] = nullptr;
+  hedap::Ctx& C = *ctx->c;
+  auto key = [&](size_t i) { return band ? in[i]->c->level / band : in[i]->c->level; };
+  std::vector<bool> done(n, false);
+  try {
+    for (size_t i = 0; i < n; ++i) need(in[i] != nullptr && in[i]->c->batch == 1, "inputs must be single ciphertexts");
+    for (size_t i = 0; i < n; ++i) {
+      if (done[i]) continue;
+      std::vector<size_t> g{i};
+      for (size_t j = i + 1; j < n && g.size() < 16; ++j) {
+        if (done[j]) continue;
+        const hedap::Ct &a = *in[i]->c, &b = *in[j]->c;
+        if (key(i) == key(j) && a.scale == b.scale && memcmp(&cfgs[i], &cfgs[j], sizeof(hedap_invsqrt_cfg)) == 0)
+          g.push_back(j);
+      }
+      int lmin = INT_MAX;
+      for (size_t j : g) lmin = std::min(lmin, in[j]->c->level);
+      std::vector<std::unique_ptr<hedap::Ct>> dropped;
+      std::vector<const hedap::Ct*> v;
+      for (size_t j : g) {
+        const hedap::Ct& a = *in[j]->c;
+        if (a.level == lmin) {
+          v.push_back(&a);
+        } else {
+          dropped.push_back(hedap::ev_drop(C, a, lmin));
+          v.push_back(dropped.back().get());
+        }
+      }
+      auto res = g.size() > 1 ? hedap::invsqrt(C, *hedap::batch_pack(C, v), cfgs[i]) : hedap::invsqrt(C, *v[0], cfgs[i]);
+      for (size_t k = 0; k < g.size(); ++k) {
+        out[g[k]] = wrap(g.size() > 1 ? hedap::batch_unpack(C, *res, (int)k) : std::move(res));
+        done[g[k]] = true;
+      }
+    }
+  } catch (...) {
+    for (size_t i = 0; i < n; ++i) {
+      delete out[i];
+      out[i] = nullptr;
+    }
+    throw;
+  }
+}
 API hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs,
                                      size_t n, hedap_ct** out) {
-  return guarded_on(ctx, [&] {
-    need(ctx && in && cfgs && out, "null argument");
-    for (size_t i = 0; i < n; ++i) out[i] = nullptr;
-    hedap::Ctx& C = *ctx->c;
-    std::vector<bool> done(n, false);
-    try {
-      for (size_t i = 0; i < n; ++i) {
-        if (done[i]) continue;
-        need(in[i] != nullptr && in[i]->c->batch == 1, "inputs must be single ciphertexts");
-        // group: same level, scale and configuration, up to 16 ciphertexts, in input order
-        std::vector<size_t> g{i};
-        for (size_t j = i + 1; j < n && g.size() < 16; ++j) {
-          if (done[j] || !in[j]) continue;
-          const hedap::Ct &a = *in[i]->c, &b = *in[j]->c;
-          if (b.batch == 1 && a.level == b.level && a.scale == b.scale &&
-              memcmp(&cfgs[i], &cfgs[j], sizeof(hedap_invsqrt_cfg)) == 0)
-            g.push_back(j);
-        }
-        std::vector<const hedap::Ct*> v;
-        for (size_t j : g) v.push_back(in[j]->c.get());
-        auto packed = hedap::batch_pack(C, v);
-        auto res = hedap::invsqrt(C, *packed, cfgs[i]);
-        for (size_t k = 0; k < g.size(); ++k) {
-          out[g[k]] = wrap(hedap::batch_unpack(C, *res, (int)k));
-          done[g[k]] = true;
-        }
-      }
-    } catch (...) {
-      for (size_t i = 0; i < n; ++i) {
-        delete out[i];
-        out[i] = nullptr;
-      }
-      throw;
-    }
-  });
+  return guarded_on(ctx, [&] { invsqrt_grouped(ctx, in, cfgs, n, 0, out); });
+}
+API hedap_status hedap_invsqrt_many(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
+                                    int level_band, hedap_ct** out) {
+  return guarded_on(ctx, [&] { invsqrt_grouped(ctx, in, cfgs, n, level_band, out); });
 }
 API hedap_status hedap_ntt_batch(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, size_t n_polys, uint32_t first_prime,
                                  int inverse, int on_device) {

@@ -30,7 +30,7 @@ EXPORTED = [
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
-    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_ntt_batch",
+    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_ntt_batch",
     "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
     "hedap_server_resume", "hedap_server_estimate", "hedap_invsqrt_graph_create", "hedap_graph_run",
@@ -163,6 +163,7 @@ def _declare(L):
         "hedap_batch_unpack": (st, [vp, vp, C.c_size_t, pp]),
         "hedap_ct_batch_size": (st, [vp, C.POINTER(C.c_int)]),
         "hedap_invsqrt_batch": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, pp]),
+        "hedap_invsqrt_many": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, C.c_int, pp]),
         "hedap_ntt_batch": (st, [vp, u64p, C.c_size_t, C.c_size_t, C.c_uint32, C.c_int, C.c_int]),
         "hedap_ntt_tune": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -499,6 +500,15 @@ class Context:
         cf = (InvSqrtCfg * n)(*[InvSqrtCfg(*c) for c in cfgs])
         outs = (C.c_void_p * n)()
         _check(load().hedap_invsqrt_batch(self.h, arr, cf, n, outs))
+        return [Ciphertext(self, C.c_void_p(o)) for o in outs]
+
+    def invsqrt_many(self, cts, cfgs, level_band: int):
+        """Mixed levels: groups by level band (dropping to the band's lowest level), see hedap.h."""
+        n = len(cts)
+        arr = (C.c_void_p * n)(*[c.h for c in cts])
+        cf = (InvSqrtCfg * n)(*[InvSqrtCfg(*c) for c in cfgs])
+        outs = (C.c_void_p * n)()
+        _check(load().hedap_invsqrt_many(self.h, arr, cf, n, level_band, outs))
         return [Ciphertext(self, C.c_void_p(o)) for o in outs]
 
 

@@ -64,3 +64,25 @@ def test_bootstrap_batch_equals_single():
     g.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
     cts = [g.encrypt(inputs.uniform_values(500 + i, g.N // 2, -1, 1), 1, 600 + i) for i in range(3)]
     check(g, g.bootstrap_scaled(g.pack(cts), 1), [g.bootstrap_scaled(c, 1) for c in cts])
+
+
+def test_invsqrt_many_level_bands():
+    """Mixed levels: a band groups the inputs it holds and drops them to its lowest level; each
+    result equals the single-ciphertext InvSqrt of the input dropped to that level."""
+    g = ctx("toy")
+    L = g.n_q - 1
+    levels = [L, L - 1, L - 2, L, L - 3, L - 1]
+    vals = [inputs.uniform_values(700 + i, g.N // 2, 0.01, 1.0) for i in range(len(levels))]
+    cts = [g.encrypt(v, l, 800 + i) for i, (v, l) in enumerate(zip(vals, levels))]
+    cfg = (0.01, 1.0, 1.0, 7, 1, 0, 0)  # the lowest band ends at level 1 (decryptable)
+    band = 2
+    outs = g.invsqrt_many(cts, [cfg] * len(cts), band)
+    for i, (ct, o) in enumerate(zip(cts, outs)):
+        floor = min(l for l in levels if l // band == levels[i] // band)
+        s = g.invsqrt(g.drop(ct, floor), *cfg)
+        assert o.level == s.level and np.array_equal(o.limbs(), s.limbs())
+        y = g.decrypt(o).real
+        assert np.mean(np.abs(y * np.sqrt(vals[i]) - 1)) < 1e-2  # degree 7, one Newton step
+    same = g.invsqrt_many(cts, [cfg] * len(cts), 0)  # band 0: exact levels, as invsqrt_batch
+    for ct, o in zip(cts, same):
+        assert np.array_equal(o.limbs(), g.invsqrt(ct, *cfg).limbs())
