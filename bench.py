@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--only", choices=["ntt", "serving", "mixed"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="--only ntt: one forward and one inverse transform between cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -86,6 +89,30 @@ def measured_peaks():
         with open(path) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# Instructions of a minimal lazy Cooley-Tukey / Gentleman-Sande butterfly on 32-bit integer units
+# (no 64-bit multiplier): Shoup product 12 (high half of x * w' in four wide multiply-adds + a
+# 64-bit add; x * w - qh * q in two wide and four low multiply-adds), the lazy correction of x 4,
+# the two 64-bit sums 4, shared-memory traffic and twiddle loads of radix-16 passes 1.5 -> 21.5,
+# plus 1 for loop and address work: 22.5 issue slots per butterfly.
+NTT_INSTR_PER_BUTTERFLY = 22.5
+GB300_SMS, SCHEDULERS_PER_SM, LANES = 152, 4, 32
+
+
+def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
+    log_n = int(n).bit_length() - 1
+    limbs = alg_bytes / (16.0 * n)
+    bfly = limbs * (n // 2) * log_n
+    achieved = bfly / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = GB300_SMS * SCHEDULERS_PER_SM * LANES * mhz * 1e6 / NTT_INSTR_PER_BUTTERFLY / 1e9
+    return {"kernel": "ntt", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": f"derived: {GB300_SMS} SMs x {SCHEDULERS_PER_SM} schedulers x {LANES} lanes x {mhz:.0f} MHz "
+                           f"/ {NTT_INSTR_PER_BUTTERFLY} instructions per butterfly",
+            "launch_groups": groups, "avg_group_us": 1e3 * ms / max(1, groups),
+            "butterflies_per_group": bfly / max(1, groups)}
 
 
 class ClockSampler:
@@ -306,6 +333,16 @@ def run_ours(args):
     achieved = by_dom / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
     ntt = prof["ntt"]
     ntt_gbs = ntt[2] / (ntt[1] / 1e3) / 1e9 if ntt[1] > 0 else None
+    if dom == "ntt":
+        # the NTT is bound by integer issue, not HBM: butterflies = limbs x N/2 x log2 N, against the
+        # issue rate of a minimal 64-bit Shoup butterfly on 32-bit integer units
+        roofline = ntt_alu_roofline(ctx.N, by_dom, ms_dom, n_dom, peaks, clk)
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                    "launch_groups": n_dom, "avg_group_us": 1e3 * ms_dom / max(1, n_dom)}
+    roofline["hbm_view"] = {"achieved_gbs": achieved, "peak_gbs": peaks["hbm_gbs"],
+                            "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host_in = [torch.empty((2, L + 1, ctx.N), dtype=torch.int64, pin_memory=True) for _ in range(batch)]
@@ -360,12 +397,7 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {
-                "kernel": dom, "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": None, "peak_source": peak_kind,
-                "launch_groups": n_dom, "avg_group_us": 1e3 * ms_dom / max(1, n_dom),
-            },
+            "roofline": roofline,
             "profile_share": {k: round(v[1] / total_prof_ms, 4) for k, v in prof.items()} if total_prof_ms else {},
             "profile_classes": {k: {"groups_per_step": v[0] / n_prof_steps, "ms_per_step": v[1] / n_prof_steps,
                                     "us_per_group": 1e3 * v[1] / v[0], "algorithmic_gbs": v[2] / (v[1] / 1e3) / 1e9}
@@ -585,7 +617,7 @@ def run_serving_only(args):
                       "higher_is_better": True, "serving": r}), flush=True)
 
 
-def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5):
+def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5, profile_region=False):
     """Batched forward and inverse NTT over `limbs` limbs of N = 2^16 words resident in HBM
     (polynomials of n_q limbs, one launch per phase): algorithmic GB/s = limbs * N * 16 B
     (each word read and written once) per transform."""
@@ -611,8 +643,17 @@ def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        out[name] = {"ms": ms, "gbs": limbs * ctx.N * 16 / (ms / 1e3) / 1e9, "us_per_limb": 1e3 * ms / limbs}
+        bfly = limbs * (ctx.N // 2) * (ctx.N.bit_length() - 1)
+        out[name] = {"ms": ms, "gbs": limbs * ctx.N * 16 / (ms / 1e3) / 1e9, "us_per_limb": 1e3 * ms / limbs,
+                     "gbutterfly_s": bfly / (ms / 1e3) / 1e9}
     out["limbs"] = limbs
+    if profile_region:  # one forward and one inverse transform inside a profiler capture region
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        run(False)
+        run(True)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     return out
 
 
@@ -625,7 +666,8 @@ def run_ntt_only(args):
     ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1,
                         stream=stream.cuda_stream)
     fwd, inv, fv, iv = ctx.ntt_tune(args.ntt_limbs, 3)
-    r = measure_ntt(ctx, inputs, torch, stream, args.ntt_limbs, reps=max(1, args.steps))
+    r = measure_ntt(ctx, inputs, torch, stream, args.ntt_limbs, reps=max(1, args.steps),
+                    profile_region=args.profile_region)
     print(json.dumps({"metric": "NTT GB/s (N=2^16, 64-bit limbs, batched)", "value": r["forward"]["gbs"],
                       "unit": "GB/s", "ntt": r, "tune": {"forward_ms": fwd, "inverse_ms": inv,
                                                          "chosen": [fv, iv]}}), flush=True)

@@ -266,7 +266,7 @@ void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const
 // key layout: [dnum_max][2][n_q + n_p][N]; y: [B][dn][ext][N]; acc: [B][2][ext][N].
 // A digit's own limbs (t in digit j) are not in y: there the extended digit equals
 // the NTT-domain input itself, read from d ([B] members of stride ds, limbs of N).
-// One thread per (k, t, n): a CTA holds the batch members of the same coefficients
+// One thread per (k, t, pair of coefficients): a CTA holds the batch members of the same coefficients
 // (threadIdx.y = k), so each key word comes from DRAM once and from L1 for the
 // other members; few registers per thread keep many loads in flight.
 // With g != 0 the extended digits enter permuted by the automorphism X -> X^g (a
@@ -283,28 +283,49 @@ __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* _
                                    const u64* __restrict__ y, const u64* __restrict__ d, size_t ds,
                                    const u64* __restrict__ key, u64* __restrict__ acc, int l, int dn, int alpha,
                                    int n_q, int K, int log_n, u64 g) {
+  // two consecutive coefficients per thread (16-byte loads: longer runs per DRAM page
+  // across the dn x B digit streams); a permuted source is read word by word
   const size_t N = (size_t)1 << log_n;
   const int ext = l + 1 + K, total_primes = n_q + K;
   const int t = blockIdx.y, k = threadIdx.y;
-  const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t ns = g ? galois_index((uint32_t)n, g, log_n) : n;  // source index of the digits
+  const size_t n = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
   const int pt = t <= l ? t : n_q + (t - l - 1);
   const int own = t <= l ? t / alpha : -1;
   const u64* kb = key + (size_t)pt * N + n;
   const u64* ka = key + ((size_t)total_primes + pt) * N + n;
-  const u64* yk = y + ((size_t)k * dn * ext + t) * N + ns;
   const size_t key_step = (size_t)2 * total_primes * N, y_step = (size_t)ext * N;
-  Acc128 s0{0, 0}, s1{0, 0};
+  const u64* yk = y + ((size_t)k * dn * ext + t) * N;
+  const u64* dk = d + k * ds + (size_t)t * N;
+  Acc128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};  // (coefficient n, n+1) x (key b, key a)
+  if (!g) {
 #pragma unroll 4
-  for (int j = 0; j < dn; ++j) {
-    const u64 v = j == own ? d[k * ds + (size_t)t * N + ns] : yk[j * y_step];
-    mac128(s0, v, __ldg(kb + j * key_step));
-    mac128(s1, v, __ldg(ka + j * key_step));
+    for (int j = 0; j < dn; ++j) {
+      const ulonglong2 v = j == own ? ld2(dk + n) : ld2(yk + j * y_step + n);
+      const ulonglong2 wb = ld2(kb + j * key_step), wa = ld2(ka + j * key_step);
+      mac128(a0, v.x, wb.x);
+      mac128(a1, v.x, wa.x);
+      mac128(b0, v.y, wb.y);
+      mac128(b1, v.y, wa.y);
+    }
+  } else {
+    const size_t s0 = galois_index((uint32_t)n, g, log_n), s1 = galois_index((uint32_t)n + 1, g, log_n);
+#pragma unroll 4
+    for (int j = 0; j < dn; ++j) {
+      const u64* src = j == own ? dk : yk + j * y_step;
+      const u64 v0 = src[s0], v1 = src[s1];
+      const ulonglong2 wb = ld2(kb + j * key_step), wa = ld2(ka + j * key_step);
+      mac128(a0, v0, wb.x);
+      mac128(a1, v0, wa.x);
+      mac128(b0, v1, wb.y);
+      mac128(b1, v1, wa.y);
+    }
   }
   const PrimeDev P = pr[pt];
   const u64 r64 = r64s[2 * pt], r64p = r64s[2 * pt + 1];
-  acc[(((size_t)k * 2) * ext + t) * N + n] = reduce128(s0, P, r64, r64p);
-  acc[(((size_t)k * 2 + 1) * ext + t) * N + n] = reduce128(s1, P, r64, r64p);
+  st2(acc + (((size_t)k * 2) * ext + t) * N + n,
+      ulonglong2{reduce128(a0, P, r64, r64p), reduce128(b0, P, r64, r64p)});
+  st2(acc + (((size_t)k * 2 + 1) * ext + t) * N + n,
+      ulonglong2{reduce128(a1, P, r64, r64p), reduce128(b1, P, r64, r64p)});
 }
 void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
                  int level, u64 galois_perm) {
@@ -313,7 +334,7 @@ void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, cons
   ProfScope prof_(PROF_KSK_INNER, C.stream, ((double)batch * dn + 2.0 * dn + 2.0 * batch) * ext * C.N * 8);
   prof_count_launches(1);
   const unsigned tx = 32u * (unsigned)std::max(1, 8 / batch);  // about 256 threads per CTA
-  const dim3 block(tx, (unsigned)batch), grid((unsigned)(C.N / tx), (unsigned)ext);
+  const dim3 block(tx, (unsigned)batch), grid((unsigned)(C.N / 2 / tx), (unsigned)ext);
   k_ksk_inner_kernel<<<grid, block, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, d, d_stride, key, acc, level, dn, C.alpha,
                                                    C.n_q, C.n_p, C.log_n, galois_perm);
   HEDAP_LAUNCH_CHECK();
