@@ -9,6 +9,7 @@
 
 #include "internal.cuh"
 #include "kernels.cuh"
+#include "profiler.cuh"
 
 namespace hedap {
 
@@ -139,11 +140,18 @@ const LevelConsts& level_consts(Ctx& C, int l) {
   HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   if (l >= 1) {
     const u64 ql = q[l];
+    std::vector<u64> r(3 * (size_t)l);
     for (int i = 0; i < l; ++i) {
       L->rescale.ql_mod[i] = ql % q[i];
       L->rescale.inv[i] = h_invmod(ql % q[i], q[i]);
       L->rescale.inv_sh[i] = h_shoup(L->rescale.inv[i], q[i]);
+      r[i] = L->rescale.ql_mod[i];
+      r[l + i] = L->rescale.inv[i];
+      r[2 * l + i] = L->rescale.inv_sh[i];
     }
+    L->d_rescale = DevBuf(r.size(), C.stream);
+    HEDAP_CUDA(cudaMemcpyAsync(L->d_rescale.p, r.data(), r.size() * 8, cudaMemcpyHostToDevice, C.stream));
+    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   }
   auto& ref = *L;
   C.lc[l] = std::move(L);
@@ -203,8 +211,18 @@ static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, in
   ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream);
   DevBuf v((size_t)batch * 2 * nl * N, C.stream);
   k_moddown_spread(C, acc.p, v.p, 2 * batch, l);
-  ntt_forward(C.tab, qset(v.p, nl * N, 2 * batch, 0, l + 1), C.stream);
-  k_moddown_finish(C, acc.p, v.p, out, out_stride, 2 * batch, l, acc0, acc1);
+  // NTT of the conversion with the ModDown finish, (acc - v) P^-1 (+ out), fused into its store
+  const u64* Pinv = C.d_moddown.p + 3 * K + (size_t)K * C.n_q;
+  NttAux fw{};
+  fw.fin_dst = out;
+  fw.fin_dst_stride = out_stride;
+  fw.fin_c = acc.p;
+  fw.fin_c_stride = (size_t)ext * N;
+  fw.fin_w = Pinv;
+  fw.fin_wsh = Pinv + C.n_q;
+  fw.fin_acc_even = acc0 ? 1 : 0;
+  fw.fin_acc_odd = acc1 ? 1 : 0;
+  ntt_forward(C.tab, qset(v.p, nl * N, 2 * batch, 0, l + 1), C.stream, &fw);
 }
 
 void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
@@ -258,15 +276,26 @@ std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a) {
   const LevelConsts& LC = level_consts(C, l);
   auto o = ct_alloc(C, l - 1, a.batch);
   o->scale = a.scale / (double)C.primes[l];
+  // the last limb to the coefficient domain (read in place), then one forward transform whose
+  // load spreads its centred residue into every other prime and whose store finishes the rescale
   DevBuf last(P * N, C.stream);
-  HEDAP_CUDA(cudaMemcpy2DAsync(last.p, N * 8, a.part(0) + (size_t)l * N, a.part_stride() * 8, N * 8, P,
-                               cudaMemcpyDeviceToDevice, C.stream));
-  ntt_inverse(C.tab, qset(last.p, N, P, 0, 1, l), C.stream);
+  NttAux inv{};
+  inv.src = a.part(0) + (size_t)l * N;
+  inv.src_stride = a.part_stride();
+  ntt_inverse(C.tab, qset(last.p, N, P, 0, 1, l), C.stream, &inv);
   DevBuf tmp((size_t)P * l * N, C.stream);
-  k_rescale_spread(C, last.p, N, tmp.p, (size_t)l * N, P, l, LC.rescale);
-  ntt_forward(C.tab, qset(tmp.p, (size_t)l * N, P, 0, l), C.stream);
-  k_rescale_finish(C, a.part(0), a.part_stride(), tmp.p, (size_t)l * N, o->part(0), o->part_stride(), P, l,
-                   LC.rescale);
+  NttAux fw{};
+  fw.spread = last.p;
+  fw.spread_stride = N;
+  fw.spread_sub = LC.d_rescale.p;
+  fw.spread_prime = l;
+  fw.fin_dst = o->part(0);
+  fw.fin_dst_stride = o->part_stride();
+  fw.fin_c = a.part(0);
+  fw.fin_c_stride = a.part_stride();
+  fw.fin_w = LC.d_rescale.p + l;
+  fw.fin_wsh = LC.d_rescale.p + 2 * l;
+  ntt_forward(C.tab, qset(tmp.p, (size_t)l * N, P, 0, l), C.stream, &fw);
   return o;
 }
 

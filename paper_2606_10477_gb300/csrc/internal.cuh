@@ -131,6 +131,23 @@ struct NttAux {
   const u64* bconv = nullptr;  // [dn][alpha][ext]; their Shoup companions at bconv + bconv_sh_offset
   size_t bconv_sh_offset = 0;
   int ext = 0;
+  // forward only: the first phase loads the centred residue of one coefficient-domain limb (the
+  // last limb of a rescale, prime index spread_prime) into the prime of limb li:
+  //   m = x mod q_li, minus spread_sub[li] when x > q_spread / 2,  x = spread[part * spread_stride + n]
+  const u64* spread = nullptr;
+  size_t spread_stride = 0;
+  const u64* spread_sub = nullptr;
+  int spread_prime = 0;
+  // forward only: the second phase does not store the transform v; it writes
+  //   fin_dst[part][li] = (fin_c[part][li] - v) * fin_w[li]  (+ fin_dst[part][li] when the part's
+  //   parity bit is set), Shoup factors fin_w / fin_wsh per limb, canonical residues
+  u64* fin_dst = nullptr;
+  size_t fin_dst_stride = 0;
+  const u64* fin_c = nullptr;
+  size_t fin_c_stride = 0;
+  const u64* fin_w = nullptr;
+  const u64* fin_wsh = nullptr;
+  int fin_acc_even = 0, fin_acc_odd = 0;
 };
 void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
@@ -168,6 +185,7 @@ struct RescaleConsts {
 struct LevelConsts {  // device constants for one level (evaluator.cu)
   DevBuf modup;       // qhat_inv (+shoup) per Q prime, qhat mod target per digit (+shoup)
   DevBuf intt_post;   // per Q prime i <= l: N^-1 qhat_i^-1 mod q_i and its Shoup companion
+  DevBuf d_rescale;   // [ql_mod l][inv l][inv_sh l] (the rescale constants below, on the device)
   RescaleConsts rescale;
 };
 

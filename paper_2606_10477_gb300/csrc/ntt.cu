@@ -20,8 +20,10 @@
 // row phase's contiguous per-stage ranges for its blocks).  Optional fusions (NttAux):
 // the first phase may read another buffer (out of place) or compute its input as
 // the fast basis conversion of a key-switching digit (ModUp fused into the load),
-// the inverse may end with a per-limb factor other than N^-1, and a digit's own
-// limbs may be skipped.  Butterflies keep residues
+// the inverse may end with a per-limb factor other than N^-1, a digit's own
+// limbs may be skipped, and a rescale / ModDown may be fused around a forward
+// transform (its spread into the first phase's load, its finish into the second
+// phase's store).  Butterflies keep residues
 // lazily in [0, 4q) (forward) or [0, 2q) (inverse) following Harvey (2014);
 // the final launch writes canonical residues.
 #include "internal.cuh"
@@ -142,6 +144,18 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
       if (v >= q4) v -= q4;
       sm[idx] = v;
     }
+  } else if (A.spread) {  // fused rescale spread: centred residue of the last limb in this prime
+    const u64* x = A.spread + (size_t)part * A.spread_stride;
+    const u64 half = T.pr[A.spread_prime].q >> 1, sub = A.spread_sub[li];
+    const PrimeDev P = T.pr[pi];
+#pragma unroll
+    for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
+      const int c = idx / C, col = idx % C;
+      const u64 v = x[((size_t)c << L2) + r0 + col];
+      u64 m = barrett_reduce(v, 0, P);
+      if (v > half) m = sub_mod(m, sub, q);
+      sm[idx] = m;
+    }
   } else {
     const u64* src = first_src(A, S, part, li, N);
 #pragma unroll
@@ -225,6 +239,20 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
   __syncthreads();
   fwd_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
+  if (A.fin_dst) {  // fused epilogue of a rescale / ModDown: (c - v) * w (+ dst)
+    const u64* cp = A.fin_c + (size_t)part * A.fin_c_stride + (size_t)li * N + j0;
+    u64* dp = A.fin_dst + (size_t)part * A.fin_dst_stride + (size_t)li * N + j0;
+    const u64 w = A.fin_w[li], wp = A.fin_wsh[li];
+    const bool acc = (part & 1) ? A.fin_acc_odd : A.fin_acc_even;
+#pragma unroll
+    for (int idx = threadIdx.x; idx < E; idx += TPB) {
+      const u64 v = reduce4q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+      u64 z = shoup_mul(sub_mod(cp[idx], v, q), w, wp, q);
+      if (acc) z = add_mod(z, dp[idx], q);
+      dp[idx] = z;
+    }
+    return;
+  }
 #pragma unroll
   for (int idx = threadIdx.x; idx < E; idx += TPB)
     a[j0 + idx] = reduce4q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
@@ -392,10 +420,11 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
     return true;
   }();
   (void)attrs;
-  // the first phase applies src / z; the second runs in place on S
+  // the first phase applies src / z / spread; the second runs in place on S (or into fin_dst)
   NttAux A2 = A;
   A2.src = nullptr;
   A2.z = nullptr;
+  A2.spread = nullptr;
   if (!inverse) {
     k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
     k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A2);
@@ -427,6 +456,9 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   if (A.own_alpha && (A.own_dn < 1 || A.own_alpha > 8)) throw Error(HEDAP_ERR_ARG, "NTT: bad digit layout");
   if (A.z && (inverse || !A.own_alpha || !A.bconv || !A.bconv_sh_offset)) throw Error(HEDAP_ERR_ARG, "NTT: bad ModUp fusion");
   if (A.post && !inverse) throw Error(HEDAP_ERR_ARG, "NTT: post factors apply to the inverse only");
+  if ((A.spread || A.fin_dst) && inverse) throw Error(HEDAP_ERR_ARG, "NTT: fused rescale applies to the forward only");
+  if (A.spread && (A.z || A.src || !A.spread_sub)) throw Error(HEDAP_ERR_ARG, "NTT: bad spread fusion");
+  if (A.fin_dst && (!A.fin_c || !A.fin_w || !A.fin_wsh)) throw Error(HEDAP_ERR_ARG, "NTT: bad epilogue fusion");
   const int v = inverse ? T.ntt_inv_variant : T.ntt_fwd_variant;
   // algorithmic bytes: each transformed limb read once and written once (a digit's own limbs are skipped)
   const double limbs = (double)S.n_parts * S.n_limbs - (A.own_alpha ? (double)S.n_parts / A.own_dn * A.own_limit : 0.0);
