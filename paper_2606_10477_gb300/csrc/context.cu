@@ -133,7 +133,19 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   md.insert(md.end(), pinv.begin(), pinv.end());
   md.insert(md.end(), pinv_sh.begin(), pinv_sh.end());
   md.insert(md.end(), halfq.begin(), halfq.end());
+  // fused ModDown: the special-prime iNTT ends with N^-1 phinv_k, the conversion adds
+  // c_k = floor(P/2) phinv_k and multiplies by phat_q with Shoup companions
+  std::vector<u64> md2;
+  for (int k = 0; k < K; ++k) {
+    const u64 pk = p_of(k), w = h_mulmod(h_invmod(N % pk, pk), phinv[k], pk);
+    md2.push_back(w);
+    md2.push_back(h_shoup(w, pk));
+  }
+  for (int k = 0; k < K; ++k) md2.push_back(h_mulmod(halfP_mod(p_of(k)), phinv[k], p_of(k)));
+  for (int k = 0; k < K; ++k)
+    for (int i = 0; i < nq; ++i) md2.push_back(h_shoup(md[3 * K + (size_t)k * nq + i], C->primes[i]));
   upload(*C, C->d_moddown, md);
+  upload(*C, C->d_moddown2, md2);
   std::vector<u64> pm(T);
   for (int t = 0; t < T; ++t) pm[t] = P_mod(C->primes[t]);
   upload(*C, C->d_pmod, pm);

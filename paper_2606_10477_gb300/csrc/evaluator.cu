@@ -208,12 +208,27 @@ static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, in
   const int K = C.n_p, ext = l + 1 + K;
   DevBuf acc((size_t)batch * 2 * ext * N, C.stream);
   k_ksk_inner(C, y.p, d, d_stride, key.p, acc.p, batch, l, perm);
-  ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream);
+  // ModDown: the special-prime limbs to the coefficient domain (ending with N^-1 phinv_k when the
+  // conversion is fused), the conversion into every Q prime fused into the forward NTT's load, and
+  // (acc - v) P^-1 (+ out) fused into its store
+  const bool fuse = K <= 5;
+  NttAux inv{};
+  if (fuse) inv.post = C.d_moddown2.p;
+  ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream, &inv);
   DevBuf v((size_t)batch * 2 * nl * N, C.stream);
-  k_moddown_spread(C, acc.p, v.p, 2 * batch, l);
-  // NTT of the conversion with the ModDown finish, (acc - v) P^-1 (+ out), fused into its store
+  if (!fuse) k_moddown_spread(C, acc.p, v.p, 2 * batch, l);
   const u64* Pinv = C.d_moddown.p + 3 * K + (size_t)K * C.n_q;
   NttAux fw{};
+  if (fuse) {
+    fw.pconv = acc.p + nl * N;
+    fw.pconv_stride = (size_t)ext * N;
+    fw.pconv_K = K;
+    fw.pconv_nq = C.n_q;
+    fw.pconv_c = C.d_moddown2.p + 2 * K;
+    fw.pconv_phat = C.d_moddown.p + 3 * K;
+    fw.pconv_phat_sh = C.d_moddown2.p + 3 * K;
+    fw.pconv_half = C.d_moddown.p + 3 * K + (size_t)K * C.n_q + 2 * (size_t)C.n_q;
+  }
   fw.fin_dst = out;
   fw.fin_dst_stride = out_stride;
   fw.fin_c = acc.p;

@@ -116,8 +116,8 @@ struct NttAux {
   // out of place: the first phase reads limb li of part p at src + p * src_stride + li * N
   const u64* src = nullptr;
   size_t src_stride = 0;
-  // inverse only: the final factor of limb li is the pair post[2 li], post[2 li + 1] (value, Shoup
-  // companion) instead of N^-1
+  // inverse only: the final factor of limb li is the pair post[2 r], post[2 r + 1] (value, Shoup
+  // companion), r = li - limb_begin, instead of N^-1
   const u64* post = nullptr;
   // skip the limbs li of digit j = part % own_dn, li in [j own_alpha, min((j + 1) own_alpha, own_limit))
   int own_alpha = 0;
@@ -138,6 +138,17 @@ struct NttAux {
   size_t spread_stride = 0;
   const u64* spread_sub = nullptr;
   int spread_prime = 0;
+  // forward only: the first phase loads ModDown's conversion of the K special-prime limbs
+  // (coefficient domain, z_k = x_k phinv_k at pconv + part * pconv_stride + k * N) into the prime
+  // of limb li: sum_k [z_k + c_k]_{p_k} phat_k mod q_li - floor(P/2) mod q_li
+  const u64* pconv = nullptr;
+  size_t pconv_stride = 0;
+  int pconv_K = 0;
+  int pconv_nq = 0;
+  const u64* pconv_c = nullptr;       // [K] floor(P/2) phinv_k mod p_k
+  const u64* pconv_phat = nullptr;    // [K][n_q] (P / p_k) mod q_i
+  const u64* pconv_phat_sh = nullptr; // their Shoup companions
+  const u64* pconv_half = nullptr;    // [n_q] floor(P/2) mod q_i
   // forward only: the second phase does not store the transform v; it writes
   //   fin_dst[part][li] = (fin_c[part][li] - v) * fin_w[li]  (+ fin_dst[part][li] when the part's
   //   parity bit is set), Shoup factors fin_w / fin_wsh per limb, canonical residues
@@ -205,6 +216,7 @@ struct Ctx {
   std::vector<PrimeDev> pdev;
   DevBuf d_primes, d_psi2, d_ipsi2, d_ninv, d_ninv_sh;
   DevBuf d_moddown;   // level-independent ModDown constants
+  DevBuf d_moddown2;  // for the fused ModDown: [N^-1 phinv_k, Shoup][K] pairs, c_k [K], phat_q Shoup [K][n_q]
   DevBuf d_r64;       // per prime: 2^64 mod q and its Shoup companion
   DevBuf d_pmod;      // per prime: P mod q_t (key generation)
   Tables tab{};

@@ -144,6 +144,30 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
       if (v >= q4) v -= q4;
       sm[idx] = v;
     }
+  } else if (A.pconv) {  // fused ModDown conversion of the special-prime limbs into this prime
+    const u64* zp = A.pconv + (size_t)part * A.pconv_stride;
+    u64 c[8], pk[8], f[8], fs[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const bool on = k < A.pconv_K;
+      c[k] = on ? A.pconv_c[k] : 0;
+      pk[k] = on ? T.pr[A.pconv_nq + k].q : 0;
+      f[k] = on ? A.pconv_phat[(size_t)k * A.pconv_nq + li] : 0;
+      fs[k] = on ? A.pconv_phat_sh[(size_t)k * A.pconv_nq + li] : 0;
+    }
+    const u64 off = (q << 2) - A.pconv_half[li], q4 = q << 2, q8 = q << 3;
+#pragma unroll
+    for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
+      const int cc = idx / C, col = idx % C;
+      const size_t n = ((size_t)cc << L2) + r0 + col;
+      u64 v = off;  // sum of K <= 5 lazy products (< 2Kq) + 4q - floor(P/2) mod q  ->  < 14q
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < A.pconv_K) v += shoup_mul_lazy(add_mod(zp[(size_t)k * N + n], c[k], pk[k]), f[k], fs[k], q);
+      if (v >= q8) v -= q8;
+      if (v >= q4) v -= q4;
+      sm[idx] = v;
+    }
   } else if (A.spread) {  // fused rescale spread: centred residue of the last limb in this prime
     const u64* x = A.spread + (size_t)part * A.spread_stride;
     const u64 half = T.pr[A.spread_prime].q >> 1, sub = A.spread_sub[li];
@@ -381,7 +405,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S,
   }
   __syncthreads();
   inv_cols_passes<L1, C, RL, 0>(sm, tw, q);
-  const u64 ni = A.post ? A.post[2 * li] : T.ninv[pi], nip = A.post ? A.post[2 * li + 1] : T.ninv_sh[pi];
+  const int pr_ = li - S.limb_begin;
+  const u64 ni = A.post ? A.post[2 * pr_] : T.ninv[pi], nip = A.post ? A.post[2 * pr_ + 1] : T.ninv_sh[pi];
 #pragma unroll
   for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
     const int c = idx / C, col = idx % C;
@@ -425,6 +450,7 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
   A2.src = nullptr;
   A2.z = nullptr;
   A2.spread = nullptr;
+  A2.pconv = nullptr;
   if (!inverse) {
     k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
     k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A2);
@@ -456,7 +482,10 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   if (A.own_alpha && (A.own_dn < 1 || A.own_alpha > 8)) throw Error(HEDAP_ERR_ARG, "NTT: bad digit layout");
   if (A.z && (inverse || !A.own_alpha || !A.bconv || !A.bconv_sh_offset)) throw Error(HEDAP_ERR_ARG, "NTT: bad ModUp fusion");
   if (A.post && !inverse) throw Error(HEDAP_ERR_ARG, "NTT: post factors apply to the inverse only");
-  if ((A.spread || A.fin_dst) && inverse) throw Error(HEDAP_ERR_ARG, "NTT: fused rescale applies to the forward only");
+  if ((A.spread || A.fin_dst || A.pconv) && inverse)
+    throw Error(HEDAP_ERR_ARG, "NTT: fused rescale / ModDown applies to the forward only");
+  if (A.pconv && (A.pconv_K < 1 || A.pconv_K > 5 || A.z || A.src || A.spread))
+    throw Error(HEDAP_ERR_ARG, "NTT: bad ModDown fusion");
   if (A.spread && (A.z || A.src || !A.spread_sub)) throw Error(HEDAP_ERR_ARG, "NTT: bad spread fusion");
   if (A.fin_dst && (!A.fin_c || !A.fin_w || !A.fin_wsh)) throw Error(HEDAP_ERR_ARG, "NTT: bad epilogue fusion");
   const int v = inverse ? T.ntt_inv_variant : T.ntt_fwd_variant;
