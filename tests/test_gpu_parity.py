@@ -194,6 +194,29 @@ def test_hoisted_rotations_bit_exact(name, request):
             same_ct(gc, oc)
 
 
+@pytest.mark.parametrize("name", ["n12a4", "n12a8"])
+def test_wide_digits_bit_exact(name):
+    """Digits of 4 and 8 primes (5 and 8 special primes): the fused and the unfused ModDown paths."""
+    g, o = make_pair(name)
+    L = o.n_q - 1
+    for level in (L, 4):
+        ga, oa = imported_pair(g, o, 41 + level, level)
+        gb, ob = imported_pair(g, o, 42 + level, level)
+        same_ct(g.mul(ga, gb), o.mul(oa, ob))
+        same_ct(g.rotate(ga, 3), o.rotate(oa, 3))
+        for gc, oc in zip(g.rotate_hoisted(ga, [1, -2]), o.rotate_hoisted(oa, [1, -2])):
+            same_ct(gc, oc)
+
+
+def test_invsqrt_n16_three_digits():
+    """N = 2^16, 24 x 50-bit primes, dnum = 3 (8 special primes): MRE <= 1e-7."""
+    p = inputs.PRESETS["n16d3"]
+    g = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], 0, 5)
+    a = inputs.uniform_values(43, g.N // 2, 1e-3, 1.0)
+    y = g.decrypt(g.invsqrt(g.encrypt(a, g.n_q - 1, 44), 1e-3, 1.0, 1.0, 31, 3)).real
+    assert mre(y, a) <= MRE_TARGET
+
+
 def test_ring_ops_bit_exact_at_full_size():
     """N = 2^16, 24 + 2 primes, two primes per digit: one HMult, one rotation, one rescale."""
     p = inputs.PRESETS["n16"]
