@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-bts", action="store_true", help="skip the bootstrapped workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-level batch workload")
+    ap.add_argument("--no-dnum3", action="store_true", help="skip the three-digit key-switching variant")
     ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
     ap.add_argument("--only", choices=["ntt", "serving", "mixed"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
@@ -382,7 +383,8 @@ def run_ours(args):
     bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
                                                          stream=stream, rank=rank, batch=batch)
     mixed = None if args.no_mixed else mixed_workload(hedap, inputs, torch, stream, rank)
-    dnum3 = dnum3_variant(hedap, inputs, torch, stream, rank, batch, args.degree, args.iters, args.steps)
+    dnum3 = None if args.no_dnum3 else dnum3_variant(hedap, inputs, torch, stream, rank, batch, args.degree,
+                                                     args.iters, args.steps)
     serving = None if args.no_serving else serving_workload(hedap, inputs, torch, stream, rank, args.serve_queries)
 
     if rank == 0:
