@@ -99,6 +99,10 @@ def measured_peaks():
 # plus 1 for loop and address work: 22.5 issue slots per butterfly.
 NTT_INSTR_PER_BUTTERFLY = 22.5
 GB300_SMS, SCHEDULERS_PER_SM, LANES = 152, 4, 32
+# DRAM bytes per transformed limb (both phase launches), dram__bytes_read.sum + dram__bytes_write.sum
+# of one forward and one inverse transform of 384 limbs (`--only ntt --ntt-limbs 384 --profile-region`
+# under ncu), scaled to a launch group by its limbs
+NTT_DRAM_BYTES_PER_LIMB = 1.92e6
 
 
 def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
@@ -109,7 +113,9 @@ def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = GB300_SMS * SCHEDULERS_PER_SM * LANES * mhz * 1e6 / NTT_INSTR_PER_BUTTERFLY / 1e9
     return {"kernel": "ntt", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": NTT_DRAM_BYTES_PER_LIMB * limbs / max(1, groups),
+            "traffic_unit": "bytes per launch group (ncu, scaled per limb)",
+            "algorithmic_bytes_per_group": alg_bytes / max(1, groups),
             "peak_source": f"derived: {GB300_SMS} SMs x {SCHEDULERS_PER_SM} schedulers x {LANES} lanes x {mhz:.0f} MHz "
                            f"/ {NTT_INSTR_PER_BUTTERFLY} instructions per butterfly",
             "launch_groups": groups, "avg_group_us": 1e3 * ms / max(1, groups),
