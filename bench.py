@@ -92,13 +92,12 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# Instructions of a minimal lazy Cooley-Tukey / Gentleman-Sande butterfly on 32-bit integer units
-# (no 64-bit multiplier): Shoup product 12 (high half of x * w' in four wide multiply-adds + a
-# 64-bit add; x * w - qh * q in two wide and four low multiply-adds), the lazy correction of x 4,
-# the two 64-bit sums 4, shared-memory traffic and twiddle loads of radix-16 passes 1.5 -> 21.5,
-# plus 1 for loop and address work: 22.5 issue slots per butterfly.
-NTT_INSTR_PER_BUTTERFLY = 22.5
-GB300_SMS, SCHEDULERS_PER_SM, LANES = 152, 4, 32
+# The NTT is bound by the integer multiply-add pipe (there is no 64-bit multiplier): a lazy Shoup
+# butterfly needs the exact high half of x * w' (four 32 x 32 -> 64 products) and the low halves of
+# x * w and qh * q (two 32 x 32 -> 64 and four 32 x 32 -> 32 products): 6 wide products, each two
+# multiply-pipe slots, and 4 low ones = 16 slots per butterfly, against 64 multiply-add lanes per SM.
+NTT_MUL_SLOTS_PER_BUTTERFLY = 16
+GB300_SMS, IMAD_LANES_PER_SM = 152, 64
 # DRAM bytes per transformed limb (both phase launches), dram__bytes_read.sum + dram__bytes_write.sum
 # of one forward and one inverse transform of 384 limbs (`--only ntt --ntt-limbs 384 --profile-region`
 # under ncu), scaled to a launch group by its limbs
@@ -111,13 +110,13 @@ def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
     bfly = limbs * (n // 2) * log_n
     achieved = bfly / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = GB300_SMS * SCHEDULERS_PER_SM * LANES * mhz * 1e6 / NTT_INSTR_PER_BUTTERFLY / 1e9
+    peak = GB300_SMS * IMAD_LANES_PER_SM * mhz * 1e6 / NTT_MUL_SLOTS_PER_BUTTERFLY / 1e9
     return {"kernel": "ntt", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
             "frac": achieved / peak, "traffic": NTT_DRAM_BYTES_PER_LIMB * limbs / max(1, groups),
             "traffic_unit": "bytes per launch group (ncu, scaled per limb)",
             "algorithmic_bytes_per_group": alg_bytes / max(1, groups),
-            "peak_source": f"derived: {GB300_SMS} SMs x {SCHEDULERS_PER_SM} schedulers x {LANES} lanes x {mhz:.0f} MHz "
-                           f"/ {NTT_INSTR_PER_BUTTERFLY} instructions per butterfly",
+            "peak_source": f"derived: {GB300_SMS} SMs x {IMAD_LANES_PER_SM} integer multiply-add lanes x {mhz:.0f} MHz / "
+                           f"{NTT_MUL_SLOTS_PER_BUTTERFLY} multiply slots per Shoup butterfly",
             "launch_groups": groups, "avg_group_us": 1e3 * ms / max(1, groups),
             "butterflies_per_group": bfly / max(1, groups)}
 
@@ -341,8 +340,8 @@ def run_ours(args):
     ntt = prof["ntt"]
     ntt_gbs = ntt[2] / (ntt[1] / 1e3) / 1e9 if ntt[1] > 0 else None
     if dom == "ntt":
-        # the NTT is bound by integer issue, not HBM: butterflies = limbs x N/2 x log2 N, against the
-        # issue rate of a minimal 64-bit Shoup butterfly on 32-bit integer units
+        # the NTT is bound by the integer multiply-add pipe, not HBM: butterflies = limbs x N/2 x log2 N,
+        # against that pipe's rate for a 64-bit Shoup butterfly from 32-bit multiplies
         roofline = ntt_alu_roofline(ctx.N, by_dom, ms_dom, n_dom, peaks, clk)
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
