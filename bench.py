@@ -343,6 +343,7 @@ def run_ours(args):
         # the NTT is bound by the integer multiply-add pipe, not HBM: butterflies = limbs x N/2 x log2 N,
         # against that pipe's rate for a 64-bit Shoup butterfly from 32-bit multiplies
         roofline = ntt_alu_roofline(ctx.N, by_dom, ms_dom, n_dom, peaks, clk)
+        roofline["register_loop_gbutterfly_s"] = ctx.butterfly_rate() / 1e9
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,

@@ -398,6 +398,10 @@ void hedap_graph_destroy(hedap_graph* g);
  * to *fwd_variant / *inv_variant. */
 hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
                             int* fwd_variant, int* inv_variant);
+/* Butterflies per second of a register-only loop of the NTT's butterfly (no
+ * memory traffic): the rate the integer pipes allow this butterfly, beside
+ * which the transforms' rate is read.  Synchronises. */
+hedap_status hedap_butterfly_rate(hedap_ctx* ctx, double* per_s);
 /* Select NTT launch shapes directly (0 <= variant < 8); every shape computes
  * the same transform.  Context creation runs the autotuner once. */
 hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant);

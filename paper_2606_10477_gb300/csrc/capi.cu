@@ -501,6 +501,12 @@ API hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_
     if (inv_variant) *inv_variant = ctx->c->tab.ntt_inv_variant;
   });
 }
+API hedap_status hedap_butterfly_rate(hedap_ctx* ctx, double* per_s) {
+  return guarded_on(ctx, [&] {
+    need(ctx && per_s, "null argument");
+    *per_s = hedap::butterfly_rate(*ctx->c);
+  });
+}
 API hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant) {
   return guarded_on(ctx, [&] {
     need(ctx && fwd_variant >= 0 && fwd_variant < hedap::kNttVariants && inv_variant >= 0 &&

@@ -164,6 +164,7 @@ void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAu
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
 struct Ctx;
 void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vector<float>* inv_ms);
+double butterfly_rate(Ctx& C);  // butterflies per second of a register-only loop
 
 // ------------------------------------------------------------------ context and ciphertexts
 // One ciphertext, or a batch of `batch` ciphertexts at one level and scale:

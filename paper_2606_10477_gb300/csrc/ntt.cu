@@ -26,6 +26,8 @@
 // phase's store).  Butterflies keep residues
 // lazily in [0, 4q) (forward) or [0, 2q) (inverse) following Harvey (2014);
 // the final launch writes canonical residues.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "profiler.cuh"
 
@@ -511,6 +513,48 @@ void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAu
 }
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux) {
   dispatch(T, S, st, true, aux);
+}
+
+// Register-only loop of the transform's butterfly (the rate the integer pipes allow without any
+// memory or shared-memory traffic): each thread runs `iters` rounds of 4 independent lazy Cooley-
+// Tukey butterflies on 8 residues of the context's first prime and stores one word.
+__global__ void k_butterfly_loop(const Tables T, u64* out, int iters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const u64 q = T.pr[0].q;
+  const ulonglong2 w = T.psi2[1 + (threadIdx.x & 63)];
+  u64 v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = ((u64)i * 8 + m) % q;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ct_bfly(v[m], v[m + 4], w, q);
+  }
+  u64 s = 0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) s ^= v[m];
+  out[i] = s;
+}
+double butterfly_rate(Ctx& C) {
+  const int threads = 256, blocks = 152 * 8, iters = 512;
+  DevBuf out((size_t)threads * blocks, C.stream);
+  cudaEvent_t a, b;
+  HEDAP_CUDA(cudaEventCreate(&a));
+  HEDAP_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    HEDAP_CUDA(cudaEventRecord(a, C.stream));
+    k_butterfly_loop<<<blocks, threads, 0, C.stream>>>(C.tab, out.p, iters);
+    HEDAP_LAUNCH_CHECK();
+    HEDAP_CUDA(cudaEventRecord(b, C.stream));
+    HEDAP_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    HEDAP_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (r > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  prof_count_launches(3);
+  return (double)threads * blocks * iters * 4 / (best / 1e3);
 }
 
 // Time every variant on `limbs` limbs of scratch (forward and inverse separately,

@@ -31,7 +31,7 @@ EXPORTED = [
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_ntt_batch",
-    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
+    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
     "hedap_server_resume", "hedap_server_estimate", "hedap_invsqrt_graph_create", "hedap_graph_run",
     "hedap_graph_kernels", "hedap_graph_destroy",
@@ -168,6 +168,7 @@ def _declare(L):
         "hedap_ntt_tune": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "hedap_ntt_set_variant": (st, [vp, C.c_int, C.c_int]),
+        "hedap_butterfly_rate": (st, [vp, dp]),
         "hedap_select": (st, [vp, C.POINTER(SelectCfg), C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t),
                               C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t), C.POINTER(SelectTrace),
                               C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -324,6 +325,12 @@ class Context:
         _check(load().hedap_ntt_tune(self.h, limbs, reps, f, i, 16, C.byref(fv), C.byref(iv)))
         n = 8
         return list(f[:n]), list(i[:n]), fv.value, iv.value
+
+    def butterfly_rate(self) -> float:
+        """Butterflies per second of a register-only loop of the NTT butterfly."""
+        r = C.c_double()
+        _check(load().hedap_butterfly_rate(self.h, C.byref(r)))
+        return r.value
 
     def ntt_set_variant(self, fwd: int, inv: int):
         _check(load().hedap_ntt_set_variant(self.h, fwd, inv))
