@@ -359,11 +359,13 @@ def run_ours(args):
     h2d = sum(h.numel() * 8 for h in host_in)
     d2h = sum(h.numel() * 8 for h in host_out)
 
-    def e2e_step():
+    graph_e = ctx.invsqrt_graph(packed, LO, HI, B, args.degree, args.iters)
+
+    def e2e_step():  # host limbs in, the batch packed and run through the captured step, host limbs out
         ins = [ctx.ct_import(hi, L, ctx.scale) for hi in host_in]
-        outs = ctx.invsqrt_batch(ins, [(LO, HI, B, args.degree, args.iters, 0, 0)] * batch)
-        for co, ho in zip(outs, host_out):
-            co.export_to(ho)
+        out = graph_e.run(ctx.pack(ins))
+        for k, ho in enumerate(host_out):
+            ctx.unpack(out, k).export_to(ho)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -375,6 +377,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value, e2e_s, _ = replicas.aggregate(batch * k_e2e, e2e_s, torch.distributed if ws > 1 else None)
+    graph_e.close()
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
