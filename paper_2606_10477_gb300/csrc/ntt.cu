@@ -81,7 +81,9 @@ __device__ __forceinline__ void fwd_cols_passes(u64* sm, const ulonglong2* tw, u
     constexpr int K = (L1 - S0) < RL ? (L1 - S0) : RL;
     constexpr int TL = 1 << (L1 - S0 - K);
     constexpr int GROUPS = C << (L1 - K);
-    for (int g = threadIdx.x; g < GROUPS; g += blockDim.x) {
+    constexpr int TPB = (C << L1) >> RL;  // threads per CTA
+#pragma unroll
+    for (int g = threadIdx.x; g < GROUPS; g += TPB) {
       const uint32_t col = g % C, gg = g / C;
       const uint32_t low = gg & (TL - 1), high = gg >> (L1 - S0 - K);
       const uint32_t base = (high << (L1 - S0)) | low;
@@ -222,7 +224,9 @@ __device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* tw, u
     constexpr int TL = 1 << (L2 - S0 - K);
     constexpr int GPB = 1 << (L2 - K);
     constexpr int R = (1 << L2) + (1 << (L2 - 4));
-    for (int g = threadIdx.x; g < BPC * GPB; g += blockDim.x) {
+    constexpr int TPB = (BPC << L2) >> RL;
+#pragma unroll
+    for (int g = threadIdx.x; g < BPC * GPB; g += TPB) {
       const uint32_t b = g / GPB, gg = g % GPB;
       const uint32_t low = gg & (TL - 1), high = gg >> (L2 - S0 - K);
       const uint32_t base = (high << (L2 - S0)) | low;
@@ -304,7 +308,9 @@ __device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* tw, u
     constexpr int K = (L2 - LT0) < RL ? (L2 - LT0) : RL;
     constexpr int GPB = 1 << (L2 - K);
     constexpr int R = (1 << L2) + (1 << (L2 - 4));
-    for (int g = threadIdx.x; g < BPC * GPB; g += blockDim.x) {
+    constexpr int TPB = (BPC << L2) >> RL;
+#pragma unroll
+    for (int g = threadIdx.x; g < BPC * GPB; g += TPB) {
       const uint32_t b = g / GPB, gg = g % GPB;
       const uint32_t low = gg & ((1u << LT0) - 1), high = gg >> LT0;
       const uint32_t base = (high << (LT0 + K)) | low;
@@ -361,7 +367,9 @@ __device__ __forceinline__ void inv_cols_passes(u64* sm, const ulonglong2* tw, u
   if constexpr (LC0 < L1) {
     constexpr int K = (L1 - LC0) < RL ? (L1 - LC0) : RL;
     constexpr int GROUPS = C << (L1 - K);
-    for (int g = threadIdx.x; g < GROUPS; g += blockDim.x) {
+    constexpr int TPB = (C << L1) >> RL;
+#pragma unroll
+    for (int g = threadIdx.x; g < GROUPS; g += TPB) {
       const uint32_t col = g % C, gg = g / C;
       const uint32_t low = gg & ((1u << LC0) - 1), high = gg >> LC0;
       const uint32_t base = (high << (LC0 + K)) | low;
