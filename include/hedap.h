@@ -74,10 +74,13 @@ typedef struct {
  * degree-`degree` Chebyshev interpolant of 1/sqrt(x) on [lo/B, hi/B];
  * `newton_iters` Newton steps y <- y (3 - (a/B) y^2) / 2 follow; the output is
  * y / sqrt(B) (applied to the scale label).  pre_bts = 1 bootstraps a/B
- * before everything (the paper's Pre-BTS indicator c); bit j < 63 of bts_mask
+ * before everything (the paper's Pre-BTS indicator c); bit j < 62 of bts_mask
  * bootstraps y before Newton step j (bit 0 = right after the Chebyshev step,
  * Alg. 1); bit 63 bootstraps y lazily whenever the next step would run out of
- * levels.  Both need hedap_bootstrap_setup on the context. */
+ * levels; bit 62 (a variant, not in Alg. 1) also bootstraps ct_x = 0.5 a/B
+ * whenever y is bootstrapped and ct_x has fewer than 5 levels (a Newton output
+ * sits two levels below ct_x).  All need hedap_bootstrap_setup on the
+ * context. */
 typedef struct {
   double lo, hi, B;
   uint32_t degree;

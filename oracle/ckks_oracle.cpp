@@ -1132,8 +1132,10 @@ static Ct newton_step(Ctx& C, const Ct& x, const Ct& y) {
 // bit j (< 63) of bts_mask bootstraps y before Newton step j (bit 0: right
 // after the Chebyshev step, as in Alg. 1); bit 63 bootstraps lazily, before a
 // step that would leave y below level 1 (fewer than 3 levels), so that later
-// bootstraps stay possible whatever number of steps follows.  ct_x is never
-// bootstrapped.  Y, the power of two
+// bootstraps stay possible whatever number of steps follows.  ct_x is not
+// bootstrapped in Alg. 1 (a Newton output sits two levels below it); bit 62 (a
+// variant) bootstraps it too whenever y is bootstrapped and x has fewer than 5
+// levels, scaled by Yx, the power of two bounding x = 0.5 a/B.  Y, the power of two
 // that bounds y = 1/sqrt(a/B), scales y into [-1, 1] around each BTS.
 static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   if (cfg.B <= 0 || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.iters < 0)
@@ -1156,11 +1158,15 @@ static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   std::vector<double> coeffs = cheb_coeffs(lo, hi, cfg.degree);
   ChebEval ev(C);
   Ct y = ev.run(t, coeffs);
-  const bool lazy = (cfg.bts_mask >> 63) & 1;
+  const bool lazy = (cfg.bts_mask >> 63) & 1, lazy_x = (cfg.bts_mask >> 62) & 1;
+  i64 Yx = 1; while ((double)Yx < 0.5 * hi) Yx *= 2;
   for (int i = 0; i < cfg.iters; ++i) {
-    bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
+    bool force = i < 62 && ((cfg.bts_mask >> i) & 1);
     bool need = lazy && y.level < 3;  // the step would leave y below level 1
-    if (force || need) y = bootstrap_scaled(C, y, Y);
+    if (force || need) {
+      y = bootstrap_scaled(C, y, Y);
+      if (lazy_x && x.level < 5) x = bootstrap_scaled(C, x, Yx);
+    }
     if (std::min(y.level, x.level) < 2) throw std::runtime_error("invsqrt: level exhausted in Newton loop");
     y = newton_step(C, x, y);
   }

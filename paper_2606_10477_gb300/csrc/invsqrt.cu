@@ -153,12 +153,15 @@ static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
 }
 
 // Bootstrapping placement (the Pre-BTS indicator c of Sec. 4.1 and BTS during
-// the Newton loop, Sec. 4.3): pre_bts bootstraps a/B first; bit j (< 63) of
+// the Newton loop, Sec. 4.3): pre_bts bootstraps a/B first; bit j (< 62) of
 // bts_mask bootstraps y before Newton step j (bit 0: right after the Chebyshev
 // step, as in Alg. 1); bit 63 bootstraps lazily, before any step that would
 // leave y below level 1 (y has fewer than 3 levels), so that a later bootstrap
 // stays possible and the state after i steps does not depend on how many steps
-// follow.  ct_x is never bootstrapped.  Y, the power of two bounding y, scales
+// follow.  ct_x is not bootstrapped in Alg. 1 (a Newton output sits two levels
+// below it); bit 62 (a variant) bootstraps it too whenever y is bootstrapped and
+// x has fewer than 5 levels, scaled by the power of two bounding x = 0.5 a/B.
+// Y, the power of two bounding y, scales
 // y into [-1, 1] around each BTS.  The final 1/sqrt(B) is applied to the scale
 // label (no level is used).
 InvSqrtRun::InvSqrtRun(Ctx& C_, const Ct& in, const hedap_invsqrt_cfg& c) : C(C_), cfg(c) {
@@ -186,9 +189,16 @@ InvSqrtRun::InvSqrtRun(Ctx& C_, const Ct& in, const hedap_invsqrt_cfg& c) : C(C_
 }
 void InvSqrtRun::chebyshev() { y = cheb_eval(C, *t, cheb_interp(lo, hi, (int)cfg.degree), C.scale); }
 void InvSqrtRun::newton(int i) {
-  const bool force = i < 63 && ((cfg.bts_mask >> i) & 1);
+  const bool force = i < 62 && ((cfg.bts_mask >> i) & 1);
   const bool lazy = ((cfg.bts_mask >> 63) & 1) && y->level < 3;
-  if (force || lazy) y = bootstrap_scaled(C, *y, Y);
+  if (force || lazy) {
+    y = bootstrap_scaled(C, *y, Y);
+    if (((cfg.bts_mask >> 62) & 1) && x->level < 5) {  // variant: ct_x refreshed with y
+      i64 Yx = 1;
+      while ((double)Yx < 0.5 * hi) Yx *= 2;
+      x = bootstrap_scaled(C, *x, Yx);
+    }
+  }
   if (std::min(y->level, x->level) < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: level exhausted in Newton loop");
   y = newton_step(C, *x, *y);
 }

@@ -123,3 +123,12 @@ def test_encoder_and_diagonals_match_oracle(pair12):
         for grp in range(3):
             for off, d in o.fft_group(3, inverse, grp).items():
                 assert np.array_equal(g.bts_diagonal(inverse, grp, off), d)
+
+
+def test_ct_x_rebootstrapping_variant_bit_exact(pair12):
+    g, o = pair12
+    a = inputs.uniform_values(5, o.N // 2, 0.1, 1.0)
+    oc = o.encrypt(a, 5, 6)
+    gc = g.ct_import(oc.limbs(), oc.level, oc.scale)
+    mask = (1 << 63) | (1 << 62)
+    same(g.invsqrt(gc, 0.1, 1.0, 1.0, 3, 5, 0, mask), o.invsqrt(oc, 0.1, 1.0, 1.0, 3, 5, 0, mask))

@@ -99,3 +99,19 @@ def test_invsqrt_with_lazy_bootstrapping_reproduces_fp64_model(ctx):
     y = ctx.decrypt(ctx.invsqrt(ctx.encrypt(a, L_after, 17), 1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63)).real
     plain = oracle.plain_invsqrt(a, 1e-4, 1.0, 1.0, 15, 5)
     assert np.max(np.abs(y - plain) / plain) < 1e-4
+
+
+def test_ct_x_rebootstrapping_variant(ctx):
+    """Bit 62: ct_x is bootstrapped with y when it has fewer than 5 levels.  From level 5 (x at 4)
+    every Alg. 1 Newton step needs a bootstrap of y; with the variant the refreshed x lets steps run
+    from the bootstrapped level, so the result sits higher, and its error is that of one bootstrap of
+    x (Newton does not correct x), far above Alg. 1's."""
+    a = inputs.uniform_values(5, ctx.N // 2, 0.1, 1.0)
+    ct = ctx.encrypt(a, 5, 6)
+    lazy = 1 << 63
+    alg1 = ctx.invsqrt(ct, 0.1, 1.0, 1.0, 3, 5, 0, lazy)
+    var = ctx.invsqrt(ct, 0.1, 1.0, 1.0, 3, 5, 0, lazy | (1 << 62))
+    assert var.level > alg1.level
+    err_alg1 = np.mean(np.abs(ctx.decrypt(alg1).real * np.sqrt(a) - 1))
+    err_var = np.mean(np.abs(ctx.decrypt(var).real * np.sqrt(a) - 1))
+    assert err_alg1 < 1e-8 and err_var < 1e-4
