@@ -479,7 +479,7 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
 
 def dnum3_variant(hedap, inputs, torch, stream, rank, batch, degree, iters, steps):
     """The same InvSqrt step on the same ring with three key-switching digits (dnum = 3, as the
-    workload names it; 8 special primes of 60 bits instead of 2 so that P exceeds a 400-bit digit)."""
+    workload names it; 7 special primes of 60 bits instead of 2 so that P exceeds a 400-bit digit)."""
     p = inputs.PRESETS["n16d3"]
     ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 51 + rank,
                         stream=stream.cuda_stream)
@@ -504,7 +504,7 @@ def dnum3_variant(hedap, inputs, torch, stream, rank, batch, degree, iters, step
     value = batch * steps / (e0.elapsed_time(e1) / 1e3)
     graph.close()
     ctx.close()
-    return {"workload": f"as the main step with 8 primes per key-switching digit (dnum 3) and 8 x 60-bit special "
+    return {"workload": f"as the main step with 8 primes per key-switching digit (dnum 3) and 7 x 60-bit special "
                         f"primes, batch {batch}", "value": value, "unit": UNIT, "mre": max(mres)}
 
 

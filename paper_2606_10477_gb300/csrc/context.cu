@@ -144,8 +144,10 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   for (int k = 0; k < K; ++k) md2.push_back(h_mulmod(halfP_mod(p_of(k)), phinv[k], p_of(k)));
   for (int k = 0; k < K; ++k)
     for (int i = 0; i < nq; ++i) md2.push_back(h_shoup(md[3 * K + (size_t)k * nq + i], C->primes[i]));
+  for (int k = 0; k < K; ++k) md2.push_back(p_of(k));
   upload(*C, C->d_moddown, md);
   upload(*C, C->d_moddown2, md2);
+
   std::vector<u64> pm(T);
   for (int t = 0; t < T; ++t) pm[t] = P_mod(C->primes[t]);
   upload(*C, C->d_pmod, pm);

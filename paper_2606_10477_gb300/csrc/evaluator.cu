@@ -211,7 +211,7 @@ static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, in
   // ModDown: the special-prime limbs to the coefficient domain (ending with N^-1 phinv_k when the
   // conversion is fused), the conversion into every Q prime fused into the forward NTT's load, and
   // (acc - v) P^-1 (+ out) fused into its store
-  const bool fuse = K <= 5;
+  const bool fuse = K <= 8;
   NttAux inv{};
   if (fuse) inv.post = C.d_moddown2.p;
   ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream, &inv);
@@ -223,7 +223,8 @@ static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, in
     fw.pconv = acc.p + nl * N;
     fw.pconv_stride = (size_t)ext * N;
     fw.pconv_K = K;
-    fw.pconv_nq = C.n_q;
+    fw.pconv_ld = C.n_q;
+    fw.pconv_q = C.d_moddown2.p + 3 * K + (size_t)K * C.n_q;
     fw.pconv_c = C.d_moddown2.p + 2 * K;
     fw.pconv_phat = C.d_moddown.p + 3 * K;
     fw.pconv_phat_sh = C.d_moddown2.p + 3 * K;

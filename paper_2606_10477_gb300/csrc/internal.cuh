@@ -138,17 +138,18 @@ struct NttAux {
   size_t spread_stride = 0;
   const u64* spread_sub = nullptr;
   int spread_prime = 0;
-  // forward only: the first phase loads ModDown's conversion of the K special-prime limbs
-  // (coefficient domain, z_k = x_k phinv_k at pconv + part * pconv_stride + k * N) into the prime
-  // of limb li: sum_k [z_k + c_k]_{p_k} phat_k mod q_li - floor(P/2) mod q_li
+  // forward only: the first phase loads the ModDown conversion of K special limbs (coefficient
+  // domain, z_k = x_k shat_k^-1 at pconv + part * pconv_stride + k * N, moduli s_k = pconv_q[k],
+  // S = prod s_k) into the prime of limb li: sum_k [z_k + c_k]_{s_k} shat_k mod q_li - floor(S/2)
   const u64* pconv = nullptr;
   size_t pconv_stride = 0;
   int pconv_K = 0;
-  int pconv_nq = 0;
-  const u64* pconv_c = nullptr;       // [K] floor(P/2) phinv_k mod p_k
-  const u64* pconv_phat = nullptr;    // [K][n_q] (P / p_k) mod q_i
+  int pconv_ld = 0;                   // row length of the per-target tables
+  const u64* pconv_q = nullptr;       // [K] the special moduli s_k
+  const u64* pconv_c = nullptr;       // [K] floor(S/2) shat_k^-1 mod s_k
+  const u64* pconv_phat = nullptr;    // [K][ld] (S / s_k) mod q_i
   const u64* pconv_phat_sh = nullptr; // their Shoup companions
-  const u64* pconv_half = nullptr;    // [n_q] floor(P/2) mod q_i
+  const u64* pconv_half = nullptr;    // [ld] floor(S/2) mod q_i
   // forward only: the second phase does not store the transform v; it writes
   //   fin_dst[part][li] = (fin_c[part][li] - v) * fin_w[li]  (+ fin_dst[part][li] when the part's
   //   parity bit is set), Shoup factors fin_w / fin_wsh per limb, canonical residues
@@ -217,7 +218,7 @@ struct Ctx {
   std::vector<PrimeDev> pdev;
   DevBuf d_primes, d_psi2, d_ipsi2, d_ninv, d_ninv_sh;
   DevBuf d_moddown;   // level-independent ModDown constants
-  DevBuf d_moddown2;  // for the fused ModDown: [N^-1 phinv_k, Shoup][K] pairs, c_k [K], phat_q Shoup [K][n_q]
+  DevBuf d_moddown2;  // fused ModDown: [N^-1 phinv_k, Shoup][K] pairs, c_k [K], phat_q Shoup [K][n_q], p_k [K]
   DevBuf d_r64;       // per prime: 2^64 mod q and its Shoup companion
   DevBuf d_pmod;      // per prime: P mod q_t (key generation)
   Tables tab{};

@@ -155,19 +155,26 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
     for (int k = 0; k < 8; ++k) {
       const bool on = k < A.pconv_K;
       c[k] = on ? A.pconv_c[k] : 0;
-      pk[k] = on ? T.pr[A.pconv_nq + k].q : 0;
-      f[k] = on ? A.pconv_phat[(size_t)k * A.pconv_nq + li] : 0;
-      fs[k] = on ? A.pconv_phat_sh[(size_t)k * A.pconv_nq + li] : 0;
+      pk[k] = on ? A.pconv_q[k] : 0;
+      f[k] = on ? A.pconv_phat[(size_t)k * A.pconv_ld + li] : 0;
+      fs[k] = on ? A.pconv_phat_sh[(size_t)k * A.pconv_ld + li] : 0;
     }
     const u64 off = (q << 2) - A.pconv_half[li], q4 = q << 2, q8 = q << 3;
+    const bool lazy = A.pconv_K <= 5;
 #pragma unroll
     for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
       const int cc = idx / C, col = idx % C;
       const size_t n = ((size_t)cc << L2) + r0 + col;
-      u64 v = off;  // sum of K <= 5 lazy products (< 2Kq) + 4q - floor(P/2) mod q  ->  < 14q
+      // 4q - floor(S/2) mod q plus K products: lazy (< 2q each) for K <= 5, canonical (< q) for
+      // K <= 8, so the sum stays below 16q < 2^64
+      u64 v = off;
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (k < A.pconv_K) v += shoup_mul_lazy(add_mod(zp[(size_t)k * N + n], c[k], pk[k]), f[k], fs[k], q);
+        if (k < A.pconv_K) {
+          u64 term = shoup_mul_lazy(add_mod(zp[(size_t)k * N + n], c[k], pk[k]), f[k], fs[k], q);
+          if (!lazy && term >= q) term -= q;
+          v += term;
+        }
       if (v >= q8) v -= q8;
       if (v >= q4) v -= q4;
       sm[idx] = v;
@@ -494,7 +501,7 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   if (A.post && !inverse) throw Error(HEDAP_ERR_ARG, "NTT: post factors apply to the inverse only");
   if ((A.spread || A.fin_dst || A.pconv) && inverse)
     throw Error(HEDAP_ERR_ARG, "NTT: fused rescale / ModDown applies to the forward only");
-  if (A.pconv && (A.pconv_K < 1 || A.pconv_K > 5 || A.z || A.src || A.spread))
+  if (A.pconv && (A.pconv_K < 1 || A.pconv_K > 8 || A.z || A.src || A.spread))
     throw Error(HEDAP_ERR_ARG, "NTT: bad ModDown fusion");
   if (A.spread && (A.z || A.src || !A.spread_sub)) throw Error(HEDAP_ERR_ARG, "NTT: bad spread fusion");
   if (A.fin_dst && (!A.fin_c || !A.fin_w || !A.fin_wsh)) throw Error(HEDAP_ERR_ARG, "NTT: bad epilogue fusion");

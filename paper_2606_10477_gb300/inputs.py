@@ -16,10 +16,10 @@ PRESETS = {
     # N = 2^16, 24 primes of ~50 bits + 2 special primes of ~60 bits, 2 primes per digit
     "n16": dict(log_n=16, q_bits=[50] * 24, p_bits=[60, 60], alpha=2, log_scale=50, hw=0),
     # the same ring with three key-switching digits (8 primes each, dnum = 3 as the workload names it);
-    # 8 special primes of 60 bits keep P (480 bits) above a digit (400 bits)
-    "n16d3": dict(log_n=16, q_bits=[50] * 24, p_bits=[60] * 8, alpha=8, log_scale=50, hw=0),
+    # 7 special primes of 60 bits keep P (420 bits) above a digit (400 bits)
+    "n16d3": dict(log_n=16, q_bits=[50] * 24, p_bits=[60] * 7, alpha=8, log_scale=50, hw=0),
     # small rings with the same prime shapes, for fast parity checks
-    "n12a8": dict(log_n=12, q_bits=[40] * 10, p_bits=[60] * 8, alpha=8, log_scale=40, hw=0),
+    "n12a8": dict(log_n=12, q_bits=[40] * 10, p_bits=[60] * 7, alpha=8, log_scale=40, hw=0),
     "n12a4": dict(log_n=12, q_bits=[40] * 10, p_bits=[60] * 5, alpha=4, log_scale=40, hw=0),
     "n13": dict(log_n=13, q_bits=[50] * 8, p_bits=[60, 60], alpha=2, log_scale=50, hw=0),
     "n10": dict(log_n=10, q_bits=[45, 36, 36, 36, 36, 36], p_bits=[50, 50], alpha=2, log_scale=36, hw=0),

@@ -196,7 +196,7 @@ def test_hoisted_rotations_bit_exact(name, request):
 
 @pytest.mark.parametrize("name", ["n12a4", "n12a8"])
 def test_wide_digits_bit_exact(name):
-    """Digits of 4 and 8 primes (5 and 8 special primes): the fused and the unfused ModDown paths."""
+    """Digits of 4 and 8 primes (5 and 7 special primes): lazy and canonical terms in the fused conversions."""
     g, o = make_pair(name)
     L = o.n_q - 1
     for level in (L, 4):
@@ -209,7 +209,7 @@ def test_wide_digits_bit_exact(name):
 
 
 def test_invsqrt_n16_three_digits():
-    """N = 2^16, 24 x 50-bit primes, dnum = 3 (8 special primes): MRE <= 1e-7."""
+    """N = 2^16, 24 x 50-bit primes, dnum = 3 (7 special primes): MRE <= 1e-7."""
     p = inputs.PRESETS["n16d3"]
     g = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], 0, 5)
     a = inputs.uniform_values(43, g.N // 2, 1e-3, 1.0)
