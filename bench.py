@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-level batch workload")
     ap.add_argument("--no-dnum3", action="store_true", help="skip the three-digit key-switching variant")
     ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
-    ap.add_argument("--only", choices=["ntt", "serving", "mixed"],
+    ap.add_argument("--only", choices=["ntt", "serving", "mixed", "bts"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     ap.add_argument("--profile-region", action="store_true",
@@ -431,9 +431,10 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63, iters=4, steps=2):
+def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, steps=2):
     """CryptoInvSqrt with lazy bootstrapping in the Newton loop: N = 2^16, bts16 chain
-    (log2 QP = 1555, h = 192), inputs log-uniform in [1e-4, 1] at l_max, batch of ciphertexts."""
+    (log2 QP = 1555, h = 192), inputs log-uniform in [1e-4, 1] at l_max, batch of ciphertexts, with
+    (d, c, i) chosen by HE-DAP's selector (Alg. 2 / Alg. 3) on this GPU for MRE <= 1e-7 at l_max."""
     p = inputs.PRESETS["bts16"]
     b = inputs.BTS
     t0 = time.perf_counter()
@@ -441,10 +442,15 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
                   stream=stream.cuda_stream)
     lmax = ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
     lo = 1e-4
+    s0 = time.perf_counter()
+    _, R, _ = ctx.select(lo, 1.0, 1.0, 5, 6, 8, mre_target=1e-7, level_min=lmax, level_max=lmax)
+    choice = next((r for r in R if r["kind"] == 3), None) or next(r for r in R if r["kind"] == 1)
+    degree, iters, pre = choice["degree"], choice["iters"], choice["c"]
+    select_s = time.perf_counter() - s0
     vals = [inputs.log_uniform_values(2000 + i, ctx.N // 2, lo, 1.0) for i in range(batch)]
     packed = ctx.pack([ctx.encrypt(v, lmax, 3000 + i) for i, v in enumerate(vals)])
     mask = 1 << 63
-    out = ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, 0, mask)  # warm-up: keys and diagonals are built here
+    out = ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, pre, mask)  # warm-up: keys and diagonals are built here
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     mres = []
@@ -454,14 +460,14 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, 0, mask)
+        ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, pre, mask)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     single = ctx.encrypt(vals[0], lmax, 4000)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(stream)
-    ctx.invsqrt(single, lo, 1.0, 1.0, degree, iters, 0, mask)
+    ctx.invsqrt(single, lo, 1.0, 1.0, degree, iters, pre, mask)
     s1.record(stream)
     torch.cuda.synchronize()
     bts_ct = ctx.encrypt(vals[0] / 2, 1, 5000)
@@ -472,7 +478,9 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, degree=63
     torch.cuda.synchronize()
     ctx.close()
     return {"workload": f"CryptoInvSqrt with lazy bootstrapping, N=2^16, log2(QP)=1555, h=192, inputs log-U[{lo},1] "
-                        f"at level {lmax}, degree {degree}, {iters} Newton steps, batch {batch}",
+                        f"at level {lmax}, (degree {degree}, Pre-BTS {pre}, {iters} Newton steps) chosen by the "
+                        f"selector for MRE <= 1e-7, batch {batch}",
+            "selected": choice, "select_s": select_s,
             "value": batch * 1e3 / ms, "unit": UNIT, "ms_per_batch": ms, "mre": max(mres),
             "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s}
 
@@ -723,6 +731,11 @@ def main():
         run_ntt_only(args)
     elif args.only == "serving":
         run_serving_only(args)
+    elif args.only == "bts":
+        import torch
+        from paper_2606_10477_gb300 import hedap, inputs
+        print(json.dumps({"bootstrapped": bootstrapped_workload(hedap.Context, inputs, torch,
+                                                                torch.cuda.current_stream(), 0, args.batch)}))
     elif args.only == "mixed":
         import torch
         from paper_2606_10477_gb300 import hedap, inputs
