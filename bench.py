@@ -477,12 +477,42 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, steps=2):
     b1.record(stream)
     torch.cuda.synchronize()
     ctx.close()
+    dense = dense_secret_bootstrap(ctx_cls, inputs, torch, stream, rank)
     return {"workload": f"CryptoInvSqrt with lazy bootstrapping, N=2^16, log2(QP)=1555, h=192, inputs log-U[{lo},1] "
                         f"at level {lmax}, (degree {degree}, Pre-BTS {pre}, {iters} Newton steps) chosen by the "
                         f"selector for MRE <= 1e-7, batch {batch}",
             "selected": choice, "select_s": select_s,
             "value": batch * 1e3 / ms, "unit": UNIT, "ms_per_batch": ms, "mre": max(mres),
-            "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s}
+            "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s,
+            "bootstrap_dense_secret": dense}
+
+
+def dense_secret_bootstrap(ctx_cls, inputs, torch, stream, rank, steps=3):
+    """One bootstrap under a dense ternary secret through sparse-secret encapsulation (an ephemeral
+    weight-192 secret; two key switches more than the sparse chain), N = 2^16, bts16d chain: time and
+    decrypted error of 32768 complex slots in [-1, 1]."""
+    p = inputs.PRESETS["bts16d"]
+    b = inputs.BTS
+    ctx = ctx_cls(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 61 + rank,
+                  stream=stream.cuda_stream)
+    ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    ctx.bts_encapsulate(inputs.ENC_HW)
+    half = ctx.N // 2
+    z = inputs.uniform_values(8000, half, -1, 1) + 1j * inputs.uniform_values(8001, half, -1, 1)
+    ct = ctx.encrypt(z, 1, 8002)
+    out = ctx.bootstrap_scaled(ct, 1)  # warm-up: keys and diagonals are built here
+    err = np.abs(ctx.decrypt(out) - z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.bootstrap_scaled(ct, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    return {"workload": "bootstrapping under a dense ternary secret with sparse-secret encapsulation (h = 192), "
+                        "N=2^16, log2(QP)=1605, 32768 complex slots",
+            "bootstrap_ms": e0.elapsed_time(e1) / steps, "max_err": float(err.max()), "mean_err": float(err.mean())}
 
 
 def dnum3_variant(hedap, inputs, torch, stream, rank, batch, degree, iters, steps):

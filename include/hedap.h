@@ -261,6 +261,18 @@ typedef struct {
   uint32_t stc_levels;
 } hedap_bts_params;
 hedap_status hedap_bootstrap_setup(hedap_ctx* ctx, const hedap_bts_params* p, int* level_after);
+/* Sparse-secret encapsulation (Bossuat, Troncoso-Pastoriza, Hubaux 2022), for
+ * bootstrapping under a dense ternary secret (secret_hw = 0) with the small K
+ * of a sparse one: draws an ephemeral ternary secret s~ of exactly h non-zero
+ * coefficients from the context's seed and generates the switching keys s -> s~
+ * and s~ -> s.  Every later bootstrap switches its level-0 input to s~, raises
+ * it, and switches the raised ciphertext back to s (two key switches more; the
+ * ModRaise overflow is then that of weight h).  HEDAP_ERR_ARG unless 1 <= h <= N.
+ * hedap_encapsulation_switch: one of the two key switches alone (to_sparse = 1:
+ * s -> s~, else s~ -> s), for parity tests; HEDAP_ERR_ARG before
+ * hedap_bootstrap_encapsulate. */
+hedap_status hedap_bootstrap_encapsulate(hedap_ctx* ctx, uint32_t h);
+hedap_status hedap_encapsulation_switch(hedap_ctx* ctx, const hedap_ct* a, int to_sparse, hedap_ct** out);
 hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
 hedap_status hedap_bootstrap_scaled(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, hedap_ct** out);
 /* Single steps of bootstrapping, for parity tests.  hedap_mod_raise: level-0
@@ -366,12 +378,23 @@ typedef struct {
   uint32_t n_ct;
   uint64_t n_records;            /* <= n_ct * N/2 */
   hedap_invsqrt_cfg invsqrt;
+  uint32_t choice;               /* 0: invsqrt as given; 1/2/3: (degree, c, iters) from the server's
+                                    HE-DAP table, entry u1/u2/u3 (see hedap_server_set_table) */
 } hedap_query;
 hedap_status hedap_server_create(hedap_ctx* ctx, const hedap_server_cfg* cfg, hedap_server** out);
 hedap_status hedap_server_submit(hedap_server* s, const hedap_query* q, uint64_t* id);
 hedap_status hedap_server_poll(hedap_server* s, uint64_t id, int wait, int* done, hedap_ct** out, size_t cap,
                                size_t* n_out, double* latency_ms, uint32_t* group_size);
 hedap_status hedap_server_resume(hedap_server* s);
+/* HE-DAP in serving: install the per-level table R of hedap_select (entries of
+ * kind 1, 2, 3 = u1 accuracy, u2 speed, u3 absolute MRE target; copied).  A
+ * query with choice k takes (degree, Pre-BTS c, Newton steps) from the kind-k
+ * entry at the level its variance reaches InvSqrt (input level - 2 for z-score,
+ * - 3 for PCC) or, when that level has none, at the highest tabled level below
+ * it (a configuration that fits a level fits every higher one); lo, hi, B come
+ * from the query's invsqrt, and bootstrapping in the Newton loop is lazy (bit
+ * 63) on a context set up for it.  No such entry: HEDAP_ERR_ARG at submit. */
+hedap_status hedap_server_set_table(hedap_server* s, const hedap_select_entry* R, size_t n);
 hedap_status hedap_server_estimate(const hedap_server* s, uint32_t kind, uint32_t n_ct, int level, uint64_t* bytes);
 hedap_status hedap_server_stats(hedap_server* s, double* p50_ms, double* p99_ms, double* qps, uint64_t* completed);
 void hedap_server_destroy(hedap_server* s);

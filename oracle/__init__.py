@@ -100,6 +100,9 @@ def _declare(L):
         "orc_threads": (C.c_int, []),
         "orc_bts_setup": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
         "orc_bootstrap": (vp, [vp, vp]),
+        "orc_bts_encapsulate": (C.c_int, [vp, C.c_int]),
+        "orc_encapsulation_switch": (vp, [vp, vp, C.c_int]),
+        "orc_decrypt_sparse": (C.c_int, [vp, vp, f64p, f64p]),
         "orc_bootstrap_scaled": (vp, [vp, vp, C.c_int64]),
         "orc_mod_raise": (vp, [vp, vp]),
         "orc_linear_transform_group": (vp, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_double]),
@@ -317,6 +320,20 @@ class Context:
 
     def bootstrap(self, a):
         return Ciphertext(self, lib().orc_bootstrap(self.h, a.h))
+
+    def bts_encapsulate(self, h: int) -> None:
+        """Sparse-secret encapsulation of bootstrapping: an ephemeral secret of weight h and its two keys."""
+        _check(lib().orc_bts_encapsulate(self.h, h))
+
+    def encapsulation_switch(self, a, to_sparse: bool):
+        return Ciphertext(self, lib().orc_encapsulation_switch(self.h, a.h, 1 if to_sparse else 0))
+
+    def decrypt_sparse(self, ct: Ciphertext) -> np.ndarray:
+        """Decryption under the ephemeral sparse secret of the encapsulation."""
+        re = np.empty(self.N // 2)
+        im = np.empty(self.N // 2)
+        _check(lib().orc_decrypt_sparse(self.h, ct.h, re, im))
+        return re + 1j * im
 
     def bootstrap_scaled(self, a, Y: int):
         return Ciphertext(self, lib().orc_bootstrap_scaled(self.h, a.h, Y))

@@ -153,7 +153,7 @@ struct Stream {
 // object tags
 static u64 tag_evk_a(u64 g, u64 j) { return (2ull << 56) | (g << 8) | j; }
 static u64 tag_evk_e(u64 g, u64 j) { return (3ull << 56) | (g << 8) | j; }
-static const u64 TAG_SK = 1, TAG_ENC_A = 4ull << 56, TAG_ENC_E = 5ull << 56;
+static const u64 TAG_SK = 1, TAG_ENC_A = 4ull << 56, TAG_ENC_E = 5ull << 56, TAG_SK_SPARSE = 6ull << 56;
 
 static u64 sample_uniform(Stream& st, u64 q) {
   int bits = 64 - __builtin_clzll(q);
@@ -267,6 +267,10 @@ struct Ctx {
   std::vector<i64> s;                    // secret coefficients
   Poly s_ntt;                            // per prime
   std::map<u64, std::vector<KeyDigit>> keys;  // galois element (0 = relinearisation) -> digits
+  // sparse-secret encapsulation of bootstrapping: ephemeral secret of weight enc_hw (0 = off);
+  // key 2 switches from s to it, key 4 back (even ids are never Galois elements)
+  int enc_hw = 0;
+  Poly s_sparse_ntt;
   // bootstrapping: off unless configured; K bounds the ModRaise overflow |I| < K,
   // r double-angle steps, degree of the cosine interpolant, levels of CtS / StC
   bool bts_on = false;
@@ -312,8 +316,8 @@ static Limb residues_of(const Ctx& C, const std::vector<i64>& v, int pi) {
   for (size_t i = 0; i < C.N; ++i) r[i] = smod(v[i], C.q[pi]);
   return r;
 }
-// the evk digit j for a key switch from s' (NTT over all primes) to s
-static KeyDigit make_key_digit(const Ctx& C, const Poly& sp, u64 g, int j) {
+// the evk digit j for a key switch from s' (NTT over all primes) to s_to
+static KeyDigit make_key_digit(const Ctx& C, const Poly& sp, const Poly& s_to, u64 g, int j) {
   int total = C.n_q + C.n_p;
   KeyDigit kd; kd.a.assign(total, Limb(C.N)); kd.b.assign(total, Limb(C.N));
   Stream sa(C.seed, tag_evk_a(g, j));
@@ -329,7 +333,7 @@ static KeyDigit make_key_digit(const Ctx& C, const Poly& sp, u64 g, int j) {
     for (int k = 0; k < C.n_p; ++k) Pmod = mulmod(Pmod, C.q[C.n_q + k] % qt, qt);
     bool in_digit = t >= lo && t < hi;
     for (size_t i = 0; i < C.N; ++i) {
-      u64 v = submod(et[i], mulmod(kd.a[t][i], C.s_ntt[t][i], qt), qt);
+      u64 v = submod(et[i], mulmod(kd.a[t][i], s_to[t][i], qt), qt);
       if (in_digit) v = addmod(v, mulmod(Pmod, sp[t][i], qt), qt);
       kd.b[t][i] = v;
     }
@@ -369,8 +373,27 @@ static void gen_key(Ctx& C, u64 g) {
     }
   }
   std::vector<KeyDigit> ds;
-  for (int j = 0; j < n_digits(C, C.L()); ++j) ds.push_back(make_key_digit(C, sp, g, j));
+  for (int j = 0; j < n_digits(C, C.L()); ++j) ds.push_back(make_key_digit(C, sp, C.s_ntt, g, j));
   C.keys[g] = std::move(ds);
+}
+// Sparse-secret encapsulation (Bossuat, Troncoso-Pastoriza, Hubaux 2022): an
+// ephemeral ternary secret with exactly h non-zero coefficients and the keys
+// s -> s~ (id 2) and s~ -> s (id 4)
+static void encapsulate(Ctx& C, int h) {
+  if (h < 1 || (size_t)h > C.N) throw std::runtime_error("encapsulation weight out of range");
+  int total = C.n_q + C.n_p;
+  Stream st(C.seed, TAG_SK_SPARSE);
+  std::vector<i64> v = sample_ternary(st, C.log_n, h);
+  C.s_sparse_ntt.assign(total, Limb());
+  for (int t = 0; t < total; ++t) { C.s_sparse_ntt[t] = residues_of(C, v, t); ntt_forward(C, C.s_sparse_ntt[t], t); }
+  std::vector<KeyDigit> to_sparse, to_dense;
+  for (int j = 0; j < n_digits(C, C.L()); ++j) {
+    to_sparse.push_back(make_key_digit(C, C.s_ntt, C.s_sparse_ntt, 2, j));
+    to_dense.push_back(make_key_digit(C, C.s_sparse_ntt, C.s_ntt, 4, j));
+  }
+  C.keys[2] = std::move(to_sparse);
+  C.keys[4] = std::move(to_dense);
+  C.enc_hw = h;
 }
 
 static Ctx* ctx_create(int log_n, const std::vector<int>& qb, const std::vector<int>& pb, int alpha,
@@ -476,16 +499,18 @@ static Ct encrypt(const Ctx& C, const std::vector<cd>& z, int level, u64 seed) {
   }
   return ct;
 }
-static std::vector<double> decrypt_coeffs(const Ctx& C, const Ct& ct) {
+// c0 + c1 s over the ciphertext's primes, centred (the secret s in NTT form over every prime)
+static std::vector<double> decrypt_coeffs_under(const Ctx& C, const Ct& ct, const Poly& S) {
   Poly m(ct.level + 1, Limb(C.N));
   PER_LIMB
   for (int i = 0; i <= ct.level; ++i) {
     u64 q = C.q[i];
-    for (size_t k = 0; k < C.N; ++k) m[i][k] = addmod(ct.c[0][i][k], mulmod(ct.c[1][i][k], C.s_ntt[i][k], q), q);
+    for (size_t k = 0; k < C.N; ++k) m[i][k] = addmod(ct.c[0][i][k], mulmod(ct.c[1][i][k], S[i][k], q), q);
     ntt_inverse(C, m[i], i);
   }
   return crt_centred(C, m, ct.level);
 }
+static std::vector<double> decrypt_coeffs(const Ctx& C, const Ct& ct) { return decrypt_coeffs_under(C, ct, C.s_ntt); }
 static std::vector<cd> decrypt(const Ctx& C, const Ct& ct) { return decode_coeffs(C, decrypt_coeffs(C, ct), ct.scale); }
 
 static Ct drop_to(const Ct& a, int level) {
@@ -674,6 +699,13 @@ static Ct apply_galois(Ctx& C, const Ct& a, u64 g) {
   return r;
 }
 static Ct rotate(Ctx& C, const Ct& a, i64 steps) { return apply_galois(C, a, galois_of_rotation(C, steps)); }
+// key switch of c1 under the key `id`: (c0 + ks0, ks1)
+static Ct switch_key(const Ctx& C, const Ct& a, u64 id) {
+  Poly k0, k1; key_switch(C, a.c[1], a.level, id, k0, k1);
+  Ct r = a; r.c[1] = k1;
+  for (int i = 0; i <= a.level; ++i) for (size_t k = 0; k < C.N; ++k) r.c[0][i][k] = addmod(a.c[0][i][k], k0[i][k], C.q[i]);
+  return r;
+}
 // Several rotations of one ciphertext sharing the ModUp of its second part (hoisting): the
 // extended digits of c1 are formed once in the coefficient domain; each rotation applies its
 // automorphism to every extended limb, then takes the inner product with its key, ModDown, and
@@ -1088,7 +1120,8 @@ static Ct bootstrap_core(Ctx& C, const Ct& a) {
   if (a.level != 0) throw std::runtime_error("bootstrap: input must be at level 0");
   const size_t n = C.N / 2;
   const double s_in = a.scale, q0 = (double)C.q[0];
-  Ct t = mod_raise(C, a);
+  // with encapsulation: to the sparse secret at level 0, ModRaise, back to s at the top level
+  Ct t = C.enc_hw ? switch_key(C, mod_raise(C, switch_key(C, a, 2)), 4) : mod_raise(C, a);
   t.scale = 2.0 * q0 * C.bts_K;
   for (const DiagMap& M : fft_groups(n, C.bts_cts, true)) t = linear_transform(C, t, M, (double)C.q[t.level - 1]);
   Ct cj = conjugate(C, t);
@@ -1320,6 +1353,18 @@ API void* orc_encrypt(void* c, const double* re, const double* im, uint64_t n_sl
   )
   return nullptr;
 }
+API int orc_bts_encapsulate(void* c, int h) { GUARD(encapsulate(*(Ctx*)c, h); return 0;) return -1; }
+// decryption under the ephemeral sparse secret (for checks of the switch to it)
+API int orc_decrypt_sparse(void* c, void* h, double* re, double* im) {
+  GUARD(
+    const Ctx& C = *(Ctx*)c; const Ct& ct = *(Ct*)h;
+    if (!C.enc_hw) throw std::runtime_error("no encapsulation");
+    std::vector<cd> z = decode_coeffs(C, decrypt_coeffs_under(C, ct, C.s_sparse_ntt), ct.scale);
+    for (size_t j = 0; j < z.size(); ++j) { re[j] = z[j].real(); if (im) im[j] = z[j].imag(); }
+    return 0;
+  )
+  return -1;
+}
 API int orc_decrypt(void* c, void* h, double* re, double* im) {
   GUARD(
     std::vector<cd> z = decrypt(*(Ctx*)c, *(Ct*)h);
@@ -1342,6 +1387,10 @@ API void* orc_mul_relin(void* c, void* a, void* b) { CT_OP(mul_relin(*(Ctx*)c, *
 API void* orc_mul(void* c, void* a, void* b) { CT_OP(mul(*(Ctx*)c, *(Ct*)a, *(Ct*)b)) }
 API void* orc_rescale(void* c, void* a) { CT_OP(rescale(*(Ctx*)c, *(Ct*)a)) }
 API void* orc_rotate(void* c, void* a, int64_t steps) { CT_OP(rotate(*(Ctx*)c, *(Ct*)a, steps)) }
+API void* orc_encapsulation_switch(void* c, void* a, int to_sparse) {
+  CT_OP(((Ctx*)c)->enc_hw ? switch_key(*(Ctx*)c, *(Ct*)a, to_sparse ? 2 : 4)
+                          : throw std::runtime_error("no encapsulation"))
+}
 API void* orc_conjugate(void* c, void* a) { CT_OP(conjugate(*(Ctx*)c, *(Ct*)a)) }
 // hoisted rotations: out[i] receives the rotation by steps[i]; returns 0 or -1
 API int orc_rotate_hoisted(void* c, void* a, const int64_t* steps, int n, void** out) {

@@ -2,7 +2,9 @@
 // l_BTS, inputs in [-1, 1], returns a ciphertext at l_afterBTS).  The paper
 // treats it as a library primitive; this is the textbook construction:
 //   ModRaise     level-0 coefficients (centred mod q_0) lifted to every Q prime:
-//                plaintext t = m + q_0 I with |I| < K
+//                plaintext t = m + q_0 I with |I| < K; with sparse-secret
+//                encapsulation the level-0 ciphertext is first switched to an
+//                ephemeral secret of small weight and the raised one back to s
 //   CoeffToSlot  slots <- V^-1 slots for the decoding matrix V (z = V w), as the
 //                radix-2 stages of the special FFT grouped into `cts` sparse
 //                factors, each applied as a baby-step / giant-step sum of
@@ -361,7 +363,12 @@ std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a) {
   BtsState& S = state(C);
   if (a.level != 0) throw Error(HEDAP_ERR_LEVEL, "bootstrap input must be at level 0");
   const double s_in = a.scale, q0 = (double)C.primes[0];
-  auto t = mod_raise(C, a);
+  std::unique_ptr<Ct> t;
+  if (C.enc_hw) {  // sparse-secret encapsulation: ModRaise under s~, then back to s at the top level
+    t = ev_switch_key(C, *mod_raise(C, *ev_switch_key(C, a, kKeyToSparse)), kKeyToDense);
+  } else {
+    t = mod_raise(C, a);
+  }
   t->scale = 2.0 * q0 * S.K;
   for (int g = 0; g < S.cts; ++g) t = bts_linear_transform(C, *t, true, g, (double)C.primes[t->level - 1]);
   auto cj = ev_galois(C, *t, 2 * C.N - 1);

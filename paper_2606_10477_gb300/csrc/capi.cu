@@ -334,6 +334,16 @@ API hedap_status hedap_bootstrap_setup(hedap_ctx* ctx, const hedap_bts_params* p
     if (level_after) *level_after = l;
   });
 }
+API hedap_status hedap_bootstrap_encapsulate(hedap_ctx* ctx, uint32_t h) {
+  return guarded_on(ctx, [&] {
+    need(ctx, "null argument");
+    hedap::bts_encapsulate(*ctx->c, (int)h);
+  });
+}
+API hedap_status hedap_encapsulation_switch(hedap_ctx* ctx, const hedap_ct* a, int to_sparse, hedap_ct** out) {
+  CT_OP((need(a && ctx->c->enc_hw, "null ciphertext or no encapsulation"),
+         hedap::ev_switch_key(*ctx->c, *a->c, to_sparse ? hedap::kKeyToSparse : hedap::kKeyToDense)));
+}
 API hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
   CT_OP((need(a, "null ciphertext"), hedap::bootstrap_core(*ctx->c, *a->c)));
 }

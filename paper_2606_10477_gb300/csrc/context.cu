@@ -166,17 +166,12 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   return C.release();
 }
 
-// Switching key for s' -> s with s' = s^2 (g = 0) or s(X^g); digit j over all
-// primes: b = e - a s + [t in digit j] (P mod q_t) s',  a uniform (NTT domain).
-void gen_galois_key(Ctx& C, u64 g) {
-  if (C.keys.count(g)) return;
-  if (g != 0 && (g % 2 == 0 || g >= 2 * C.N)) throw Error(HEDAP_ERR_ARG, "galois element must be odd and < 2N");
+// Switching key with id `g` from s' to s_to (NTT domain over all primes); digit j:
+// b = e - a s_to + [t in digit j] (P mod q_t) s',  a uniform (NTT domain).
+void gen_switch_key(Ctx& C, u64 g, const u64* sp, const u64* s_to) {
   const int T = C.total_primes(), nq = C.n_q, dn = C.dnum(C.L());
   const size_t N = C.N;
   DevBuf key((size_t)dn * 2 * T * N, C.stream);
-  DevBuf sp(T * N, C.stream);
-  if (g == 0) k_fma(C, nullptr, C.d_sk.p, C.d_sk.p, sp.p, T, 2);
-  else k_automorph(C, C.d_sk.p, 0, sp.p, 0, 1, T, g);
   std::vector<u64> ah(T * N), eh(T * N);
   std::vector<i64> e(N);
   for (int j = 0; j < dn; ++j) {
@@ -193,10 +188,47 @@ void gen_galois_key(Ctx& C, u64 g) {
     HEDAP_CUDA(cudaMemcpyAsync(a, ah.data(), T * N * 8, cudaMemcpyHostToDevice, C.stream));
     ntt_forward(C.tab, LimbSet{b, 0, 1, 0, T, nq, 0, nq}, C.stream);
     const int lo = j * C.alpha, hi = std::min(lo + C.alpha, nq);
-    k_keygen_combine(C, b, a, C.d_sk.p, sp.p, C.d_pmod.p, lo, hi);
+    k_keygen_combine(C, b, a, s_to, sp, C.d_pmod.p, lo, hi);
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));  // host buffers are reused
   }
   C.keys[g] = std::move(key);
+}
+
+// Switching key for s' -> s with s' = s^2 (g = 0) or s(X^g)
+void gen_galois_key(Ctx& C, u64 g) {
+  if (C.keys.count(g)) return;
+  if (g != 0 && (g % 2 == 0 || g >= 2 * C.N)) throw Error(HEDAP_ERR_ARG, "galois element must be odd and < 2N");
+  const int T = C.total_primes();
+  DevBuf sp(T * C.N, C.stream);
+  if (g == 0) k_fma(C, nullptr, C.d_sk.p, C.d_sk.p, sp.p, T, 2);
+  else k_automorph(C, C.d_sk.p, 0, sp.p, 0, 1, T, g);
+  gen_switch_key(C, g, sp.p, C.d_sk.p);
+}
+
+// Sparse-secret encapsulation of bootstrapping (Bossuat, Troncoso-Pastoriza and
+// Hubaux 2022): an ephemeral secret s~ with h non-zero coefficients, a key from
+// s to s~ (used at level 0, before ModRaise) and one from s~ back to s (used at
+// the top level, after it), so that the ModRaise overflow is that of a weight-h
+// secret whatever the distribution of s.
+void bts_encapsulate(Ctx& C, int h) {
+  if (h < 1 || (size_t)h > C.N) throw Error(HEDAP_ERR_ARG, "encapsulation weight must lie in [1, N]");
+  const int T = C.total_primes();
+  const size_t N = C.N;
+  SplitMix ss(C.seed, tags::sk_sparse);
+  const std::vector<i64> v = draw_ternary(ss, C.log_n, h);
+  std::vector<u64> r(T * N);
+  for (int t = 0; t < T; ++t)
+    for (size_t i = 0; i < N; ++i) r[t * N + i] = h_smod(v[i], C.primes[t]);
+  DevBuf d;
+  upload(C, d, r);
+  ntt_forward(C.tab, LimbSet{d.p, 0, 1, 0, T, C.n_q, 0, C.n_q}, C.stream);
+  C.keys.erase(kKeyToSparse);
+  C.keys.erase(kKeyToDense);
+  gen_switch_key(C, kKeyToSparse, C.d_sk.p, d.p);
+  gen_switch_key(C, kKeyToDense, d.p, C.d_sk.p);
+  HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  C.d_sk_sparse = std::move(d);
+  C.enc_hw = h;
 }
 
 // ------------------------------------------------------------------ encoding

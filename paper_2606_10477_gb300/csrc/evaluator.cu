@@ -332,6 +332,15 @@ std::unique_ptr<Ct> ev_galois(Ctx& C, const Ct& a, u64 g) {
   return o;
 }
 
+// key switch of (c0, c1) with the key `id` (from the secret c1 multiplies to the key's target)
+std::unique_ptr<Ct> ev_switch_key(Ctx& C, const Ct& a, u64 id) {
+  if (!C.keys.count(id)) throw Error(HEDAP_ERR_ARG, "switching key not generated");
+  const int l = a.level;
+  auto o = ct_copy(C, a, l);
+  key_switch(C, o->part(1), 2 * o->part_stride(), a.batch, l, id, o->part(0), o->part_stride(), true, false);
+  return o;
+}
+
 // Mul_P by a real constant c at plaintext scale target * q_l / scale, then rescale;
 // the result's scale is set to exactly `target`.
 std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target) {

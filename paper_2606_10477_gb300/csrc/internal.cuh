@@ -56,7 +56,7 @@ struct SplitMix {
 namespace tags {
 inline u64 evk_a(u64 g, u64 j) { return (2ull << 56) | (g << 8) | j; }
 inline u64 evk_e(u64 g, u64 j) { return (3ull << 56) | (g << 8) | j; }
-const u64 sk = 1, enc_a = 4ull << 56, enc_e = 5ull << 56;
+const u64 sk = 1, enc_a = 4ull << 56, enc_e = 5ull << 56, sk_sparse = 6ull << 56;
 }  // namespace tags
 u64 draw_uniform(SplitMix& s, u64 q);
 i64 draw_cbd21(SplitMix& s);
@@ -224,7 +224,9 @@ struct Ctx {
   Tables tab{};
   std::vector<i64> sk;
   DevBuf d_sk;        // [n_q+n_p][N] NTT domain
-  std::map<u64, DevBuf> keys;  // galois (0 = relinearisation) -> [dnum][2][n_q+n_p][N]
+  std::map<u64, DevBuf> keys;  // galois (0 = relinearisation; 2, 4 encapsulation) -> [dnum][2][n_q+n_p][N]
+  int enc_hw = 0;             // sparse-secret encapsulation of bootstrapping: weight of s~ (0 = off)
+  DevBuf d_sk_sparse;         // s~, [n_q+n_p][N] NTT domain
   std::map<int, std::unique_ptr<LevelConsts>> lc;
   std::unique_ptr<BtsState, BtsStateDeleter> bts;
   int device = 0;             // the CUDA device current at creation
@@ -257,6 +259,11 @@ std::unique_ptr<Ct> batch_pack(Ctx& C, const std::vector<const Ct*>& cts);
 std::unique_ptr<Ct> batch_unpack(Ctx& C, const Ct& b, int k);
 std::unique_ptr<Ct> batch_slice(Ctx& C, const Ct& b, int first, int count);  // members first .. first+count-1
 void gen_galois_key(Ctx& C, u64 g);
+// key ids of the sparse-secret encapsulation (even, so never a Galois element)
+constexpr u64 kKeyToSparse = 2, kKeyToDense = 4;
+void gen_switch_key(Ctx& C, u64 id, const u64* s_from, const u64* s_to);
+void bts_encapsulate(Ctx& C, int h);
+std::unique_ptr<Ct> ev_switch_key(Ctx& C, const Ct& a, u64 id);
 const LevelConsts& level_consts(Ctx& C, int level);
 
 // ------------------------------------------------------------------ context (context.cu)

@@ -123,6 +123,7 @@ struct hedap_server {
   std::vector<double> latencies;
   Clock::time_point first_submit, last_done;
   bool any = false;
+  std::vector<hedap_select_entry> table;  // HE-DAP per-level choices (guarded by mu)
 
   size_t estimate_bytes(size_t n_out, int level) const;
   void loop();
@@ -439,6 +440,19 @@ API hedap_status hedap_server_submit(hedap_server* s, const hedap_query* q, uint
       }
     }
     if (Q->level < 4) throw Error(HEDAP_ERR_LEVEL, "query inputs need level >= 4");
+    if (q->choice) {  // (degree, c, iters) from the HE-DAP table for the variance's level
+      if (q->choice > 3) throw Error(HEDAP_ERR_ARG, "query choice must be 0, 1, 2 or 3");
+      const int vlevel = Q->level - (pcc ? 3 : 2);
+      std::lock_guard<std::mutex> lk(s->mu);
+      const hedap_select_entry* best = nullptr;
+      for (const hedap_select_entry& e : s->table)
+        if (e.kind == q->choice && e.level <= vlevel && (!best || e.level > best->level)) best = &e;
+      if (!best) throw Error(HEDAP_ERR_ARG, "no HE-DAP table entry of that kind at or below the variance's level");
+      Q->cfg.degree = best->degree;
+      Q->cfg.pre_bts = best->c;
+      Q->cfg.newton_iters = best->iters;
+      Q->cfg.bts_mask = s->C->bts ? (1ull << 63) : 0;
+    }
     Q->bytes = s->estimate_bytes(pcc ? 1 : q->n_ct, Q->level);
     if (Q->bytes > s->cfg.hbm_budget_bytes) throw Error(HEDAP_ERR_OOM, "query exceeds the server's memory budget");
     {
@@ -519,6 +533,14 @@ API hedap_status hedap_server_resume(hedap_server* s) {
       s->paused = false;
     }
     s->cv.notify_all();
+  });
+}
+
+API hedap_status hedap_server_set_table(hedap_server* s, const hedap_select_entry* R, size_t n) {
+  return srv_guard([&] {
+    if (!s || (n && !R)) throw Error(HEDAP_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->table.assign(R, R + n);
   });
 }
 

@@ -28,12 +28,13 @@ EXPORTED = [
     "hedap_rescale", "hedap_rotate", "hedap_rotate_hoisted", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
-    "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_mod_raise", "hedap_mul_monomial",
+    "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_bootstrap_encapsulate",
+    "hedap_encapsulation_switch", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_ntt_batch",
     "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
-    "hedap_server_resume", "hedap_server_estimate", "hedap_invsqrt_graph_create", "hedap_graph_run",
+    "hedap_server_resume", "hedap_server_estimate", "hedap_server_set_table", "hedap_invsqrt_graph_create", "hedap_graph_run",
     "hedap_graph_kernels", "hedap_graph_destroy",
 ]
 
@@ -89,7 +90,7 @@ class ServerCfg(C.Structure):
 
 class Query(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("x", C.POINTER(C.c_void_p)), ("y", C.POINTER(C.c_void_p)),
-                ("n_ct", C.c_uint32), ("n_records", C.c_uint64), ("invsqrt", InvSqrtCfg)]
+                ("n_ct", C.c_uint32), ("n_records", C.c_uint64), ("invsqrt", InvSqrtCfg), ("choice", C.c_uint32)]
 
 
 QUERY_ZSCORE, QUERY_PCC = 1, 2
@@ -152,6 +153,8 @@ def _declare(L):
         "hedap_bootstrap_setup": (st, [vp, C.POINTER(BtsParams), C.POINTER(C.c_int)]),
         "hedap_bootstrap": (st, [vp, vp, pp]),
         "hedap_bootstrap_scaled": (st, [vp, vp, C.c_int64, pp]),
+        "hedap_bootstrap_encapsulate": (st, [vp, C.c_uint32]),
+        "hedap_encapsulation_switch": (st, [vp, vp, C.c_int, pp]),
         "hedap_mod_raise": (st, [vp, vp, pp]),
         "hedap_mul_monomial": (st, [vp, vp, C.c_uint64, pp]),
         "hedap_bts_linear_transform": (st, [vp, vp, C.c_int, C.c_int, C.c_double, pp]),
@@ -181,6 +184,7 @@ def _declare(L):
         "hedap_server_poll": (st, [vp, C.c_uint64, C.c_int, C.POINTER(C.c_int), pp, C.c_size_t,
                                    C.POINTER(C.c_size_t), dp, C.POINTER(C.c_uint32)]),
         "hedap_server_resume": (st, [vp]),
+        "hedap_server_set_table": (st, [vp, C.POINTER(SelectEntry), C.c_size_t]),
         "hedap_invsqrt_graph_create": (st, [vp, vp, C.POINTER(InvSqrtCfg), pp]),
         "hedap_graph_run": (st, [vp, vp, pp]),
         "hedap_graph_kernels": (st, [vp, u64p]),
@@ -432,6 +436,13 @@ class Context:
     def bootstrap(self, a):
         return self._ct(load().hedap_bootstrap, a.h)
 
+    def bts_encapsulate(self, h: int) -> None:
+        """Sparse-secret encapsulation of bootstrapping (ephemeral secret of weight h)."""
+        _check(load().hedap_bootstrap_encapsulate(self.h, h))
+
+    def encapsulation_switch(self, a, to_sparse: bool):
+        return self._ct(load().hedap_encapsulation_switch, a.h, 1 if to_sparse else 0)
+
     def bootstrap_scaled(self, a, Y: int):
         return self._ct(load().hedap_bootstrap_scaled, a.h, Y)
 
@@ -566,13 +577,14 @@ class Server:
         _check(load().hedap_server_create(ctx.h, C.byref(cfg), C.byref(h)))
         self.h = h
 
-    def submit(self, kind: int, xs, n_records: int, cfg, ys=None) -> int:
-        """Submit a query; cfg = (lo, hi, B, degree, iters, pre_bts, bts_mask). Returns its id."""
+    def submit(self, kind: int, xs, n_records: int, cfg, ys=None, choice: int = 0) -> int:
+        """Submit a query; cfg = (lo, hi, B, degree, iters, pre_bts, bts_mask); choice 1/2/3 takes
+        (degree, c, iters) from the HE-DAP table (u1/u2/u3). Returns its id."""
         xa = (C.c_void_p * len(xs))(*[c.h for c in xs])
         ya = (C.c_void_p * len(ys))(*[c.h for c in ys]) if ys is not None else None
         q = Query(kind, C.cast(xa, C.POINTER(C.c_void_p)),
                   C.cast(ya, C.POINTER(C.c_void_p)) if ya is not None else None,
-                  len(xs), n_records, InvSqrtCfg(*cfg))
+                  len(xs), n_records, InvSqrtCfg(*cfg), choice)
         qid = C.c_uint64()
         _check(load().hedap_server_submit(self.h, C.byref(q), C.byref(qid)))
         self._held[qid.value] = (list(xs), list(ys or []))
@@ -597,6 +609,12 @@ class Server:
 
     def resume(self) -> None:
         _check(load().hedap_server_resume(self.h))
+
+    def set_table(self, R) -> None:
+        """Install HE-DAP's per-level table (list of dicts as returned by Context.select)."""
+        arr = (SelectEntry * max(1, len(R)))(*[SelectEntry(e["level"], e["degree"], e["c"], e["iters"], e["mre"],
+                                                           e["ms"], e["kind"]) for e in R])
+        _check(load().hedap_server_set_table(self.h, arr, len(R)))
 
     def estimate(self, kind: int, n_ct: int, level: int) -> int:
         b = C.c_uint64()

@@ -132,3 +132,45 @@ def test_ct_x_rebootstrapping_variant_bit_exact(pair12):
     gc = g.ct_import(oc.limbs(), oc.level, oc.scale)
     mask = (1 << 63) | (1 << 62)
     same(g.invsqrt(gc, 0.1, 1.0, 1.0, 3, 5, 0, mask), o.invsqrt(oc, 0.1, 1.0, 1.0, 3, 5, 0, mask))
+
+
+# ------------------------------------------------------------------ dense secret, sparse-secret encapsulation
+@pytest.fixture(scope="module")
+def dense12():
+    g, _ = make("bts12d", hedap.Context)
+    o, _ = make("bts12d", oracle.Context)
+    g.bts_encapsulate(inputs.ENC_HW)
+    o.bts_encapsulate(inputs.ENC_HW)
+    return g, o
+
+
+def test_encapsulation_switches_bit_exact(dense12):
+    g, o = dense12
+    z = inputs.uniform_values(20, o.N // 2, -1, 1)
+    gc, oc = level0_pair(g, o, 21, z)
+    gs, os_ = g.encapsulation_switch(gc, True), o.encapsulation_switch(oc, True)
+    same(gs, os_)
+    L = o.n_q - 1
+    limbs = inputs.random_ciphertext_limbs(22, o.primes(), L, o.N)
+    ga, oa = g.ct_import(limbs, L, o.scale), o.ct_import(limbs, L, o.scale)
+    same(g.encapsulation_switch(ga, False), o.encapsulation_switch(oa, False))
+
+
+def test_dense_secret_bootstrap_matches_oracle(dense12):
+    g, o = dense12
+    z = inputs.uniform_values(23, o.N // 2, -1, 1) + 1j * inputs.uniform_values(24, o.N // 2, -1, 1)
+    gc, oc = level0_pair(g, o, 25, z)
+    gb, ob = g.bootstrap(gc), o.bootstrap(oc)
+    same(gb, ob)
+    assert np.max(np.abs(g.decrypt(gb) - z)) < 1e-4
+
+
+def test_dense_secret_bootstrap_full_size():
+    """N = 2^16 under a dense ternary secret, bootstrapped through an encapsulated weight-192 secret."""
+    g, lvl = make("bts16d", hedap.Context, seed=3)
+    g.bts_encapsulate(inputs.ENC_HW)
+    z = inputs.uniform_values(26, g.N // 2, -1, 1) + 1j * inputs.uniform_values(27, g.N // 2, -1, 1)
+    b = g.bootstrap_scaled(g.encrypt(z, 1, 28), 1)
+    assert b.level == lvl
+    err = np.abs(g.decrypt(b) - z)
+    assert np.max(err) < 1e-3 and np.mean(err) < 1e-4

@@ -233,3 +233,50 @@ def test_full_size_zscore_and_pcc_accuracy():
     assert np.max(np.abs(z - zscores(x))) < 1e-6
     r = g.decrypt(rs[0]).real
     assert np.max(np.abs(r - np.corrcoef(x, y)[0, 1])) < 1e-6
+
+
+def test_table_driven_parameters_equal_explicit_ones(pair12):
+    """A query that takes (degree, c, iters) from the HE-DAP table (Sec. 4.2) runs
+    exactly the query with those parameters written out; the lookup takes the
+    variance's level (input - 2 for z-score, - 3 for PCC) or the highest tabled
+    level below it."""
+    g, o, lvl = pair12
+    slots = o.N // 2
+    n = 2500
+    x = inputs.gaussian_records(31, n)
+    y = inputs.correlated_records(32, x, 0.5)
+    gx, _ = encrypt_pair(g, o, inputs.pack_slots(x, slots), lvl, 310)
+    gy, _ = encrypt_pair(g, o, inputs.pack_slots(y, slots), lvl, 320)
+
+    def entry(level, d, c, i, kind):
+        return {"level": level, "degree": d, "c": c, "iters": i, "mre": 0.0, "ms": 0.0, "kind": kind}
+
+    table = [entry(lvl - 3, 31, 0, 4, 2),      # u2: below the z-score variance's level, at the PCC one
+             entry(lvl - 4, 15, 0, 6, 2),      # a lower u2 entry, not taken
+             entry(lvl - 3, 31, 0, 5, 3),      # u3 for PCC
+             entry(lvl + 5, 31, 0, 4, 1)]      # u1 only above every variance level
+    other = (ZCFG[0], ZCFG[1], ZCFG[2], 7, 1, 0, 0)  # overridden by the table
+    other_p = (PCFG[0], PCFG[1], PCFG[2], 7, 1, 0, 0)
+    srv = hedap.Server(g, max_batch=4)
+    try:
+        srv.set_table(table)
+        tz = srv.submit(hedap.QUERY_ZSCORE, gx, n, other, choice=2)
+        tp = srv.submit(hedap.QUERY_PCC, gx, n, other_p, ys=gy, choice=3)
+        ez = srv.submit(hedap.QUERY_ZSCORE, gx, n, ZCFG)
+        ep = srv.submit(hedap.QUERY_PCC, gx, n, PCFG, ys=gy)
+        res = {k: srv.poll(k) for k in (tz, tp, ez, ep)}
+        with pytest.raises(hedap.HedapError):
+            srv.submit(hedap.QUERY_ZSCORE, gx, n, other, choice=1)  # no u1 entry at or below
+        with pytest.raises(hedap.HedapError):
+            srv.submit(hedap.QUERY_ZSCORE, gx, n, other, choice=4)
+        srv.set_table([])
+        with pytest.raises(hedap.HedapError):
+            srv.submit(hedap.QUERY_ZSCORE, gx, n, other, choice=2)
+    finally:
+        srv.close()
+    for a, b in ((tz, ez), (tp, ep)):
+        assert res[a][0] and res[b][0] and len(res[a][1]) == len(res[b][1])
+        for c, d in zip(res[a][1], res[b][1]):
+            assert np.array_equal(c.limbs(), d.limbs())
+    r = g.decrypt(res[tp][1][0]).real
+    assert np.max(np.abs(r - np.corrcoef(x, y)[0, 1])) < 1e-6

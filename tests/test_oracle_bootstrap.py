@@ -115,3 +115,60 @@ def test_ct_x_rebootstrapping_variant(ctx):
     err_alg1 = np.mean(np.abs(ctx.decrypt(alg1).real * np.sqrt(a) - 1))
     err_var = np.mean(np.abs(ctx.decrypt(var).real * np.sqrt(a) - 1))
     assert err_alg1 < 1e-8 and err_var < 1e-4
+
+
+# ------------------------------------------------------------------ dense secret, sparse-secret encapsulation
+@pytest.fixture(scope="module")
+def dense():
+    p = inputs.PRESETS["bts12d"]
+    b = inputs.BTS
+    o = oracle.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
+    o.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    o.bts_encapsulate(inputs.ENC_HW)
+    return o
+
+
+def level0(o, seed):
+    q0 = int(o.primes()[0])
+    z = inputs.uniform_values(seed, o.N // 2, -1, 1) + 1j * inputs.uniform_values(seed + 1, o.N // 2, -1, 1)
+    return z, o.mul_const(o.encrypt(z, 1, seed + 2), 1.0, q0 / 4096)
+
+
+def test_switch_to_sparse_secret_keeps_the_message(dense):
+    """After the key switch s -> s~ the level-0 ciphertext decrypts to its message under s~ and
+    to noise under s; switching back to s restores decryption under s."""
+    z, ct0 = level0(dense, 40)
+    sw = dense.encapsulation_switch(ct0, True)
+    assert sw.level == 0
+    assert np.max(np.abs(dense.decrypt_sparse(sw) - z)) < 1e-6
+    assert np.max(np.abs(dense.decrypt(sw) - z)) > 1.0
+    back = dense.encapsulation_switch(sw, False)
+    assert np.max(np.abs(dense.decrypt(back) - z)) < 1e-6
+
+
+def test_encapsulation_bounds_the_mod_raise_overflow(dense):
+    """Under the dense secret ModRaise's overflow I (t = m + q_0 I) exceeds the K of a weight-192
+    secret (its spread is about sqrt(2N/3 / 12) ~ 15); raised under s~ and switched back, it stays
+    below K (spread about sqrt(192 / 12) = 4)."""
+    q0 = int(dense.primes()[0])
+    K = inputs.BTS["K"]
+    _, ct0 = level0(dense, 50)
+    m = dense.decrypt_coeffs(ct0)
+
+    def overflow(t):
+        d = dense.decrypt_coeffs(t) - m
+        I = np.round(d / q0)
+        assert np.max(np.abs(d - q0 * I)) <= 1e6  # key-switch noise and FP64 resolution, far below q_0
+        return np.max(np.abs(I))
+
+    assert overflow(dense.mod_raise(ct0)) > K
+    t = dense.encapsulation_switch(dense.mod_raise(dense.encapsulation_switch(ct0, True)), False)
+    assert t.level == dense.n_q - 1
+    assert 0 < overflow(t) < K
+
+
+def test_dense_secret_bootstrap_returns_its_input(dense):
+    z, ct0 = level0(dense, 60)
+    b = dense.bootstrap(ct0)
+    assert b.level == dense.n_q - 1 - 16
+    assert np.max(np.abs(dense.decrypt(b) - z)) < 1e-4
