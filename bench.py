@@ -476,6 +476,21 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, steps=2):
     ctx.bootstrap_scaled(bts_ct, 1)
     b1.record(stream)
     torch.cuda.synchronize()
+    bootstrap_ms = b0.elapsed_time(b1)
+    sparse = {}
+    for ls in (10, 13):  # sparse packing: 2^ls values repeated over the N/2 slots
+        n = 1 << ls
+        v = inputs.uniform_values(5100 + ls, n, -1, 1) + 1j * inputs.uniform_values(5200 + ls, n, -1, 1)
+        zt = np.tile(v, ctx.N // 2 // n)
+        sct = ctx.encrypt(zt, 1, 5300 + ls)
+        err = np.abs(ctx.decrypt(ctx.bootstrap_scaled_slots(sct, 1, ls)) - zt)  # warm-up builds its diagonals
+        torch.cuda.synchronize()
+        b0.record(stream)
+        ctx.bootstrap_scaled_slots(sct, 1, ls)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        sparse[f"2^{ls}"] = {"bootstrap_ms": b0.elapsed_time(b1), "max_err": float(err.max()),
+                             "mean_err": float(err.mean())}
     ctx.close()
     dense = dense_secret_bootstrap(ctx_cls, inputs, torch, stream, rank)
     return {"workload": f"CryptoInvSqrt with lazy bootstrapping, N=2^16, log2(QP)=1555, h=192, inputs log-U[{lo},1] "
@@ -483,8 +498,8 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, steps=2):
                         f"selector for MRE <= 1e-7, batch {batch}",
             "selected": choice, "select_s": select_s,
             "value": batch * 1e3 / ms, "unit": UNIT, "ms_per_batch": ms, "mre": max(mres),
-            "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": b0.elapsed_time(b1), "setup_s": setup_s,
-            "bootstrap_dense_secret": dense}
+            "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": bootstrap_ms, "setup_s": setup_s,
+            "bootstrap_sparse_slots": sparse, "bootstrap_dense_secret": dense}
 
 
 def dense_secret_bootstrap(ctx_cls, inputs, torch, stream, rank, steps=3):

@@ -80,13 +80,16 @@ typedef struct {
  * levels; bit 62 (a variant, not in Alg. 1) also bootstraps ct_x = 0.5 a/B
  * whenever y is bootstrapped and ct_x has fewer than 5 levels (a Newton output
  * sits two levels below ct_x).  All need hedap_bootstrap_setup on the
- * context. */
+ * context.  log_slots = 0: the inputs use all N/2 slots; 1..log2(N/2): they
+ * hold 2^log_slots values repeated over the N/2 slots (sparse packing) and
+ * every bootstrap inside is the sparse-slot one (hedap_bootstrap_slots). */
 typedef struct {
   double lo, hi, B;
   uint32_t degree;
   uint32_t newton_iters;
   uint32_t pre_bts;
   uint64_t bts_mask;
+  uint32_t log_slots;
 } hedap_invsqrt_cfg;
 
 const char* hedap_status_str(hedap_status s);
@@ -274,6 +277,20 @@ hedap_status hedap_bootstrap_setup(hedap_ctx* ctx, const hedap_bts_params* p, in
 hedap_status hedap_bootstrap_encapsulate(hedap_ctx* ctx, uint32_t h);
 hedap_status hedap_encapsulation_switch(hedap_ctx* ctx, const hedap_ct* a, int to_sparse, hedap_ct** out);
 hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out);
+/* Sparse-slot bootstrapping: the input holds n = 2^log_slots values repeated
+ * over the N/2 slots (its plaintext is a polynomial in X^(N/2n)).  After
+ * ModRaise, the rotations by n, 2n, ..., N/4 are added (hedap_sub_sum; the
+ * overflow q_0 I is projected onto that subring, times N/2n), then CoeffToSlot
+ * and SlotToCoeff run on n slots (the transforms of the ring of dimension 2n,
+ * diagonals repeated): log2(N/2n) rotations more, fewer diagonals.  Same levels
+ * and output level as hedap_bootstrap; log_slots = log2(N/2) is the full-slot
+ * bootstrap; HEDAP_ERR_ARG when log_slots is below cts_levels or stc_levels or
+ * above log2(N/2).  hedap_bootstrap_scaled_slots is hedap_bootstrap_scaled with
+ * it.  hedap_sub_sum: that sum of rotations alone, for parity tests. */
+hedap_status hedap_bootstrap_slots(hedap_ctx* ctx, const hedap_ct* a, uint32_t log_slots, hedap_ct** out);
+hedap_status hedap_bootstrap_scaled_slots(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, uint32_t log_slots,
+                                          hedap_ct** out);
+hedap_status hedap_sub_sum(hedap_ctx* ctx, const hedap_ct* a, uint32_t log_slots, hedap_ct** out);
 hedap_status hedap_bootstrap_scaled(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, hedap_ct** out);
 /* Single steps of bootstrapping, for parity tests.  hedap_mod_raise: level-0
  * input -> top level (centred lift).  hedap_mul_monomial: times X^e for

@@ -91,7 +91,10 @@ def _declare(L):
         "orc_mul_int": (vp, [vp, vp, C.c_int64]),
         "orc_drop": (vp, [vp, vp, C.c_int]),
         "orc_invsqrt": (vp, [vp, vp, C.c_double, C.c_double, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32,
-                             C.c_uint64]),
+                             C.c_uint64, C.c_uint32]),
+        "orc_bootstrap_slots": (vp, [vp, vp, C.c_int]),
+        "orc_bootstrap_scaled_slots": (vp, [vp, vp, C.c_int64, C.c_int]),
+        "orc_sub_sum": (vp, [vp, vp, C.c_int]),
         "orc_cheb_coeffs": (C.c_int, [C.c_double, C.c_double, C.c_uint32, f64p]),
         "orc_clenshaw": (C.c_double, [f64p, C.c_uint32, C.c_double]),
         "orc_plain_invsqrt": (C.c_int, [f64p, C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_uint32,
@@ -321,6 +324,17 @@ class Context:
     def bootstrap(self, a):
         return Ciphertext(self, lib().orc_bootstrap(self.h, a.h))
 
+    def bootstrap_slots(self, a, log_slots: int):
+        """Sparse-slot bootstrapping of a level-0 ciphertext holding 2^log_slots values repeated."""
+        return Ciphertext(self, lib().orc_bootstrap_slots(self.h, a.h, log_slots))
+
+    def bootstrap_scaled_slots(self, a, Y: int, log_slots: int):
+        return Ciphertext(self, lib().orc_bootstrap_scaled_slots(self.h, a.h, Y, log_slots))
+
+    def sub_sum(self, a, log_slots: int):
+        """Sum of the rotations by 2^log_slots, 2^(log_slots+1), ..., N/4 (projection onto the subring)."""
+        return Ciphertext(self, lib().orc_sub_sum(self.h, a.h, log_slots))
+
     def bts_encapsulate(self, h: int) -> None:
         """Sparse-secret encapsulation of bootstrapping: an ephemeral secret of weight h and its two keys."""
         _check(lib().orc_bts_encapsulate(self.h, h))
@@ -364,8 +378,9 @@ class Context:
             out[int(o)] = re + 1j * im
         return out
 
-    def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0):
-        return Ciphertext(self, lib().orc_invsqrt(self.h, a.h, lo, hi, B, degree, iters, pre_bts, bts_mask))
+    def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0, log_slots=0):
+        return Ciphertext(self, lib().orc_invsqrt(self.h, a.h, lo, hi, B, degree, iters, pre_bts, bts_mask,
+                                                  log_slots))
 
 
 def cheb_coeffs(lo: float, hi: float, d: int) -> np.ndarray:

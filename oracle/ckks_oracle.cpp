@@ -1008,10 +1008,16 @@ static Ct mul_plain(const Ctx& C, const Ct& a, const Poly& pt) {
     for (int p = 0; p < 2; ++p) for (size_t k = 0; k < C.N; ++k) r.c[p][i][k] = mulmod(a.c[p][i][k], pt[i][k], C.q[i]);
   return r;
 }
+// a vector of n slots repeated to fill the N/2 slots (sparse packing: slot j and slot j + n hold
+// the same value exactly when the plaintext lies in the subring of polynomials in X^(N/2n))
+static std::vector<cd> tiled(const Ctx& C, const std::vector<cd>& v) {
+  std::vector<cd> out(C.N / 2);
+  for (size_t s = 0; s < out.size(); ++s) out[s] = v[s % v.size()];
+  return out;
+}
 // sum_o diag_o o rot(v, o) as sum_g rot( sum_b rot(diag_{k}, -G_g) o rot(v, b h0), G_g ),
 // offsets o = k h0, k = k_min + g n1 + b; one rescale at the end, result scale = target
-static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target) {
-  long n = (long)(C.N / 2);
+static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target, long n) {
   long h0 = 0, kmin = 0, kmax = 0;
   std::map<long, const std::vector<cd>*> byk;
   for (auto& e : M) { long o = e.first <= n / 2 ? e.first : e.first - n; if (o) h0 = h0 ? std::__gcd(h0, std::labs(o)) : std::labs(o); }
@@ -1044,7 +1050,7 @@ static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target)
       long k = kmin + g * n1 + b;
       auto it = byk.find(k);
       if (it == byk.end()) continue;
-      Poly pt = encode_at(C, rot_vec(*it->second, -G), sp, v.level);
+      Poly pt = encode_at(C, tiled(C, rot_vec(*it->second, -G)), sp, v.level);
       Ct term = mul_plain(C, baby[b], pt);
       term.scale = v.scale * sp;
       inner = inner_set ? add_sub(C, inner, term, false) : term; inner_set = true;
@@ -1115,15 +1121,32 @@ static Ct eval_mod(Ctx& C, const Ct& u) {
   return c;
 }
 static int bts_levels(const Ctx& C) { return C.bts_cts + C.bts_r + C.bts_stc + 1 + [&] { int m = 0; while ((1 << m) < C.bts_deg + 1) ++m; return m; }(); }
-static Ct bootstrap_core(Ctx& C, const Ct& a) {
+// Sparse packing, n = 2^log_slots < N/2 slots: the plaintext is a polynomial in Y = X^(N/2n)
+// and its slots repeat with period n.  After ModRaise the overflow q_0 I is a general
+// polynomial; the sum of the automorphisms that fix the subring (the rotations by multiples of
+// n: X -> X^(5^(n j)), 5^(n j) = 1 mod 4n) maps X^i to (N/2n) X^i when (N/2n) | i and to 0
+// otherwise, so rotating by n, 2n, ..., N/4 and adding projects onto the subring times N/2n.
+static Ct sub_sum(Ctx& C, const Ct& a, size_t n) {
+  Ct t = a;
+  for (size_t k = n; k < C.N / 2; k *= 2) t = add_sub(C, t, rotate(C, t, (i64)k), false);
+  return t;
+}
+// Full-slot (log_slots = 0) or sparse-slot bootstrapping.  The sparse one is the full one of
+// the ring of dimension 2n (CoeffToSlot / SlotToCoeff on n slots, diagonals repeated over the
+// N/2 slots) after the projection of sub_sum, whose factor N/2n rides on the scale label.
+static Ct bootstrap_core(Ctx& C, const Ct& a, int log_slots = 0) {
   if (!C.bts_on) throw std::runtime_error("bootstrapping is not configured");
   if (a.level != 0) throw std::runtime_error("bootstrap: input must be at level 0");
-  const size_t n = C.N / 2;
+  if (log_slots < 0 || (log_slots && ((1ull << log_slots) > C.N / 2 || log_slots < std::max(C.bts_cts, C.bts_stc))))
+    throw std::runtime_error("bootstrap: log_slots out of range");
+  const size_t n = log_slots ? (1ull << log_slots) : C.N / 2;
   const double s_in = a.scale, q0 = (double)C.q[0];
   // with encapsulation: to the sparse secret at level 0, ModRaise, back to s at the top level
   Ct t = C.enc_hw ? switch_key(C, mod_raise(C, switch_key(C, a, 2)), 4) : mod_raise(C, a);
-  t.scale = 2.0 * q0 * C.bts_K;
-  for (const DiagMap& M : fft_groups(n, C.bts_cts, true)) t = linear_transform(C, t, M, (double)C.q[t.level - 1]);
+  if (n < C.N / 2) t = sub_sum(C, t, n);
+  t.scale = 2.0 * q0 * C.bts_K * (double)(C.N / 2 / n);
+  for (const DiagMap& M : fft_groups(n, C.bts_cts, true))
+    t = linear_transform(C, t, M, (double)C.q[t.level - 1], (long)n);
   Ct cj = conjugate(C, t);
   Ct re = add_sub(C, t, cj, false);
   Ct im = mul_monomial(C, add_sub(C, t, cj, true), 3 * C.N / 2);  // times -i
@@ -1133,20 +1156,22 @@ static Ct bootstrap_core(Ctx& C, const Ct& a) {
   w.scale = w.scale * 2.0 * M_PI * s_in / q0;
   std::vector<DiagMap> G = fft_groups(n, C.bts_stc, false);
   for (size_t g = 0; g < G.size(); ++g)
-    w = linear_transform(C, w, G[g], g + 1 == G.size() ? C.scale : (double)C.q[w.level - 1]);
+    w = linear_transform(C, w, G[g], g + 1 == G.size() ? C.scale : (double)C.q[w.level - 1], (long)n);
   return w;
 }
 // values of y in [-Y, Y]: scale by 1/Y into [-1, 1] (one level, landing at level 0
 // with scale q_0 / 2^12), bootstrap, multiply back by the integer Y
-static Ct bootstrap_scaled(Ctx& C, const Ct& y, i64 Y) {
+static Ct bootstrap_scaled(Ctx& C, const Ct& y, i64 Y, int log_slots = 0) {
   if (y.level < 1) throw std::runtime_error("bootstrap: input needs level >= 1");
   Ct a = mul_const_to(C, drop_to(y, 1), 1.0 / (double)Y, (double)C.q[0] / 4096.0);
-  Ct b = bootstrap_core(C, a);
+  Ct b = bootstrap_core(C, a, log_slots);
   return Y == 1 ? b : mul_int(C, b, Y);
 }
 
 // ---------------------------------------------------------------- CryptoInvSqrt (Alg. 1)
-struct InvSqrtCfg { double lo, hi, B; int degree, iters, pre_bts; u64 bts_mask; };
+// log_slots: 0 for N/2 slots, else the inputs are sparsely packed (2^log_slots values repeated)
+// and every bootstrap inside uses the sparse-slot transform
+struct InvSqrtCfg { double lo, hi, B; int degree, iters, pre_bts; u64 bts_mask; int log_slots; };
 
 // One Newton step y <- 1.5 y - (0.5 a) y^3 (Sec. 2.2), in the operation order of
 // Alg. 1's loop body; tmp_alpha is produced last so that its scale can be set to
@@ -1179,7 +1204,7 @@ static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   Ct a = in; double Bf = cfg.B;
   if (cfg.pre_bts) {  // a -> BTS(a / B): values in (0, 1]
     if (in.level < 1) throw std::runtime_error("invsqrt: level exhausted");
-    a = bootstrap_core(C, mul_const_to(C, drop_to(in, 1), 1.0 / cfg.B, (double)C.q[0] / 4096.0));
+    a = bootstrap_core(C, mul_const_to(C, drop_to(in, 1), 1.0 / cfg.B, (double)C.q[0] / 4096.0), cfg.log_slots);
     Bf = 1.0;
   }
   // pre-normalisation (Sec. 2.3): a -> a/B, then the affine map onto [-1, 1]
@@ -1197,13 +1222,13 @@ static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
     bool force = i < 62 && ((cfg.bts_mask >> i) & 1);
     bool need = lazy && y.level < 3;  // the step would leave y below level 1
     if (force || need) {
-      y = bootstrap_scaled(C, y, Y);
-      if (lazy_x && x.level < 5) x = bootstrap_scaled(C, x, Yx);
+      y = bootstrap_scaled(C, y, Y, cfg.log_slots);
+      if (lazy_x && x.level < 5) x = bootstrap_scaled(C, x, Yx, cfg.log_slots);
     }
     if (std::min(y.level, x.level) < 2) throw std::runtime_error("invsqrt: level exhausted in Newton loop");
     y = newton_step(C, x, y);
   }
-  if (cfg.iters == 0 && (cfg.bts_mask & 1)) y = bootstrap_scaled(C, y, Y);
+  if (cfg.iters == 0 && (cfg.bts_mask & 1)) y = bootstrap_scaled(C, y, Y, cfg.log_slots);
   if (cfg.B != 1.0) y.scale *= std::sqrt(cfg.B);  // y / sqrt(B): relabelled, no level used
   return y;
 }
@@ -1407,8 +1432,8 @@ API void* orc_add_const(void* c, void* a, double v) { CT_OP(add_const(*(Ctx*)c, 
 API void* orc_mul_int(void* c, void* a, int64_t m) { CT_OP(mul_int(*(Ctx*)c, *(Ct*)a, m)) }
 API void* orc_drop(void* c, void* a, int level) { (void)c; CT_OP(drop_to(*(Ct*)a, level)) }
 API void* orc_invsqrt(void* c, void* a, double lo, double hi, double B, uint32_t degree, uint32_t iters,
-                      uint32_t pre_bts, uint64_t bts_mask) {
-  InvSqrtCfg cfg{lo, hi, B, (int)degree, (int)iters, (int)pre_bts, bts_mask};
+                      uint32_t pre_bts, uint64_t bts_mask, uint32_t log_slots) {
+  InvSqrtCfg cfg{lo, hi, B, (int)degree, (int)iters, (int)pre_bts, bts_mask, (int)log_slots};
   CT_OP(invsqrt(*(Ctx*)c, *(Ct*)a, cfg))
 }
 API int orc_cheb_coeffs(double lo, double hi, uint32_t d, double* out) {
@@ -1487,7 +1512,13 @@ API int orc_fft_group_diag(void* c, int groups, int inverse, int g, int64_t offs
 }
 // single steps of bootstrapping, for tests
 API void* orc_linear_transform_group(void* c, void* a, int groups, int inverse, int g, double target) {
-  CT_OP(linear_transform(*(Ctx*)c, *(Ct*)a, fft_groups(((Ctx*)c)->N / 2, groups, inverse != 0).at(g), target))
+  CT_OP(linear_transform(*(Ctx*)c, *(Ct*)a, fft_groups(((Ctx*)c)->N / 2, groups, inverse != 0).at(g), target,
+                         (long)(((Ctx*)c)->N / 2)))
 }
+API void* orc_bootstrap_slots(void* c, void* a, int log_slots) { CT_OP(bootstrap_core(*(Ctx*)c, *(Ct*)a, log_slots)) }
+API void* orc_bootstrap_scaled_slots(void* c, void* a, int64_t Y, int log_slots) {
+  CT_OP(bootstrap_scaled(*(Ctx*)c, *(Ct*)a, Y, log_slots))
+}
+API void* orc_sub_sum(void* c, void* a, int log_slots) { CT_OP(sub_sum(*(Ctx*)c, *(Ct*)a, 1ull << log_slots)) }
 API void* orc_eval_mod(void* c, void* a) { CT_OP(eval_mod(*(Ctx*)c, *(Ct*)a)) }
 API void* orc_set_scale(void* c, void* a, double scale) { (void)c; Ct r = *(Ct*)a; r.scale = scale; return new Ct(r); }

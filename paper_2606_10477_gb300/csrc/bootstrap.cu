@@ -21,6 +21,7 @@
 #include <cmath>
 #include <complex>
 #include <numeric>
+#include <tuple>
 
 #include "internal.cuh"
 #include "kernels.cuh"
@@ -129,8 +130,9 @@ struct PlainSet {  // encoded, NTT-domain diagonals of one group at one level an
 
 struct BtsState {
   int K = 28, r = 4, deg = 31, cts = 3, stc = 3;
-  std::vector<LTGroup> cts_groups, stc_groups;
-  std::map<std::pair<int, int>, PlainSet> plains;  // (inverse, group) -> encoded diagonals
+  std::vector<LTGroup> cts_groups, stc_groups;      // N/2 slots
+  std::map<size_t, std::pair<std::vector<LTGroup>, std::vector<LTGroup>>> sparse;  // n -> (CtS, StC) groups
+  std::map<std::tuple<size_t, int, int>, PlainSet> plains;  // (slots, inverse, group) -> encoded diagonals
   std::vector<double> mod_coeffs;                  // Chebyshev coefficients of the scaled cosine
 };
 void BtsStateDeleter::operator()(BtsState* p) const { delete p; }
@@ -248,8 +250,20 @@ static BtsState& state(Ctx& C) {
   return *C.bts;
 }
 
-// encode a diagonal at plaintext scale sp onto limbs 0..level (NTT domain)
-static DevBuf encode_diag(Ctx& C, const std::vector<cplx>& d, double sp, int level) {
+// CtS (inverse) or StC groups for n slots (n = N/2, or sparse packing with period n)
+static const std::vector<LTGroup>& groups_for(Ctx& C, BtsState& S, size_t n, bool inverse) {
+  if (n == C.N / 2) return inverse ? S.cts_groups : S.stc_groups;
+  auto it = S.sparse.find(n);
+  if (it == S.sparse.end())
+    it = S.sparse.emplace(n, std::make_pair(make_groups(n, S.cts, true), make_groups(n, S.stc, false))).first;
+  return inverse ? it->second.first : it->second.second;
+}
+
+// encode a diagonal (n values, repeated over the N/2 slots) at plaintext scale sp onto limbs
+// 0..level (NTT domain)
+static DevBuf encode_diag(Ctx& C, const std::vector<cplx>& dn, double sp, int level) {
+  std::vector<cplx> d(C.N / 2);
+  for (size_t s = 0; s < d.size(); ++s) d[s] = dn[s % dn.size()];
   std::vector<double> m = encode_slots(C, d, sp);
   std::vector<long long> ci(C.N);
   for (size_t k = 0; k < C.N; ++k) {
@@ -269,13 +283,14 @@ static DevBuf encode_diag(Ctx& C, const std::vector<cplx>& d, double sp, int lev
 
 // sum_g rot( sum_b rot(D_k, -G_g) o rot(v, b h0), G_g ),  k = kmin + g n1 + b,  G_g = h0 (kmin + g n1);
 // one rescale at the end; the result's scale is `target`
-std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int gi, double target) {
+std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int gi, double target, size_t slots) {
   BtsState& S = state(C);
-  const LTGroup& G = (inverse ? S.cts_groups : S.stc_groups).at(gi);
+  if (!slots) slots = C.N / 2;
+  const LTGroup& G = groups_for(C, S, slots, inverse).at(gi);
   const int l = v.level;
   if (l < 1) throw Error(HEDAP_ERR_LEVEL, "linear transform needs level >= 1");
   const double sp = target * (double)C.primes[l] / v.scale;
-  PlainSet& P = S.plains[{inverse ? 1 : 0, gi}];
+  PlainSet& P = S.plains[{slots, inverse ? 1 : 0, gi}];
   if (P.level != l || P.sp != sp) {  // (re)encode; the cache is marked valid only once complete
     P.pt.clear();
     P.level = -1;
@@ -304,7 +319,7 @@ std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int 
     for (size_t i = 0; i < need.size(); ++i) baby[need[i]] = std::move(rot[i]);
   }
   std::unique_ptr<Ct> acc;
-  const long n = (long)(C.N / 2);
+  const long n = (long)slots;
   for (long g = 0; g < G.giants; ++g) {
     PtMacArgs A;
     A.count = 0;
@@ -359,9 +374,22 @@ std::unique_ptr<Ct> eval_mod(Ctx& C, const Ct& u) {
   return c;
 }
 
-std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a) {
+// sum of the rotations by n, 2n, ..., N/4: the plaintext's part in Z[X^(N/2n)] times N/2n (the
+// automorphisms X -> X^(5^(n j)) are those fixing that subring, since 5^(n j) = 1 mod 4n)
+std::unique_ptr<Ct> sub_sum(Ctx& C, const Ct& a, size_t n) {
+  if (n < 1 || n > C.N / 2 || (n & (n - 1))) throw Error(HEDAP_ERR_ARG, "slot count must be a power of two <= N/2");
+  auto t = ct_copy(C, a, a.level);
+  for (size_t k = n; k < C.N / 2; k *= 2) t = ev_add(C, *t, *ev_galois(C, *t, galois_for_rotation(C, (i64)k)), false);
+  return t;
+}
+
+std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a, int log_slots) {
   BtsState& S = state(C);
   if (a.level != 0) throw Error(HEDAP_ERR_LEVEL, "bootstrap input must be at level 0");
+  if (log_slots < 0 || (log_slots && ((size_t)1 << log_slots) > C.N / 2) ||
+      (log_slots && log_slots < std::max(S.cts, S.stc)))
+    throw Error(HEDAP_ERR_ARG, "log_slots out of range for this bootstrapping configuration");
+  const size_t n = log_slots ? (size_t)1 << log_slots : C.N / 2;
   const double s_in = a.scale, q0 = (double)C.primes[0];
   std::unique_ptr<Ct> t;
   if (C.enc_hw) {  // sparse-secret encapsulation: ModRaise under s~, then back to s at the top level
@@ -369,8 +397,9 @@ std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a) {
   } else {
     t = mod_raise(C, a);
   }
-  t->scale = 2.0 * q0 * S.K;
-  for (int g = 0; g < S.cts; ++g) t = bts_linear_transform(C, *t, true, g, (double)C.primes[t->level - 1]);
+  if (n < C.N / 2) t = sub_sum(C, *t, n);  // sparse packing: project q_0 I onto the subring
+  t->scale = 2.0 * q0 * S.K * (double)(C.N / 2 / n);
+  for (int g = 0; g < S.cts; ++g) t = bts_linear_transform(C, *t, true, g, (double)C.primes[t->level - 1], n);
   auto cj = ev_galois(C, *t, 2 * C.N - 1);
   auto re = ev_add(C, *t, *cj, false);
   auto im = mul_monomial(C, *ev_add(C, *t, *cj, true), 3 * C.N / 2);  // times -i
@@ -386,17 +415,17 @@ std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a) {
   auto w = ev_add(C, *re, *mul_monomial(C, *im, C.N / 2), false);  // re + i im
   w->scale = w->scale * 2.0 * M_PI * s_in / q0;
   for (int g = 0; g < S.stc; ++g)
-    w = bts_linear_transform(C, *w, false, g, g + 1 == S.stc ? C.scale : (double)C.primes[w->level - 1]);
+    w = bts_linear_transform(C, *w, false, g, g + 1 == S.stc ? C.scale : (double)C.primes[w->level - 1], n);
   return w;
 }
 
 // y with values in [-Y, Y]: scale by 1/Y into [-1, 1], landing at level 0 with scale
 // q_0 / 2^12, bootstrap, then multiply by the integer Y
-std::unique_ptr<Ct> bootstrap_scaled(Ctx& C, const Ct& y, i64 Y) {
+std::unique_ptr<Ct> bootstrap_scaled(Ctx& C, const Ct& y, i64 Y, int log_slots) {
   if (y.level < 1) throw Error(HEDAP_ERR_LEVEL, "bootstrap needs an input at level >= 1");
   std::unique_ptr<Ct> d = y.level > 1 ? ev_drop(C, y, 1) : nullptr;
   auto a = ev_mul_const(C, d ? *d : y, 1.0 / (double)Y, (double)C.primes[0] / 4096.0);
-  auto b = bootstrap_core(C, *a);
+  auto b = bootstrap_core(C, *a, log_slots);
   return Y == 1 ? std::move(b) : ev_mul_int(C, *b, Y);
 }
 

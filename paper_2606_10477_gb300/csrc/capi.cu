@@ -344,6 +344,18 @@ API hedap_status hedap_encapsulation_switch(hedap_ctx* ctx, const hedap_ct* a, i
   CT_OP((need(a && ctx->c->enc_hw, "null ciphertext or no encapsulation"),
          hedap::ev_switch_key(*ctx->c, *a->c, to_sparse ? hedap::kKeyToSparse : hedap::kKeyToDense)));
 }
+API hedap_status hedap_bootstrap_slots(hedap_ctx* ctx, const hedap_ct* a, uint32_t log_slots, hedap_ct** out) {
+  CT_OP((need(a && log_slots >= 1 && log_slots < 31, "bad argument"),
+         hedap::bootstrap_core(*ctx->c, *a->c, (int)log_slots)));
+}
+API hedap_status hedap_bootstrap_scaled_slots(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, uint32_t log_slots,
+                                              hedap_ct** out) {
+  CT_OP((need(a && Y >= 1 && log_slots >= 1 && log_slots < 31, "bad argument"),
+         hedap::bootstrap_scaled(*ctx->c, *a->c, Y, (int)log_slots)));
+}
+API hedap_status hedap_sub_sum(hedap_ctx* ctx, const hedap_ct* a, uint32_t log_slots, hedap_ct** out) {
+  CT_OP((need(a && log_slots < 31, "bad argument"), hedap::sub_sum(*ctx->c, *a->c, (size_t)1 << log_slots)));
+}
 API hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
   CT_OP((need(a, "null ciphertext"), hedap::bootstrap_core(*ctx->c, *a->c)));
 }
@@ -433,7 +445,7 @@ static void invsqrt_grouped(hedap_ctx* ctx, const hedap_ct* const* in, const hed
       for (size_t j = i + 1; j < n && g.size() < 16; ++j) {
         if (done[j]) continue;
         const hedap::Ct &a = *in[i]->c, &b = *in[j]->c;
-        if (key(i) == key(j) && a.scale == b.scale && memcmp(&cfgs[i], &cfgs[j], sizeof(hedap_invsqrt_cfg)) == 0)
+        if (key(i) == key(j) && a.scale == b.scale && hedap::same_cfg(cfgs[i], cfgs[j]))
           g.push_back(j);
       }
       int lmin = INT_MAX;

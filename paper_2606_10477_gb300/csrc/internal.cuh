@@ -300,11 +300,17 @@ void select(Ctx& C, const hedap_select_cfg& sc, std::vector<hedap_select_entry>&
 
 // ------------------------------------------------------------------ bootstrapping (bootstrap.cu)
 int bts_setup(Ctx& C, int K, int r, int deg, int cts, int stc);
-std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a);
-std::unique_ptr<Ct> bootstrap_scaled(Ctx& C, const Ct& y, i64 Y);
+std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a, int log_slots = 0);
+std::unique_ptr<Ct> bootstrap_scaled(Ctx& C, const Ct& y, i64 Y, int log_slots = 0);
+std::unique_ptr<Ct> sub_sum(Ctx& C, const Ct& a, size_t n);
+// equality of two CryptoInvSqrt configurations, field by field (the struct has padding)
+inline bool same_cfg(const hedap_invsqrt_cfg& x, const hedap_invsqrt_cfg& y) {
+  return x.lo == y.lo && x.hi == y.hi && x.B == y.B && x.degree == y.degree && x.newton_iters == y.newton_iters &&
+         x.pre_bts == y.pre_bts && x.bts_mask == y.bts_mask && x.log_slots == y.log_slots;
+}
 std::unique_ptr<Ct> mod_raise(Ctx& C, const Ct& a);
 std::unique_ptr<Ct> mul_monomial(Ctx& C, const Ct& a, u64 e);
-std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& a, bool inverse, int g, double target);
+std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& a, bool inverse, int g, double target, size_t slots = 0);
 std::unique_ptr<Ct> eval_mod(Ctx& C, const Ct& a);
 bool bts_diagonal(Ctx& C, bool inverse, int g, long offset, std::vector<std::complex<double>>& out);
 

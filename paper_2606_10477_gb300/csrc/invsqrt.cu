@@ -165,7 +165,8 @@ static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
 // y into [-1, 1] around each BTS.  The final 1/sqrt(B) is applied to the scale
 // label (no level is used).
 InvSqrtRun::InvSqrtRun(Ctx& C_, const Ct& in, const hedap_invsqrt_cfg& c) : C(C_), cfg(c) {
-  if (!(cfg.B > 0) || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.degree > 4096)
+  if (!(cfg.B > 0) || !(cfg.lo > 0) || !(cfg.hi > cfg.lo) || cfg.degree < 1 || cfg.degree > 4096 ||
+      ((size_t)1 << std::min(cfg.log_slots, 40u)) > C.N / 2)
     throw Error(HEDAP_ERR_ARG, "invsqrt: invalid configuration");
   if ((cfg.pre_bts || cfg.bts_mask) && !C.bts)
     throw Error(HEDAP_ERR_ARG, "invsqrt: bootstrapping not configured on this context");
@@ -178,7 +179,8 @@ InvSqrtRun::InvSqrtRun(Ctx& C_, const Ct& in, const hedap_invsqrt_cfg& c) : C(C_
   if (cfg.pre_bts) {  // a -> BTS(a / B), values in (0, 1]
     if (in.level < 1) throw Error(HEDAP_ERR_LEVEL, "invsqrt: input level too low");
     CtP d = in.level > 1 ? ev_drop(C, in, 1) : nullptr;
-    pre = bootstrap_core(C, *ev_mul_const(C, d ? *d : in, 1.0 / cfg.B, (double)C.primes[0] / 4096.0));
+    pre = bootstrap_core(C, *ev_mul_const(C, d ? *d : in, 1.0 / cfg.B, (double)C.primes[0] / 4096.0),
+                         (int)cfg.log_slots);
     Bf = 1.0;
   }
   const Ct& a = pre ? *pre : in;
@@ -192,11 +194,11 @@ void InvSqrtRun::newton(int i) {
   const bool force = i < 62 && ((cfg.bts_mask >> i) & 1);
   const bool lazy = ((cfg.bts_mask >> 63) & 1) && y->level < 3;
   if (force || lazy) {
-    y = bootstrap_scaled(C, *y, Y);
+    y = bootstrap_scaled(C, *y, Y, (int)cfg.log_slots);
     if (((cfg.bts_mask >> 62) & 1) && x->level < 5) {  // variant: ct_x refreshed with y
       i64 Yx = 1;
       while ((double)Yx < 0.5 * hi) Yx *= 2;
-      x = bootstrap_scaled(C, *x, Yx);
+      x = bootstrap_scaled(C, *x, Yx, (int)cfg.log_slots);
     }
   }
   if (std::min(y->level, x->level) < 2) throw Error(HEDAP_ERR_LEVEL, "invsqrt: level exhausted in Newton loop");
@@ -213,7 +215,7 @@ std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) 
   run.chebyshev();
   const int n = (int)cfg.newton_iters;
   for (int i = 0; i < n; ++i) run.newton(i);
-  if (n == 0 && (cfg.bts_mask & 1)) run.y = bootstrap_scaled(C, *run.y, run.Y);
+  if (n == 0 && (cfg.bts_mask & 1)) run.y = bootstrap_scaled(C, *run.y, run.Y, (int)cfg.log_slots);
   if (cfg.B != 1.0) run.y->scale *= std::sqrt(cfg.B);
   return std::move(run.y);
 }

@@ -62,8 +62,7 @@ struct Query {
 };
 
 bool same_group(const Query& a, const Query& b) {
-  return a.kind == b.kind && a.level == b.level && a.scale == b.scale &&
-         std::memcmp(&a.cfg, &b.cfg, sizeof(hedap_invsqrt_cfg)) == 0;
+  return a.kind == b.kind && a.level == b.level && a.scale == b.scale && same_cfg(a.cfg, b.cfg);
 }
 
 struct Group {
@@ -262,7 +261,7 @@ void hedap_server::step(Group& g) {
     if (!Cx.bts) throw Error(HEDAP_ERR_LEVEL, "server: InvSqrt left no level for the final product");
     i64 Y = 1;
     while ((double)Y < 1.0 / std::sqrt(g.q[0]->cfg.lo)) Y *= 2;
-    s = bootstrap_scaled(Cx, *s, Y);
+    s = bootstrap_scaled(Cx, *s, Y, (int)g.q[0]->cfg.log_slots);
   }
   std::vector<CtP> sk;
   for (int k = 0; k < B; ++k) sk.push_back(B > 1 ? batch_unpack(Cx, *s, k) : std::move(s));

@@ -29,7 +29,7 @@ EXPORTED = [
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_bootstrap_encapsulate",
-    "hedap_encapsulation_switch", "hedap_mod_raise", "hedap_mul_monomial",
+    "hedap_encapsulation_switch", "hedap_bootstrap_slots", "hedap_bootstrap_scaled_slots", "hedap_sub_sum", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_ntt_batch",
     "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
@@ -81,7 +81,8 @@ class Params(C.Structure):
 
 class InvSqrtCfg(C.Structure):
     _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("B", C.c_double), ("degree", C.c_uint32),
-                ("newton_iters", C.c_uint32), ("pre_bts", C.c_uint32), ("bts_mask", C.c_uint64)]
+                ("newton_iters", C.c_uint32), ("pre_bts", C.c_uint32), ("bts_mask", C.c_uint64),
+                ("log_slots", C.c_uint32)]
 
 
 class ServerCfg(C.Structure):
@@ -154,6 +155,9 @@ def _declare(L):
         "hedap_bootstrap": (st, [vp, vp, pp]),
         "hedap_bootstrap_scaled": (st, [vp, vp, C.c_int64, pp]),
         "hedap_bootstrap_encapsulate": (st, [vp, C.c_uint32]),
+        "hedap_bootstrap_slots": (st, [vp, vp, C.c_uint32, pp]),
+        "hedap_bootstrap_scaled_slots": (st, [vp, vp, C.c_int64, C.c_uint32, pp]),
+        "hedap_sub_sum": (st, [vp, vp, C.c_uint32, pp]),
         "hedap_encapsulation_switch": (st, [vp, vp, C.c_int, pp]),
         "hedap_mod_raise": (st, [vp, vp, pp]),
         "hedap_mul_monomial": (st, [vp, vp, C.c_uint64, pp]),
@@ -436,6 +440,16 @@ class Context:
     def bootstrap(self, a):
         return self._ct(load().hedap_bootstrap, a.h)
 
+    def bootstrap_slots(self, a, log_slots: int):
+        """Sparse-slot bootstrapping (2^log_slots values repeated over the N/2 slots)."""
+        return self._ct(load().hedap_bootstrap_slots, a.h, log_slots)
+
+    def bootstrap_scaled_slots(self, a, Y: int, log_slots: int):
+        return self._ct(load().hedap_bootstrap_scaled_slots, a.h, Y, log_slots)
+
+    def sub_sum(self, a, log_slots: int):
+        return self._ct(load().hedap_sub_sum, a.h, log_slots)
+
     def bts_encapsulate(self, h: int) -> None:
         """Sparse-secret encapsulation of bootstrapping (ephemeral secret of weight h)."""
         _check(load().hedap_bootstrap_encapsulate(self.h, h))
@@ -480,8 +494,8 @@ class Context:
         _check(load().hedap_set_scale(self.h, b.h, scale))
         return b
 
-    def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0):
-        cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask)
+    def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0, log_slots=0):
+        cfg = InvSqrtCfg(lo, hi, B, degree, iters, pre_bts, bts_mask, log_slots)
         return self._ct(load().hedap_invsqrt, a.h, C.byref(cfg))
 
     def invsqrt_graph(self, example, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0) -> "Graph":

@@ -174,3 +174,49 @@ def test_dense_secret_bootstrap_full_size():
     assert b.level == lvl
     err = np.abs(g.decrypt(b) - z)
     assert np.max(err) < 1e-3 and np.mean(err) < 1e-4
+
+
+# ------------------------------------------------------------------ sparse packing
+@pytest.mark.parametrize("ls", [7, 10])
+def test_sub_sum_bit_exact(pair12, ls):
+    g, o = pair12
+    L = o.n_q - 1
+    limbs = inputs.random_ciphertext_limbs(30 + ls, o.primes(), L, o.N)
+    ga, oa = g.ct_import(limbs, L, o.scale), o.ct_import(limbs, L, o.scale)
+    same(g.sub_sum(ga, ls), o.sub_sum(oa, ls))
+
+
+@pytest.mark.parametrize("ls", [7, 10])
+def test_sparse_slot_bootstrap_bit_exact(pair12, ls):
+    g, o = pair12
+    n = 1 << ls
+    v = inputs.uniform_values(40 + ls, n, -1, 1) + 1j * inputs.uniform_values(50 + ls, n, -1, 1)
+    zt = np.tile(v, o.N // 2 // n)
+    gc, oc = level0_pair(g, o, 60 + ls, zt)
+    gb, ob = g.bootstrap_slots(gc, ls), o.bootstrap_slots(oc, ls)
+    same(gb, ob)
+    assert np.max(np.abs(g.decrypt(gb) - zt)) < 1e-4
+
+
+def test_sparse_slot_invsqrt_bit_exact(pair12):
+    g, o = pair12
+    n = 1 << 8
+    a = np.tile(inputs.log_uniform_values(70, n, 1e-4, 1.0), o.N // 2 // n)
+    lvl = o.n_q - 1 - 16
+    oc = o.encrypt(a, lvl, 71)
+    gc = g.ct_import(oc.limbs(), oc.level, oc.scale)
+    cfg = (1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63, 8)
+    same(g.invsqrt(gc, *cfg), o.invsqrt(oc, *cfg))
+
+
+def test_sparse_slot_bootstrap_full_size():
+    """N = 2^16 with 2^10 values repeated over the 32768 slots: five rotations of SubSum, then
+    CoeffToSlot / SlotToCoeff on 1024 slots."""
+    g, lvl = make("bts16", hedap.Context, seed=4)
+    n = 1 << 10
+    v = inputs.uniform_values(72, n, -1, 1) + 1j * inputs.uniform_values(73, n, -1, 1)
+    zt = np.tile(v, g.N // 2 // n)
+    b = g.bootstrap_scaled_slots(g.encrypt(zt, 1, 74), 1, 10)
+    assert b.level == lvl
+    err = np.abs(g.decrypt(b) - zt)
+    assert np.max(err) < 1e-3 and np.mean(err) < 1e-4

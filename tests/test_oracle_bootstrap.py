@@ -172,3 +172,45 @@ def test_dense_secret_bootstrap_returns_its_input(dense):
     b = dense.bootstrap(ct0)
     assert b.level == dense.n_q - 1 - 16
     assert np.max(np.abs(dense.decrypt(b) - z)) < 1e-4
+
+
+# ------------------------------------------------------------------ sparse packing (2^log_slots slots repeated)
+def test_sub_sum_projects_onto_the_subring(ctx):
+    """Rotating by n, 2n, ..., N/4 and adding maps a plaintext m to (N/2n) times its part in
+    Z[X^(N/2n)]: coefficients at multiples of N/2n multiplied by N/2n, all others zero (within
+    the noise of the rotations' key switches)."""
+    half = ctx.N // 2
+    z = inputs.uniform_values(70, half, -1, 1) + 1j * inputs.uniform_values(71, half, -1, 1)
+    ct = ctx.encrypt(z, 5, 72)
+    m = ctx.decrypt_coeffs(ct)
+    for ls in (7, 10):
+        g = half >> ls
+        d = ctx.decrypt_coeffs(ctx.sub_sum(ct, ls))
+        expect = np.where(np.arange(ctx.N) % g == 0, g * m, 0.0)
+        assert np.max(np.abs(d - expect)) < 4096  # against coefficients up to ~1.5e12
+
+
+@pytest.mark.parametrize("ls", [7, 10])
+def test_sparse_slot_bootstrap_returns_its_input(ctx, ls):
+    """2^ls values repeated over the N/2 slots: the bootstrap returns them within 1e-4, still
+    repeated with period 2^ls, at the level of a full-slot bootstrap."""
+    half = ctx.N // 2
+    n = 1 << ls
+    q0 = float(ctx.primes()[0])
+    v = inputs.uniform_values(80 + ls, n, -1, 1) + 1j * inputs.uniform_values(90 + ls, n, -1, 1)
+    zt = np.tile(v, half // n)
+    b = ctx.bootstrap_slots(ctx.mul_const(ctx.encrypt(zt, 1, 100 + ls), 1.0, q0 / 4096), ls)
+    assert b.level == ctx.n_q - 1 - 16
+    out = ctx.decrypt(b)
+    assert np.max(np.abs(out - zt)) < 1e-4
+    assert np.max(np.abs(out - np.tile(out[:n], half // n))) < 1e-4
+
+
+def test_sparse_slot_invsqrt_with_lazy_bootstrapping(ctx):
+    n = 1 << 8
+    a = inputs.log_uniform_values(110, n, 1e-4, 1.0)
+    at = np.tile(a, ctx.N // 2 // n)
+    L_after = ctx.n_q - 1 - 16
+    y = ctx.decrypt(ctx.invsqrt(ctx.encrypt(at, L_after, 111), 1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63, 8)).real
+    plain = oracle.plain_invsqrt(at, 1e-4, 1.0, 1.0, 15, 5)
+    assert np.max(np.abs(y - plain) / plain) < 1e-4
