@@ -24,8 +24,8 @@
 // limbs may be skipped, and a rescale / ModDown may be fused around a forward
 // transform (its spread into the first phase's load, its finish into the second
 // phase's store).  Butterflies keep residues
-// lazily in [0, 4q) (forward) or [0, 2q) (inverse) following Harvey (2014);
-// the final launch writes canonical residues.
+// lazily (Harvey 2014): forward below 8q with the first operand reduced at every
+// other stage, inverse in [0, 2q); the final launch writes canonical residues.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -33,12 +33,25 @@
 
 namespace hedap {
 
+// Forward (Cooley-Tukey) butterfly on lazy residues.  Every stage adds at most 2q to the bound
+// (t < 2q), so the first operand is brought from [0, 8q) into [0, 4q) only at even stages
+// (REDUCE): an even stage leaves values below 6q, the odd stage after it below 8q (< 2^64 for
+// q < 2^61), and the next even stage starts again from [0, 4q).
+template <bool REDUCE>
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
-  const u64 q2 = q << 1;
-  if (x >= q2) x -= q2;
+  if constexpr (REDUCE) {
+    const u64 q4 = q << 2;
+    if (x >= q4) x -= q4;
+  }
   const u64 t = shoup_mul_lazy(y, w.x, w.y, q);  // [0, 2q)
+  const u64 q2 = q << 1;
   y = x + q2 - t;
   x = x + t;
+}
+// stage `s` of the forward transform (global index)
+__device__ __forceinline__ void ct_bfly_stage(int s, u64& x, u64& y, const ulonglong2 w, u64 q) {
+  if (s % 2 == 0) ct_bfly<true>(x, y, w, q);
+  else ct_bfly<false>(x, y, w, q);
 }
 __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const ulonglong2 w, u64 q) {
   const u64 q2 = q << 1;
@@ -48,8 +61,9 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const ulonglong2 w, u64 
   y = shoup_mul_lazy(d, w.x, w.y, q);
   x = s;
 }
-__device__ __forceinline__ u64 reduce4q(u64 x, u64 q) {
-  const u64 q2 = q << 1;
+__device__ __forceinline__ u64 reduce8q(u64 x, u64 q) {
+  const u64 q4 = q << 2, q2 = q << 1;
+  if (x >= q4) x -= q4;
   if (x >= q2) x -= q2;
   if (x >= q) x -= q;
   return x;
@@ -97,7 +111,7 @@ __device__ __forceinline__ void fwd_cols_passes(u64* sm, const ulonglong2* tw, u
         for (int m1 = 0; m1 < (1 << K); ++m1) {
           if (m1 & half) continue;
           const uint32_t wi = (1u << (S0 + u)) + (high << u) + (m1 >> (K - u));
-          ct_bfly(v[m1], v[m1 + half], tw[wi], q);
+          ct_bfly_stage(S0 + u, v[m1], v[m1 + half], tw[wi], q);
         }
       }
 #pragma unroll
@@ -208,6 +222,87 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
   }
 }
 
+// ---------------------------------------------------------------- forward, column phase with ModUp, several limbs
+// The fused ModUp of one digit reads the same na (<= 3) coefficient-domain tiles of z for every
+// output limb.  This kernel stages them once (cp.async, straight into shared memory) and runs the
+// column phase of `lpc` consecutive output limbs of one part from there, so the wait for global
+// memory is paid once per lpc limbs; each limb's twiddles are fetched with cp.async while the
+// previous limb computes (two twiddle buffers).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int L1, int L2, int C, int TPB, int MINB, int RL>
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_modup(Tables T, LimbSet S, NttAux A, int lpc) {
+  extern __shared__ u64 sm[];
+  constexpr size_t N = (size_t)1 << (L1 + L2);
+  constexpr int E = C << L1;
+  ulonglong2* twb = reinterpret_cast<ulonglong2*>(sm + E);  // two buffers of 2^L1 pairs
+  u64* zt = sm + E + 4 * (1 << L1);                         // na staged tiles of E words
+  const int groups = (S.n_limbs + lpc - 1) / lpc;
+  const int part = blockIdx.y / groups, g = blockIdx.y % groups;
+  const int l0 = S.limb_begin + g * lpc, l1 = min(l0 + lpc, S.limb_begin + S.n_limbs);
+  const int j = part % A.own_dn, lo = j * A.own_alpha, na = min(A.own_alpha, A.own_limit - lo);
+  const u64* zk = A.z + (size_t)(part / A.own_dn) * A.z_stride + (size_t)lo * N;
+  const int r0 = blockIdx.x * C;
+  // the z tiles: row c of tile t holds words r0 .. r0 + C - 1 of column c (16-byte copies)
+  for (int idx = threadIdx.x; idx < na * (E / 2); idx += TPB) {
+    const int t = idx / (E / 2), e = 2 * (idx % (E / 2));
+    const int c = e / C, col = e % C;
+    cp_async16(zt + (size_t)t * E + e, zk + (size_t)t * N + ((size_t)c << L2) + r0 + col);
+  }
+  auto fetch_tw = [&](int li, int buf) {
+    const ulonglong2* W = T.psi2 + (size_t)S.prime(li) * N;
+    for (int i = threadIdx.x; i < (1 << L1); i += TPB) cp_async16(twb + buf * (1 << L1) + i, W + i);
+  };
+  int li = l0;
+  while (li < l1 && own_limb(A, part, li)) ++li;
+  if (li < l1) fetch_tw(li, 0);
+  cp_async_commit();
+  int buf = 0;
+  for (; li < l1; buf ^= 1) {
+    int next = li + 1;
+    while (next < l1 && own_limb(A, part, next)) ++next;
+    cp_async_wait_all();
+    __syncthreads();  // z tiles and this limb's twiddles have landed; the previous limb is done
+    if (next < l1) fetch_tw(next, buf ^ 1);
+    cp_async_commit();
+    const u64 q = T.pr[S.prime(li)].q;
+    const u64* bc = A.bconv + (size_t)j * A.own_alpha * A.ext + li;
+    const u64* bcs = bc + A.bconv_sh_offset;
+    u64 f[3], fs[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      f[t] = t < na ? bc[(size_t)t * A.ext] : 0;
+      fs[t] = t < na ? bcs[(size_t)t * A.ext] : 0;
+    }
+    const u64 q4 = q << 2, q8 = q << 3;
+#pragma unroll
+    for (int idx = threadIdx.x; idx < E; idx += TPB) {
+      u64 v = 0;
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t < na) v += shoup_mul_lazy(zt[(size_t)t * E + idx], f[t], fs[t], q);
+      if (v >= q8) v -= q8;
+      if (v >= q4) v -= q4;
+      sm[idx] = v;
+    }
+    __syncthreads();
+    fwd_cols_passes<L1, C, RL, 0>(sm, twb + buf * (1 << L1), q);
+    u64* a = S.limb(part, li, N);
+#pragma unroll
+    for (int idx = threadIdx.x; idx < E; idx += TPB) {
+      const int c = idx / C, col = idx % C;
+      a[((size_t)c << L2) + r0 + col] = sm[idx];
+    }
+    li = next;
+  }
+  cp_async_wait_all();
+}
+
 // ---------------------------------------------------------------- forward, block phase
 // block b, local x at sm[b * R + padx(x)]; j = (B0 + b) * 2^L2 + x; local stage s'
 // couples x and x + 2^(L2-s'-1); twiddle index 2^(L1+s') + ((B0+b) << s') + (x >> (L2 - s')).
@@ -248,7 +343,7 @@ __device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* tw, u
         for (int m1 = 0; m1 < (1 << K); ++m1) {
           if (m1 & half) continue;
           const uint32_t wi = BPC * ((1u << sl) - 1) + (b << sl) + (high << u) + (m1 >> (K - u));
-          ct_bfly(v[m1], v[m1 + half], tw[wi], q);
+          ct_bfly_stage(L1 + sl, v[m1], v[m1 + half], tw[wi], q);
         }
       }
 #pragma unroll
@@ -283,7 +378,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
     const bool acc = (part & 1) ? A.fin_acc_odd : A.fin_acc_even;
 #pragma unroll
     for (int idx = threadIdx.x; idx < E; idx += TPB) {
-      const u64 v = reduce4q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+      const u64 v = reduce8q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
       u64 z = shoup_mul(sub_mod(cp[idx], v, q), w, wp, q);
       if (acc) z = add_mod(z, dp[idx], q);
       dp[idx] = z;
@@ -292,7 +387,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   }
 #pragma unroll
   for (int idx = threadIdx.x; idx < E; idx += TPB)
-    a[j0 + idx] = reduce4q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+    a[j0 + idx] = reduce8q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
 }
 
 // ---------------------------------------------------------------- inverse, block phase
@@ -469,7 +564,27 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
   A2.spread = nullptr;
   A2.pconv = nullptr;
   if (!inverse) {
-    k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
+    const int na_max = A.z ? std::min(A.own_alpha, A.own_limit) : 0;
+    if (A.z && na_max <= 3) {
+      // several output limbs per CTA, sharing the staged z tiles: enough limb groups for about
+      // four waves of 4 CTAs on 152 SMs, at most all the limbs in one group
+      const size_t per_group = (size_t)grid.x * S.n_parts;
+      const int groups = (int)std::min<size_t>(S.n_limbs, std::max<size_t>(1, (2432 + per_group - 1) / per_group));
+      const int lpc = (S.n_limbs + groups - 1) / groups;
+      const dim3 g2(grid.x, (unsigned)(S.n_parts * ((S.n_limbs + lpc - 1) / lpc)));
+      const size_t smem_m = (size_t)EE * sizeof(u64) + 2 * ((size_t)1 << L1) * sizeof(ulonglong2) +
+                            (size_t)na_max * EE * sizeof(u64);
+      static const bool attr_m = [&] {
+        HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols_modup<L1, L2, C, TPB, MINB, RL>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)EE * 8 + 2 * ((size_t)1 << L1) * 16 + 3 * (size_t)EE * 8)));
+        return true;
+      }();
+      (void)attr_m;
+      k_ntt_fwd_cols_modup<L1, L2, C, TPB, MINB, RL><<<g2, TPB, smem_m, st>>>(T, S, A, lpc);
+    } else {
+      k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
+    }
     k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A2);
   } else {
     k_ntt_inv_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A);
@@ -482,12 +597,12 @@ template <int L1, int L2>
 static void launch_variant(int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
                            const NttAux& A) {
   switch (v) {
-    case 0: launch_pair<L1, L2, 4096, 1, 4>(S, T, st, inverse, A); break;
+    case 0: launch_pair<L1, L2, 2048, 5, 3>(S, T, st, inverse, A); break;
     case 1: launch_pair<L1, L2, 4096, 3, 4>(S, T, st, inverse, A); break;
     case 2: launch_pair<L1, L2, 2048, 4, 4>(S, T, st, inverse, A); break;
     case 3: launch_pair<L1, L2, 2048, 6, 4>(S, T, st, inverse, A); break;
-    case 4: launch_pair<L1, L2, 8192, 1, 4>(S, T, st, inverse, A); break;
-    case 5: launch_pair<L1, L2, 1024, 8, 4>(S, T, st, inverse, A); break;
+    case 4: launch_pair<L1, L2, 2048, 6, 3>(S, T, st, inverse, A); break;
+    case 5: launch_pair<L1, L2, 1024, 12, 3>(S, T, st, inverse, A); break;
     case 6: launch_pair<L1, L2, 2048, 4, 3>(S, T, st, inverse, A); break;
     default: launch_pair<L1, L2, 1024, 8, 3>(S, T, st, inverse, A); break;
   }
@@ -531,8 +646,9 @@ void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAu
 }
 
 // Register-only loop of the transform's butterfly (the rate the integer pipes allow without any
-// memory or shared-memory traffic): each thread runs `iters` rounds of 4 independent lazy Cooley-
-// Tukey butterflies on 8 residues of the context's first prime and stores one word.
+// memory or shared-memory traffic): each thread runs `iters` rounds (even, alternating the even-
+// and odd-stage forms) of 4 independent lazy Cooley-Tukey butterflies on 8 residues of the
+// context's first prime and stores one word.
 __global__ void k_butterfly_loop(const Tables T, u64* out, int iters) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const u64 q = T.pr[0].q;
@@ -540,9 +656,11 @@ __global__ void k_butterfly_loop(const Tables T, u64* out, int iters) {
   u64 v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = ((u64)i * 8 + m) % q;
-  for (int it = 0; it < iters; ++it) {
+  for (int it = 0; it < iters; it += 2) {  // an even and an odd stage
 #pragma unroll
-    for (int m = 0; m < 4; ++m) ct_bfly(v[m], v[m + 4], w, q);
+    for (int m = 0; m < 4; ++m) ct_bfly<true>(v[m], v[m + 4], w, q);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ct_bfly<false>(v[m], v[m + 4], w, q);
   }
   u64 s = 0;
 #pragma unroll
