@@ -222,12 +222,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
   }
 }
 
-// ---------------------------------------------------------------- forward, column phase with ModUp, several limbs
-// The fused ModUp of one digit reads the same na (<= 3) coefficient-domain tiles of z for every
-// output limb.  This kernel stages them once (cp.async, straight into shared memory) and runs the
-// column phase of `lpc` consecutive output limbs of one part from there, so the wait for global
-// memory is paid once per lpc limbs; each limb's twiddles are fetched with cp.async while the
-// previous limb computes (two twiddle buffers).
+// ---------------------------------------------------------------- forward, column phase from shared tiles, several limbs
+// Three fused first phases read the same few tiles for every output limb: the ModUp of one digit
+// (its na <= 3 coefficient-domain limbs z), the ModDown conversion (the K <= 3 special-prime limbs)
+// and the rescale spread (the last limb).  This kernel stages those tiles once (cp.async, straight
+// into shared memory) and runs the column phase of `lpc` consecutive output limbs of one part from
+// there, so the wait for global memory is paid once per lpc limbs; each limb's twiddles are
+// fetched with cp.async while the previous limb computes (two twiddle buffers).
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
@@ -236,23 +237,36 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int L1, int L2, int C, int TPB, int MINB, int RL>
-__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_modup(Tables T, LimbSet S, NttAux A, int lpc) {
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, LimbSet S, NttAux A, int lpc) {
   extern __shared__ u64 sm[];
   constexpr size_t N = (size_t)1 << (L1 + L2);
   constexpr int E = C << L1;
   ulonglong2* twb = reinterpret_cast<ulonglong2*>(sm + E);  // two buffers of 2^L1 pairs
-  u64* zt = sm + E + 4 * (1 << L1);                         // na staged tiles of E words
+  u64* zt = sm + E + 4 * (1 << L1);                         // ns staged tiles of E words
   const int groups = (S.n_limbs + lpc - 1) / lpc;
   const int part = blockIdx.y / groups, g = blockIdx.y % groups;
   const int l0 = S.limb_begin + g * lpc, l1 = min(l0 + lpc, S.limb_begin + S.n_limbs);
-  const int j = part % A.own_dn, lo = j * A.own_alpha, na = min(A.own_alpha, A.own_limit - lo);
-  const u64* zk = A.z + (size_t)(part / A.own_dn) * A.z_stride + (size_t)lo * N;
+  // the shared tiles: ns limbs at src + t N
+  int ns, j = 0;
+  const u64* src;
+  if (A.z) {
+    j = part % A.own_dn;
+    const int lo = j * A.own_alpha;
+    ns = min(A.own_alpha, A.own_limit - lo);
+    src = A.z + (size_t)(part / A.own_dn) * A.z_stride + (size_t)lo * N;
+  } else if (A.pconv) {
+    ns = A.pconv_K;
+    src = A.pconv + (size_t)part * A.pconv_stride;
+  } else {
+    ns = 1;
+    src = A.spread + (size_t)part * A.spread_stride;
+  }
   const int r0 = blockIdx.x * C;
-  // the z tiles: row c of tile t holds words r0 .. r0 + C - 1 of column c (16-byte copies)
-  for (int idx = threadIdx.x; idx < na * (E / 2); idx += TPB) {
+  // row c of tile t holds words r0 .. r0 + C - 1 of column c (16-byte copies)
+  for (int idx = threadIdx.x; idx < ns * (E / 2); idx += TPB) {
     const int t = idx / (E / 2), e = 2 * (idx % (E / 2));
     const int c = e / C, col = e % C;
-    cp_async16(zt + (size_t)t * E + e, zk + (size_t)t * N + ((size_t)c << L2) + r0 + col);
+    cp_async16(zt + (size_t)t * E + e, src + (size_t)t * N + ((size_t)c << L2) + r0 + col);
   }
   auto fetch_tw = [&](int li, int buf) {
     const ulonglong2* W = T.psi2 + (size_t)S.prime(li) * N;
@@ -267,28 +281,60 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_modup(Tables T, Limb
     int next = li + 1;
     while (next < l1 && own_limb(A, part, next)) ++next;
     cp_async_wait_all();
-    __syncthreads();  // z tiles and this limb's twiddles have landed; the previous limb is done
+    __syncthreads();  // the tiles and this limb's twiddles have landed; the previous limb is done
     if (next < l1) fetch_tw(next, buf ^ 1);
     cp_async_commit();
-    const u64 q = T.pr[S.prime(li)].q;
-    const u64* bc = A.bconv + (size_t)j * A.own_alpha * A.ext + li;
-    const u64* bcs = bc + A.bconv_sh_offset;
-    u64 f[3], fs[3];
+    const int pi = S.prime(li);
+    const u64 q = T.pr[pi].q, q4 = q << 2, q8 = q << 3;
+    if (A.z) {  // ModUp: sum of na Shoup products (each < 2q) brought into [0, 4q)
+      const u64* bc = A.bconv + (size_t)j * A.own_alpha * A.ext + li;
+      const u64* bcs = bc + A.bconv_sh_offset;
+      u64 f[3], fs[3];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      f[t] = t < na ? bc[(size_t)t * A.ext] : 0;
-      fs[t] = t < na ? bcs[(size_t)t * A.ext] : 0;
-    }
-    const u64 q4 = q << 2, q8 = q << 3;
+      for (int t = 0; t < 3; ++t) {
+        f[t] = t < ns ? bc[(size_t)t * A.ext] : 0;
+        fs[t] = t < ns ? bcs[(size_t)t * A.ext] : 0;
+      }
 #pragma unroll
-    for (int idx = threadIdx.x; idx < E; idx += TPB) {
-      u64 v = 0;
+      for (int idx = threadIdx.x; idx < E; idx += TPB) {
+        u64 v = 0;
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t < na) v += shoup_mul_lazy(zt[(size_t)t * E + idx], f[t], fs[t], q);
-      if (v >= q8) v -= q8;
-      if (v >= q4) v -= q4;
-      sm[idx] = v;
+        for (int t = 0; t < 3; ++t)
+          if (t < ns) v += shoup_mul_lazy(zt[(size_t)t * E + idx], f[t], fs[t], q);
+        if (v >= q4) v -= q4;
+        sm[idx] = v;
+      }
+    } else if (A.pconv) {  // ModDown conversion: 4q - floor(P/2) mod q plus K lazy products (< 10q)
+      u64 c[3], pk[3], f[3], fs[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const bool on = k < ns;
+        c[k] = on ? A.pconv_c[k] : 0;
+        pk[k] = on ? A.pconv_q[k] : 0;
+        f[k] = on ? A.pconv_phat[(size_t)k * A.pconv_ld + li] : 0;
+        fs[k] = on ? A.pconv_phat_sh[(size_t)k * A.pconv_ld + li] : 0;
+      }
+      const u64 off = q4 - A.pconv_half[li];
+#pragma unroll
+      for (int idx = threadIdx.x; idx < E; idx += TPB) {
+        u64 v = off;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (k < ns) v += shoup_mul_lazy(add_mod(zt[(size_t)k * E + idx], c[k], pk[k]), f[k], fs[k], q);
+        if (v >= q8) v -= q8;
+        if (v >= q4) v -= q4;
+        sm[idx] = v;
+      }
+    } else {  // rescale spread: centred residue of the last limb in this prime
+      const u64 half = T.pr[A.spread_prime].q >> 1, sub = A.spread_sub[li];
+      const PrimeDev P = T.pr[pi];
+#pragma unroll
+      for (int idx = threadIdx.x; idx < E; idx += TPB) {
+        const u64 v = zt[idx];
+        u64 m = barrett_reduce(v, 0, P);
+        if (v > half) m = sub_mod(m, sub, q);
+        sm[idx] = m;
+      }
     }
     __syncthreads();
     fwd_cols_passes<L1, C, RL, 0>(sm, twb + buf * (1 << L1), q);
@@ -564,24 +610,24 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
   A2.spread = nullptr;
   A2.pconv = nullptr;
   if (!inverse) {
-    const int na_max = A.z ? std::min(A.own_alpha, A.own_limit) : 0;
-    if (A.z && na_max <= 3) {
-      // several output limbs per CTA, sharing the staged z tiles: enough limb groups for about
+    const int ns_max = A.z ? std::min(A.own_alpha, A.own_limit) : A.pconv ? A.pconv_K : A.spread ? 1 : 0;
+    if (ns_max >= 1 && ns_max <= 3 && !A.src) {
+      // several output limbs per CTA, sharing the staged tiles: enough limb groups for about
       // four waves of 4 CTAs on 152 SMs, at most all the limbs in one group
       const size_t per_group = (size_t)grid.x * S.n_parts;
       const int groups = (int)std::min<size_t>(S.n_limbs, std::max<size_t>(1, (2432 + per_group - 1) / per_group));
       const int lpc = (S.n_limbs + groups - 1) / groups;
       const dim3 g2(grid.x, (unsigned)(S.n_parts * ((S.n_limbs + lpc - 1) / lpc)));
       const size_t smem_m = (size_t)EE * sizeof(u64) + 2 * ((size_t)1 << L1) * sizeof(ulonglong2) +
-                            (size_t)na_max * EE * sizeof(u64);
+                            (size_t)ns_max * EE * sizeof(u64);
       static const bool attr_m = [&] {
-        HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols_modup<L1, L2, C, TPB, MINB, RL>,
+        HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols_shared<L1, L2, C, TPB, MINB, RL>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)((size_t)EE * 8 + 2 * ((size_t)1 << L1) * 16 + 3 * (size_t)EE * 8)));
         return true;
       }();
       (void)attr_m;
-      k_ntt_fwd_cols_modup<L1, L2, C, TPB, MINB, RL><<<g2, TPB, smem_m, st>>>(T, S, A, lpc);
+      k_ntt_fwd_cols_shared<L1, L2, C, TPB, MINB, RL><<<g2, TPB, smem_m, st>>>(T, S, A, lpc);
     } else {
       k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
     }
