@@ -57,12 +57,12 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-level batch workload")
     ap.add_argument("--no-dnum3", action="store_true", help="skip the three-digit key-switching variant")
     ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
-    ap.add_argument("--only", choices=["ntt", "serving", "mixed", "bts"],
+    ap.add_argument("--only", choices=["ntt", "serving", "mixed", "bts", "hmult"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     ap.add_argument("--profile-region", action="store_true",
                     help="--only ntt: one forward and one inverse transform between cudaProfilerStart/Stop "
-                         "(for ncu --profile-from-start off)")
+                         "(for ncu --profile-from-start off); --only hmult: one batched HMult")
     return ap.parse_args()
 
 
@@ -98,10 +98,11 @@ def measured_peaks():
 # multiply-pipe slots, and 4 low ones = 16 slots per butterfly, against 64 multiply-add lanes per SM.
 NTT_MUL_SLOTS_PER_BUTTERFLY = 16
 GB300_SMS, IMAD_LANES_PER_SM = 152, 64
-# DRAM bytes per transformed limb (both phase launches), dram__bytes_read.sum + dram__bytes_write.sum
-# of one forward and one inverse transform of 384 limbs (`--only ntt --ntt-limbs 384 --profile-region`
-# under ncu), scaled to a launch group by its limbs
-NTT_DRAM_BYTES_PER_LIMB = 1.92e6
+# DRAM bytes per transformed limb, dram__bytes_read.sum + dram__bytes_write.sum of the 12 transform
+# launches of one batched HMult at the top level (`--only hmult --batch 2 --profile-region` under ncu:
+# 1336 MB for 824 limb transforms, the mix of fused ModUp / ModDown / rescale transforms of the step),
+# scaled to a launch group by its limbs
+NTT_DRAM_BYTES_PER_LIMB = 1.62e6
 
 
 def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
@@ -754,6 +755,47 @@ def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5, profile_region=False)
     return out
 
 
+def run_hmult_only(args):
+    """One batched HMult (tensor, key switch with the fused ModUp / ModDown transforms, rescale) of
+    `--batch` ciphertexts at the top level of the N=2^16 workload chain: its time and the NTT class's
+    algorithmic bytes (limbs transformed x N x 16 B) from the event profiler, the unit the DRAM
+    traffic of its NTT launches is scaled by."""
+    import torch
+    from paper_2606_10477_gb300 import hedap, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    p = inputs.PRESETS[PRESET]
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1,
+                        stream=stream.cuda_stream)
+    L = ctx.n_q - 1
+    vals = [inputs.uniform_values(9500 + i, ctx.N // 2, LO, HI) for i in range(args.batch)]
+    packed = ctx.pack([ctx.encrypt(v, L, 9600 + i) for i, v in enumerate(vals)])
+    for _ in range(3):
+        ctx.mul(packed, packed)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.mul(packed, packed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hedap.profile_enable(True)
+    ctx.mul(packed, packed)
+    torch.cuda.synchronize()
+    prof = hedap.profile_read()
+    hedap.profile_enable(False)
+    n_ntt, ms_ntt, by_ntt = prof["ntt"]
+    if args.profile_region:
+        torch.cuda.profiler.start()
+        ctx.mul(packed, packed)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    print(json.dumps({"hmult": {"batch": args.batch, "level": L, "ms": e0.elapsed_time(e1) / reps,
+                                "ntt_launch_groups": n_ntt, "ntt_ms": ms_ntt, "ntt_algorithmic_bytes": by_ntt,
+                                "ntt_limbs": by_ntt / (16.0 * ctx.N)}}), flush=True)
+
+
 def run_ntt_only(args):
     import torch
     from paper_2606_10477_gb300 import hedap, inputs
@@ -774,6 +816,8 @@ def main():
     args = parse()
     if args.only == "ntt":
         run_ntt_only(args)
+    elif args.only == "hmult":
+        run_hmult_only(args)
     elif args.only == "serving":
         run_serving_only(args)
     elif args.only == "bts":
