@@ -771,6 +771,19 @@ static Ct mul_const_sp(const Ctx& C, const Ct& a, double c, double sp) {
   r.scale = a.scale * sp;
   return rescale(C, r);
 }
+// multiply by c at plaintext scale target * q_l / scale, without the rescale: the product is
+// labelled target * q_l, so that products at one level with one target add exactly
+static Ct mul_const_raw(const Ctx& C, const Ct& a, double c, double target) {
+  double sp = target * (double)C.q[a.level] / a.scale;
+  double v = round_half_away(c * sp);
+  Ct r = a;
+  for (int i = 0; i <= a.level; ++i) {
+    u64 cm = double_to_mod(v, C.q[i]);
+    for (int p = 0; p < 2; ++p) for (size_t k = 0; k < C.N; ++k) r.c[p][i][k] = mulmod(r.c[p][i][k], cm, C.q[i]);
+  }
+  r.scale = target * (double)C.q[a.level];
+  return r;
+}
 // multiply by c so that the result (one level lower) has exactly scale target
 static Ct mul_const_to(const Ctx& C, const Ct& a, double c, double target) {
   double sp = target * (double)C.q[a.level] / a.scale;
@@ -863,13 +876,15 @@ struct ChebEval {
   }
   Ct eval(const std::vector<double>& p, int level, double scale) {
     int D = deg_of(p);
-    if (D < k) {  // leaf: sum_j c_j T_j at (level, scale), then + c_0
+    if (D < k) {  // leaf: sum_j c_j T_j at level + 1 (unrescaled, all labelled scale q), one rescale, + c_0
       Ct acc;
       for (int j = 1; j <= D; ++j) {
         const Ct& tj = T.at(j);
-        Ct term = mul_const_to(C, drop_to(tj, level + 1), p[j], scale);
+        Ct term = mul_const_raw(C, drop_to(tj, level + 1), p[j], scale);
         acc = (j == 1) ? term : add_sub(C, acc, term, false);
       }
+      acc = rescale(C, acc);
+      acc.scale = scale;
       return add_const(C, acc, p[0]);
     }
     int G = giant_for(D);
@@ -889,13 +904,15 @@ struct ChebEval {
   }
   // T_a * T_b -> 2 T_a T_b - T_c  with T_c = T_{|a-b|} (or the constant 1 when a == b)
   Ct cheb_product(const Ct& ta, const Ct& tb, int c_index) {
-    Ct prod = mul(C, ta, tb);
     Ct diff;
-    if (c_index == 0) diff = add_const(C, prod, -0.5);
-    else {
+    if (c_index == 0) diff = add_const(C, mul(C, ta, tb), -0.5);
+    else {  // the product and 0.5 T_c subtracted before one rescale
+      Ct pr = mul_relin(C, ta, tb);
+      const double out = pr.scale / (double)C.q[pr.level];
       const Ct& tc = T.at(c_index);
-      Ct half = mul_const_to(C, drop_to(tc, prod.level + 1), 0.5, prod.scale);
-      diff = add_sub(C, prod, half, true);
+      Ct half = mul_const_raw(C, drop_to(tc, pr.level), 0.5, out);
+      diff = rescale(C, add_sub(C, pr, half, true));
+      diff.scale = out;
     }
     return mul_int(C, diff, 2);
   }
@@ -1174,15 +1191,18 @@ static Ct bootstrap_scaled(Ctx& C, const Ct& y, i64 Y, int log_slots = 0) {
 struct InvSqrtCfg { double lo, hi, B; int degree, iters, pre_bts; u64 bts_mask; int log_slots; };
 
 // One Newton step y <- 1.5 y - (0.5 a) y^3 (Sec. 2.2), in the operation order of
-// Alg. 1's loop body; tmp_alpha is produced last so that its scale can be set to
-// exactly the scale of tmp_beta.
+// Alg. 1's loop body; tmp_alpha is produced last, at the level of the relinearised
+// tmp_beta and labelled with its scale, and tmp_alpha - tmp_beta is rescaled once.
 static Ct newton_step(Ctx& C, const Ct& x, const Ct& y) {
   int ly = y.level;
   Ct yy = mul(C, y, y);                            // y^2
   Ct xy = mul(C, drop_to(x, std::min(x.level, ly)), y);  // (0.5 a) y
-  Ct tb = mul(C, xy, yy);                           // tmp_beta = (0.5 a) y^3
-  Ct ta = mul_const_to(C, drop_to(y, tb.level + 1), 1.5, tb.scale);  // tmp_alpha = 1.5 y
-  return add_sub(C, ta, tb, true);
+  Ct tb = mul_relin(C, xy, yy);                     // tmp_beta = (0.5 a) y^3, before its rescale
+  const double out = tb.scale / (double)C.q[tb.level];
+  Ct ta = mul_const_raw(C, drop_to(y, tb.level), 1.5, out);  // tmp_alpha = 1.5 y, labelled tb's scale
+  Ct r = rescale(C, add_sub(C, ta, tb, true));        // tmp_alpha - tmp_beta, one rescale
+  r.scale = out;
+  return r;
 }
 
 // Bootstrapping placement (the paper's Pre-BTS indicator c, Sec. 4.1, and BTS

@@ -343,7 +343,9 @@ std::unique_ptr<Ct> ev_switch_key(Ctx& C, const Ct& a, u64 id) {
 
 // Mul_P by a real constant c at plaintext scale target * q_l / scale, then rescale;
 // the result's scale is set to exactly `target`.
-std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target) {
+// Mul_P by c without the rescale: the product is labelled target * q_l (several such products at one
+// level with one target add exactly and share one rescale)
+std::unique_ptr<Ct> ev_mul_const_raw(Ctx& C, const Ct& a, double c, double target) {
   const int l = a.level;
   if (l < 1) throw Error(HEDAP_ERR_LEVEL, "constant multiplication needs level >= 1");
   const double sp = target * (double)C.primes[l] / a.scale;
@@ -354,9 +356,12 @@ std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target) {
     K.wsh[i] = h_shoup(K.w[i], C.primes[i]);
   }
   auto t = ct_alloc(C, l, a.batch);
-  t->scale = a.scale * sp;
+  t->scale = target * (double)C.primes[l];
   k_mul_limbconst(C, a.part(0), a.part_stride(), t->part(0), t->part_stride(), a.parts(), l + 1, K);
-  auto o = ev_rescale(C, *t);
+  return t;
+}
+std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target) {
+  auto o = ev_rescale(C, *ev_mul_const_raw(C, a, c, target));
   o->scale = target;
   return o;
 }

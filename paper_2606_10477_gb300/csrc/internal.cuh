@@ -247,6 +247,7 @@ std::unique_ptr<Ct> ev_galois(Ctx& C, const Ct& a, u64 g);
 std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const std::vector<u64>& gs);
 std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level);
 std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target_scale);
+std::unique_ptr<Ct> ev_mul_const_raw(Ctx& C, const Ct& a, double c, double target);
 std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c);
 std::unique_ptr<Ct> ev_mul_int(Ctx& C, const Ct& a, i64 m);
 u64 galois_for_rotation(const Ctx& C, i64 steps);

@@ -80,12 +80,16 @@ struct ChebPS {
   }
   CtP eval(const std::vector<double>& p, int level, double scale) {
     const int D = degree(p);
-    if (D < k) {
+    if (D < k) {  // sum of c_j T_j at level + 1 (products labelled scale * q), one rescale, + c_0
       CtP acc;
       for (int j = 1; j <= D; ++j) {
-        CtP term = mul_const_at(C, *T.at(j), level + 1, p[j], scale);
+        const Ct& tj = *T.at(j);
+        CtP d = tj.level == level + 1 ? nullptr : ev_drop(C, tj, level + 1);
+        CtP term = ev_mul_const_raw(C, d ? *d : tj, p[j], scale);
         acc = acc ? ev_add(C, *acc, *term, false) : std::move(term);
       }
+      acc = ev_rescale(C, *acc);
+      acc->scale = scale;
       return ev_add_const(C, *acc, p[0]);
     }
     const int G = giant(D);
@@ -104,15 +108,21 @@ struct ChebPS {
     CtP rv = eval(rm, level, scale);
     return ev_add(C, *prod, *rv, false);
   }
-  // 2 T_a T_b - T_c, with T_c the constant 1 when c == 0
+  // 2 T_a T_b - T_c, with T_c the constant 1 when c == 0; for c > 0 the product and 0.5 T_c are
+  // subtracted before the rescale (one rescale for both)
   CtP product(const Ct& ta, const Ct& tb, int c) {
-    CtP prod = ev_mul(C, ta, tb);
     CtP diff;
     if (c == 0) {
-      diff = ev_add_const(C, *prod, -0.5);
+      diff = ev_add_const(C, *ev_mul(C, ta, tb), -0.5);
     } else {
-      CtP half = mul_const_at(C, *T.at(c), prod->level + 1, 0.5, prod->scale);
-      diff = ev_add(C, *prod, *half, true);
+      CtP pr = ev_mul_relin(C, ta, tb);
+      const int l = pr->level;
+      const double out = pr->scale / (double)C.primes[l];
+      const Ct& tc = *T.at(c);
+      CtP d = tc.level == l ? nullptr : ev_drop(C, tc, l);
+      CtP half = ev_mul_const_raw(C, d ? *d : tc, 0.5, out);
+      diff = ev_rescale(C, *ev_add(C, *pr, *half, true));
+      diff->scale = out;
     }
     return ev_mul_int(C, *diff, 2);
   }
@@ -142,14 +152,19 @@ std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& co
   return ps.run(t, coeffs, target);
 }
 
-// One Newton step in Alg. 1's loop order; tmp_alpha = 1.5 y is produced last so
-// that its scale equals tmp_beta's exactly.
+// One Newton step in Alg. 1's loop order; tmp_alpha = 1.5 y is produced last, at the level of
+// the relinearised tmp_beta and labelled with its scale, and tmp_alpha - tmp_beta is rescaled once.
 static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
   CtP yy = ev_mul(C, y, y);
   CtP xy = ev_mul(C, x, y);
-  CtP tb = ev_mul(C, *xy, *yy);
-  CtP ta = mul_const_at(C, y, tb->level + 1, 1.5, tb->scale);
-  return ev_add(C, *ta, *tb, true);
+  CtP tb = ev_mul_relin(C, *xy, *yy);
+  const int l = tb->level;
+  const double out = tb->scale / (double)C.primes[l];
+  CtP d = y.level == l ? nullptr : ev_drop(C, y, l);
+  CtP ta = ev_mul_const_raw(C, d ? *d : y, 1.5, out);
+  CtP r = ev_rescale(C, *ev_add(C, *ta, *tb, true));
+  r->scale = out;
+  return r;
 }
 
 // Bootstrapping placement (the Pre-BTS indicator c of Sec. 4.1 and BTS during
