@@ -874,17 +874,20 @@ struct ChebEval {
     int lvl = std::min(std::min(lq, T.at(G).level) - 1, best_level(rp));
     return lvl;
   }
-  Ct eval(const std::vector<double>& p, int level, double scale) {
+  // p at (level + 1, label scale * q_{level+1}) before its final rescale: a leaf is the sum of the
+  // unrescaled products c_j T_j plus c_0; an inner node adds the relinearised (q T_G) to the
+  // unrescaled remainder r
+  Ct eval_raw(const std::vector<double>& p, int level, double scale) {
     int D = deg_of(p);
-    if (D < k) {  // leaf: sum_j c_j T_j at level + 1 (unrescaled, all labelled scale q), one rescale, + c_0
+    const double raw = scale * (double)C.q[level + 1];
+    if (D < k) {
       Ct acc;
       for (int j = 1; j <= D; ++j) {
         const Ct& tj = T.at(j);
         Ct term = mul_const_raw(C, drop_to(tj, level + 1), p[j], scale);
         acc = (j == 1) ? term : add_sub(C, acc, term, false);
       }
-      acc = rescale(C, acc);
-      acc.scale = scale;
+      acc.scale = raw;
       return add_const(C, acc, p[0]);
     }
     int G = giant_for(D);
@@ -892,15 +895,20 @@ struct ChebEval {
     const Ct& tg = T.at(G);
     Ct prod;
     if (deg_of(qp) == 0) {
-      prod = mul_const_to(C, drop_to(tg, level + 1), qp[0], scale);
+      prod = mul_const_raw(C, drop_to(tg, level + 1), qp[0], scale);
     } else {
       double sq = scale * (double)C.q[level + 1] / tg.scale;
       Ct qv = eval(qp, level + 1, sq);
-      prod = rescale(C, mul_relin(C, qv, drop_to(tg, level + 1)));
-      prod.scale = scale;  // = sq * tg.scale / q_{level+1} by construction
+      prod = mul_relin(C, qv, drop_to(tg, level + 1));
     }
-    Ct rv = eval(rp, level, scale);
+    prod.scale = raw;
+    Ct rv = eval_raw(rp, level, scale);
     return add_sub(C, prod, rv, false);
+  }
+  Ct eval(const std::vector<double>& p, int level, double scale) {
+    Ct r = rescale(C, eval_raw(p, level, scale));
+    r.scale = scale;
+    return r;
   }
   // T_a * T_b -> 2 T_a T_b - T_c  with T_c = T_{|a-b|} (or the constant 1 when a == b)
   Ct cheb_product(const Ct& ta, const Ct& tb, int c_index) {

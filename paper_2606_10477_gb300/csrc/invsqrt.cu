@@ -78,9 +78,13 @@ struct ChebPS {
     const int lq = degree(qt) == 0 ? INT_MAX : top_level(qt);
     return std::min(std::min(lq, T.at(G)->level) - 1, top_level(rm));
   }
-  CtP eval(const std::vector<double>& p, int level, double scale) {
+  // p at (level + 1, label scale * q_{level+1}) before its final rescale: the leaf sums c_j T_j as
+  // unrescaled products plus c_0, an inner node adds the relinearised q T_G to the unrescaled r,
+  // so a whole evaluation ends with one rescale per product of the recursion and one more
+  CtP eval_raw(const std::vector<double>& p, int level, double scale) {
     const int D = degree(p);
-    if (D < k) {  // sum of c_j T_j at level + 1 (products labelled scale * q), one rescale, + c_0
+    const double raw = scale * (double)C.primes[level + 1];
+    if (D < k) {
       CtP acc;
       for (int j = 1; j <= D; ++j) {
         const Ct& tj = *T.at(j);
@@ -88,8 +92,7 @@ struct ChebPS {
         CtP term = ev_mul_const_raw(C, d ? *d : tj, p[j], scale);
         acc = acc ? ev_add(C, *acc, *term, false) : std::move(term);
       }
-      acc = ev_rescale(C, *acc);
-      acc->scale = scale;
+      acc->scale = raw;
       return ev_add_const(C, *acc, p[0]);
     }
     const int G = giant(D);
@@ -98,15 +101,21 @@ struct ChebPS {
     const Ct& tg = *T.at(G);
     CtP prod;
     if (degree(qt) == 0) {
-      prod = mul_const_at(C, tg, level + 1, qt[0], scale);
+      CtP d = tg.level == level + 1 ? nullptr : ev_drop(C, tg, level + 1);
+      prod = ev_mul_const_raw(C, d ? *d : tg, qt[0], scale);
     } else {
       const double sq = scale * (double)C.primes[level + 1] / tg.scale;
       CtP qv = eval(qt, level + 1, sq);
-      prod = ev_rescale(C, *ev_mul_relin(C, *qv, tg));  // at min level = level + 1
-      prod->scale = scale;
+      prod = ev_mul_relin(C, *qv, tg);  // at min level = level + 1
     }
-    CtP rv = eval(rm, level, scale);
+    prod->scale = raw;
+    CtP rv = eval_raw(rm, level, scale);
     return ev_add(C, *prod, *rv, false);
+  }
+  CtP eval(const std::vector<double>& p, int level, double scale) {
+    CtP r = ev_rescale(C, *eval_raw(p, level, scale));
+    r->scale = scale;
+    return r;
   }
   // 2 T_a T_b - T_c, with T_c the constant 1 when c == 0; for c > 0 the product and 0.5 T_c are
   // subtracted before the rescale (one rescale for both)
