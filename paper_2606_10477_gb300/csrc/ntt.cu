@@ -15,9 +15,10 @@
 // 256-point phase; RL = 3: three).  For a group with elements at c = high*2^(S+K) + m*2^S + low (or the
 // mirrored forward form), the twiddle of every butterfly has a closed-form index
 // in (high, m, u), so no per-element index arithmetic is needed.  Twiddles are
-// (w, floor(w 2^64 / q)) pairs read with one 16-byte load; every CTA stages the
-// twiddles it uses in shared memory with its data (the column phase's 2^L1, the
-// row phase's contiguous per-stage ranges for its blocks).  Optional fusions (NttAux):
+// (w, floor(w 2^64 / q)) pairs; every CTA stages the twiddles it uses in shared
+// memory with its data (the column phase's 2^L1, the row phase's contiguous
+// per-stage ranges for its blocks), both copied with cp.async so that all of a
+// tile's copies are in flight at once.  Optional fusions (NttAux):
 // the first phase may read another buffer (out of place) or compute its input as
 // the fast basis conversion of a key-switching digit (ModUp fused into the load),
 // the inverse may end with a per-limb factor other than N^-1, a digit's own
@@ -68,7 +69,18 @@ __device__ __forceinline__ u64 reduce8q(u64 x, u64 q) {
   if (x >= q) x -= q;
   return x;
 }
-__device__ __forceinline__ ulonglong2 ldg2(const ulonglong2* p) { return __ldg(p); }
+// asynchronous global -> shared copies (cp.async): every copy of a tile is in flight at once, with
+// no register round trip; one wait_group 0 and a barrier make them visible to the CTA
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // RL: stages per register pass (radix 2^RL), a template parameter of every kernel
 
@@ -134,7 +146,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
   u64* a = S.limb(part, li, N);
   const ulonglong2* W = T.psi2 + (size_t)pi * N;
 #pragma unroll
-  for (int i = threadIdx.x; i < (1 << L1); i += TPB) tw[i] = ldg2(W + i);
+  for (int i = threadIdx.x; i < (1 << L1); i += TPB) cp_async16(tw + i, W + i);
   const int r0 = blockIdx.x * C;
   if (A.z) {  // fused ModUp: fast basis conversion of digit j into this limb's prime
     // sum of na <= 8 Shoup products, each in [0, 2q), brought into [0, 4q): the
@@ -210,9 +222,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
 #pragma unroll
     for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
       const int c = idx / C, col = idx % C;
-      sm[idx] = src[((size_t)c << L2) + r0 + col];
+      cp_async8(sm + idx, src + ((size_t)c << L2) + r0 + col);
     }
   }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   fwd_cols_passes<L1, C, RL, 0>(sm, tw, q);
 #pragma unroll
@@ -229,12 +243,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
 // into shared memory) and runs the column phase of `lpc` consecutive output limbs of one part from
 // there, so the wait for global memory is paid once per lpc limbs; each limb's twiddles are
 // fetched with cp.async while the previous limb computes (two twiddle buffers).
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int L1, int L2, int C, int TPB, int MINB, int RL>
 __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, LimbSet S, NttAux A, int lpc) {
@@ -362,7 +370,7 @@ __device__ __forceinline__ void fwd_rows_stage_twiddles(ulonglong2* tw, const ul
   for (int sl = 0; sl < L2; ++sl) {
     const ulonglong2* src = W + (1u << (L1 + sl)) + (B0 << sl);
     ulonglong2* dst = tw + BPC * ((1 << sl) - 1);
-    for (int i = threadIdx.x; i < (BPC << sl); i += TPB) dst[i] = ldg2(src + i);
+    for (int i = threadIdx.x; i < (BPC << sl); i += TPB) cp_async16(dst + i, src + i);
   }
 }
 template <int L1, int L2, int BPC, int RL, int S0>
@@ -413,8 +421,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + BPC * R);
   const size_t j0 = (size_t)blockIdx.x * E;
 #pragma unroll
-  for (int idx = threadIdx.x; idx < E; idx += TPB) sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))] = a[j0 + idx];
+  for (int idx = threadIdx.x; idx < E; idx += TPB) cp_async8(sm + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), a + j0 + idx);
   fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   fwd_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
   if (A.fin_dst) {  // fused epilogue of a rescale / ModDown: (c - v) * w (+ dst)
@@ -447,7 +457,7 @@ __device__ __forceinline__ void inv_rows_stage_twiddles(ulonglong2* tw, const ul
   for (int lt = 0; lt < L2; ++lt) {
     const ulonglong2* src = W + (1u << (L1 + L2 - lt - 1)) + (B0 << (L2 - lt - 1));
     ulonglong2* dst = tw + BPC * ((1 << L2) - (1 << (L2 - lt)));
-    for (int i = threadIdx.x; i < (BPC << (L2 - lt - 1)); i += TPB) dst[i] = ldg2(src + i);
+    for (int i = threadIdx.x; i < (BPC << (L2 - lt - 1)); i += TPB) cp_async16(dst + i, src + i);
   }
 }
 template <int L1, int L2, int BPC, int RL, int LT0>
@@ -499,8 +509,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_rows(Tables T, LimbSet S,
   ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + BPC * R);
   const size_t j0 = (size_t)blockIdx.x * E;
 #pragma unroll
-  for (int idx = threadIdx.x; idx < E; idx += TPB) sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))] = src[j0 + idx];
+  for (int idx = threadIdx.x; idx < E; idx += TPB) cp_async8(sm + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), src + j0 + idx);
   inv_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.ipsi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   inv_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
 #pragma unroll
@@ -554,13 +566,15 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S,
   u64* a = S.limb(part, li, N);
   const ulonglong2* W = T.ipsi2 + (size_t)pi * N;
 #pragma unroll
-  for (int i = threadIdx.x; i < (1 << L1); i += TPB) tw[i] = ldg2(W + i);
+  for (int i = threadIdx.x; i < (1 << L1); i += TPB) cp_async16(tw + i, W + i);
   const int r0 = blockIdx.x * C;
 #pragma unroll
   for (int idx = threadIdx.x; idx < (C << L1); idx += TPB) {
     const int c = idx / C, col = idx % C;
-    sm[idx] = a[((size_t)c << L2) + r0 + col];
+    cp_async8(sm + idx, a + ((size_t)c << L2) + r0 + col);
   }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   inv_cols_passes<L1, C, RL, 0>(sm, tw, q);
   const int pr_ = li - S.limb_begin;
