@@ -119,6 +119,10 @@ hedap_status hedap_encrypt(hedap_ctx* ctx, const double* re, const double* im, s
 /* Dec + decode into re/im (im may be NULL); n_slots must be N/2. */
 hedap_status hedap_decrypt(hedap_ctx* ctx, const hedap_ct* ct, double* re, double* im, size_t n_slots);
 
+/* Import [2][level+1][N] NTT-domain words from host memory (on_device = 0: the
+ * call returns once they are copied; they are checked on the device to lie
+ * below their primes, HEDAP_ERR_RANGE otherwise; pinned host memory copies
+ * fastest) or from device memory (on_device = 1, stream ordered, unchecked). */
 hedap_status hedap_ct_import(hedap_ctx* ctx, const uint64_t* limbs, int level, double scale, int on_device,
                              hedap_ct** out);
 /* Export [2][level+1][N] words into out (capacity cap words). */

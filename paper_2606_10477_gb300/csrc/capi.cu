@@ -142,20 +142,20 @@ API hedap_status hedap_ct_import(hedap_ctx* ctx, const uint64_t* limbs, int leve
     need(level >= 0 && level <= C.L(), "level out of range");
     need(scale > 0, "scale must be positive");
     const size_t per = (size_t)(level + 1) * C.N;
-    if (!on_device) {
-      for (int p = 0; p < 2; ++p)
-        for (int i = 0; i <= level; ++i) {
-          const uint64_t* src = limbs + (p * (size_t)(level + 1) + i) * C.N;
-          for (size_t k = 0; k < C.N; ++k)
-            if (src[k] >= C.primes[i]) throw hedap::Error(HEDAP_ERR_RANGE, "residue not below its prime");
-        }
-    }
     auto c = hedap::ct_alloc(C, level);
     c->scale = scale;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     HEDAP_CUDA(cudaMemcpyAsync(c->part(0), limbs, per * 8, kind, C.stream));
     HEDAP_CUDA(cudaMemcpyAsync(c->part(1), limbs + per, per * 8, kind, C.stream));
-    if (!on_device) HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+    if (!on_device) {  // host words are checked on the device after the copy (residues below their primes)
+      hedap::DevBuf flag(1, C.stream);
+      HEDAP_CUDA(cudaMemsetAsync(flag.p, 0, 8, C.stream));
+      hedap::k_check_residues(C, c->part(0), c->part_stride(), 2, level + 1, (unsigned int*)flag.p);
+      uint64_t bad = 0;
+      HEDAP_CUDA(cudaMemcpyAsync(&bad, flag.p, 8, cudaMemcpyDeviceToHost, C.stream));
+      HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+      if (bad) throw hedap::Error(HEDAP_ERR_RANGE, "residue not below its prime");
+    }
     *out = wrap(std::move(c));
   });
 }

@@ -44,6 +44,29 @@ void k_add_sub(const Ctx& C, const u64* a, size_t as, const u64* b, size_t bs, u
   HEDAP_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- residue range check
+// flag[0] |= 1 when some word of the n_parts x limbs limbs at a (part stride as) is not below its prime
+__global__ void k_check_residues_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ a, size_t as,
+                                        int n_parts, int limbs, int log_n, unsigned int* flag) {
+  const size_t per_part = (size_t)limbs << log_n;
+  bool bad = false;
+  GRID_LOOP(t, n_parts * per_part / 2) {
+    const size_t e = 2 * t;
+    const size_t p = e / per_part, r = e - p * per_part;
+    const u64 q = pr[r >> log_n].q;
+    const ulonglong2 x = ld2(a + p * as + r);
+    bad |= x.x >= q || x.y >= q;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+void k_check_residues(const Ctx& C, const u64* a, size_t as, int n_parts, int limbs, unsigned int* flag) {
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 1.0 * n_parts * limbs * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)n_parts * limbs * C.N / 2;
+  k_check_residues_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, a, as, n_parts, limbs, C.log_n, flag);
+  HEDAP_LAUNCH_CHECK();
+}
+
 // ---------------------------------------------------------------- tensor product
 // ciphertext k: (a_2k, a_2k+1) x (b_2k, b_2k+1) -> d0 = o_2k, d1 = o_2k+1, d2 at d2 + k*limbs*N
 __global__ void k_tensor_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ a, size_t as,

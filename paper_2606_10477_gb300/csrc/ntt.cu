@@ -424,6 +424,15 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   for (int idx = threadIdx.x; idx < E; idx += TPB) cp_async8(sm + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), a + j0 + idx);
   fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
   cp_async_commit();
+  if (A.fin_dst) {  // the epilogue's operands: fetched into L2 while the passes run (128-byte lines)
+    const u64* cp = A.fin_c + (size_t)part * A.fin_c_stride + (size_t)li * N + j0;
+    const u64* dp = A.fin_dst + (size_t)part * A.fin_dst_stride + (size_t)li * N + j0;
+    const bool acc = (part & 1) ? A.fin_acc_odd : A.fin_acc_even;
+    for (int idx = 16 * threadIdx.x; idx < E; idx += 16 * TPB) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(cp + idx));
+      if (acc) asm volatile("prefetch.global.L2 [%0];" ::"l"(dp + idx));
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
   fwd_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);

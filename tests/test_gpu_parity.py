@@ -290,5 +290,10 @@ def test_error_codes(toy):
     with pytest.raises(hedap.HedapError) as e:
         g.ct_import(bad, 0, o.scale)
     assert e.value.code == -7
+    bad = inputs.random_ciphertext_limbs(54, o.primes(), 3, o.N)  # the last word of part 1's last limb
+    bad[1, 3, o.N - 1] = int(o.primes()[3]) + 5
+    with pytest.raises(hedap.HedapError) as e:
+        g.ct_import(bad, 3, o.scale)
+    assert e.value.code == -7
     with pytest.raises(hedap.HedapError):
         g.invsqrt(ga, 0.01, 1.0, 1.0, 15, 2)  # level 0 input
