@@ -360,6 +360,50 @@ std::unique_ptr<Ct> ev_mul_const_raw(Ctx& C, const Ct& a, double c, double targe
   k_mul_limbconst(C, a.part(0), a.part_stride(), t->part(0), t->part_stride(), a.parts(), l + 1, K);
   return t;
 }
+std::unique_ptr<Ct> ev_lincomb_raw(Ctx& C, const std::vector<std::pair<const Ct*, double>>& terms, int level,
+                                   double target, double c0) {
+  if (terms.empty() || level < 1) throw Error(HEDAP_ERR_ARG, "linear combination needs terms at level >= 1");
+  const double raw = target * (double)C.primes[level];
+  const int batch = terms[0].first->batch;
+  for (const auto& t : terms)
+    if (t.first->level < level || t.first->batch != batch) throw Error(HEDAP_ERR_ARG, "linear combination operands");
+  auto o = ct_alloc(C, level, batch);
+  o->scale = raw;
+  if (level + 1 > kLcLimbs) {  // wide chains: one product and one addition at a time
+    std::unique_ptr<Ct> acc;
+    for (const auto& t : terms) {
+      std::unique_ptr<Ct> d = t.first->level == level ? nullptr : ev_drop(C, *t.first, level);
+      auto term = ev_mul_const_raw(C, d ? *d : *t.first, t.second, target);
+      acc = acc ? ev_add(C, *acc, *term, false) : std::move(term);
+    }
+    acc->scale = raw;
+    return ev_add_const(C, *acc, c0);
+  }
+  for (size_t first = 0; first < terms.size(); first += kLcTerms) {
+    LinCombArgs A{};
+    A.count = (int)std::min<size_t>(kLcTerms, terms.size() - first);
+    A.accumulate = first > 0;
+    A.add_c0 = first == 0;
+    for (int j = 0; j < A.count; ++j) {
+      const Ct& a = *terms[first + j].first;
+      A.in[j] = a.part(0);
+      A.stride[j] = a.part_stride();
+      const double sp = target * (double)C.primes[level] / a.scale;  // as in ev_mul_const_raw
+      const double v = std::round(terms[first + j].second * sp);
+      for (int i = 0; i <= level; ++i) {
+        A.w[j][i] = h_double_to_mod(v, C.primes[i]);
+        A.wsh[j][i] = h_shoup(A.w[j][i], C.primes[i]);
+      }
+    }
+    if (A.add_c0) {
+      const double v0 = std::round(c0 * raw);  // as in ev_add_const on the sum
+      for (int i = 0; i <= level; ++i) A.c0[i] = h_double_to_mod(v0, C.primes[i]);
+    }
+    k_lincomb(C, o->part(0), o->part_stride(), o->parts(), level + 1, A);
+  }
+  return o;
+}
+
 std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target) {
   auto o = ev_rescale(C, *ev_mul_const_raw(C, a, c, target));
   o->scale = target;

@@ -188,6 +188,16 @@ struct LimbConsts {
   u64 w[kMaxLimbs];
   u64 wsh[kMaxLimbs];
 };
+// one launch of a linear combination of ciphertexts with per-limb integer constants (k_lincomb)
+constexpr int kLcTerms = 8, kLcLimbs = 32;
+struct LinCombArgs {
+  const u64* in[kLcTerms];  // part p of term j at in[j] + p * stride[j]
+  size_t stride[kLcTerms];
+  u64 w[kLcTerms][kLcLimbs];
+  u64 wsh[kLcTerms][kLcLimbs];
+  u64 c0[kLcLimbs];  // added to the even (c0) parts when add_c0
+  int count, add_c0, accumulate;
+};
 // rescale by q_l: per i < l, q_l mod q_i and q_l^-1 mod q_i (+ Shoup)
 struct RescaleConsts {
   u64 ql_mod[kMaxLimbs];
@@ -248,6 +258,10 @@ std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const st
 std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level);
 std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target_scale);
 std::unique_ptr<Ct> ev_mul_const_raw(Ctx& C, const Ct& a, double c, double target);
+// sum_j c_j a_j + c0 at `level` (every a_j at level >= it), each product as ev_mul_const_raw would
+// form it; the result is labelled target * q_level
+std::unique_ptr<Ct> ev_lincomb_raw(Ctx& C, const std::vector<std::pair<const Ct*, double>>& terms, int level,
+                                   double target, double c0);
 std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c);
 std::unique_ptr<Ct> ev_mul_int(Ctx& C, const Ct& a, i64 m);
 u64 galois_for_rotation(const Ctx& C, i64 steps);

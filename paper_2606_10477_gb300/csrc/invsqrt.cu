@@ -84,16 +84,10 @@ struct ChebPS {
   CtP eval_raw(const std::vector<double>& p, int level, double scale) {
     const int D = degree(p);
     const double raw = scale * (double)C.primes[level + 1];
-    if (D < k) {
-      CtP acc;
-      for (int j = 1; j <= D; ++j) {
-        const Ct& tj = *T.at(j);
-        CtP d = tj.level == level + 1 ? nullptr : ev_drop(C, tj, level + 1);
-        CtP term = ev_mul_const_raw(C, d ? *d : tj, p[j], scale);
-        acc = acc ? ev_add(C, *acc, *term, false) : std::move(term);
-      }
-      acc->scale = raw;
-      return ev_add_const(C, *acc, p[0]);
+    if (D < k) {  // one pass over T_1 .. T_D (read at level + 1 in place)
+      std::vector<std::pair<const Ct*, double>> terms;
+      for (int j = 1; j <= D; ++j) terms.emplace_back(T.at(j).get(), p[j]);
+      return ev_lincomb_raw(C, terms, level + 1, scale, p[0]);
     }
     const int G = giant(D);
     std::vector<double> qt, rm;
@@ -127,10 +121,8 @@ struct ChebPS {
       CtP pr = ev_mul_relin(C, ta, tb);
       const int l = pr->level;
       const double out = pr->scale / (double)C.primes[l];
-      const Ct& tc = *T.at(c);
-      CtP d = tc.level == l ? nullptr : ev_drop(C, tc, l);
-      CtP half = ev_mul_const_raw(C, d ? *d : tc, 0.5, out);
-      diff = ev_rescale(C, *ev_add(C, *pr, *half, true));
+      // pr * 1 - 0.5 T_c in one pass (the constant of pr is round(sp) = 1, sp = out q_l / pr.scale)
+      diff = ev_rescale(C, *ev_lincomb_raw(C, {{pr.get(), 1.0}, {T.at(c).get(), -0.5}}, l, out, 0.0));
       diff->scale = out;
     }
     return ev_mul_int(C, *diff, 2);
@@ -169,9 +161,8 @@ static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
   CtP tb = ev_mul_relin(C, *xy, *yy);
   const int l = tb->level;
   const double out = tb->scale / (double)C.primes[l];
-  CtP d = y.level == l ? nullptr : ev_drop(C, y, l);
-  CtP ta = ev_mul_const_raw(C, d ? *d : y, 1.5, out);
-  CtP r = ev_rescale(C, *ev_add(C, *ta, *tb, true));
+  // 1.5 y - tmp_beta in one pass (the constant of tmp_beta is -round(sp) = -1, sp = out q_l / tb.scale)
+  CtP r = ev_rescale(C, *ev_lincomb_raw(C, {{&y, 1.5}, {tb.get(), -1.0}}, l, out, 0.0));
   r->scale = out;
   return r;
 }

@@ -127,6 +127,38 @@ void k_mul_limbconst(const Ctx& C, const u64* in, size_t is, u64* out, size_t os
   HEDAP_LAUNCH_CHECK();
 }
 
+// out = sum_j in_j * w_j (+ c0 on the even parts, the c0 of each batch member) over limbs 0..limbs-1:
+// the leaf sum of a Chebyshev evaluation in one pass (inputs read at their own part strides, so
+// ciphertexts above the output level are read without a copy)
+__global__ void k_lincomb_kernel(const PrimeDev* __restrict__ pr, u64* __restrict__ out, size_t os, int n_parts,
+                                 int limbs, int log_n, LinCombArgs A) {
+  const size_t per_part = (size_t)limbs << log_n;
+  GRID_LOOP(t, n_parts * per_part / 2) {
+    const size_t e = 2 * t;
+    const size_t p = e / per_part, r = e - p * per_part;
+    const int i = (int)(r >> log_n);
+    const u64 q = pr[i].q;
+    ulonglong2 s = A.accumulate ? ld2(out + p * os + r) : ulonglong2{0, 0};
+    for (int j = 0; j < A.count; ++j) {
+      const ulonglong2 x = ld2(A.in[j] + p * A.stride[j] + r);
+      s.x = add_mod(s.x, shoup_mul(x.x, A.w[j][i], A.wsh[j][i], q), q);
+      s.y = add_mod(s.y, shoup_mul(x.y, A.w[j][i], A.wsh[j][i], q), q);
+    }
+    if (A.add_c0 && !(p & 1)) {
+      s.x = add_mod(s.x, A.c0[i], q);
+      s.y = add_mod(s.y, A.c0[i], q);
+    }
+    st2(out + p * os + r, s);
+  }
+}
+void k_lincomb(const Ctx& C, u64* out, size_t os, int n_parts, int limbs, const LinCombArgs& A) {
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, (A.count + 1.0 + A.accumulate) * n_parts * limbs * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)n_parts * limbs * C.N / 2;
+  k_lincomb_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, out, os, n_parts, limbs, C.log_n, A);
+  HEDAP_LAUNCH_CHECK();
+}
+
 // add a per-limb constant to n_parts parts spaced `stride` apart (the c0 parts of a batch)
 __global__ void k_add_limbconst_kernel(const PrimeDev* __restrict__ pr, u64* __restrict__ io, size_t stride,
                                        int n_parts, int limbs, int log_n, LimbConsts K) {

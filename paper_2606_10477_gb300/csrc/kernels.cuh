@@ -9,6 +9,7 @@ constexpr int kMaxBatch = 16;  // ciphertexts per batched operation
 
 // sets flag[0] (device word, not cleared here) when some residue is not below its prime
 void k_check_residues(const Ctx& C, const u64* a, size_t as, int n_parts, int limbs, unsigned int* flag);
+void k_lincomb(const Ctx& C, u64* out, size_t os, int n_parts, int limbs, const LinCombArgs& A);
 void k_add_sub(const Ctx& C, const u64* a, size_t as, const u64* b, size_t bs, u64* o, size_t os, int n_parts,
                int limbs, bool sub);
 void k_tensor(const Ctx& C, const u64* a, size_t as, const u64* b, size_t bs, u64* o, size_t os, u64* d2, int batch,
