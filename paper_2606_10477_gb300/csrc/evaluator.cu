@@ -419,6 +419,28 @@ std::unique_ptr<Ct> ev_add_const(Ctx& C, const Ct& a, double c) {
   return o;
 }
 
+// (a + c) * m in one pass: the constant c is added at a's scale exactly as ev_add_const adds it,
+// then everything is multiplied by the integer m (same residues as the two operations in turn)
+std::unique_ptr<Ct> ev_add_const_mul_int(Ctx& C, const Ct& a, double c, i64 m) {
+  if (a.level + 1 > kLcLimbs) return ev_mul_int(C, *ev_add_const(C, a, c), m);
+  const double v = std::round(c * a.scale);
+  LinCombArgs A{};
+  A.count = 1;
+  A.add_c0 = 1;
+  A.in[0] = a.part(0);
+  A.stride[0] = a.part_stride();
+  for (int i = 0; i <= a.level; ++i) {
+    const u64 q = C.primes[i], mm = h_smod(m, q);
+    A.w[0][i] = mm;
+    A.wsh[0][i] = h_shoup(mm, q);
+    A.c0[i] = h_mulmod(h_double_to_mod(v, q), mm, q);
+  }
+  auto o = ct_alloc(C, a.level, a.batch);
+  o->scale = a.scale;
+  k_lincomb(C, o->part(0), o->part_stride(), o->parts(), a.level + 1, A);
+  return o;
+}
+
 std::unique_ptr<Ct> ev_mul_int(Ctx& C, const Ct& a, i64 m) {
   LimbConsts K;
   for (int i = 0; i <= a.level; ++i) {

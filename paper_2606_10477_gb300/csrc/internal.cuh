@@ -258,6 +258,7 @@ std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const st
 std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level);
 std::unique_ptr<Ct> ev_mul_const(Ctx& C, const Ct& a, double c, double target_scale);
 std::unique_ptr<Ct> ev_mul_const_raw(Ctx& C, const Ct& a, double c, double target);
+std::unique_ptr<Ct> ev_add_const_mul_int(Ctx& C, const Ct& a, double c, i64 m);
 // sum_j c_j a_j + c0 at `level` (every a_j at level >= it), each product as ev_mul_const_raw would
 // form it; the result is labelled target * q_level
 std::unique_ptr<Ct> ev_lincomb_raw(Ctx& C, const std::vector<std::pair<const Ct*, double>>& terms, int level,

@@ -20,12 +20,6 @@ namespace hedap {
 
 typedef std::unique_ptr<Ct> CtP;
 
-static CtP mul_const_at(Ctx& C, const Ct& a, int level, double c, double target) {
-  if (level == a.level) return ev_mul_const(C, a, c, target);
-  auto d = ev_drop(C, a, level);
-  return ev_mul_const(C, *d, c, target);
-}
-
 // Chebyshev interpolation coefficients of 1/sqrt(x) at the d+1 first-kind nodes on [lo, hi]
 static std::vector<double> cheb_interp(double lo, double hi, int d) {
   const int n = d + 1;
@@ -95,8 +89,7 @@ struct ChebPS {
     const Ct& tg = *T.at(G);
     CtP prod;
     if (degree(qt) == 0) {
-      CtP d = tg.level == level + 1 ? nullptr : ev_drop(C, tg, level + 1);
-      prod = ev_mul_const_raw(C, d ? *d : tg, qt[0], scale);
+      prod = ev_lincomb_raw(C, {{&tg, qt[0]}}, level + 1, scale, 0.0);
     } else {
       const double sq = scale * (double)C.primes[level + 1] / tg.scale;
       CtP qv = eval(qt, level + 1, sq);
@@ -116,7 +109,7 @@ struct ChebPS {
   CtP product(const Ct& ta, const Ct& tb, int c) {
     CtP diff;
     if (c == 0) {
-      diff = ev_add_const(C, *ev_mul(C, ta, tb), -0.5);
+      return ev_add_const_mul_int(C, *ev_mul(C, ta, tb), -0.5, 2);
     } else {
       CtP pr = ev_mul_relin(C, ta, tb);
       const int l = pr->level;
