@@ -1053,6 +1053,7 @@ static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target,
   }
   long span = kmax - kmin + 1, n1 = 1;
   while (n1 * n1 < span) n1 <<= 1;
+  n1 = std::min(n1, 16L);  // at most 16 baby steps per giant step
   long giants = (span + n1 - 1) / n1;
   double sp = target * (double)C.q[v.level] / v.scale;
   // baby steps: every rotation of v used by some giant step, hoisted
@@ -1156,6 +1157,41 @@ static Ct sub_sum(Ctx& C, const Ct& a, size_t n) {
   for (size_t k = n; k < C.N / 2; k *= 2) t = add_sub(C, t, rotate(C, t, (i64)k), false);
   return t;
 }
+// Sparse slots pack the real and imaginary parts into 2n slots of one ciphertext (2n <= N/2): the
+// last CoeffToSlot factor is multiplied on its output by the 2n-periodic mask (1 on the first n
+// slots, -i on the next n), so that s + conj(s) carries 2 Re u on [0, n) and 2 Im u on [n, 2n);
+// after one EvalMod the first SlotToCoeff factor reads slot m and slot m + n as the real and
+// imaginary parts of its n-periodic input: each diagonal d_k goes to offsets k and k + n, with the
+// factor 1 on the offset that lands in [0, n) and i on the other.
+static cd mul_minus_i(cd z) { return cd(z.imag(), -z.real()); }
+static cd mul_i(cd z) { return cd(-z.imag(), z.real()); }
+static DiagMap pack_cts_last(const DiagMap& M, size_t n) {
+  DiagMap R;
+  for (auto& e : M) {
+    std::vector<cd> d(2 * n);
+    for (size_t j = 0; j < 2 * n; ++j) d[j] = j < n ? e.second[j] : mul_minus_i(e.second[j - n]);
+    R[e.first] = d;
+  }
+  return R;
+}
+static DiagMap pack_stc_first(const DiagMap& M, size_t n) {
+  DiagMap R;
+  long P = (long)(2 * n);
+  for (auto& e : M) {
+    long k = e.first;
+    for (size_t j = 0; j < 2 * n; ++j) {
+      cd v = e.second[j % n];
+      bool lo = ((long)j + k) % P < (long)n;  // offset k reads a slot of [0, n)
+      for (int h = 0; h < 2; ++h) {
+        long off = (((k + h * (long)n) % P) + P) % P;
+        std::vector<cd>& d = R[off];
+        if (d.empty()) d.assign(2 * n, cd(0, 0));
+        d[j] += (lo == (h == 0)) ? v : mul_i(v);
+      }
+    }
+  }
+  return R;
+}
 // Full-slot (log_slots = 0) or sparse-slot bootstrapping.  The sparse one is the full one of
 // the ring of dimension 2n (CoeffToSlot / SlotToCoeff on n slots, diagonals repeated over the
 // N/2 slots) after the projection of sub_sum, whose factor N/2n rides on the scale label.
@@ -1170,6 +1206,19 @@ static Ct bootstrap_core(Ctx& C, const Ct& a, int log_slots = 0) {
   Ct t = C.enc_hw ? switch_key(C, mod_raise(C, switch_key(C, a, 2)), 4) : mod_raise(C, a);
   if (n < C.N / 2) t = sub_sum(C, t, n);
   t.scale = 2.0 * q0 * C.bts_K * (double)(C.N / 2 / n);
+  if (n < C.N / 2) {  // packed real and imaginary parts, one EvalMod
+    std::vector<DiagMap> F = fft_groups(n, C.bts_cts, true);
+    for (size_t g = 0; g + 1 < F.size(); ++g) t = linear_transform(C, t, F[g], (double)C.q[t.level - 1], (long)n);
+    t = linear_transform(C, t, pack_cts_last(F.back(), n), (double)C.q[t.level - 1], (long)(2 * n));
+    Ct w = eval_mod(C, add_sub(C, t, conjugate(C, t), false));  // 2 Re | 2 Im
+    w.scale = w.scale * 2.0 * M_PI * s_in / q0;
+    std::vector<DiagMap> G = fft_groups(n, C.bts_stc, false);
+    w = linear_transform(C, w, pack_stc_first(G[0], n), G.size() == 1 ? C.scale : (double)C.q[w.level - 1],
+                         (long)(2 * n));
+    for (size_t g = 1; g < G.size(); ++g)
+      w = linear_transform(C, w, G[g], g + 1 == G.size() ? C.scale : (double)C.q[w.level - 1], (long)n);
+    return w;
+  }
   for (const DiagMap& M : fft_groups(n, C.bts_cts, true))
     t = linear_transform(C, t, M, (double)C.q[t.level - 1], (long)n);
   Ct cj = conjugate(C, t);

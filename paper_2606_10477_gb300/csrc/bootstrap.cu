@@ -88,6 +88,27 @@ struct LTGroup {  // one grouped factor and its baby-step / giant-step layout
   std::map<long, const std::vector<cplx>*> by_k;  // k = offset / h0 (signed)
 };
 
+// baby-step / giant-step layout of the diagonals G.d, offsets taken mod n (signed)
+static void layout_group(LTGroup& G, size_t n) {
+  long h0 = 0;
+  for (const auto& e : G.d) {
+    const long o = e.first <= (long)n / 2 ? e.first : e.first - (long)n;
+    if (o) h0 = h0 ? std::gcd(h0, std::labs(o)) : std::labs(o);
+  }
+  G.h0 = h0 ? h0 : 1;
+  long kmax = 0;
+  for (const auto& e : G.d) {
+    const long o = e.first <= (long)n / 2 ? e.first : e.first - (long)n;
+    const long k = o / G.h0;
+    G.by_k[k] = &e.second;
+    G.kmin = std::min(G.kmin, k);
+    kmax = std::max(kmax, k);
+  }
+  const long span = kmax - G.kmin + 1;
+  while (G.n1 * G.n1 < span) G.n1 <<= 1;
+  G.n1 = std::min(G.n1, 16L);  // at most 16 baby steps per giant step (one diagonal MAC launch)
+  G.giants = (span + G.n1 - 1) / G.n1;
+}
 static std::vector<LTGroup> make_groups(size_t n, int groups, bool inverse) {
   int logn = 0;
   while (((size_t)1 << logn) < n) ++logn;
@@ -99,27 +120,46 @@ static std::vector<LTGroup> make_groups(size_t n, int groups, bool inverse) {
     const int stages = logn / groups + (g < logn % groups ? 1 : 0);
     Diags M = stage_diags(n, lens[at++], inverse);
     for (int k = 1; k < stages; ++k) M = diags_product(stage_diags(n, lens[at++], inverse), M, n);
-    LTGroup& G = out[g];
-    G.d = std::move(M);
-    long h0 = 0;
-    for (const auto& e : G.d) {
-      const long o = e.first <= (long)n / 2 ? e.first : e.first - (long)n;
-      if (o) h0 = h0 ? std::gcd(h0, std::labs(o)) : std::labs(o);
-    }
-    G.h0 = h0 ? h0 : 1;
-    long kmax = 0;
-    for (const auto& e : G.d) {
-      const long o = e.first <= (long)n / 2 ? e.first : e.first - (long)n;
-      const long k = o / G.h0;
-      G.by_k[k] = &e.second;
-      G.kmin = std::min(G.kmin, k);
-      kmax = std::max(kmax, k);
-    }
-    const long span = kmax - G.kmin + 1;
-    while (G.n1 * G.n1 < span) G.n1 <<= 1;
-    G.giants = (span + G.n1 - 1) / G.n1;
+    out[g].d = std::move(M);
+    layout_group(out[g], n);
   }
   return out;
+}
+// Packed sparse slots (2n <= N/2): the last CoeffToSlot group multiplied on its output by the
+// 2n-periodic mask (1 on [0, n), -i on [n, 2n)), so that s + conj(s) holds 2 Re on the first n slots
+// and 2 Im on the next n; and the first SlotToCoeff group rewritten for a 2n-periodic input y whose
+// slots j and j + n hold the real and imaginary parts of the n-periodic input it stands for: each
+// diagonal d_k is split over offsets k and k + n with the factor 1 on the offset that reads [0, n)
+// and i on the one that reads [n, 2n).
+static cplx times_minus_i(cplx z) { return cplx(z.imag(), -z.real()); }
+static cplx times_i(cplx z) { return cplx(-z.imag(), z.real()); }
+static Diags packed_cts_last(const Diags& M, size_t n) {
+  Diags R;
+  for (const auto& e : M) {
+    std::vector<cplx> d(2 * n);
+    for (size_t j = 0; j < 2 * n; ++j) d[j] = j < n ? e.second[j] : times_minus_i(e.second[j - n]);
+    R[e.first] = std::move(d);
+  }
+  return R;
+}
+static Diags packed_stc_first(const Diags& M, size_t n) {
+  Diags R;
+  const long P = (long)(2 * n);
+  auto add = [&](long off, size_t j, cplx v) {
+    auto& d = R[((off % P) + P) % P];
+    if (d.empty()) d.assign(2 * n, cplx(0, 0));
+    d[j] += v;
+  };
+  for (const auto& e : M) {
+    const long k = e.first;
+    for (size_t j = 0; j < 2 * n; ++j) {
+      const cplx v = e.second[j % n];
+      const bool lo = ((long)j + k) % P < (long)n;  // offset k reads the first n slots
+      add(k, j, lo ? v : times_i(v));
+      add(k + (long)n, j, lo ? times_i(v) : v);
+    }
+  }
+  return R;
 }
 
 struct PlainSet {  // encoded, NTT-domain diagonals of one group at one level and plaintext scale
@@ -132,6 +172,7 @@ struct BtsState {
   int K = 28, r = 4, deg = 31, cts = 3, stc = 3;
   std::vector<LTGroup> cts_groups, stc_groups;      // N/2 slots
   std::map<size_t, std::pair<std::vector<LTGroup>, std::vector<LTGroup>>> sparse;  // n -> (CtS, StC) groups
+  std::map<size_t, std::pair<LTGroup, LTGroup>> packed;  // n -> (last CtS group, first StC group), period 2n
   std::map<std::tuple<size_t, int, int>, PlainSet> plains;  // (slots, inverse, group) -> encoded diagonals
   std::vector<double> mod_coeffs;                  // Chebyshev coefficients of the scaled cosine
 };
@@ -283,14 +324,11 @@ static DevBuf encode_diag(Ctx& C, const std::vector<cplx>& dn, double sp, int le
 
 // sum_g rot( sum_b rot(D_k, -G_g) o rot(v, b h0), G_g ),  k = kmin + g n1 + b,  G_g = h0 (kmin + g n1);
 // one rescale at the end; the result's scale is `target`
-std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int gi, double target, size_t slots) {
-  BtsState& S = state(C);
-  if (!slots) slots = C.N / 2;
-  const LTGroup& G = groups_for(C, S, slots, inverse).at(gi);
+// group G (diagonals of period `slots`) applied to v, its encoded diagonals cached in P
+static std::unique_ptr<Ct> lt_apply(Ctx& C, const Ct& v, const LTGroup& G, PlainSet& P, double target, size_t slots) {
   const int l = v.level;
   if (l < 1) throw Error(HEDAP_ERR_LEVEL, "linear transform needs level >= 1");
   const double sp = target * (double)C.primes[l] / v.scale;
-  PlainSet& P = S.plains[{slots, inverse ? 1 : 0, gi}];
   if (P.level != l || P.sp != sp) {  // (re)encode; the cache is marked valid only once complete
     P.pt.clear();
     P.level = -1;
@@ -351,6 +389,26 @@ std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int 
   out->scale = target;
   return out;
 }
+std::unique_ptr<Ct> bts_linear_transform(Ctx& C, const Ct& v, bool inverse, int gi, double target, size_t slots) {
+  BtsState& S = state(C);
+  if (!slots) slots = C.N / 2;
+  return lt_apply(C, v, groups_for(C, S, slots, inverse).at(gi), S.plains[{slots, inverse ? 1 : 0, gi}], target,
+                  slots);
+}
+// the packed last CoeffToSlot group (inverse) or first SlotToCoeff group of n sparse slots, period 2n
+static std::unique_ptr<Ct> lt_packed(Ctx& C, const Ct& v, bool inverse, size_t n, double target) {
+  BtsState& S = state(C);
+  auto it = S.packed.find(n);
+  if (it == S.packed.end()) {
+    it = S.packed.emplace(std::piecewise_construct, std::forward_as_tuple(n), std::forward_as_tuple()).first;
+    it->second.first.d = packed_cts_last(groups_for(C, S, n, true).back().d, n);
+    layout_group(it->second.first, 2 * n);
+    it->second.second.d = packed_stc_first(groups_for(C, S, n, false).front().d, n);
+    layout_group(it->second.second, 2 * n);
+  }
+  const LTGroup& G = inverse ? it->second.first : it->second.second;
+  return lt_apply(C, v, G, S.plains[{2 * n, inverse ? 3 : 2, 0}], target, 2 * n);
+}
 
 // Chebyshev interpolant (first-kind nodes on [lo, hi]) of an arbitrary function
 template <class F>
@@ -399,6 +457,16 @@ std::unique_ptr<Ct> bootstrap_core(Ctx& C, const Ct& a, int log_slots) {
   }
   if (n < C.N / 2) t = sub_sum(C, *t, n);  // sparse packing: project q_0 I onto the subring
   t->scale = 2.0 * q0 * S.K * (double)(C.N / 2 / n);
+  if (n < C.N / 2) {  // real and imaginary parts packed in 2n slots: one EvalMod
+    for (int g = 0; g + 1 < S.cts; ++g) t = bts_linear_transform(C, *t, true, g, (double)C.primes[t->level - 1], n);
+    t = lt_packed(C, *t, true, n, (double)C.primes[t->level - 1]);
+    auto w = eval_mod(C, *ev_add(C, *t, *ev_galois(C, *t, 2 * C.N - 1), false));  // 2 Re | 2 Im, then EvalMod
+    w->scale = w->scale * 2.0 * M_PI * s_in / q0;
+    w = lt_packed(C, *w, false, n, S.stc == 1 ? C.scale : (double)C.primes[w->level - 1]);
+    for (int g = 1; g < S.stc; ++g)
+      w = bts_linear_transform(C, *w, false, g, g + 1 == S.stc ? C.scale : (double)C.primes[w->level - 1], n);
+    return w;
+  }
   for (int g = 0; g < S.cts; ++g) t = bts_linear_transform(C, *t, true, g, (double)C.primes[t->level - 1], n);
   auto cj = ev_galois(C, *t, 2 * C.N - 1);
   auto re = ev_add(C, *t, *cj, false);
