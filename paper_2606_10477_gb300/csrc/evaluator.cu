@@ -362,11 +362,14 @@ std::unique_ptr<Ct> ev_mul_const_raw(Ctx& C, const Ct& a, double c, double targe
 }
 std::unique_ptr<Ct> ev_lincomb_raw(Ctx& C, const std::vector<std::pair<const Ct*, double>>& terms, int level,
                                    double target, double c0) {
-  if (terms.empty() || level < 1) throw Error(HEDAP_ERR_ARG, "linear combination needs terms at level >= 1");
+  if (terms.empty()) throw Error(HEDAP_ERR_ARG, "linear combination without terms");
+  if (level < 1) throw Error(HEDAP_ERR_LEVEL, "constant multiplication needs level >= 1");
   const double raw = target * (double)C.primes[level];
   const int batch = terms[0].first->batch;
-  for (const auto& t : terms)
-    if (t.first->level < level || t.first->batch != batch) throw Error(HEDAP_ERR_ARG, "linear combination operands");
+  for (const auto& t : terms) {
+    if (t.first->level < level) throw Error(HEDAP_ERR_LEVEL, "linear combination operand below the output level");
+    if (t.first->batch != batch) throw Error(HEDAP_ERR_ARG, "operands have different batch sizes");
+  }
   auto o = ct_alloc(C, level, batch);
   o->scale = raw;
   if (level + 1 > kLcLimbs) {  // wide chains: one product and one addition at a time

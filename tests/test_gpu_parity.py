@@ -295,5 +295,11 @@ def test_error_codes(toy):
     with pytest.raises(hedap.HedapError) as e:
         g.ct_import(bad, 3, o.scale)
     assert e.value.code == -7
-    with pytest.raises(hedap.HedapError):
+    with pytest.raises(hedap.HedapError) as e:
         g.invsqrt(ga, 0.01, 1.0, 1.0, 15, 2)  # level 0 input
+    assert e.value.code == -2
+    for lvl in (1, 2, 3):  # too few levels for the Chebyshev products: a level error, which the selector skips
+        gl, _ = imported_pair(g, o, 60 + lvl, lvl)
+        with pytest.raises(hedap.HedapError) as e:
+            g.invsqrt(gl, 0.01, 1.0, 1.0, 15, 2)
+        assert e.value.code == -2
