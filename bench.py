@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-level batch workload")
     ap.add_argument("--no-dnum3", action="store_true", help="skip the three-digit key-switching variant")
     ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
-    ap.add_argument("--only", choices=["ntt", "serving", "mixed", "bts", "hmult"],
+    ap.add_argument("--only", choices=["ntt", "serving", "mixed", "bts", "hmult", "ops"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     ap.add_argument("--profile-region", action="store_true",
@@ -390,6 +390,7 @@ def run_ours(args):
                "sample": "one full oracle CryptoInvSqrt of one ciphertext on the same workload", "mre": omre}
 
     ntt = measure_ntt(ctx, inputs, torch, stream, 384)
+    ops = per_op_us(ctx, inputs, torch, stream, batch)
     bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
                                                          stream=stream, rank=rank, batch=batch)
     mixed = None if args.no_mixed else mixed_workload(hedap, inputs, torch, stream, rank)
@@ -407,6 +408,7 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "ntt_gbs": ntt_gbs,
             "ntt_batched": ntt,
+            "per_op_us": ops,
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -755,6 +757,51 @@ def measure_ntt(ctx, inputs, torch, stream, limbs, reps=5, profile_region=False)
     return out
 
 
+def per_op_us(ctx, inputs, torch, stream, batch, reps=10):
+    """Device time of single operations at the top level of the N=2^16 workload chain, one ciphertext
+    and a batch of `batch` (CUDA events over `reps` calls each, after one untimed call)."""
+    L = ctx.n_q - 1
+    out = {}
+    for b in (1, batch):
+        cts = [ctx.encrypt(inputs.uniform_values(9700 + i, ctx.N // 2, LO, HI), L, 9800 + i) for i in range(b)]
+        x = ctx.pack(cts) if b > 1 else cts[0]
+        r = ctx.mul_relin(x, x)
+        ops = {
+            "hmult (tensor, key switch, rescale)": lambda: ctx.mul(x, x),
+            "tensor + key switch": lambda: ctx.mul_relin(x, x),
+            "rescale": lambda: ctx.rescale(r),
+            "rotation by 1": lambda: ctx.rotate(x, 1),
+            "conjugation": lambda: ctx.conjugate(x),
+            "constant multiply + rescale": lambda: ctx.mul_const(x, 1.5, x.scale),
+            "addition": lambda: ctx.add(x, x),
+        }
+        row = {}
+        for name, fn in ops.items():
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = 1e3 * e0.elapsed_time(e1) / reps
+        out[f"batch {b}"] = row
+    out["level"] = L
+    return out
+
+
+def run_ops_only(args):
+    import torch
+    from paper_2606_10477_gb300 import hedap, inputs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    p = inputs.PRESETS[PRESET]
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1,
+                        stream=stream.cuda_stream)
+    print(json.dumps({"per_op_us": per_op_us(ctx, inputs, torch, stream, args.batch)}), flush=True)
+
+
 def run_hmult_only(args):
     """One batched HMult (tensor, key switch with the fused ModUp / ModDown transforms, rescale) of
     `--batch` ciphertexts at the top level of the N=2^16 workload chain: its time and the NTT class's
@@ -818,6 +865,8 @@ def main():
         run_ntt_only(args)
     elif args.only == "hmult":
         run_hmult_only(args)
+    elif args.only == "ops":
+        run_ops_only(args)
     elif args.only == "serving":
         run_serving_only(args)
     elif args.only == "bts":
