@@ -114,6 +114,9 @@ def _declare(L):
         "orc_mul_monomial": (vp, [vp, vp, C.c_uint64]),
         "orc_fft_group_offsets": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, i64p, C.c_int]),
         "orc_fft_group_diag": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int64, f64p, f64p]),
+        "orc_fft_group_ex_offsets": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, i64p, C.c_int]),
+        "orc_fft_group_ex_diag": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, f64p, f64p,
+                                            C.c_int]),
         "orc_splitmix_stream": (C.c_uint64, [C.c_uint64, C.c_uint64, C.c_uint64, u64p]),
     }
     for name, (res, args) in sig.items():
@@ -376,6 +379,21 @@ class Context:
             re, im = np.empty(self.N // 2), np.empty(self.N // 2)
             _check(lib().orc_fft_group_diag(self.h, groups, int(inverse), g, int(o), re, im))
             out[int(o)] = re + 1j * im
+        return out
+
+    def fft_group_ex(self, groups: int, inverse: bool, g: int, log_slots: int, packed: bool = False) -> dict:
+        """{offset: diagonal} of group g for 2^log_slots slots; packed: the 2n-periodic form used when the
+        real and imaginary parts share one ciphertext (last CoeffToSlot / first SlotToCoeff group)."""
+        offs = np.empty(1 << 16, dtype=np.int64)
+        k = _check(lib().orc_fft_group_ex_offsets(self.h, groups, int(inverse), g, log_slots, int(packed), offs,
+                                                  len(offs)))
+        out = {}
+        cap = self.N  # a diagonal has at most 2n <= N entries
+        for o in offs[:k]:
+            re, im = np.empty(cap), np.empty(cap)
+            m = _check(lib().orc_fft_group_ex_diag(self.h, groups, int(inverse), g, log_slots, int(packed), int(o),
+                                                   re, im, cap))
+            out[int(o)] = re[:m] + 1j * im[:m]
         return out
 
     def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0, log_slots=0):

@@ -1587,6 +1587,36 @@ API int orc_fft_group_diag(void* c, int groups, int inverse, int g, int64_t offs
   )
   return -1;
 }
+// the same for 2^log_slots slots (sparse packing); packed = 1 gives the packed form of the last
+// CoeffToSlot group (inverse) or the first SlotToCoeff group, of period 2^(log_slots+1)
+static DiagMap fft_group_ex(const Ctx& C, int groups, int inverse, int g, int log_slots, int packed) {
+  size_t n = log_slots ? (size_t)1 << log_slots : C.N / 2;
+  std::vector<DiagMap> G = fft_groups(n, groups, inverse != 0);
+  if (!packed) return G.at(g);
+  if (inverse) { if (g != groups - 1) throw std::runtime_error("packed: last CoeffToSlot group only"); return pack_cts_last(G.back(), n); }
+  if (g != 0) throw std::runtime_error("packed: first SlotToCoeff group only");
+  return pack_stc_first(G[0], n);
+}
+API int orc_fft_group_ex_offsets(void* c, int groups, int inverse, int g, int log_slots, int packed, int64_t* offsets,
+                                 int cap) {
+  GUARD(
+    DiagMap M = fft_group_ex(*(Ctx*)c, groups, inverse, g, log_slots, packed);
+    int k = 0; for (auto& e : M) { if (k < cap) offsets[k] = e.first; ++k; }
+    return k;
+  )
+  return -1;
+}
+API int orc_fft_group_ex_diag(void* c, int groups, int inverse, int g, int log_slots, int packed, int64_t offset,
+                              double* re, double* im, int cap) {
+  GUARD(
+    DiagMap M = fft_group_ex(*(Ctx*)c, groups, inverse, g, log_slots, packed);
+    const std::vector<cd>& d = M.at(offset);
+    if ((int)d.size() > cap) throw std::runtime_error("diagonal longer than the buffer");
+    for (size_t s = 0; s < d.size(); ++s) { re[s] = d[s].real(); im[s] = d[s].imag(); }
+    return (int)d.size();
+  )
+  return -1;
+}
 // single steps of bootstrapping, for tests
 API void* orc_linear_transform_group(void* c, void* a, int groups, int inverse, int g, double target) {
   CT_OP(linear_transform(*(Ctx*)c, *(Ct*)a, fft_groups(((Ctx*)c)->N / 2, groups, inverse != 0).at(g), target,

@@ -214,3 +214,49 @@ def test_sparse_slot_invsqrt_with_lazy_bootstrapping(ctx):
     y = ctx.decrypt(ctx.invsqrt(ctx.encrypt(at, L_after, 111), 1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63, 8)).real
     plain = oracle.plain_invsqrt(at, 1e-4, 1.0, 1.0, 15, 5)
     assert np.max(np.abs(y - plain) / plain) < 1e-4
+
+
+def apply_period(D, x):
+    """sum over offsets o of d_o * (x rotated left by o), x of the diagonals' length"""
+    return sum(d * np.roll(x, -off) for off, d in D.items())
+
+
+def test_sparse_groups_are_the_small_decoding_matrix(ctx):
+    """For n = 2^7 slots the grouped factors are those of the ring of dimension 2n: CoeffToSlot is the
+    bit-reversed inverse of V_n (z_j = m(zeta_4n^(5^j))), SlotToCoeff is V_n on bit-reversed input."""
+    ls = 7
+    n = 1 << ls
+    V = decoding_matrix(2 * n)
+    perm = bitrev_perm(n)
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=n) + 1j * rng.normal(size=n)
+    w = np.linalg.solve(V, v)
+    x = v.copy()
+    for g in range(3):
+        x = apply_period(ctx.fft_group_ex(3, True, g, ls), x)
+    assert np.max(np.abs(x - w[perm])) < 1e-12
+    y = w[perm].copy()
+    for g in range(3):
+        y = apply_period(ctx.fft_group_ex(3, False, g, ls), y)
+    assert np.max(np.abs(y - v)) < 1e-11
+
+
+def test_packed_groups_split_real_and_imaginary_parts(ctx):
+    """Packed sparse slots: the last CoeffToSlot group of period 2n gives (1 | -i) times the plain group's
+    output, so that s + conj(s) is 2 Re | 2 Im; the first SlotToCoeff group of period 2n applied to y equals
+    the plain group applied to z_m = y_m + i y_(m+n), on both halves."""
+    ls = 7
+    n = 1 << ls
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=n) + 1j * rng.normal(size=n)
+    plain = apply_period(ctx.fft_group_ex(3, True, 2, ls), v)
+    packed = apply_period(ctx.fft_group_ex(3, True, 2, ls, packed=True), np.tile(v, 2))
+    mask = np.concatenate([np.ones(n), -1j * np.ones(n)])
+    assert np.max(np.abs(packed - mask * np.tile(plain, 2))) < 1e-12
+    s = packed + np.conj(packed)
+    assert np.max(np.abs(s[:n] - 2 * plain.real)) < 1e-12 and np.max(np.abs(s[n:] - 2 * plain.imag)) < 1e-12
+    y = rng.normal(size=2 * n)
+    z = y[:n] + 1j * y[n:]
+    ref = apply_period(ctx.fft_group_ex(3, False, 0, ls), z)
+    got = apply_period(ctx.fft_group_ex(3, False, 0, ls, packed=True), y.astype(complex))
+    assert np.max(np.abs(got - np.tile(ref, 2))) < 1e-12
