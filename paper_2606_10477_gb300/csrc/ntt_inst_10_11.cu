@@ -1,0 +1,15 @@
+// Instantiations of the transform kernels for N = 2^10/2^11 (see ntt_impl.cuh).
+#include "ntt_impl.cuh"
+
+namespace hedap {
+
+void ntt_launch_10_11(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
+                      const NttAux& A) {
+  switch (log_n) {
+    case 10: launch_variant<5, 5>(v, S, T, st, inverse, A); break;
+    case 11: launch_variant<5, 6>(v, S, T, st, inverse, A); break;
+    default: throw Error(HEDAP_ERR_ARG, "ring size not instantiated in this unit");
+  }
+}
+
+}  // namespace hedap

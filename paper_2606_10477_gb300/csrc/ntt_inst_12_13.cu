@@ -1,0 +1,15 @@
+// Instantiations of the transform kernels for N = 2^12/2^13 (see ntt_impl.cuh).
+#include "ntt_impl.cuh"
+
+namespace hedap {
+
+void ntt_launch_12_13(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
+                      const NttAux& A) {
+  switch (log_n) {
+    case 12: launch_variant<6, 6>(v, S, T, st, inverse, A); break;
+    case 13: launch_variant<6, 7>(v, S, T, st, inverse, A); break;
+    default: throw Error(HEDAP_ERR_ARG, "ring size not instantiated in this unit");
+  }
+}
+
+}  // namespace hedap
