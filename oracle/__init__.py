@@ -62,6 +62,7 @@ def _declare(L):
         "orc_ctx_primes": (C.c_int, [vp, u64p]),
         "orc_ctx_psi": (C.c_int, [vp, u64p]),
         "orc_export_secret": (C.c_int, [vp, i64p]),
+        "orc_export_sparse_secret": (C.c_int, [vp, i64p]),
         "orc_gen_galois_key": (C.c_int, [vp, C.c_uint64]),
         "orc_galois_of_rotation": (C.c_uint64, [vp, C.c_int64]),
         "orc_export_key": (C.c_int, [vp, C.c_uint64, C.c_uint32, u64p, u64p]),
@@ -201,6 +202,12 @@ class Context:
     def secret(self) -> np.ndarray:
         out = np.empty(self.N, dtype=np.int64)
         lib().orc_export_secret(self.h, out)
+        return out
+
+    def sparse_secret(self) -> np.ndarray:
+        """The ephemeral secret of the bootstrapping encapsulation (coefficients)."""
+        out = np.empty(self.N, dtype=np.int64)
+        _check(lib().orc_export_sparse_secret(self.h, out))
         return out
 
     def galois_of_rotation(self, r: int) -> int:

@@ -270,6 +270,7 @@ struct Ctx {
   // sparse-secret encapsulation of bootstrapping: ephemeral secret of weight enc_hw (0 = off);
   // key 2 switches from s to it, key 4 back (even ids are never Galois elements)
   int enc_hw = 0;
+  std::vector<i64> s_sparse;
   Poly s_sparse_ntt;
   // bootstrapping: off unless configured; K bounds the ModRaise overflow |I| < K,
   // r double-angle steps, degree of the cosine interpolant, levels of CtS / StC
@@ -384,6 +385,7 @@ static void encapsulate(Ctx& C, int h) {
   int total = C.n_q + C.n_p;
   Stream st(C.seed, TAG_SK_SPARSE);
   std::vector<i64> v = sample_ternary(st, C.log_n, h);
+  C.s_sparse = v;
   C.s_sparse_ntt.assign(total, Limb());
   for (int t = 0; t < total; ++t) { C.s_sparse_ntt[t] = residues_of(C, v, t); ntt_forward(C, C.s_sparse_ntt[t], t); }
   std::vector<KeyDigit> to_sparse, to_dense;
@@ -1349,6 +1351,15 @@ API int orc_ctx_psi(void* c, uint64_t* out) {
 }
 API int orc_export_secret(void* c, int64_t* out) {
   Ctx* C = (Ctx*)c; for (size_t i = 0; i < C->N; ++i) out[i] = C->s[i]; return 0;
+}
+API int orc_export_sparse_secret(void* c, int64_t* out) {
+  GUARD(
+    Ctx* C = (Ctx*)c;
+    if (!C->enc_hw) throw std::runtime_error("no encapsulation");
+    for (size_t i = 0; i < C->N; ++i) out[i] = C->s_sparse[i];
+    return 0;
+  )
+  return -1;
 }
 API int orc_gen_galois_key(void* c, uint64_t g) { GUARD(gen_key(*(Ctx*)c, g); return 0;) return -1; }
 API uint64_t orc_galois_of_rotation(void* c, int64_t r) { return galois_of_rotation(*(Ctx*)c, r); }

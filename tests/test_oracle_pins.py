@@ -450,3 +450,29 @@ def test_homomorphic_invsqrt_tracks_plain_model():
         assert np.max(np.abs(y - plain) / plain) < 1e-6
         depth = 1 + (math.ceil(math.log2(d + 1)) + 1) + 2 * k
         assert out.level == 10 - depth
+
+
+def test_encapsulation_keys_relation():
+    """Sparse-secret encapsulation: the ephemeral secret has exactly h entries in {-1, 1}; the key s -> s~
+    satisfies b + a s~ = e + P s on its digit's primes and the key s~ -> s satisfies b + a s = e + P s~,
+    e small (centred binomial, |e| <= 21), checked with Python integers."""
+    h = 5
+    ctx = oracle.Context(TINY["log_n"], TINY["q_bits"], TINY["p_bits"], TINY["alpha"], TINY["log_scale"], 0, 11)
+    ctx.bts_encapsulate(h)
+    qs = [int(q) for q in ctx.primes()]
+    P = math.prod(qs[ctx.n_q:])
+    s = [int(v) for v in ctx.secret()]
+    st = [int(v) for v in ctx.sparse_secret()]
+    assert sum(1 for v in st if v) == h and all(v in (-1, 0, 1) for v in st)
+    for key_id, s_from, s_to in ((2, s, st), (4, st, s)):
+        for j in range(2):
+            b, a = ctx.key_digit(key_id, j)
+            for t, q in enumerate(qs):
+                s_ntt = ctx.ntt(np.array([v % q for v in s_to], dtype=np.uint64), t)
+                lhs = np.array([(int(x) + int(y) * int(z)) % q for x, y, z in zip(b[t], a[t], s_ntt)],
+                               dtype=np.uint64)
+                coef = [int(v) for v in ctx.ntt(lhs, t, inverse=True)]
+                in_digit = 2 * j <= t < 2 * j + 2 and t < ctx.n_q
+                err = [(c - (P % q) * (v % q) * in_digit) % q for c, v in zip(coef, s_from)]
+                err = [e if e <= q // 2 else e - q for e in err]
+                assert max(abs(e) for e in err) <= 21
