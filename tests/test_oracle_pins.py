@@ -173,6 +173,29 @@ def test_rescale_rounds_to_nearest(small):
             assert [int(coef[i][k]) for i in range(level)] == [r % m for m in moduli[:level]]
 
 
+def test_rescale_edge_values(small):
+    """Rescale at the extremes of the centred range and at the rounding boundaries of q_l:
+    0, +-1, +-(q_l - 1)/2, +-(q_l + 1)/2, multiples of q_l and their neighbours, the largest and the most
+    negative centred value."""
+    ctx = small
+    qs = [int(q) for q in ctx.primes()]
+    level = 3
+    moduli = qs[:level + 1]
+    M = math.prod(moduli)
+    ql = moduli[-1]
+    edge = [0, 1, -1, (ql - 1) // 2, -(ql - 1) // 2, (ql + 1) // 2, -(ql + 1) // 2, ql, -ql, 7 * ql + 1,
+            7 * ql - 1, M // 2, -(M // 2), M // 2 - ql // 2, -(M // 2) + ql // 2]
+    vals = [(edge[k % len(edge)] + k // len(edge)) % M for k in range(ctx.N)]
+    limbs = np.array([[v % m for v in vals] for m in moduli], dtype=np.uint64)
+    ntt = np.stack([ctx.ntt(limbs[i], i) for i in range(level + 1)])
+    out = ctx.rescale_ntt(ntt, level)
+    coef = np.stack([ctx.ntt(out[i], i, inverse=True) for i in range(level)])
+    for k in range(ctx.N):
+        x = vals[k] if vals[k] <= M // 2 else vals[k] - M
+        r = (2 * x + ql) // (2 * ql)  # round(x / q_l), q_l odd so no ties
+        assert [int(coef[i][k]) for i in range(level)] == [r % m for m in moduli[:level]]
+
+
 def test_moddown_is_round_div_p_up_to_bconv_slack():
     ctx = oracle.Context(4, [30, 30, 30], [31, 31, 32], 3, 20, 0, 1)
     qs = [int(q) for q in ctx.primes()]
