@@ -214,6 +214,29 @@ def test_moddown_is_round_div_p_up_to_bconv_slack():
             assert 0 <= u < len(Ps)
 
 
+def test_moddown_edge_values():
+    """ModDown at the rounding boundaries of P (P/2 and its neighbours, multiples of P) and at the ends of
+    [0, Q P): the result is round(x / P) up to the conversion slack u in [0, K)."""
+    ctx = oracle.Context(4, [30, 30, 30], [31, 31, 32], 3, 20, 0, 1)
+    qs = [int(q) for q in ctx.primes()]
+    Ps = qs[3:]
+    P = math.prod(Ps)
+    for level in (0, 2):
+        Qs = qs[:level + 1]
+        QP = math.prod(Qs) * P
+        vals = [0, 1, P // 2 - 1, P // 2, P // 2 + 1, P - 1, P, P + 1, 5 * P + P // 2, 5 * P + P // 2 + 1,
+                QP - 1, QP - P // 2, QP - P // 2 - 1, QP // 2, QP // 2 + 1, QP - P]
+        assert len(vals) == ctx.N
+        limbs = np.array([[v % m for v in vals] for m in Qs + Ps], dtype=np.uint64)
+        out = ctx.moddown_coeff(limbs, level)
+        Ql = math.prod(Qs)
+        for k in range(ctx.N):
+            got = crt([out[i][k] for i in range(level + 1)], Qs)
+            expect = (2 * vals[k] + P) // (2 * P)  # round(x / P)
+            u = (expect - got) % Ql
+            assert 0 <= u < len(Ps)
+
+
 def test_modup_is_exact_up_to_multiple_of_digit_modulus():
     ctx = oracle.Context(4, [30] * 5, [40, 40], 2, 20, 0, 1)
     qs = [int(q) for q in ctx.primes()]
