@@ -97,7 +97,7 @@ def measured_peaks():
 # x * w and qh * q (two 32 x 32 -> 64 and four 32 x 32 -> 32 products): 6 wide products, each two
 # multiply-pipe slots, and 4 low ones = 16 slots per butterfly, against 64 multiply-add lanes per SM.
 NTT_MUL_SLOTS_PER_BUTTERFLY = 16
-GB300_SMS, IMAD_LANES_PER_SM = 152, 64
+IMAD_LANES_PER_SM = 64
 # DRAM bytes per transformed limb, dram__bytes_read.sum + dram__bytes_write.sum of the 12 transform
 # launches of one batched HMult at the top level (`--only hmult --batch 2 --profile-region` under ncu:
 # 1336 MB for 824 limb transforms, the mix of fused ModUp / ModDown / rescale transforms of the step),
@@ -111,12 +111,14 @@ def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
     bfly = limbs * (n // 2) * log_n
     achieved = bfly / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = GB300_SMS * IMAD_LANES_PER_SM * mhz * 1e6 / NTT_MUL_SLOTS_PER_BUTTERFLY / 1e9
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * IMAD_LANES_PER_SM * mhz * 1e6 / NTT_MUL_SLOTS_PER_BUTTERFLY / 1e9
     return {"kernel": "ntt", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gbutterfly/s",
             "frac": achieved / peak, "traffic": NTT_DRAM_BYTES_PER_LIMB * limbs / max(1, groups),
             "traffic_unit": "bytes per launch group (ncu, scaled per limb)",
             "algorithmic_bytes_per_group": alg_bytes / max(1, groups),
-            "peak_source": f"derived: {GB300_SMS} SMs x {IMAD_LANES_PER_SM} integer multiply-add lanes x {mhz:.0f} MHz / "
+            "peak_source": f"derived: {sms} SMs (read from the device) x {IMAD_LANES_PER_SM} integer multiply-add lanes x {mhz:.0f} MHz / "
                            f"{NTT_MUL_SLOTS_PER_BUTTERFLY} multiply slots per Shoup butterfly",
             "launch_groups": groups, "avg_group_us": 1e3 * ms / max(1, groups),
             "butterflies_per_group": bfly / max(1, groups)}

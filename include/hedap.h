@@ -109,6 +109,10 @@ hedap_status hedap_sync(hedap_ctx* ctx);
  * g = 5^r mod 2N, conjugation g = 2N - 1.  Keys are generated on first use;
  * these calls generate them ahead of time. */
 hedap_status hedap_gen_galois_key(hedap_ctx* ctx, uint64_t galois);
+/* The Galois element of a rotation by `steps` slots (Sec. 2.1's Rotate):
+ * 5^(steps mod N/2) mod 2N; with conjugate != 0 the element of complex
+ * conjugation, 2N - 1 (steps ignored).  Host only. */
+hedap_status hedap_galois_element(const hedap_ctx* ctx, int64_t steps, int conjugate, uint64_t* out);
 /* Export digit j of the key for g (g = 0: relinearisation key) into host
  * arrays b, a of [n_q + n_p][N] words each (NTT domain). */
 hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t galois, uint32_t digit, uint64_t* b, uint64_t* a);
@@ -335,18 +339,20 @@ hedap_status hedap_key_switch(hedap_ctx* ctx, const uint64_t* d, int level, uint
  * budget, a host framework whose allocator owns the device memory, or code
  * that must not let a cudaMalloc/cudaFree synchronise the device.
  * in:  device pointer, [2][level+1][N] words (NTT domain, as hedap_ct_export).
- * out: device pointer, [2][level][N] words; must not overlap `in`.
+ * out: device pointer, [2][level][N] words; must not overlap `in`
+ *      (HEDAP_ERR_ARG when the two ranges overlap).
  * Same result as hedap_rescale (scale divided by q_level is the caller's to
  * track).  Work is issued on the context's stream; the call returns without
- * synchronising.  Scratch is one library-wide device array of 4 Mi words
- * (32 MiB) that every GPU loading the library holds until the process exits;
- * (2 + 2*level) * N must not exceed 4 Mi words (level <= 31 at N = 2^16),
- * otherwise HEDAP_ERR_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array: calls
- * whose work overlaps on the GPU (other streams, other threads, other
- * contexts on the same device) race on it.  It calls no cudaMalloc, cudaFree
- * or allocating routine (with profiling off, the default). */
+ * synchronising.  The context's device must be the current device
+ * (HEDAP_ERR_ARG otherwise).  Scratch is one library-wide device array of
+ * 4 Mi words (32 MiB) per device, allocated when the first context is created
+ * on that device (context creation looks up its address) and held until the
+ * process exits; (2 + 2*level) * N must not exceed 4 Mi words (level <= 31 at
+ * N = 2^16), otherwise HEDAP_ERR_ARG.  All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other threads, other contexts on the
+ * same device) race on it.  The call runs under the context's lock like every
+ * other entry point, and calls no cudaMalloc, cudaFree or allocating routine
+ * (with profiling off, the default). */
 hedap_status hedap_rescale_noalloc(hedap_ctx* ctx, const uint64_t* in, int level, uint64_t* out);
 
 /* Serving (the statistical workloads of Sec. 5.3: Z-score normalisation and

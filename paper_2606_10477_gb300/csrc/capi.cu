@@ -46,6 +46,7 @@ hedap_ct* wrap(std::unique_ptr<hedap::Ct> c) {
 
 namespace hedap {
 void set_last_error(const std::string& m) { g_last_error = m; }
+hedap_status run_on_ctx(const hedap_ctx* ctx, const std::function<void()>& f) { return guarded_on(ctx, f); }
 }  // namespace hedap
 
 #define API extern "C" __attribute__((visibility("default")))
@@ -92,6 +93,12 @@ API hedap_status hedap_sync(hedap_ctx* ctx) {
   return guarded_on(ctx, [&] {
     need(ctx, "null argument");
     HEDAP_CUDA(cudaStreamSynchronize(ctx->c->stream));
+  });
+}
+API hedap_status hedap_galois_element(const hedap_ctx* ctx, int64_t steps, int conjugate, uint64_t* out) {
+  return guarded([&] {
+    need(ctx && out, "null argument");
+    *out = conjugate ? 2 * ctx->c->N - 1 : hedap::galois_for_rotation(*ctx->c, steps);
   });
 }
 API hedap_status hedap_gen_galois_key(hedap_ctx* ctx, uint64_t g) {

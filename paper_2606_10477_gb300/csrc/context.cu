@@ -43,6 +43,9 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   int dev = 0;
   HEDAP_CUDA(cudaGetDevice(&dev));
   C->device = dev;
+  // hedap_rescale_noalloc's scratch: resolved here, so that its module is loaded (and the array
+  // allocated) now rather than inside a call that promises not to allocate
+  C->noalloc_scratch = noalloc_scratch_address(dev);
   cudaMemPool_t pool;
   HEDAP_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
   uint64_t thr = UINT64_MAX;

@@ -5,6 +5,7 @@
 #include <climits>
 #include <complex>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <memory>
@@ -240,6 +241,7 @@ struct Ctx {
   std::map<int, std::unique_ptr<LevelConsts>> lc;
   std::unique_ptr<BtsState, BtsStateDeleter> bts;
   int device = 0;             // the CUDA device current at creation
+  u64* noalloc_scratch = nullptr;  // device address of hedap_rescale_noalloc's scratch array on `device`
   mutable std::mutex mu;      // held by every C-ABI call on this context and by a server's worker per step
   int L() const { return n_q - 1; }
   int total_primes() const { return n_q + n_p; }
@@ -332,6 +334,11 @@ bool bts_diagonal(Ctx& C, bool inverse, int g, long offset, std::vector<std::com
 
 // thread-local message returned by hedap_last_error (capi.cu)
 void set_last_error(const std::string& m);
+// runs f under ctx's lock, turning exceptions into a status and the thread's last error (capi.cu)
+hedap_status run_on_ctx(const hedap_ctx* ctx, const std::function<void()>& f);
+// device address of hedap_rescale_noalloc's scratch array on `device` (the current device);
+// looked up once per device (rescale_noalloc.cu)
+u64* noalloc_scratch_address(int device);
 
 // ------------------------------------------------------------------ launch helpers
 inline int grid_for(size_t work, int threads) {

@@ -77,7 +77,9 @@ __global__ void k_butterfly_loop(const Tables T, u64* out, int iters) {
   out[i] = s;
 }
 double butterfly_rate(Ctx& C) {
-  const int threads = 256, blocks = 152 * 8, iters = 512;
+  int sms = 0;
+  HEDAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C.device));
+  const int threads = 256, blocks = sms * 8, iters = 512;
   DevBuf out((size_t)threads * blocks, C.stream);
   cudaEvent_t a, b;
   HEDAP_CUDA(cudaEventCreate(&a));

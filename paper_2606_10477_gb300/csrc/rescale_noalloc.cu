@@ -8,8 +8,15 @@
 // owns the device memory cannot have a library allocate behind its back; and
 // a cudaMalloc/cudaFree can synchronise the device and stall other streams.
 // This variant takes device pointers for its input and output and keeps its
-// scratch in one file-scope device array, allocated when the library is loaded
-// on a GPU and held until the process exits.
+// scratch in one file-scope device array.
+//
+// When the array comes into being: this file is its own CUDA module (it is
+// compiled apart from the kernels, without relocatable device code), and the
+// runtime loads a module lazily, on the first use of something in it.  The
+// first use is the cudaGetSymbolAddress below, which context creation calls
+// with the context's device current; so the 32 MiB are allocated on a device
+// when the first context is created there, and held until the process exits.
+// hedap_rescale_noalloc itself only reads the address cached in the context.
 #include <cstring>
 #include <mutex>
 
@@ -28,31 +35,39 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 u64* g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  The array's name
-// is only a host-side stand-in, so the address is looked up once per device,
-// with that device current, and cached.
-u64* scratch_on_current_device() {
-  int dev = 0;
-  HEDAP_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) throw hedap::Error(HEDAP_ERR_CUDA, "device index out of range");
+}  // namespace
+
+namespace hedap {
+
+// Device address of the scratch array on `device`, which must be the current device.  The array's
+// name is only a host-side stand-in, so the address is looked up once per device, with that device
+// current, and cached.
+u64* noalloc_scratch_address(int device) {
+  int cur = -1;
+  HEDAP_CUDA(cudaGetDevice(&cur));
+  if (cur != device) throw Error(HEDAP_ERR_ARG, "scratch lookup: the device is not current");
+  if (device < 0 || device >= kMaxDevices) throw Error(HEDAP_ERR_CUDA, "device index out of range");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[device]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_rescale_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rescale_scratch);
     if (e != cudaSuccess || !p)
-      throw hedap::Error(HEDAP_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    g_addr[dev] = (u64*)p;
+      throw Error(HEDAP_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_addr[device] = (u64*)p;
   }
-  return g_addr[dev];
+  return g_addr[device];
 }
 
-}  // namespace
+}  // namespace hedap
 
 extern "C" __attribute__((visibility("default"))) hedap_status hedap_rescale_noalloc(hedap_ctx* ctx,
                                                                                        const uint64_t* in, int level,
                                                                                        uint64_t* out) {
-  try {
-    if (!ctx || !in || !out) throw hedap::Error(HEDAP_ERR_ARG, "null argument");
+  if (!ctx || !in || !out) {
+    hedap::set_last_error("hedap_rescale_noalloc: null argument");
+    return HEDAP_ERR_ARG;
+  }
+  return hedap::run_on_ctx(ctx, [&] {
     hedap::Ctx& C = *ctx->c;
     if (level < 1 || level > C.L()) throw hedap::Error(HEDAP_ERR_LEVEL, "rescale needs 1 <= level <= L");
     const size_t N = C.N, l = (size_t)level;
@@ -60,7 +75,15 @@ extern "C" __attribute__((visibility("default"))) hedap_status hedap_rescale_noa
     if (need > kScratchWords)
       throw hedap::Error(HEDAP_ERR_ARG, "hedap_rescale_noalloc: (2 + 2*level) * N = " + std::to_string(need) +
                                            " words exceeds the scratch maximum of " + std::to_string(kScratchWords));
-    u64* scratch = scratch_on_current_device();
+    // [in, in + 2(l+1)N) and [out, out + 2lN) must be disjoint: the last kernel reads one and writes the other
+    const uintptr_t i0 = (uintptr_t)in, i1 = i0 + 2 * (l + 1) * N * 8, o0 = (uintptr_t)out, o1 = o0 + 2 * l * N * 8;
+    if (i0 < o1 && o0 < i1) throw hedap::Error(HEDAP_ERR_ARG, "hedap_rescale_noalloc: out overlaps in");
+    int cur = -1;
+    HEDAP_CUDA(cudaGetDevice(&cur));
+    if (cur != C.device)
+      throw hedap::Error(HEDAP_ERR_ARG, "hedap_rescale_noalloc: the context's device is not the current device");
+    u64* scratch = C.noalloc_scratch;
+    if (!scratch) throw hedap::Error(HEDAP_ERR_CUDA, "hedap_rescale_noalloc: scratch address not set up");
     u64* last = scratch;          // [2][N]: limb `level` of each part, coefficient domain
     u64* tmp = scratch + 2 * N;   // [2][level][N]: centred residues, then their NTT
     // every word of last and tmp is written before it is read: nothing to clear
@@ -79,12 +102,5 @@ extern "C" __attribute__((visibility("default"))) hedap_status hedap_rescale_noa
     hedap::k_rescale_spread(C, last, N, tmp, l * N, 2, level, R);
     hedap::ntt_forward(C.tab, hedap::LimbSet{tmp, l * N, 2, 0, level, INT_MAX, 0, 0}, C.stream);
     hedap::k_rescale_finish(C, in, (l + 1) * N, tmp, l * N, out, l * N, 2, level, R);
-    return HEDAP_OK;
-  } catch (const hedap::Error& e) {
-    hedap::set_last_error(e.what());
-    return e.code;
-  } catch (const std::exception& e) {
-    hedap::set_last_error(e.what());
-    return HEDAP_ERR_ARG;
-  }
+  });
 }

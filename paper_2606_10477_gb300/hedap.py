@@ -23,7 +23,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "not enough levels", -3: "scale m
 
 EXPORTED = [
     "hedap_status_str", "hedap_last_error", "hedap_ctx_create", "hedap_ctx_destroy", "hedap_ctx_primes", "hedap_sync",
-    "hedap_gen_galois_key", "hedap_export_key", "hedap_encrypt", "hedap_decrypt", "hedap_ct_import",
+    "hedap_gen_galois_key", "hedap_galois_element", "hedap_export_key", "hedap_encrypt", "hedap_decrypt", "hedap_ct_import",
     "hedap_ct_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
     "hedap_rescale", "hedap_rotate", "hedap_rotate_hoisted", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
@@ -123,6 +123,7 @@ def _declare(L):
         "hedap_ctx_primes": (st, [vp, u64p, C.c_size_t]),
         "hedap_sync": (st, [vp]),
         "hedap_gen_galois_key": (st, [vp, C.c_uint64]),
+        "hedap_galois_element": (st, [vp, C.c_int64, C.c_int, u64p]),
         "hedap_export_key": (st, [vp, C.c_uint64, C.c_uint32, u64p, u64p]),
         "hedap_encrypt": (st, [vp, dp, dp, C.c_size_t, C.c_int, C.c_uint64, pp]),
         "hedap_decrypt": (st, [vp, vp, dp, dp, C.c_size_t]),
@@ -302,7 +303,14 @@ class Context:
         _check(load().hedap_gen_galois_key(self.h, g))
 
     def galois_of_rotation(self, r: int) -> int:
-        return pow(5, r % (self.N // 2), 2 * self.N)
+        out = C.c_uint64()
+        _check(load().hedap_galois_element(self.h, r, 0, C.byref(out)))
+        return out.value
+
+    def galois_of_conjugation(self) -> int:
+        out = C.c_uint64()
+        _check(load().hedap_galois_element(self.h, 0, 1, C.byref(out)))
+        return out.value
 
     def key_digit(self, g: int, j: int):
         tot = self.n_q + self.n_p

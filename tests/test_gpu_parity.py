@@ -72,11 +72,20 @@ def test_relinearisation_key_bit_exact(toy, n10):
             assert np.array_equal(ga, oa) and np.array_equal(gb, ob)
 
 
+def test_galois_elements_from_the_library(n10):
+    """The library's Galois elements (hedap_galois_element) against the oracle's, including negative
+    steps, zero and steps beyond N/2 (rotation is periodic in N/2), and conjugation 2N - 1."""
+    g, o = n10
+    for r in (1, -5, 0, 7, o.N // 2, o.N // 2 + 3, -(o.N // 2) - 1):
+        assert g.galois_of_rotation(r) == o.galois_of_rotation(r), r
+    assert g.galois_of_conjugation() == 2 * o.N - 1
+
+
 def test_rotation_key_bit_exact(n10):
     g, o = n10
     for r in (1, -5):
-        gal = o.galois_of_rotation(r)
-        assert g.galois_of_rotation(r) == gal
+        gal = g.galois_of_rotation(r)
+        assert gal == o.galois_of_rotation(r)
         for j in (0, 2):
             gb, ga = g.key_digit(gal, j)
             ob, oa = o.key_digit(gal, j)
