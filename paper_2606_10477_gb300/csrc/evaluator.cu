@@ -168,7 +168,7 @@ const LevelConsts& level_consts(Ctx& C, int l) {
 // own limbs (whose NTT is d itself) are neither converted nor transformed.
 // ModUp of a batch of NTT-domain polynomials d (member stride d_stride) into NTT-domain extended
 // digits [B][dn][ext][N] (a digit's own limbs are left out: they are d itself)
-static DevBuf ks_modup(Ctx& C, const u64* d, size_t d_stride, int batch, int l) {
+static DevBuf ks_modup(Ctx& C, const u64* d, size_t d_stride, int batch, int l, const KskFuse* fuse = nullptr) {
   const size_t N = C.N, nl = (size_t)l + 1;
   const int ext = l + 1 + C.n_p, dn = C.dnum(l);
   const LevelConsts& LC = level_consts(C, l);
@@ -188,7 +188,7 @@ static DevBuf ks_modup(Ctx& C, const u64* d, size_t d_stride, int batch, int l) 
   up.bconv = LC.modup.p + 2 * nl;
   up.bconv_sh_offset = (size_t)dn * C.alpha * ext;
   up.ext = ext;
-  ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream, &up);
+  ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream, &up, fuse);
   return y;
 }
 static const DevBuf& key_for(Ctx& C, u64 galois) {
@@ -199,15 +199,12 @@ static const DevBuf& key_for(Ctx& C, u64 galois) {
   }
   return it->second;
 }
-// inner product of the extended digits (permuted by X -> X^perm when perm != 0) with the key for
-// `galois`, iNTT of the P limbs, ModDown, NTT, written to / added into out
-static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64 perm,
-                      u64* out, size_t out_stride, bool acc0, bool acc1) {
-  const DevBuf& key = key_for(C, galois);
+// iNTT of the P limbs of the key-switch sums acc [batch][2][ext][N], ModDown, NTT, written to / added
+// into out
+static void ks_moddown(Ctx& C, const DevBuf& acc, int batch, int l, u64* out, size_t out_stride, bool acc0,
+                       bool acc1) {
   const size_t N = C.N, nl = (size_t)l + 1;
   const int K = C.n_p, ext = l + 1 + K;
-  DevBuf acc((size_t)batch * 2 * ext * N, C.stream);
-  k_ksk_inner(C, y.p, d, d_stride, key.p, acc.p, batch, l, perm);
   // ModDown: the special-prime limbs to the coefficient domain (ending with N^-1 phinv_k when the
   // conversion is fused), the conversion into every Q prime fused into the forward NTT's load, and
   // (acc - v) P^-1 (+ out) fused into its store
@@ -241,11 +238,35 @@ static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, in
   ntt_forward(C.tab, qset(v.p, nl * N, 2 * batch, 0, l + 1), C.stream, &fw);
 }
 
+// inner product of the transformed extended digits y (permuted by X -> X^perm when perm != 0) with
+// the key for `galois`, then ModDown into out
+static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64 perm,
+                      u64* out, size_t out_stride, bool acc0, bool acc1) {
+  const DevBuf& key = key_for(C, galois);
+  DevBuf acc((size_t)batch * 2 * (l + 1 + C.n_p) * C.N, C.stream);
+  k_ksk_inner(C, y.p, d, d_stride, key.p, acc.p, batch, l, perm);
+  ks_moddown(C, acc, batch, l, out, out_stride, acc0, acc1);
+}
+
+// One key switch: iNTT of d, the extended digits' forward transform with the key inner product fused
+// into its second phase (the transformed digits are never stored), then ModDown.
 void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
                 bool acc0, bool acc1) {
-  key_for(C, galois);
-  DevBuf y = ks_modup(C, d, d_stride, batch, l);
-  ks_finish(C, y, d, d_stride, batch, l, galois, 0, out, out_stride, acc0, acc1);
+  const DevBuf& key = key_for(C, galois);
+  const int T = C.total_primes();
+  DevBuf acc((size_t)batch * 2 * (l + 1 + C.n_p) * C.N, C.stream);
+  KskFuse F;
+  F.d = d;
+  F.d_stride = d_stride;
+  F.key = key.p;
+  F.key_digit_stride = (size_t)2 * T * C.N;
+  F.key_a_offset = (size_t)T * C.N;
+  F.acc = acc.p;
+  F.acc_part_stride = (size_t)(l + 1 + C.n_p) * C.N;
+  F.r64 = C.d_r64.p;
+  F.batch = batch;
+  ks_modup(C, d, d_stride, batch, l, &F);  // its column-phase buffer is released stream-ordered
+  ks_moddown(C, acc, batch, l, out, out_stride, acc0, acc1);
 }
 
 // Rotations of one (batched) ciphertext by several Galois elements sharing one ModUp of its

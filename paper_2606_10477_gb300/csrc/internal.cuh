@@ -162,7 +162,23 @@ struct NttAux {
   const u64* fin_wsh = nullptr;
   int fin_acc_even = 0, fin_acc_odd = 0;
 };
-void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
+// Forward only: the second phase of the ModUp transform of a key switch fused with the key inner
+// product (k_ntt_fwd_rows_ksk): the transformed digits are multiplied by the switching key and summed
+// over the digits instead of being stored.  The LimbSet's parts are (ciphertext k, digit j) = k dn + j
+// (dn = NttAux::own_dn), its limbs the extended limbs t; a digit's own limbs are read from d.
+struct KskFuse {
+  const u64* d = nullptr;        // NTT-domain inputs: ciphertext k's limb t at d + k d_stride + t N
+  size_t d_stride = 0;
+  const u64* key = nullptr;      // switching key [dn][2][n_q + n_p][N] (digit j: b then a)
+  size_t key_digit_stride = 0;   // 2 (n_q + n_p) N
+  size_t key_a_offset = 0;       // (n_q + n_p) N
+  u64* acc = nullptr;            // output: part p of ciphertext k, limb t at acc + (2k + p) acc_part_stride + t N
+  size_t acc_part_stride = 0;
+  const u64* r64 = nullptr;      // per prime: 2^64 mod q and its Shoup companion
+  int batch = 0;
+};
+void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr,
+                 const KskFuse* fuse = nullptr);
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux = nullptr);
 struct Ctx;
 void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vector<float>* inv_ms);

@@ -6,30 +6,34 @@
 namespace hedap {
 
 void ntt_launch_10_11(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                      const NttAux& A);
+                      const NttAux& A, const KskFuse* F);
 void ntt_launch_12_13(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                      const NttAux& A);
+                      const NttAux& A, const KskFuse* F);
 void ntt_launch_14_15(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                      const NttAux& A);
+                      const NttAux& A, const KskFuse* F);
 void ntt_launch_16(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                   const NttAux& A);
+                   const NttAux& A, const KskFuse* F);
 void ntt_launch_17(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                   const NttAux& A);
+                   const NttAux& A, const KskFuse* F);
 void ntt_launch(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                const NttAux& A) {
+                const NttAux& A, const KskFuse* F) {
   switch (log_n) {
-    case 10: case 11: ntt_launch_10_11(log_n, v, S, T, st, inverse, A); break;
-    case 12: case 13: ntt_launch_12_13(log_n, v, S, T, st, inverse, A); break;
-    case 14: case 15: ntt_launch_14_15(log_n, v, S, T, st, inverse, A); break;
-    case 16: ntt_launch_16(log_n, v, S, T, st, inverse, A); break;
-    case 17: ntt_launch_17(log_n, v, S, T, st, inverse, A); break;
+    case 10: case 11: ntt_launch_10_11(log_n, v, S, T, st, inverse, A, F); break;
+    case 12: case 13: ntt_launch_12_13(log_n, v, S, T, st, inverse, A, F); break;
+    case 14: case 15: ntt_launch_14_15(log_n, v, S, T, st, inverse, A, F); break;
+    case 16: ntt_launch_16(log_n, v, S, T, st, inverse, A, F); break;
+    case 17: ntt_launch_17(log_n, v, S, T, st, inverse, A, F); break;
     default: throw Error(HEDAP_ERR_ARG, "log_n must lie in [10, 17]");
   }
 }
 
-static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool inverse, const NttAux* aux) {
+static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool inverse, const NttAux* aux,
+                     const KskFuse* F = nullptr) {
   if (S.n_parts * S.n_limbs == 0) return;
   const NttAux A = aux ? *aux : NttAux{};
+  if (F && (inverse || !A.own_alpha || !A.z || A.fin_dst || !F->d || !F->key || !F->acc || !F->r64 ||
+            F->batch < 1 || S.n_parts != F->batch * A.own_dn))
+    throw Error(HEDAP_ERR_ARG, "NTT: bad key inner product fusion");
   if (A.own_alpha && (A.own_dn < 1 || A.own_alpha > 8)) throw Error(HEDAP_ERR_ARG, "NTT: bad digit layout");
   if (A.z && (inverse || !A.own_alpha || !A.bconv || !A.bconv_sh_offset)) throw Error(HEDAP_ERR_ARG, "NTT: bad ModUp fusion");
   if (A.post && !inverse) throw Error(HEDAP_ERR_ARG, "NTT: post factors apply to the inverse only");
@@ -44,11 +48,11 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   const double limbs = (double)S.n_parts * S.n_limbs - (A.own_alpha ? (double)S.n_parts / A.own_dn * A.own_limit : 0.0);
   ProfScope prof_(PROF_NTT, st, 16.0 * limbs * ((size_t)1 << T.log_n));
   prof_count_launches(2);
-  ntt_launch(T.log_n, v, S, T, st, inverse, A);
+  ntt_launch(T.log_n, v, S, T, st, inverse, A, F);
 }
 
-void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux) {
-  dispatch(T, S, st, false, aux);
+void ntt_forward(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux, const KskFuse* fuse) {
+  dispatch(T, S, st, false, aux, fuse);
 }
 void ntt_inverse(const Tables& T, const LimbSet& S, cudaStream_t st, const NttAux* aux) {
   dispatch(T, S, st, true, aux);

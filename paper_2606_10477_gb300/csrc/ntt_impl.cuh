@@ -456,6 +456,78 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
     a[j0 + idx] = reduce8q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
 }
 
+// ---------------------------------------------------------------- forward, block phase fused with the key inner product
+// The extended digits of a key switch are transformed and immediately consumed by the inner product
+// with the switching key, so the transformed digits are never written.  A CTA owns one ciphertext k,
+// one extended limb t (prime pt) and one run of BPC row blocks; it stages the twiddles of prime pt
+// once and walks the dn digits: the column-phase output of digit j (or, for the digit that owns limb
+// t, the NTT-domain input d itself) is copied into shared memory with cp.async (the next digit's
+// copy in flight while this one computes), the row passes run, and every thread multiplies its
+// words by the two key words of digit j, limb t and adds the products into 128-bit accumulators.
+// One reduction per word at the end; acc[k][0/1][t] are the only stores.  Modular sums do not
+// depend on order, so the result equals the separate transform and inner product bit for bit.
+// Residues entering the products are canonical (< q < 2^61), so the sum of up to 64 products stays
+// below 2^128.
+template <int L1, int L2, int BPC, int TPB, int MINB, int RL>
+__global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows_ksk(Tables T, LimbSet S, NttAux A, KskFuse F) {
+  extern __shared__ u64 sm[];
+  constexpr size_t N = (size_t)1 << (L1 + L2);
+  constexpr int E = BPC << L2, R = (1 << L2) + (1 << (L2 - 4)), PER = E / TPB;
+  u64* buf[2] = {sm, sm + BPC * R};
+  ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + 2 * BPC * R);
+  const int k = blockIdx.x % F.batch, blk = blockIdx.x / F.batch;
+  const int t = S.limb_begin + blockIdx.y, pt = S.prime(t);
+  const u64 q = T.pr[pt].q;
+  const size_t j0 = (size_t)blk * E;
+  const int dn = A.own_dn;
+  const int own = (A.own_alpha && t < A.own_limit) ? t / A.own_alpha : -1;
+  auto fetch = [&](int j, u64* dst) {
+    const u64* src = j == own ? F.d + (size_t)k * F.d_stride + (size_t)t * N + j0
+                              : S.limb(k * dn + j, t, N) + j0;
+    for (int idx = threadIdx.x; idx < E; idx += TPB)
+      cp_async8(dst + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), src + idx);
+  };
+  fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pt * N, (uint32_t)(blk * BPC));
+  fetch(0, buf[0]);
+  cp_async_commit();
+  Acc128 ab[PER], aa[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) ab[i] = aa[i] = Acc128{0, 0};
+  const u64* kb = F.key + (size_t)pt * N + j0;
+  for (int j = 0; j < dn; ++j) {
+    u64* cur = buf[j & 1];
+    if (j + 1 < dn) {
+      fetch(j + 1, buf[(j + 1) & 1]);
+      cp_async_commit();
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    if (j != own) fwd_rows_passes<L1, L2, BPC, RL, 0>(cur, tw, q);
+    const u64* kbj = kb + (size_t)j * F.key_digit_stride;
+    const u64* kaj = kbj + F.key_a_offset;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int idx = threadIdx.x + i * TPB;  // consecutive threads, consecutive words
+      const u64 v = reduce8q(cur[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+      mac128(ab[i], v, __ldg(kbj + idx));
+      mac128(aa[i], v, __ldg(kaj + idx));
+    }
+    __syncthreads();  // every thread is done with `cur` before the copy of digit j + 2 lands there
+  }
+  const PrimeDev P = T.pr[pt];
+  const u64 r64 = F.r64[2 * pt], r64p = F.r64[2 * pt + 1];
+  u64* o0 = F.acc + (size_t)(2 * k) * F.acc_part_stride + (size_t)t * N + j0;
+  u64* o1 = o0 + F.acc_part_stride;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = threadIdx.x + i * TPB;
+    o0[idx] = reduce128(ab[i], P, r64, r64p);
+    o1[idx] = reduce128(aa[i], P, r64, r64p);
+  }
+}
+
 // ---------------------------------------------------------------- inverse, block phase
 // GS stage with pair distance 2^lt (lt < L2): twiddle index 2^(LOGN-lt-1) + (j >> (lt+1)),
 // j >> (lt+1) = ((B0+b) << (L2-lt-1)) + (x >> (lt+1)); groups x = high*2^(LT0+K) + m*2^LT0 + low.
@@ -601,8 +673,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S,
 // allocation must allow (MINB) and the stages per register pass (RL: radix 16 or
 // radix 8, the latter with half the registers per thread); threads per CTA = E / 2^RL.  The autotuner in
 // ntt_tune() times every variant and keeps the fastest per direction.
+// launch shape of the second phase fused with the key inner product (k_ntt_fwd_rows_ksk): 2048 words
+// per CTA, radix-8 passes (256 threads, 8 words and 32 accumulator registers each), 3 CTAs per SM
+constexpr int kKskWords = 2048, kKskMinBlocks = 2, kKskRL = 3;
+
 template <int L1, int L2, int E, int MINB, int RL>
-static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse, const NttAux& A) {
+static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse, const NttAux& A,
+                        const KskFuse* F) {
   constexpr int LOGN = L1 + L2;
   constexpr int EE = E <= (1 << LOGN) ? E : (1 << LOGN);
   constexpr int C = EE >> L1, BPC = EE >> L2, TPB = EE >> RL;
@@ -655,7 +732,22 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
     } else {
       k_ntt_fwd_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A);
     }
-    k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A2);
+    if (F) {
+      constexpr int EK = kKskWords <= (1 << LOGN) ? kKskWords : (1 << LOGN);
+      constexpr int BPCK = EK >> L2, TPBK = EK >> kKskRL;
+      const size_t smem_k = 2 * (size_t)BPCK * ((1 << L2) + (1 << (L2 - 4))) * sizeof(u64) +
+                            (size_t)BPCK * (1 << L2) * sizeof(ulonglong2);
+      static const bool attr_k = [&] {
+        HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_rows_ksk<L1, L2, BPCK, TPBK, kKskMinBlocks, kKskRL>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+        return true;
+      }();
+      (void)attr_k;
+      const dim3 gk((unsigned)(F->batch * (((size_t)1 << LOGN) / EK)), (unsigned)S.n_limbs);
+      k_ntt_fwd_rows_ksk<L1, L2, BPCK, TPBK, kKskMinBlocks, kKskRL><<<gk, TPBK, smem_k, st>>>(T, S, A2, *F);
+    } else {
+      k_ntt_fwd_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A2);
+    }
   } else {
     k_ntt_inv_rows<L1, L2, BPC, TPB, MINB, RL><<<grid, TPB, smem_rows, st>>>(T, S, A);
     k_ntt_inv_cols<L1, L2, C, TPB, MINB, RL><<<grid, TPB, smem_cols, st>>>(T, S, A2);
@@ -665,22 +757,22 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
 
 template <int L1, int L2>
 static void launch_variant(int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                           const NttAux& A) {
+                           const NttAux& A, const KskFuse* F) {
   switch (v) {
-    case 0: launch_pair<L1, L2, 2048, 5, 3>(S, T, st, inverse, A); break;
-    case 1: launch_pair<L1, L2, 4096, 3, 4>(S, T, st, inverse, A); break;
-    case 2: launch_pair<L1, L2, 2048, 4, 4>(S, T, st, inverse, A); break;
-    case 3: launch_pair<L1, L2, 2048, 6, 4>(S, T, st, inverse, A); break;
-    case 4: launch_pair<L1, L2, 2048, 6, 3>(S, T, st, inverse, A); break;
-    case 5: launch_pair<L1, L2, 1024, 12, 3>(S, T, st, inverse, A); break;
-    case 6: launch_pair<L1, L2, 2048, 4, 3>(S, T, st, inverse, A); break;
-    default: launch_pair<L1, L2, 1024, 8, 3>(S, T, st, inverse, A); break;
+    case 0: launch_pair<L1, L2, 2048, 5, 3>(S, T, st, inverse, A, F); break;
+    case 1: launch_pair<L1, L2, 4096, 3, 4>(S, T, st, inverse, A, F); break;
+    case 2: launch_pair<L1, L2, 2048, 4, 4>(S, T, st, inverse, A, F); break;
+    case 3: launch_pair<L1, L2, 2048, 6, 4>(S, T, st, inverse, A, F); break;
+    case 4: launch_pair<L1, L2, 2048, 6, 3>(S, T, st, inverse, A, F); break;
+    case 5: launch_pair<L1, L2, 1024, 12, 3>(S, T, st, inverse, A, F); break;
+    case 6: launch_pair<L1, L2, 2048, 4, 3>(S, T, st, inverse, A, F); break;
+    default: launch_pair<L1, L2, 1024, 8, 3>(S, T, st, inverse, A, F); break;
   }
 }
 
 // one launch pair of the transform at N = 2^log_n (log_n 10 .. 16) with launch shape v; the
 // instantiations are spread over the ntt_inst_*.cu translation units so that they compile in parallel
 void ntt_launch(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                const NttAux& A);
+                const NttAux& A, const KskFuse* F);
 
 }  // namespace hedap

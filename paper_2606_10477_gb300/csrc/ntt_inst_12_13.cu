@@ -4,10 +4,10 @@
 namespace hedap {
 
 void ntt_launch_12_13(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                      const NttAux& A) {
+                      const NttAux& A, const KskFuse* F) {
   switch (log_n) {
-    case 12: launch_variant<6, 6>(v, S, T, st, inverse, A); break;
-    case 13: launch_variant<6, 7>(v, S, T, st, inverse, A); break;
+    case 12: launch_variant<6, 6>(v, S, T, st, inverse, A, F); break;
+    case 13: launch_variant<6, 7>(v, S, T, st, inverse, A, F); break;
     default: throw Error(HEDAP_ERR_ARG, "ring size not instantiated in this unit");
   }
 }

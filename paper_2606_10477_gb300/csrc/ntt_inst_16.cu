@@ -4,9 +4,9 @@
 namespace hedap {
 
 void ntt_launch_16(int log_n, int v, const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse,
-                   const NttAux& A) {
+                   const NttAux& A, const KskFuse* F) {
   switch (log_n) {
-    case 16: launch_variant<8, 8>(v, S, T, st, inverse, A); break;
+    case 16: launch_variant<8, 8>(v, S, T, st, inverse, A, F); break;
     default: throw Error(HEDAP_ERR_ARG, "ring size not instantiated in this unit");
   }
 }
