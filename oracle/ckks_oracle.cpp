@@ -841,6 +841,12 @@ static double clenshaw(const std::vector<double>& c, double t) {
 //   p = q * T_G + r,  q_0 = c_G, q_i = 2 c_{G+i},  r_i = c_i - c_{2G-i} (2G-i <= deg),
 // which follows from 2 T_G T_{j-G} = T_j + T_{2G-j}.  Every partial result is
 // produced at a prescribed (level, scale), so additions never need adjustment.
+// Depth: a degree-d evaluation takes ceil(log2(d+1)) levels (the paper: degree
+// 2^{d_e} - 2 consumes d_e levels, Sec. 4.3).  A polynomial below the baby-step
+// degree is summed as a leaf (constant products of T_1..T_D, one level below its
+// lowest T_j) when that reaches the level asked of it; otherwise it is split too,
+// at the largest power of two G <= D (a baby step), so that constants multiply
+// lower-degree T_j's that have a level to spare.
 struct ChebEval {
   Ctx& C;
   std::map<int, Ct> T;  // index -> T_index(t)
@@ -862,19 +868,31 @@ struct ChebEval {
     for (int g : giants) if (g <= D) G = g;
     return G;
   }
+  // where p of degree D is split: the largest giant step <= D, or, below the baby-step degree, the
+  // largest power of two <= D
+  int split_for(int D) const {
+    if (D >= k) return giant_for(D);
+    int G = 1;
+    while (2 * G <= D) G *= 2;
+    return G;
+  }
+  // output level of p summed as a leaf: one below the lowest of T_1 .. T_D
+  int leaf_level(int D) const {
+    int lv = 1 << 30;
+    for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j).level - 1);
+    return lv;
+  }
+  bool as_leaf(int D, int level) const { return D < k && (D < 2 || leaf_level(D) >= level); }
   // highest level at which p can be produced
   int best_level(const std::vector<double>& p) const {
     int D = deg_of(p);
-    if (D < k) {
-      int lv = 1 << 30;
-      for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j).level - 1);
-      return lv;
-    }
-    int G = giant_for(D);
+    int leaf = D < k ? leaf_level(D) : -(1 << 30);
+    if (D < k && D < 2) return leaf;
+    int G = split_for(D);
     std::vector<double> qp, rp; split(p, G, qp, rp);
     int lq = deg_of(qp) == 0 ? (1 << 30) : best_level(qp);
     int lvl = std::min(std::min(lq, T.at(G).level) - 1, best_level(rp));
-    return lvl;
+    return std::max(leaf, lvl);
   }
   // p at (level + 1, label scale * q_{level+1}) before its final rescale: a leaf is the sum of the
   // unrescaled products c_j T_j plus c_0; an inner node adds the relinearised (q T_G) to the
@@ -882,7 +900,7 @@ struct ChebEval {
   Ct eval_raw(const std::vector<double>& p, int level, double scale) {
     int D = deg_of(p);
     const double raw = scale * (double)C.q[level + 1];
-    if (D < k) {
+    if (as_leaf(D, level)) {
       Ct acc;
       for (int j = 1; j <= D; ++j) {
         const Ct& tj = T.at(j);
@@ -892,7 +910,7 @@ struct ChebEval {
       acc.scale = raw;
       return add_const(C, acc, p[0]);
     }
-    int G = giant_for(D);
+    int G = split_for(D);
     std::vector<double> qp, rp; split(p, G, qp, rp);
     const Ct& tg = T.at(G);
     Ct prod;
@@ -1148,7 +1166,7 @@ static Ct eval_mod(Ctx& C, const Ct& u) {
   for (int i = 0; i < C.bts_r; ++i) c = mul_int(C, add_const(C, mul(C, c, c), -0.5), 2);  // cos 2x = 2 cos^2 x - 1
   return c;
 }
-static int bts_levels(const Ctx& C) { return C.bts_cts + C.bts_r + C.bts_stc + 1 + [&] { int m = 0; while ((1 << m) < C.bts_deg + 1) ++m; return m; }(); }
+static int bts_levels(const Ctx& C) { return C.bts_cts + C.bts_r + C.bts_stc + [&] { int m = 0; while ((1 << m) < C.bts_deg + 1) ++m; return m; }(); }
 // Sparse packing, n = 2^log_slots < N/2 slots: the plaintext is a polynomial in Y = X^(N/2n)
 // and its slots repeat with period n.  After ModRaise the overflow q_0 I is a general
 // polynomial; the sum of the automorphisms that fix the subring (the rotations by multiples of

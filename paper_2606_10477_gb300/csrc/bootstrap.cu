@@ -512,7 +512,7 @@ int bts_setup(Ctx& C, int K, int r, int deg, int cts, int stc) {
     throw Error(HEDAP_ERR_ARG, "invalid bootstrapping parameters");
   int m = 0;
   while ((1 << m) < deg + 1) ++m;
-  const int levels = cts + (m + 1) + r + stc;
+  const int levels = cts + m + r + stc;  // EvalMod: the Chebyshev interpolant (m levels), r double angles
   if (C.L() - levels < 1) throw Error(HEDAP_ERR_LEVEL, "prime chain too short for bootstrapping");
   std::unique_ptr<BtsState> S(new BtsState);
   S->K = K;

@@ -11,7 +11,12 @@
 // degree D >= G is split as p = q T_G + r with
 //   q_0 = c_G, q_i = 2 c_{G+i},  r_i = c_i - c_{2G-i} (when 2G-i <= D),
 // from 2 T_G T_{j-G} = T_j + T_{2G-j}.  Each partial result is produced at a
-// prescribed (level, scale) so that additions never need a correction.
+// prescribed (level, scale) so that additions never need a correction.  The
+// evaluation takes ceil(log2(d+1)) levels (degree 2^{d_e} - 2 in d_e levels, as
+// the paper's libraries, Sec. 4.3): a polynomial below the baby-step degree is a
+// leaf (constant products of T_1..T_D) when that reaches the level asked of it,
+// and is otherwise split again at the largest power of two <= D, so that the
+// constants multiply lower T_j's that have a level to spare.
 #include <cmath>
 
 #include "internal.cuh"
@@ -50,6 +55,14 @@ struct ChebPS {
       if (v <= D) g = v;
     return g;
   }
+  // the split point of a degree-D polynomial: the largest giant step <= D, or, below the baby-step
+  // degree, the largest power of two <= D
+  int split_at(int D) const {
+    if (D >= k) return giant(D);
+    int g = 1;
+    while (2 * g <= D) g *= 2;
+    return g;
+  }
   static void divide(const std::vector<double>& p, int G, std::vector<double>& qt, std::vector<double>& rm) {
     const int D = degree(p);
     qt.assign(D - G + 1, 0.0);
@@ -59,18 +72,23 @@ struct ChebPS {
     for (int i = 0; i < G; ++i)
       if (2 * G - i <= D) rm[i] -= p[2 * G - i];
   }
+  // level of a leaf sum over T_1 .. T_D: one below the lowest of them
+  int leaf_level(int D) const {
+    int lv = INT_MAX;
+    for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j)->level - 1);
+    return lv;
+  }
+  bool leaf_at(int D, int level) const { return D < k && (D < 2 || leaf_level(D) >= level); }
+  // highest level p can be produced at: the better of a leaf (below the baby-step degree) and a split
   int top_level(const std::vector<double>& p) const {
     const int D = degree(p);
-    if (D < k) {
-      int lv = INT_MAX;
-      for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j)->level - 1);
-      return lv;
-    }
-    const int G = giant(D);
+    const int leaf = D < k ? leaf_level(D) : INT_MIN;
+    if (D < k && D < 2) return leaf;
+    const int G = split_at(D);
     std::vector<double> qt, rm;
     divide(p, G, qt, rm);
     const int lq = degree(qt) == 0 ? INT_MAX : top_level(qt);
-    return std::min(std::min(lq, T.at(G)->level) - 1, top_level(rm));
+    return std::max(leaf, std::min(std::min(lq, T.at(G)->level) - 1, top_level(rm)));
   }
   // p at (level + 1, label scale * q_{level+1}) before its final rescale: the leaf sums c_j T_j as
   // unrescaled products plus c_0, an inner node adds the relinearised q T_G to the unrescaled r,
@@ -78,12 +96,12 @@ struct ChebPS {
   CtP eval_raw(const std::vector<double>& p, int level, double scale) {
     const int D = degree(p);
     const double raw = scale * (double)C.primes[level + 1];
-    if (D < k) {  // one pass over T_1 .. T_D (read at level + 1 in place)
+    if (leaf_at(D, level)) {  // one pass over T_1 .. T_D (read at level + 1 in place)
       std::vector<std::pair<const Ct*, double>> terms;
       for (int j = 1; j <= D; ++j) terms.emplace_back(T.at(j).get(), p[j]);
       return ev_lincomb_raw(C, terms, level + 1, scale, p[0]);
     }
-    const int G = giant(D);
+    const int G = split_at(D);
     std::vector<double> qt, rm;
     divide(p, G, qt, rm);
     const Ct& tg = *T.at(G);

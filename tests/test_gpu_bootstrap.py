@@ -12,6 +12,11 @@ import pytest
 import oracle
 from paper_2606_10477_gb300 import hedap, inputs
 
+# levels a bootstrap consumes: CoeffToSlot, the EvalMod interpolant (ceil(log2(deg+1)) levels), the double
+# angles, SlotToCoeff
+BTS_LEVELS = (inputs.BTS["cts"] + inputs.BTS["deg"].bit_length() + inputs.BTS["r"]
+              + inputs.BTS["stc"])
+
 pytestmark = pytest.mark.gpu
 
 
@@ -85,7 +90,7 @@ def test_bootstrap_matches_oracle_and_input(pair12):
     z = inputs.uniform_values(10, o.N // 2, -1, 1) + 1j * inputs.uniform_values(11, o.N // 2, -1, 1)
     gc, oc = level0_pair(g, o, 12, z)
     gb, ob = g.bootstrap(gc), o.bootstrap(oc)
-    assert gb.level == o.n_q - 1 - 16
+    assert gb.level == o.n_q - 1 - BTS_LEVELS
     same(gb, ob)
     assert np.max(np.abs(g.decrypt(gb) - z)) < 1e-4
 
@@ -93,7 +98,7 @@ def test_bootstrap_matches_oracle_and_input(pair12):
 def test_bootstrap_full_size():
     """N = 2^16, 32768 complex slots, log2(QP) = 1555, h = 192."""
     g, lvl = make("bts16", hedap.Context)
-    assert lvl == g.n_q - 1 - 16
+    assert lvl == g.n_q - 1 - BTS_LEVELS
     z = inputs.uniform_values(13, g.N // 2, -1, 1) + 1j * inputs.uniform_values(14, g.N // 2, -1, 1)
     ct = g.encrypt(z, 1, 15)
     b = g.bootstrap_scaled(ct, 1)
@@ -202,7 +207,7 @@ def test_sparse_slot_invsqrt_bit_exact(pair12):
     g, o = pair12
     n = 1 << 8
     a = np.tile(inputs.log_uniform_values(70, n, 1e-4, 1.0), o.N // 2 // n)
-    lvl = o.n_q - 1 - 16
+    lvl = o.n_q - 1 - BTS_LEVELS
     oc = o.encrypt(a, lvl, 71)
     gc = g.ct_import(oc.limbs(), oc.level, oc.scale)
     cfg = (1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63, 8)

@@ -13,6 +13,11 @@ import pytest
 import oracle
 from paper_2606_10477_gb300 import inputs
 
+# levels a bootstrap consumes: CoeffToSlot, the EvalMod interpolant (ceil(log2(deg+1)) levels), the double
+# angles, SlotToCoeff
+BTS_LEVELS = (inputs.BTS["cts"] + inputs.BTS["deg"].bit_length() + inputs.BTS["r"]
+              + inputs.BTS["stc"])
+
 
 @pytest.fixture(scope="module")
 def ctx():
@@ -89,13 +94,13 @@ def test_bootstrap_returns_its_input(ctx):
     z = inputs.uniform_values(9, ctx.N // 2, -1, 1) + 1j * inputs.uniform_values(10, ctx.N // 2, -1, 1)
     ct0 = ctx.mul_const(ctx.encrypt(z, 1, 11), 1.0, q0 / 4096)
     b = ctx.bootstrap(ct0)
-    assert b.level == ctx.n_q - 1 - 16
+    assert b.level == ctx.n_q - 1 - BTS_LEVELS
     assert np.max(np.abs(ctx.decrypt(b) - z)) < 1e-4
 
 
 def test_invsqrt_with_lazy_bootstrapping_reproduces_fp64_model(ctx):
     a = inputs.log_uniform_values(16, ctx.N // 2, 1e-4, 1.0)
-    L_after = ctx.n_q - 1 - 16
+    L_after = ctx.n_q - 1 - BTS_LEVELS
     y = ctx.decrypt(ctx.invsqrt(ctx.encrypt(a, L_after, 17), 1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63)).real
     plain = oracle.plain_invsqrt(a, 1e-4, 1.0, 1.0, 15, 5)
     assert np.max(np.abs(y - plain) / plain) < 1e-4
@@ -170,7 +175,7 @@ def test_encapsulation_bounds_the_mod_raise_overflow(dense):
 def test_dense_secret_bootstrap_returns_its_input(dense):
     z, ct0 = level0(dense, 60)
     b = dense.bootstrap(ct0)
-    assert b.level == dense.n_q - 1 - 16
+    assert b.level == dense.n_q - 1 - BTS_LEVELS
     assert np.max(np.abs(dense.decrypt(b) - z)) < 1e-4
 
 
@@ -200,7 +205,7 @@ def test_sparse_slot_bootstrap_returns_its_input(ctx, ls):
     v = inputs.uniform_values(80 + ls, n, -1, 1) + 1j * inputs.uniform_values(90 + ls, n, -1, 1)
     zt = np.tile(v, half // n)
     b = ctx.bootstrap_slots(ctx.mul_const(ctx.encrypt(zt, 1, 100 + ls), 1.0, q0 / 4096), ls)
-    assert b.level == ctx.n_q - 1 - 16
+    assert b.level == ctx.n_q - 1 - BTS_LEVELS
     out = ctx.decrypt(b)
     assert np.max(np.abs(out - zt)) < 1e-4
     assert np.max(np.abs(out - np.tile(out[:n], half // n))) < 1e-4
@@ -210,7 +215,7 @@ def test_sparse_slot_invsqrt_with_lazy_bootstrapping(ctx):
     n = 1 << 8
     a = inputs.log_uniform_values(110, n, 1e-4, 1.0)
     at = np.tile(a, ctx.N // 2 // n)
-    L_after = ctx.n_q - 1 - 16
+    L_after = ctx.n_q - 1 - BTS_LEVELS
     y = ctx.decrypt(ctx.invsqrt(ctx.encrypt(at, L_after, 111), 1e-4, 1.0, 1.0, 15, 5, 0, 1 << 63, 8)).real
     plain = oracle.plain_invsqrt(at, 1e-4, 1.0, 1.0, 15, 5)
     assert np.max(np.abs(y - plain) / plain) < 1e-4
