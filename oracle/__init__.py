@@ -97,6 +97,7 @@ def _declare(L):
         "orc_bootstrap_scaled_slots": (vp, [vp, vp, C.c_int64, C.c_int]),
         "orc_sub_sum": (vp, [vp, vp, C.c_int]),
         "orc_cheb_coeffs": (C.c_int, [C.c_double, C.c_double, C.c_uint32, f64p]),
+        "orc_cheb_eval": (vp, [vp, vp, f64p, C.c_uint32, C.c_int]),
         "orc_clenshaw": (C.c_double, [f64p, C.c_uint32, C.c_double]),
         "orc_plain_invsqrt": (C.c_int, [f64p, C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_uint32,
                                         C.c_uint32, f64p]),
@@ -402,6 +403,12 @@ class Context:
                                                    re, im, cap))
             out[int(o)] = re[:m] + 1j * im[:m]
         return out
+
+    def cheb_eval(self, t, coeffs, need: int = -1):
+        """sum_j c_j T_j(t) (t in [-1, 1]); need < 0: the fewest-levels plan, else the fewest-products plan
+        when it ends at level >= need."""
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        return Ciphertext(self, lib().orc_cheb_eval(self.h, t.h, c, len(c) - 1, need))
 
     def invsqrt(self, a, lo, hi, B, degree, iters, pre_bts=0, bts_mask=0, log_slots=0):
         return Ciphertext(self, lib().orc_invsqrt(self.h, a.h, lo, hi, B, degree, iters, pre_bts, bts_mask,

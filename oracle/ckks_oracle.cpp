@@ -841,12 +841,15 @@ static double clenshaw(const std::vector<double>& c, double t) {
 //   p = q * T_G + r,  q_0 = c_G, q_i = 2 c_{G+i},  r_i = c_i - c_{2G-i} (2G-i <= deg),
 // which follows from 2 T_G T_{j-G} = T_j + T_{2G-j}.  Every partial result is
 // produced at a prescribed (level, scale), so additions never need adjustment.
-// Depth: a degree-d evaluation takes ceil(log2(d+1)) levels (the paper: degree
-// 2^{d_e} - 2 consumes d_e levels, Sec. 4.3).  A polynomial below the baby-step
-// degree is summed as a leaf (constant products of T_1..T_D, one level below its
-// lowest T_j) when that reaches the level asked of it; otherwise it is split too,
-// at the largest power of two G <= D (a baby step), so that constants multiply
-// lower-degree T_j's that have a level to spare.
+// Two plans.  Fewest products: every polynomial below the baby-step degree is a
+// leaf (constant products of T_1..T_D summed, one level below its lowest T_j);
+// this takes ceil(log2(d+1)) + 1 levels for most d.  Fewest levels: such a
+// polynomial is a leaf only when that reaches the level asked of it, and is
+// otherwise split too, at the largest power of two G <= D (a baby step), so that
+// constants multiply lower-degree T_j's that have a level to spare; a degree-d
+// evaluation then takes ceil(log2(d+1)) levels (the paper: degree 2^{d_e} - 2
+// consumes d_e levels, Sec. 4.3) for a few more products.  run() takes the
+// fewest-products plan when its output level is at least `need`, else the other.
 struct ChebEval {
   Ctx& C;
   std::map<int, Ct> T;  // index -> T_index(t)
@@ -882,12 +885,15 @@ struct ChebEval {
     for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j).level - 1);
     return lv;
   }
-  bool as_leaf(int D, int level) const { return D < k && (D < 2 || leaf_level(D) >= level); }
+  bool fewest_levels = false;  // the plan (see above)
+  bool as_leaf(int D, int level) const {
+    return D < k && (!fewest_levels || D < 2 || leaf_level(D) >= level);
+  }
   // highest level at which p can be produced
   int best_level(const std::vector<double>& p) const {
     int D = deg_of(p);
     int leaf = D < k ? leaf_level(D) : -(1 << 30);
-    if (D < k && D < 2) return leaf;
+    if (D < k && (!fewest_levels || D < 2)) return leaf;
     int G = split_for(D);
     std::vector<double> qp, rp; split(p, G, qp, rp);
     int lq = deg_of(qp) == 0 ? (1 << 30) : best_level(qp);
@@ -944,8 +950,9 @@ struct ChebEval {
     }
     return mul_int(C, diff, 2);
   }
-  Ct run(const Ct& t, const std::vector<double>& coeffs) { return run(t, coeffs, C.scale); }
-  Ct run(const Ct& t, const std::vector<double>& coeffs, double target) {
+  // need < 0: the fewest-levels plan; else the fewest-products plan if it ends at level >= need
+  Ct run(const Ct& t, const std::vector<double>& coeffs, int need) { return run(t, coeffs, C.scale, need); }
+  Ct run(const Ct& t, const std::vector<double>& coeffs, double target, int need) {
     int d = deg_of(coeffs);
     int m = 0; while ((1 << m) < d + 1) ++m;
     int lb = (m + 1) / 2; if (lb < 1) lb = 1;
@@ -960,7 +967,12 @@ struct ChebEval {
       giants.push_back(g);
       if (!T.count(g)) T[g] = cheb_product(T.at(g / 2), T.at(g / 2), 0);
     }
+    fewest_levels = need < 0;
     int lvl = best_level(coeffs);
+    if (!fewest_levels && lvl < need) {
+      fewest_levels = true;
+      lvl = best_level(coeffs);
+    }
     if (lvl < 0) throw std::runtime_error("Chebyshev evaluation: level exhausted");
     return eval(coeffs, lvl, target);
   }
@@ -1162,7 +1174,7 @@ static Ct eval_mod(Ctx& C, const Ct& u) {
   std::vector<double> coeffs = cheb_interp_fn([&](double x) { return std::cos(2.0 * M_PI * (K * x - 0.25) / R); },
                                               -1.0, 1.0, C.bts_deg);
   ChebEval ev(C);
-  Ct c = ev.run(u, coeffs, u.scale);
+  Ct c = ev.run(u, coeffs, u.scale, -1);  // fewest levels: every level of the chain is a level of output
   for (int i = 0; i < C.bts_r; ++i) c = mul_int(C, add_const(C, mul(C, c, c), -0.5), 2);  // cos 2x = 2 cos^2 x - 1
   return c;
 }
@@ -1311,8 +1323,10 @@ static Ct invsqrt(Ctx& C, const Ct& in, const InvSqrtCfg& cfg) {
   Ct t = add_const(C, mul_const_to(C, a, alpha, C.scale), beta);
   Ct x = mul_const_to(C, a, 0.5 / Bf, C.scale);  // ct_x = 0.5 * a/B
   std::vector<double> coeffs = cheb_coeffs(lo, hi, cfg.degree);
+  // with bootstrapping in the configuration, the fewest-levels plan (a level saved is a bootstrap
+  // saved or postponed); without, the fewest products while the Newton steps still fit
   ChebEval ev(C);
-  Ct y = ev.run(t, coeffs);
+  Ct y = ev.run(t, coeffs, (cfg.pre_bts || cfg.bts_mask) ? -1 : 2 * cfg.iters);
   const bool lazy = (cfg.bts_mask >> 63) & 1, lazy_x = (cfg.bts_mask >> 62) & 1;
   i64 Yx = 1; while ((double)Yx < 0.5 * hi) Yx *= 2;
   for (int i = 0; i < cfg.iters; ++i) {
@@ -1541,6 +1555,13 @@ API void* orc_invsqrt(void* c, void* a, double lo, double hi, double B, uint32_t
                       uint32_t pre_bts, uint64_t bts_mask, uint32_t log_slots) {
   InvSqrtCfg cfg{lo, hi, B, (int)degree, (int)iters, (int)pre_bts, bts_mask, (int)log_slots};
   CT_OP(invsqrt(*(Ctx*)c, *(Ct*)a, cfg))
+}
+// sum_j c_j T_j(t) for t in [-1, 1], output at the context scale; need < 0: the fewest-levels plan,
+// else the fewest-products plan when it ends at level >= need
+API void* orc_cheb_eval(void* c, void* t, const double* coeffs, uint32_t d, int need) {
+  std::vector<double> cv(coeffs, coeffs + d + 1);
+  ChebEval ev(*(Ctx*)c);
+  CT_OP(ev.run(*(Ct*)t, cv, need))
 }
 API int orc_cheb_coeffs(double lo, double hi, uint32_t d, double* out) {
   std::vector<double> c = cheb_coeffs(lo, hi, (int)d);

@@ -426,7 +426,7 @@ static std::vector<double> interp(F f, double lo, double hi, int d) {
 
 std::unique_ptr<Ct> eval_mod(Ctx& C, const Ct& u) {
   BtsState& S = state(C);
-  std::unique_ptr<Ct> c = cheb_eval(C, u, S.mod_coeffs, u.scale);
+  std::unique_ptr<Ct> c = cheb_eval(C, u, S.mod_coeffs, u.scale, -1);  // fewest levels
   for (int i = 0; i < S.r; ++i)  // cos 2x = 2 cos^2 x - 1
     c = ev_add_const_mul_int(C, *ev_mul(C, *c, *c), -0.5, 2);
   return c;

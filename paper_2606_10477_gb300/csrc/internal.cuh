@@ -323,7 +323,9 @@ struct InvSqrtRun {
   void newton(int i);
   std::unique_ptr<Ct> result() const;  // y / sqrt(B)
 };
-std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target);
+// sum_j c_j T_j(t) at scale `target`; need < 0: the fewest-levels plan, else the fewest-products plan
+// when it ends at level >= need (invsqrt.cu)
+std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target, int need);
 
 // ------------------------------------------------------------------ selector (selector.cu)
 int getoptiter_rule(const double* M, size_t n, double delta, double* thr_out);

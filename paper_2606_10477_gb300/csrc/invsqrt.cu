@@ -11,12 +11,15 @@
 // degree D >= G is split as p = q T_G + r with
 //   q_0 = c_G, q_i = 2 c_{G+i},  r_i = c_i - c_{2G-i} (when 2G-i <= D),
 // from 2 T_G T_{j-G} = T_j + T_{2G-j}.  Each partial result is produced at a
-// prescribed (level, scale) so that additions never need a correction.  The
-// evaluation takes ceil(log2(d+1)) levels (degree 2^{d_e} - 2 in d_e levels, as
-// the paper's libraries, Sec. 4.3): a polynomial below the baby-step degree is a
-// leaf (constant products of T_1..T_D) when that reaches the level asked of it,
-// and is otherwise split again at the largest power of two <= D, so that the
-// constants multiply lower T_j's that have a level to spare.
+// prescribed (level, scale) so that additions never need a correction.  Two
+// plans: fewest products (every polynomial below the baby-step degree is a leaf,
+// its constant products of T_1..T_D summed at one level below the lowest T_j:
+// ceil(log2(d+1)) + 1 levels for most d) and fewest levels (such a polynomial is
+// a leaf only when that reaches the level asked of it, else it is split again at
+// the largest power of two <= D, so that the constants multiply lower T_j's with
+// a level to spare: ceil(log2(d+1)) levels, i.e. degree 2^{d_e} - 2 in d_e
+// levels as the paper's libraries, Sec. 4.3, for a few more products).  The
+// fewest-products plan is taken when it ends at a level >= `need`.
 #include <cmath>
 
 #include "internal.cuh"
@@ -78,12 +81,14 @@ struct ChebPS {
     for (int j = 1; j <= D; ++j) lv = std::min(lv, T.at(j)->level - 1);
     return lv;
   }
-  bool leaf_at(int D, int level) const { return D < k && (D < 2 || leaf_level(D) >= level); }
-  // highest level p can be produced at: the better of a leaf (below the baby-step degree) and a split
+  bool fewest_levels = false;  // the plan (see above)
+  bool leaf_at(int D, int level) const { return D < k && (!fewest_levels || D < 2 || leaf_level(D) >= level); }
+  // highest level p can be produced at: below the baby-step degree a leaf or (fewest levels) the better
+  // of a leaf and a split
   int top_level(const std::vector<double>& p) const {
     const int D = degree(p);
     const int leaf = D < k ? leaf_level(D) : INT_MIN;
-    if (D < k && D < 2) return leaf;
+    if (D < k && (!fewest_levels || D < 2)) return leaf;
     const int G = split_at(D);
     std::vector<double> qt, rm;
     divide(p, G, qt, rm);
@@ -138,7 +143,7 @@ struct ChebPS {
     }
     return ev_mul_int(C, *diff, 2);
   }
-  CtP run(const Ct& t, const std::vector<double>& coeffs, double target) {
+  CtP run(const Ct& t, const std::vector<double>& coeffs, double target, int need) {
     const int d = degree(coeffs);
     int m = 0;
     while ((1 << m) < d + 1) ++m;
@@ -153,15 +158,20 @@ struct ChebPS {
       giants.push_back(g);
       if (!T.count(g)) T[g] = product(*T.at(g / 2), *T.at(g / 2), 0);
     }
-    const int lvl = top_level(coeffs);
+    fewest_levels = need < 0;
+    int lvl = top_level(coeffs);
+    if (!fewest_levels && lvl < need) {
+      fewest_levels = true;
+      lvl = top_level(coeffs);
+    }
     if (lvl < 0) throw Error(HEDAP_ERR_LEVEL, "Chebyshev evaluation: not enough levels");
     return eval(coeffs, lvl, target);
   }
 };
 
-std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target) {
+std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& coeffs, double target, int need) {
   ChebPS ps(C);
-  return ps.run(t, coeffs, target);
+  return ps.run(t, coeffs, target, need);
 }
 
 // One Newton step in Alg. 1's loop order; tmp_alpha = 1.5 y is produced last, at the level of
@@ -215,7 +225,12 @@ InvSqrtRun::InvSqrtRun(Ctx& C_, const Ct& in, const hedap_invsqrt_cfg& c) : C(C_
   t = ev_add_const(C, *ev_mul_const(C, a, alpha, C.scale), beta);
   x = ev_mul_const(C, a, 0.5 / Bf, C.scale);
 }
-void InvSqrtRun::chebyshev() { y = cheb_eval(C, *t, cheb_interp(lo, hi, (int)cfg.degree), C.scale); }
+// with bootstrapping in the configuration, the fewest-levels plan (a level saved is a bootstrap saved or
+// postponed); without, the fewest products while the Newton steps still fit (two levels each)
+void InvSqrtRun::chebyshev() {
+  const int need = (cfg.pre_bts || cfg.bts_mask) ? -1 : 2 * (int)cfg.newton_iters;
+  y = cheb_eval(C, *t, cheb_interp(lo, hi, (int)cfg.degree), C.scale, need);
+}
 void InvSqrtRun::newton(int i) {
   const bool force = i < 62 && ((cfg.bts_mask >> i) & 1);
   const bool lazy = ((cfg.bts_mask >> 63) & 1) && y->level < 3;

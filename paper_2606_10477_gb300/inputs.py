@@ -23,10 +23,17 @@ PRESETS = {
     "n12a4": dict(log_n=12, q_bits=[40] * 10, p_bits=[60] * 5, alpha=4, log_scale=40, hw=0),
     "n13": dict(log_n=13, q_bits=[50] * 8, p_bits=[60, 60], alpha=2, log_scale=50, hw=0),
     "n10": dict(log_n=10, q_bits=[45, 36, 36, 36, 36, 36], p_bits=[50, 50], alpha=2, log_scale=36, hw=0),
-    # N = 2^16 with bootstrapping: q_0 (60 bits), 10 compute primes (45), SlotToCoeff 3 x 45,
-    # EvalMod 10 x 55, CoeffToSlot 3 x 60, P = 3 x 60; log2(QP) = 1555; sparse ternary secret h = 192
+    # N = 2^16 with bootstrapping: q_0 (60 bits), 10 compute primes (45), 3 x 45, 10 x 55, 3 x 60, P = 3 x 60;
+    # log2(QP) = 1555; sparse ternary secret h = 192.  A bootstrap consumes 15 levels (CoeffToSlot the three
+    # 60-bit primes, EvalMod nine 55-bit ones, SlotToCoeff the last 55-bit and two 45-bit ones), so a
+    # bootstrapped ciphertext sits at level 11
     "bts16": dict(log_n=16, q_bits=[60] + [45] * 10 + [45] * 3 + [55] * 10 + [60] * 3, p_bits=[60] * 3, alpha=3,
                   log_scale=45, hw=192),
+    # N = 2^16 shaped like the paper's HEaaN "FGb" parameters (Delta = 2^42, l_max = 12 after bootstrapping,
+    # Sec. 3): q_0 (60 bits), 12 compute primes (42), SlotToCoeff 3 x 42, EvalMod 9 x 55, CoeffToSlot 3 x 60,
+    # P = 3 x 60; log2(QP) = 1545; sparse ternary secret h = 192
+    "bts16f": dict(log_n=16, q_bits=[60] + [42] * 12 + [42] * 3 + [55] * 9 + [60] * 3, p_bits=[60] * 3, alpha=3,
+                   log_scale=42, hw=192),
     # the same chain shape at N = 2^12, for parity with the CPU oracle
     "bts12": dict(log_n=12, q_bits=[60] + [45] * 8 + [45] * 3 + [55] * 10 + [60] * 3, p_bits=[60] * 3, alpha=3,
                   log_scale=45, hw=192),

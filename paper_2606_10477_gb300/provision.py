@@ -67,6 +67,45 @@ def chebyshev_vs_bts(ctx, lmax, A, B_max, B, degrees, reps=3):
     return rows
 
 
+def table4(ctx, R, levels, A, B_max, B, fixed, reps=3):
+    """Table 4 analogue: at each level, CryptoInvSqrt with HE-DAP's accuracy (u1) and speed (u2) choices
+    against a fixed (degree, Newton steps) configuration (PP-STAT's d = 510, i = 6 in the paper), each with
+    lazy bootstrapping in the Newton loop and Pre-BTS only where the fixed degree needs it; time (CUDA
+    stream synchronised, best of reps after a warm-up) and MRE against FP64 on linspace(A, B_max, N/2)."""
+    import torch
+    vals = np.linspace(A, B_max, ctx.N // 2)
+    ref = 1 / np.sqrt(vals)
+    rows = []
+    for lvl in levels:
+        ct = ctx.encrypt(vals, lvl, 3)
+        cands = [("HE-DAP u1 (accuracy)", r["degree"], r["c"], r["iters"]) for r in R
+                 if r["level"] == lvl and r["kind"] == 1]
+        cands += [("HE-DAP u2 (speed)", r["degree"], r["c"], r["iters"]) for r in R
+                  if r["level"] == lvl and r["kind"] == 2]
+        d, i = fixed
+        for c in (0, 1):
+            try:
+                ctx.invsqrt(ct, A, B_max, B, d, 0, c, 1 << 63)
+            except hedap.HedapError:
+                continue
+            cands.append((f"fixed d={d}, i={i}", d, c, i))
+            break
+        for name, d, c, i in cands:
+            best = float("inf")
+            y = None
+            for _ in range(reps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                out = ctx.invsqrt(ct, A, B_max, B, d, i, c, 1 << 63)
+                ctx.sync()
+                best = min(best, time.perf_counter() - t0)
+                y = ctx.decrypt(out).real
+            mre = float(np.mean(np.abs(y - ref) / ref))
+            rows.append({"level": lvl, "config": name, "degree": d, "c": c, "iters": i, "ms": 1e3 * best,
+                         "mre": mre})
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--preset", default="bts16")
@@ -74,12 +113,14 @@ def main(argv=None):
     ap.add_argument("--B-max", type=float, default=100.0)
     ap.add_argument("--B", type=float, default=100.0)
     ap.add_argument("--de-min", type=int, default=4)
-    ap.add_argument("--de-max", type=int, default=7)
+    ap.add_argument("--de-max", type=int, default=9)
     ap.add_argument("--i-max", type=int, default=15)
     ap.add_argument("--theta", type=float, default=1.0)
     ap.add_argument("--delta", type=float, default=1.0)
     ap.add_argument("--mre-target", type=float, default=1e-7)
     ap.add_argument("--out", default="provisioning.json")
+    ap.add_argument("--table4-levels", default="", help="comma-separated levels for the Table 4 analogue")
+    ap.add_argument("--fixed", default="510,6", help="the fixed (degree, Newton steps) compared in Table 4")
     args = ap.parse_args(argv)
 
     p = inputs.PRESETS[args.preset]
@@ -94,16 +135,19 @@ def main(argv=None):
     explore_s = time.perf_counter() - t0
     table1 = chebyshev_vs_bts(ctx, lmax, args.A, args.B_max, args.B,
                               [(1 << e) - 2 for e in range(args.de_min, args.de_max + 1)]) if p["hw"] else []
+    levels4 = [int(v) for v in args.table4_levels.split(",") if v]
+    fixed = tuple(int(v) for v in args.fixed.split(","))
+    t4 = table4(ctx, R, levels4, args.A, args.B_max, args.B, fixed) if levels4 else []
     out = {
         "key": {"device": device_name(), "preset": args.preset, "params": p, "git": git_revision()},
         "config": vars(args), "l_max": lmax, "exploration_s": explore_s,
-        "R": R, "D": D, "trace": T, "table1": table1,
+        "R": R, "D": D, "trace": T, "table1": table1, "table4": t4,
     }
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps({"exploration_s": explore_s, "levels": sorted({r["level"] for r in R}),
                       "R": [(r["level"], r["kind"], r["degree"], r["c"], r["iters"], r["mre"], round(r["ms"], 2))
-                            for r in R], "table1": table1}))
+                            for r in R], "table1": table1, "table4": t4}))
 
 
 if __name__ == "__main__":

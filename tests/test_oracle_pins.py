@@ -494,23 +494,31 @@ def test_homomorphic_invsqrt_tracks_plain_model():
         y = ctx.decrypt(out).real
         plain = oracle.plain_invsqrt(a, 0.01, 1.0, 1.0, d, k)
         assert np.max(np.abs(y - plain) / plain) < 1e-6
-        depth = 1 + math.ceil(math.log2(d + 1)) + 2 * k
+        # no bootstrapping: the fewest-products Chebyshev plan (ceil(log2(d+1)) + 1 levels for d = 2^m - 1)
+        depth = 1 + (math.ceil(math.log2(d + 1)) + 1) + 2 * k
         assert out.level == 10 - depth
 
 
 @pytest.mark.parametrize("d", [3, 6, 7, 14, 15, 30, 31, 62, 63])
 def test_chebyshev_depth_and_values(d):
-    """The Chebyshev step alone (no Newton step) of a degree-d interpolant takes ceil(log2(d+1))
-    levels after the one level of pre-normalisation -- Sec. 4.3: degree 2^{d_e} - 2 consumes d_e
-    levels (14 -> 4, 30 -> 5, 62 -> 6) -- and decrypts to numpy's chebval of the same coefficients."""
+    """The fewest-levels plan takes ceil(log2(d+1)) levels -- Sec. 4.3: degree 2^{d_e} - 2 consumes d_e
+    levels (14 -> 4, 30 -> 5, 62 -> 6); the fewest-products plan takes one more for these degrees but
+    never more than that; both decrypt to numpy's chebval of the same (random) coefficients."""
     ctx = oracle.Context(10, [50] + [40] * 10, [60], 1, 40, 0, 2)
-    a = np.random.default_rng(30 + d).uniform(0.05, 1, ctx.N // 2)
-    out = ctx.invsqrt(ctx.encrypt(a, 10, 31), 0.05, 1.0, 1.0, d, 0)
-    assert out.level == 10 - 1 - math.ceil(math.log2(d + 1))
-    c = oracle.cheb_coeffs(0.05, 1.0, d)
-    t = (2 * a - 1.05) / 0.95
+    rng = np.random.default_rng(30 + d)
+    t = rng.uniform(-1, 1, ctx.N // 2)
+    c = rng.uniform(-1, 1, d + 1) / (d + 1)
     ref = np.polynomial.chebyshev.chebval(t, c)
-    assert np.max(np.abs(ctx.decrypt(out).real - ref) / ref) < 1e-6
+    ct = ctx.encrypt(t, 10, 31)
+    m = math.ceil(math.log2(d + 1))
+    fewest_levels = ctx.cheb_eval(ct, c, -1)
+    assert fewest_levels.level == 10 - m
+    fewest_products = ctx.cheb_eval(ct, c, 0)
+    assert 10 - m - 1 <= fewest_products.level <= 10 - m
+    # asking the fewest-products plan for more levels than it reaches falls back to the other plan
+    assert ctx.cheb_eval(ct, c, 10 - m).level == 10 - m
+    for out in (fewest_levels, fewest_products):
+        assert np.max(np.abs(ctx.decrypt(out).real - ref)) < 1e-7
 
 
 def test_encapsulation_keys_relation():
