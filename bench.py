@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-level batch workload")
     ap.add_argument("--no-dnum3", action="store_true", help="skip the three-digit key-switching variant")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the degree x Newton-steps sweep")
     ap.add_argument("--serve-queries", type=int, default=48, help="queries in the Poisson serving run")
     ap.add_argument("--only", choices=["ntt", "serving", "mixed", "bts", "hmult", "ops"],
                     help="time only the batched NTT (for kernel profiling) or only the serving workload")
@@ -393,6 +394,7 @@ def run_ours(args):
 
     ntt = measure_ntt(ctx, inputs, torch, stream, 384)
     ops = per_op_us(ctx, inputs, torch, stream, batch)
+    sweep = None if args.no_sweep else config2_sweep(ctx, hedap, inputs, torch, stream, packed, vals)
     bts = None if args.no_bts else bootstrapped_workload(ctx_cls=hedap.Context, inputs=inputs, torch=torch,
                                                          stream=stream, rank=rank, batch=batch)
     mixed = None if args.no_mixed else mixed_workload(hedap, inputs, torch, stream, rank)
@@ -428,6 +430,7 @@ def run_ours(args):
             "graph": graph_info,
             "bootstrapped": bts,
             "dnum3_variant": dnum3,
+            "sweep": sweep,
             "mixed_levels": mixed,
             "serving": serving,
         }
@@ -462,13 +465,29 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, steps=2):
     for k, v in enumerate(vals):
         y = ctx.decrypt(ctx.unpack(out, k)).real
         mres.append(float(np.mean(np.abs(y - 1 / np.sqrt(v)) * np.sqrt(v))))
+    # eager: the batched step launched kernel by kernel
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
+    for _ in range(2):
         ctx.invsqrt(packed, lo, 1.0, 1.0, degree, iters, pre, mask)
     e1.record(stream)
     torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / 2
+    # timed: the batched step captured as a CUDA graph and replayed for at least a second (inputs resident
+    # and larger than L2), clocks sampled during the replays
+    graph = ctx.invsqrt_graph(packed, lo, 1.0, 1.0, degree, iters, pre, mask)
+    graph.run(want_output=False)
+    torch.cuda.synchronize()
+    steps = max(steps, int(np.ceil(1000.0 / max(eager_ms, 1.0))) + 1)
+    clk = ClockSampler()
+    e0.record(stream)
+    for _ in range(steps):
+        graph.run(want_output=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
     ms = e0.elapsed_time(e1) / steps
+    graph.close()
     single = ctx.encrypt(vals[0], lmax, 4000)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(stream)
@@ -503,6 +522,10 @@ def bootstrapped_workload(ctx_cls, inputs, torch, stream, rank, batch, steps=2):
                         f"selector for MRE <= 1e-7, batch {batch}",
             "selected": choice, "select_s": select_s,
             "value": batch * 1e3 / ms, "unit": UNIT, "ms_per_batch": ms, "mre": max(mres),
+            "execution": f"batched step captured as a CUDA graph, {steps} replays timed with CUDA events "
+                         f"({steps * ms / 1e3:.2f} s)", "steps": steps, "clocks": clocks,
+            "eager_value": batch * 1e3 / eager_ms, "plain_value": 1e3 / s0.elapsed_time(s1),
+            "speedup_batched_vs_plain": (batch * 1e3 / ms) / (1e3 / s0.elapsed_time(s1)),
             "plain_ms_per_ct": s0.elapsed_time(s1), "bootstrap_ms": bootstrap_ms, "setup_s": setup_s,
             "bootstrap_sparse_slots": sparse, "bootstrap_dense_secret": dense}
 
@@ -566,33 +589,50 @@ def dnum3_variant(hedap, inputs, torch, stream, rank, batch, degree, iters, step
                         f"primes, batch {batch}", "value": value, "unit": UNIT, "mre": max(mres)}
 
 
-def mixed_workload(hedap, inputs, torch, stream, rank, n_cts=64, band=4):
-    """64 ciphertexts at N=2^16 (the n16 chain: 24 x 50-bit primes) at mixed levels and slot
-    counts: level ~ U{14..23} (15..24 limbs; CryptoInvSqrt with degree 31 and 3 Newton steps takes 13
-    levels and the result must keep one), 2^U{10..15} slots (sparse packing: the values repeated to
-    fill N/2 slots), inputs log-uniform in [1e-3, 1].  Three executions of the same work: one
-    ciphertext per call, batches of equal level, and batches of level bands (dropped to the band's
-    lowest level)."""
-    p = inputs.PRESETS["n16"]
+def mixed_workload(hedap, inputs, torch, stream, rank, n_cts=64):
+    """The batched workload: 64 ciphertexts at N=2^16 at mixed levels and slot counts on the FGb-shaped
+    bootstrapping chain (bts16f, 12 levels after bootstrapping): limbs ~ U{3..13} (levels 2..12, every
+    level a user ciphertext can have on this chain), 2^U{10..15} slots (the values repeated to fill N/2
+    slots), inputs log-uniform in [1e-4, 1].  Each member's (degree, Pre-BTS, Newton steps) is HE-DAP's
+    choice at its level (Alg. 3 on this GPU: u3, the fastest with MRE <= 1e-7, else u1), with lazy
+    bootstrapping.  Executions of the same work: one ciphertext per call (sparse-slot bootstraps),
+    hedap_invsqrt_mixed with per-member slot counts, hedap_invsqrt_mixed with full-slot bootstraps for every
+    member (valid for any packing; larger batches), and the latter captured as one CUDA graph."""
+    p = inputs.PRESETS["bts16f"]
+    b = inputs.BTS
     ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 31 + rank,
                         stream=stream.cuda_stream)
+    lmax = ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    lo = 1e-4
+    s0 = time.perf_counter()
+    _, R, _ = ctx.select(lo, 1.0, 1.0, 4, 5, 8, mre_target=1e-7)
+    select_s = time.perf_counter() - s0
+    table = {}
+    for r in R:
+        if r["kind"] in (1, 3) and (r["level"] not in table or r["kind"] == 3):
+            table[r["level"]] = r
     rng = np.random.default_rng(41 + rank)
-    levels = rng.integers(14, 24, n_cts)
-    slots = 2 ** rng.integers(10, 16, n_cts)
+    levels = rng.integers(2, lmax + 1, n_cts)
+    log_slots = rng.integers(10, 16, n_cts)
     half = ctx.N // 2
-    vals = [inputs.log_uniform_values(5000 + i, int(s), 1e-3, 1.0) for i, s in enumerate(slots)]
+    vals = [inputs.log_uniform_values(5000 + i, 1 << int(s), lo, 1.0) for i, s in enumerate(log_slots)]
     cts = [ctx.encrypt(np.tile(v, half // v.size), int(l), 6000 + i) for i, (v, l) in enumerate(zip(vals, levels))]
-    cfg = (1e-3, 1.0, 1.0, 31, 3, 0, 0)
-    cfgs = [cfg] * n_cts
+    mask = 1 << 63
+
+    def cfg(i, slot_aware):
+        e = table[int(levels[i])]
+        ls = int(log_slots[i]) if slot_aware and int(log_slots[i]) < ctx.log_n - 1 else 0
+        return (lo, 1.0, 1.0, e["degree"], e["iters"], e["c"], mask, ls)
+
+    sparse_cfgs = [cfg(i, True) for i in range(n_cts)]
+    full_cfgs = [cfg(i, False) for i in range(n_cts)]
 
     def timed(fn):
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        t0 = time.perf_counter()
         out = fn()
-        e1.record(stream)
         torch.cuda.synchronize()
-        return out, e0.elapsed_time(e1) / 1e3
+        return out, time.perf_counter() - t0
 
     def mre(outs):
         worst = 0.0
@@ -602,18 +642,72 @@ def mixed_workload(hedap, inputs, torch, stream, rank, n_cts=64, band=4):
         return worst
 
     res = {}
-    ctx.invsqrt_many(cts, cfgs, band)  # warm-up: level constants of every level
-    ctx.invsqrt_many(cts, cfgs, 0)
-    for name, fn in (("plain", lambda: [ctx.invsqrt(c, *cfg) for c in cts]),
-                     ("batched_equal_levels", lambda: ctx.invsqrt_many(cts, cfgs, 0)),
-                     ("batched_level_bands", lambda: ctx.invsqrt_many(cts, cfgs, band))):
+    ctx.invsqrt_mixed(cts, sparse_cfgs)  # warm-up: every level's constants and both kinds of diagonals
+    ctx.invsqrt_mixed(cts, full_cfgs)
+    for name, fn in (("plain", lambda: [ctx.invsqrt(c, *f) for c, f in zip(cts, sparse_cfgs)]),
+                     ("mixed_per_member_slots", lambda: ctx.invsqrt_mixed(cts, sparse_cfgs)),
+                     ("mixed_full_slot_bootstraps", lambda: ctx.invsqrt_mixed(cts, full_cfgs))):
         outs, sec = timed(fn)
         res[name] = {"value": n_cts / sec, "unit": UNIT, "seconds": sec, "max_mre": mre(outs)}
+    graph = ctx.invsqrt_mixed_graph(cts, full_cfgs)
+    graph.run_many(want_output=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record(stream)
+    for _ in range(reps):
+        graph.run_many(want_output=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    outs = graph.run_many(cts)
+    res["graph_full_slot_bootstraps"] = {"value": n_cts / sec, "unit": UNIT, "seconds": sec, "max_mre": mre(outs),
+                                         "kernels_per_replay": graph.kernels}
+    graph.close()
     ctx.close()
-    res["workload"] = (f"{n_cts} ciphertexts, N=2^16 n16 chain, levels U{{14..23}}, slots 2^U{{10..15}}, inputs "
-                       f"log-U[1e-3,1], CryptoInvSqrt degree 31, 3 Newton steps; level band {band}")
-    res["speedup_bands_vs_plain"] = res["batched_level_bands"]["value"] / res["plain"]["value"]
+    res["workload"] = (f"{n_cts} ciphertexts, N=2^16 FGb-shaped chain (log2 QP 1545, l_max {lmax}), levels "
+                       f"U{{2..{lmax}}}, slots 2^U{{10..15}}, inputs log-U[1e-4,1], per-level (d, c, i) from HE-DAP's "
+                       f"table on this GPU, lazy bootstrapping")
+    res["table"] = {int(k): (v["degree"], v["c"], v["iters"], v["kind"]) for k, v in sorted(table.items())}
+    res["select_s"] = select_s
+    res["speedup_mixed_vs_plain"] = res["mixed_full_slot_bootstraps"]["value"] / res["plain"]["value"]
+    res["speedup_graph_vs_plain"] = res["graph_full_slot_bootstraps"]["value"] / res["plain"]["value"]
     return res
+
+
+def config2_sweep(ctx, hedap, inputs, torch, stream, packed, vals, degrees=(7, 15, 31, 63), iters=(1, 2, 3, 4)):
+    """The N=2^16 workload's sweep: Chebyshev degree d x Newton steps k on the same resident batch, each
+    point with its decrypted MRE (worst member), output level, batched device time per step (CUDA events,
+    best of 3 after a warm-up) and its per-kernel-class device time (event profiler, one run)."""
+    rows = []
+    for d in degrees:
+        for k in iters:
+            out = ctx.invsqrt(packed, LO, HI, B, d, k)
+            worst = 0.0
+            for m, v in enumerate(vals):
+                y = ctx.decrypt(ctx.unpack(out, m)).real
+                worst = max(worst, float(np.mean(np.abs(y * np.sqrt(v) - 1))))
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.invsqrt(packed, LO, HI, B, d, k)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            hedap.profile_enable(True)
+            ctx.invsqrt(packed, LO, HI, B, d, k)
+            torch.cuda.synchronize()
+            prof = hedap.profile_read()
+            hedap.profile_enable(False)
+            rows.append({"degree": d, "newton_iters": k, "mre": worst, "meets_target": worst <= MRE_TARGET,
+                         "output_level": out.level, "ms_per_batch": best, "ct_per_s": packed.batch * 1e3 / best,
+                         "class_ms": {c: round(v[1], 3) for c, v in prof.items() if v[0] > 0}})
+    ok = [r for r in rows if r["meets_target"]]
+    fastest = max(ok, key=lambda r: r["ct_per_s"]) if ok else None
+    return {"batch": packed.batch, "rows": rows,
+            "fastest_meeting_target": {"degree": fastest["degree"], "newton_iters": fastest["newton_iters"],
+                                       "ct_per_s": fastest["ct_per_s"], "mre": fastest["mre"]} if fastest else None}
 
 
 SERVE_RECORDS = [1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20]
@@ -690,11 +784,12 @@ def serving_workload(hedap, inputs, torch, stream, rank, n_queries, max_batch=8)
             ids.append(submit(srv, kind, k))
         groups = [srv.poll(i)[2]["group_size"] for i in ids]
         st = srv.stats()
+        merged = srv.merges()
         srv.close()
         records = sum(pool[k][0] for _, k in queries)
         return {"load": frac, "arrival_rate_qps": rate, "queries": m, "qps": st["qps"], "p50_ms": st["p50_ms"],
                 "p99_ms": st["p99_ms"], "records_per_s": records * st["qps"] / m,
-                "mean_group_size": float(np.mean(groups))}
+                "mean_group_size": float(np.mean(groups)), "merged_groups": merged}
 
     main = poisson(0.75, n_queries)
     sweep = [poisson(f, n_queries) for f in (0.25, 0.5, 0.9)]

@@ -47,7 +47,8 @@ typedef enum {
   HEDAP_ERR_CUDA = -5,     /* a CUDA runtime call failed                             */
   HEDAP_ERR_TIMEOUT = -6,  /* a bounded device wait ran out                          */
   HEDAP_ERR_RANGE = -7,    /* input values outside the configured interval           */
-  HEDAP_ERR_KEY = -8       /* a required switching key was not generated             */
+  HEDAP_ERR_KEY = -8,      /* a required switching key was not generated             */
+  HEDAP_ERR_CANCELLED = -9 /* the query was withdrawn (hedap_server_cancel)          */
 } hedap_status;
 
 typedef struct hedap_ctx hedap_ctx;
@@ -191,6 +192,18 @@ hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, cons
  * input's own level).  level_band = 0 is hedap_invsqrt_batch. */
 hedap_status hedap_invsqrt_many(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
                                 int level_band, hedap_ct** out);
+
+/* As hedap_invsqrt_batch, for single inputs each at its own level and with its
+ * own configuration, none dropped to a lower level: inputs with equal level,
+ * scale and configuration form a batch (input order, up to 16); after every
+ * stage of CryptoInvSqrt (the pre-normalisation with its Pre-BTS, the
+ * Chebyshev step, each Newton step) batches of one configuration whose carried
+ * ciphertexts stand at equal levels and scales merge (up to 16).  Inputs at
+ * different levels meet where Alg. 1 brings them to one level: after a Pre-BTS
+ * (c = 1), every input is at the bootstrapped level.  out[i] equals
+ * hedap_invsqrt of in[i] alone, bit for bit.  On error every out[i] is NULL. */
+hedap_status hedap_invsqrt_mixed(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
+                                 hedap_ct** out);
 
 /* HE-DAP provisioning (Sec. 4.2): Alg. 2 GetOptIter and Alg. 3, run on this
  * library with CUDA-event costs.  For every profiled level l (l_BTS + 1 up to
@@ -361,10 +374,14 @@ hedap_status hedap_rescale_noalloc(hedap_ctx* ctx, const uint64_t* in, int level
  * oldest waiting query is admitted with the later ones that can share its
  * group (one kind, input level, input scale and InvSqrt configuration; up to
  * max_batch) while the estimated device memory of the admitted queries stays
- * within hbm_budget_bytes; each group is
- * advanced step by step, interleaved with the other groups in flight, each
- * step one batched operation over the group.  A query's result is bit for
- * bit the same whatever other queries share its group.
+ * within hbm_budget_bytes.  Each group runs on a CUDA stream of its own, one
+ * batched step at a time (statistics, pre-normalisation, Chebyshev, each
+ * Newton step, the final product), the next step issued when the previous one
+ * has finished on the device, so the groups in flight overlap on the GPU.  At
+ * each step boundary, groups with the same signature at the same step merge
+ * into one batch (up to max_batch); a group waits up to 3 steps for a later
+ * one with its signature to catch up.  A query's result is bit for bit the
+ * same whatever other queries share its group.
  *   z-score: x = n_ct ciphertexts holding the records in their slots (unused
  *     slots zero); result: n_ct ciphertexts z = (x - mean) * InvSqrt(var).
  *   PCC: x and y as above, record k of x paired with record k of y;
@@ -394,9 +411,10 @@ hedap_status hedap_rescale_noalloc(hedap_ctx* ctx, const uint64_t* in, int level
 typedef struct hedap_server hedap_server;
 enum { HEDAP_QUERY_ZSCORE = 1, HEDAP_QUERY_PCC = 2 };
 typedef struct {
-  uint32_t max_batch;
+  uint32_t max_batch;        /* queries in one group, after merges too: [1, 16] */
   uint32_t start_paused;
   uint64_t hbm_budget_bytes;
+  uint32_t admit_max;        /* queries admitted into one new group (0: max_batch); merges grow it later */
 } hedap_server_cfg;
 typedef struct {
   uint32_t kind;                 /* HEDAP_QUERY_ZSCORE or HEDAP_QUERY_PCC */
@@ -413,6 +431,25 @@ hedap_status hedap_server_submit(hedap_server* s, const hedap_query* q, uint64_t
 hedap_status hedap_server_poll(hedap_server* s, uint64_t id, int wait, int* done, hedap_ct** out, size_t cap,
                                size_t* n_out, double* latency_ms, uint32_t* group_size);
 hedap_status hedap_server_resume(hedap_server* s);
+/* Failure handling on the host (none of it touches the GPU).
+ * hedap_server_wait: blocks until query `id` is done or timeout_ms passes
+ *   (HEDAP_ERR_TIMEOUT; the query goes on); the result is then taken with
+ *   hedap_server_poll.
+ * hedap_server_cancel: withdraws a query that is not done: a waiting one at
+ *   once, one in flight at its group's next step boundary (a group whose every
+ *   query is withdrawn is dropped; otherwise the others finish unchanged).  Its
+ *   poll then reports HEDAP_ERR_CANCELLED; HEDAP_ERR_ARG for an unknown or
+ *   finished query.
+ * hedap_server_inject: fault injection; HEDAP_FAULT_ADMISSION_OOM makes the
+ *   next `count` admitted groups fail as a device allocation failure at
+ *   admission would: their queries end with HEDAP_ERR_OOM, their memory budget
+ *   is released and the server goes on with the others.
+ * hedap_server_merges: how many groups have been merged into others. */
+enum { HEDAP_FAULT_ADMISSION_OOM = 1 };
+hedap_status hedap_server_wait(hedap_server* s, uint64_t id, double timeout_ms);
+hedap_status hedap_server_cancel(hedap_server* s, uint64_t id);
+hedap_status hedap_server_inject(hedap_server* s, uint32_t fault, uint32_t count);
+hedap_status hedap_server_merges(hedap_server* s, uint64_t* merged);
 /* HE-DAP in serving: install the per-level table R of hedap_select (entries of
  * kind 1, 2, 3 = u1 accuracy, u2 speed, u3 absolute MRE target; copied).  A
  * query with choice k takes (degree, Pre-BTS c, Newton steps) from the kind-k
@@ -441,6 +478,16 @@ typedef struct hedap_graph hedap_graph;
 hedap_status hedap_invsqrt_graph_create(hedap_ctx* ctx, const hedap_ct* example, const hedap_invsqrt_cfg* cfg,
                                         hedap_graph** out);
 hedap_status hedap_graph_run(hedap_graph* g, const hedap_ct* in, hedap_ct** out);
+/* hedap_invsqrt_mixed as one CUDA graph: captured for the examples' levels and
+ * scales (n single ciphertexts) and configurations; the graph owns n input and
+ * n output buffers.  hedap_graph_run_many copies in[0..n) (if in is not NULL;
+ * each with its example's level and scale, else HEDAP_ERR_ARG) into the inputs,
+ * replays, and (if out is not NULL) returns n new ciphertexts, equal bit for
+ * bit to hedap_invsqrt_mixed's.  hedap_graph_run refuses such a graph and
+ * hedap_graph_run_many a graph of one input. */
+hedap_status hedap_invsqrt_mixed_graph_create(hedap_ctx* ctx, const hedap_ct* const* examples,
+                                              const hedap_invsqrt_cfg* cfgs, size_t n, hedap_graph** out);
+hedap_status hedap_graph_run_many(hedap_graph* g, const hedap_ct* const* in, size_t n, hedap_ct** out);
 hedap_status hedap_graph_kernels(const hedap_graph* g, uint64_t* n);
 void hedap_graph_destroy(hedap_graph* g);
 

@@ -31,6 +31,10 @@ hedap_status guarded(F&& f) {
 template <class F>
 hedap_status guarded_on(const hedap_ctx* ctx, F&& f) {
   if (!ctx) return guarded(std::forward<F>(f));
+  if (ctx->magic != kCtxMagic || !ctx->c) {
+    g_last_error = "not a live context handle";
+    return HEDAP_ERR_ARG;
+  }
   std::lock_guard<std::mutex> lk(ctx->c->mu);
   return guarded(std::forward<F>(f));
 }
@@ -45,6 +49,16 @@ hedap_ct* wrap(std::unique_ptr<hedap::Ct> c) {
 }  // namespace
 
 namespace hedap {
+Ct& ct_of(const hedap_ctx* ctx, const hedap_ct* h) {
+  if (!h) throw Error(HEDAP_ERR_ARG, "null ciphertext");
+  if (h->magic != kCtMagic || !h->c) throw Error(HEDAP_ERR_ARG, "not a live ciphertext handle");
+  if (ctx && h->c->owner != ctx->c) throw Error(HEDAP_ERR_ARG, "ciphertext made by another context");
+  return *h->c;
+}
+Ctx& ctx_of(const hedap_ctx* ctx) {
+  if (!ctx || ctx->magic != kCtxMagic || !ctx->c) throw Error(HEDAP_ERR_ARG, "not a live context handle");
+  return *ctx->c;
+}
 void set_last_error(const std::string& m) { g_last_error = m; }
 hedap_status run_on_ctx(const hedap_ctx* ctx, const std::function<void()>& f) { return guarded_on(ctx, f); }
 }  // namespace hedap
@@ -62,6 +76,7 @@ API const char* hedap_status_str(hedap_status s) {
     case HEDAP_ERR_TIMEOUT: return "device wait timed out";
     case HEDAP_ERR_RANGE: return "input out of range";
     case HEDAP_ERR_KEY: return "missing switching key";
+    case HEDAP_ERR_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }
@@ -72,11 +87,11 @@ API hedap_status hedap_ctx_create(const hedap_params* params, uint64_t seed, voi
     need(params && out, "null argument");
     *out = nullptr;
     hedap::Ctx* c = hedap::ctx_create(*params, seed, (cudaStream_t)cuda_stream);
-    *out = new hedap_ctx{c};
+    *out = new hedap_ctx(c);
   });
 }
 API void hedap_ctx_destroy(hedap_ctx* ctx) {
-  if (!ctx) return;
+  if (!ctx || ctx->magic != kCtxMagic) return;  // not a live context handle: ignored
   cudaStream_t s = ctx->c->stream;
   delete ctx->c;
   cudaStreamSynchronize(s);
@@ -135,7 +150,7 @@ API hedap_status hedap_decrypt(hedap_ctx* ctx, const hedap_ct* ct, double* re, d
     need(ctx && ct && re, "null argument");
     need(n_slots == ctx->c->N / 2, "n_slots must equal N/2");
     std::vector<double> r, i;
-    hedap::decrypt(*ctx->c, *ct->c, r, i);
+    hedap::decrypt(*ctx->c, hedap::ct_of(ctx, ct), r, i);
     std::memcpy(re, r.data(), n_slots * 8);
     if (im) std::memcpy(im, i.data(), n_slots * 8);
   });
@@ -170,22 +185,24 @@ API hedap_status hedap_ct_export(hedap_ctx* ctx, const hedap_ct* ct, uint64_t* o
   return guarded_on(ctx, [&] {
     need(ctx && ct && out, "null argument");
     hedap::Ctx& C = *ctx->c;
-    const size_t per = (size_t)(ct->c->level + 1) * C.N;
+    const size_t per = (size_t)(hedap::ct_of(ctx, ct).level + 1) * C.N;
     need(cap >= 2 * per, "capacity too small");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    HEDAP_CUDA(cudaMemcpyAsync(out, ct->c->part(0), per * 8, kind, C.stream));
-    HEDAP_CUDA(cudaMemcpyAsync(out + per, ct->c->part(1), per * 8, kind, C.stream));
+    HEDAP_CUDA(cudaMemcpyAsync(out, hedap::ct_of(ctx, ct).part(0), per * 8, kind, C.stream));
+    HEDAP_CUDA(cudaMemcpyAsync(out + per, hedap::ct_of(ctx, ct).part(1), per * 8, kind, C.stream));
     if (!on_device) HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   });
 }
 API hedap_status hedap_ct_info(const hedap_ct* ct, int* level, double* scale) {
   return guarded([&] {
     need(ct, "null argument");
-    if (level) *level = ct->c->level;
-    if (scale) *scale = ct->c->scale;
+    if (level) *level = hedap::ct_of(nullptr, ct).level;
+    if (scale) *scale = hedap::ct_of(nullptr, ct).scale;
   });
 }
-API void hedap_ct_free(hedap_ct* ct) { delete ct; }
+API void hedap_ct_free(hedap_ct* ct) {
+  if (ct && ct->magic == kCtMagic) delete ct;  // anything else is not a live handle: ignored
+}
 
 #define CT_OP(...)                                  \
   return guarded_on(ctx, [&] {                      \
@@ -195,19 +212,19 @@ API void hedap_ct_free(hedap_ct* ct) { delete ct; }
   })
 
 API hedap_status hedap_add(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
-  CT_OP((need(a && b, "null ciphertext"), hedap::ev_add(*ctx->c, *a->c, *b->c, false)));
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_add(*ctx->c, hedap::ct_of(ctx, a), hedap::ct_of(ctx, b), false)));
 }
 API hedap_status hedap_sub(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
-  CT_OP((need(a && b, "null ciphertext"), hedap::ev_add(*ctx->c, *a->c, *b->c, true)));
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_add(*ctx->c, hedap::ct_of(ctx, a), hedap::ct_of(ctx, b), true)));
 }
 API hedap_status hedap_mul_relin(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
-  CT_OP((need(a && b, "null ciphertext"), hedap::ev_mul_relin(*ctx->c, *a->c, *b->c)));
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_mul_relin(*ctx->c, hedap::ct_of(ctx, a), hedap::ct_of(ctx, b))));
 }
 API hedap_status hedap_mul(hedap_ctx* ctx, const hedap_ct* a, const hedap_ct* b, hedap_ct** out) {
-  CT_OP((need(a && b, "null ciphertext"), hedap::ev_mul(*ctx->c, *a->c, *b->c)));
+  CT_OP((need(a && b, "null ciphertext"), hedap::ev_mul(*ctx->c, hedap::ct_of(ctx, a), hedap::ct_of(ctx, b))));
 }
 API hedap_status hedap_rescale(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::ev_rescale(*ctx->c, *a->c)));
+  CT_OP((need(a, "null ciphertext"), hedap::ev_rescale(*ctx->c, hedap::ct_of(ctx, a))));
 }
 API hedap_status hedap_rotate_hoisted(hedap_ctx* ctx, const hedap_ct* a, const int64_t* steps, size_t n,
                                       hedap_ct** out) {
@@ -215,30 +232,30 @@ API hedap_status hedap_rotate_hoisted(hedap_ctx* ctx, const hedap_ct* a, const i
     need(ctx && a && steps && out && n > 0, "null argument");
     std::vector<uint64_t> gs;
     for (size_t i = 0; i < n; ++i) gs.push_back(hedap::galois_for_rotation(*ctx->c, steps[i]));
-    auto r = hedap::ev_galois_hoisted(*ctx->c, *a->c, gs);
+    auto r = hedap::ev_galois_hoisted(*ctx->c, hedap::ct_of(ctx, a), gs);
     for (size_t i = 0; i < n; ++i) out[i] = wrap(std::move(r[i]));
   });
 }
 API hedap_status hedap_rotate(hedap_ctx* ctx, const hedap_ct* a, int64_t steps, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, *a->c, hedap::galois_for_rotation(*ctx->c, steps))));
+  CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, hedap::ct_of(ctx, a), hedap::galois_for_rotation(*ctx->c, steps))));
 }
 API hedap_status hedap_conjugate(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, *a->c, 2 * ctx->c->N - 1)));
+  CT_OP((need(a, "null ciphertext"), hedap::ev_galois(*ctx->c, hedap::ct_of(ctx, a), 2 * ctx->c->N - 1)));
 }
 API hedap_status hedap_mul_const(hedap_ctx* ctx, const hedap_ct* a, double c, double target_scale, hedap_ct** out) {
-  CT_OP((need(a && target_scale > 0, "bad argument"), hedap::ev_mul_const(*ctx->c, *a->c, c, target_scale)));
+  CT_OP((need(a && target_scale > 0, "bad argument"), hedap::ev_mul_const(*ctx->c, hedap::ct_of(ctx, a), c, target_scale)));
 }
 API hedap_status hedap_add_const(hedap_ctx* ctx, const hedap_ct* a, double c, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::ev_add_const(*ctx->c, *a->c, c)));
+  CT_OP((need(a, "null ciphertext"), hedap::ev_add_const(*ctx->c, hedap::ct_of(ctx, a), c)));
 }
 API hedap_status hedap_mul_int(hedap_ctx* ctx, const hedap_ct* a, int64_t m, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::ev_mul_int(*ctx->c, *a->c, m)));
+  CT_OP((need(a, "null ciphertext"), hedap::ev_mul_int(*ctx->c, hedap::ct_of(ctx, a), m)));
 }
 API hedap_status hedap_drop_level(hedap_ctx* ctx, const hedap_ct* a, int level, hedap_ct** out) {
-  CT_OP((need(a && level >= 0 && level <= a->c->level, "bad level"), hedap::ev_drop(*ctx->c, *a->c, level)));
+  CT_OP((need(a && level >= 0 && level <= a->c->level, "bad level"), hedap::ev_drop(*ctx->c, hedap::ct_of(ctx, a), level)));
 }
 API hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_invsqrt_cfg* cfg, hedap_ct** out) {
-  CT_OP((need(in && cfg, "null argument"), hedap::invsqrt(*ctx->c, *in->c, *cfg)));
+  CT_OP((need(in && cfg, "null argument"), hedap::invsqrt(*ctx->c, hedap::ct_of(ctx, in), *cfg)));
 }
 API hedap_status hedap_ntt(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, uint32_t first_prime, int inverse,
                            int on_device) {
@@ -349,44 +366,44 @@ API hedap_status hedap_bootstrap_encapsulate(hedap_ctx* ctx, uint32_t h) {
 }
 API hedap_status hedap_encapsulation_switch(hedap_ctx* ctx, const hedap_ct* a, int to_sparse, hedap_ct** out) {
   CT_OP((need(a && ctx->c->enc_hw, "null ciphertext or no encapsulation"),
-         hedap::ev_switch_key(*ctx->c, *a->c, to_sparse ? hedap::kKeyToSparse : hedap::kKeyToDense)));
+         hedap::ev_switch_key(*ctx->c, hedap::ct_of(ctx, a), to_sparse ? hedap::kKeyToSparse : hedap::kKeyToDense)));
 }
 API hedap_status hedap_bootstrap_slots(hedap_ctx* ctx, const hedap_ct* a, uint32_t log_slots, hedap_ct** out) {
   CT_OP((need(a && log_slots >= 1 && log_slots < 31, "bad argument"),
-         hedap::bootstrap_core(*ctx->c, *a->c, (int)log_slots)));
+         hedap::bootstrap_core(*ctx->c, hedap::ct_of(ctx, a), (int)log_slots)));
 }
 API hedap_status hedap_bootstrap_scaled_slots(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, uint32_t log_slots,
                                               hedap_ct** out) {
   CT_OP((need(a && Y >= 1 && log_slots >= 1 && log_slots < 31, "bad argument"),
-         hedap::bootstrap_scaled(*ctx->c, *a->c, Y, (int)log_slots)));
+         hedap::bootstrap_scaled(*ctx->c, hedap::ct_of(ctx, a), Y, (int)log_slots)));
 }
 API hedap_status hedap_sub_sum(hedap_ctx* ctx, const hedap_ct* a, uint32_t log_slots, hedap_ct** out) {
-  CT_OP((need(a && log_slots < 31, "bad argument"), hedap::sub_sum(*ctx->c, *a->c, (size_t)1 << log_slots)));
+  CT_OP((need(a && log_slots < 31, "bad argument"), hedap::sub_sum(*ctx->c, hedap::ct_of(ctx, a), (size_t)1 << log_slots)));
 }
 API hedap_status hedap_bootstrap(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::bootstrap_core(*ctx->c, *a->c)));
+  CT_OP((need(a, "null ciphertext"), hedap::bootstrap_core(*ctx->c, hedap::ct_of(ctx, a))));
 }
 API hedap_status hedap_bootstrap_scaled(hedap_ctx* ctx, const hedap_ct* a, int64_t Y, hedap_ct** out) {
-  CT_OP((need(a && Y >= 1, "bad argument"), hedap::bootstrap_scaled(*ctx->c, *a->c, Y)));
+  CT_OP((need(a && Y >= 1, "bad argument"), hedap::bootstrap_scaled(*ctx->c, hedap::ct_of(ctx, a), Y)));
 }
 API hedap_status hedap_mod_raise(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::mod_raise(*ctx->c, *a->c)));
+  CT_OP((need(a, "null ciphertext"), hedap::mod_raise(*ctx->c, hedap::ct_of(ctx, a))));
 }
 API hedap_status hedap_mul_monomial(hedap_ctx* ctx, const hedap_ct* a, uint64_t e, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::mul_monomial(*ctx->c, *a->c, e)));
+  CT_OP((need(a, "null ciphertext"), hedap::mul_monomial(*ctx->c, hedap::ct_of(ctx, a), e)));
 }
 API hedap_status hedap_bts_linear_transform(hedap_ctx* ctx, const hedap_ct* a, int inverse, int group,
                                             double target_scale, hedap_ct** out) {
   CT_OP((need(a && target_scale > 0, "bad argument"),
-         hedap::bts_linear_transform(*ctx->c, *a->c, inverse != 0, group, target_scale)));
+         hedap::bts_linear_transform(*ctx->c, hedap::ct_of(ctx, a), inverse != 0, group, target_scale)));
 }
 API hedap_status hedap_eval_mod(hedap_ctx* ctx, const hedap_ct* a, hedap_ct** out) {
-  CT_OP((need(a, "null ciphertext"), hedap::eval_mod(*ctx->c, *a->c)));
+  CT_OP((need(a, "null ciphertext"), hedap::eval_mod(*ctx->c, hedap::ct_of(ctx, a))));
 }
 API hedap_status hedap_set_scale(hedap_ctx* ctx, hedap_ct* a, double scale) {
   return guarded_on(ctx, [&] {
     need(ctx && a && scale > 0, "bad argument");
-    a->c->scale = scale;
+    hedap::ct_of(ctx, a).scale = scale;
   });
 }
 API hedap_status hedap_encode(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, double scale,
@@ -420,18 +437,18 @@ API hedap_status hedap_batch_pack(hedap_ctx* ctx, const hedap_ct* const* cts, si
     std::vector<const hedap::Ct*> v;
     for (size_t i = 0; i < n; ++i) {
       need(cts[i] != nullptr, "null ciphertext");
-      v.push_back(cts[i]->c.get());
+      v.push_back(&hedap::ct_of(ctx, cts[i]));
     }
     *out = wrap(hedap::batch_pack(*ctx->c, v));
   });
 }
 API hedap_status hedap_batch_unpack(hedap_ctx* ctx, const hedap_ct* batch, size_t index, hedap_ct** out) {
-  CT_OP((need(batch != nullptr, "null ciphertext"), hedap::batch_unpack(*ctx->c, *batch->c, (int)index)));
+  CT_OP((need(batch != nullptr, "null ciphertext"), hedap::batch_unpack(*ctx->c, hedap::ct_of(ctx, batch), (int)index)));
 }
 API hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n) {
   return guarded([&] {
     need(ct && n, "null argument");
-    *n = ct->c->batch;
+    *n = hedap::ct_of(nullptr, ct).batch;
   });
 }
 // groups of inputs run as one batch: equal scale and configuration, and equal level (band = 0)
@@ -442,25 +459,25 @@ static void invsqrt_grouped(hedap_ctx* ctx, const hedap_ct* const* in, const hed
   need(ctx && in && cfgs && out && band >= 0, "bad argument");
   for (size_t i = 0; i < n; ++i) out[i] = nullptr;
   hedap::Ctx& C = *ctx->c;
-  auto key = [&](size_t i) { return band ? in[i]->c->level / band : in[i]->c->level; };
+  auto key = [&](size_t i) { return band ? hedap::ct_of(ctx, in[i]).level / band : hedap::ct_of(ctx, in[i]).level; };
   std::vector<bool> done(n, false);
   try {
-    for (size_t i = 0; i < n; ++i) need(in[i] != nullptr && in[i]->c->batch == 1, "inputs must be single ciphertexts");
+    for (size_t i = 0; i < n; ++i) need(in[i] != nullptr && hedap::ct_of(ctx, in[i]).batch == 1, "inputs must be single ciphertexts");
     for (size_t i = 0; i < n; ++i) {
       if (done[i]) continue;
       std::vector<size_t> g{i};
       for (size_t j = i + 1; j < n && g.size() < 16; ++j) {
         if (done[j]) continue;
-        const hedap::Ct &a = *in[i]->c, &b = *in[j]->c;
+        const hedap::Ct &a = hedap::ct_of(ctx, in[i]), &b = hedap::ct_of(ctx, in[j]);
         if (key(i) == key(j) && a.scale == b.scale && hedap::same_cfg(cfgs[i], cfgs[j]))
           g.push_back(j);
       }
       int lmin = INT_MAX;
-      for (size_t j : g) lmin = std::min(lmin, in[j]->c->level);
+      for (size_t j : g) lmin = std::min(lmin, hedap::ct_of(ctx, in[j]).level);
       std::vector<std::unique_ptr<hedap::Ct>> dropped;
       std::vector<const hedap::Ct*> v;
       for (size_t j : g) {
-        const hedap::Ct& a = *in[j]->c;
+        const hedap::Ct& a = hedap::ct_of(ctx, in[j]);
         if (a.level == lmin) {
           v.push_back(&a);
         } else {
@@ -489,6 +506,17 @@ API hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, 
 API hedap_status hedap_invsqrt_many(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,
                                     int level_band, hedap_ct** out) {
   return guarded_on(ctx, [&] { invsqrt_grouped(ctx, in, cfgs, n, level_band, out); });
+}
+API hedap_status hedap_invsqrt_mixed(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs,
+                                     size_t n, hedap_ct** out) {
+  return guarded_on(ctx, [&] {
+    need(ctx && in && cfgs && out, "null argument");
+    for (size_t i = 0; i < n; ++i) out[i] = nullptr;
+    std::vector<const hedap::Ct*> v;
+    for (size_t i = 0; i < n; ++i) v.push_back(&hedap::ct_of(ctx, in[i]));
+    auto r = hedap::invsqrt_mixed(*ctx->c, v, std::vector<hedap_invsqrt_cfg>(cfgs, cfgs + n));
+    for (size_t i = 0; i < n; ++i) out[i] = wrap(std::move(r[i]));
+  });
 }
 API hedap_status hedap_ntt_batch(hedap_ctx* ctx, uint64_t* limbs, size_t n_limbs, size_t n_polys, uint32_t first_prime,
                                  int inverse, int on_device) {

@@ -39,6 +39,7 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   C->scale = std::pow(2.0, P.log_scale);
   C->seed = seed;
   C->stream = st;
+  C->home = st;
 
   int dev = 0;
   HEDAP_CUDA(cudaGetDevice(&dev));

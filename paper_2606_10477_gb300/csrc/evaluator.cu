@@ -21,6 +21,7 @@ std::unique_ptr<Ct> ct_alloc(Ctx& C, int level, int batch) {
   if (level < 0 || level > C.L()) throw Error(HEDAP_ERR_LEVEL, "level out of range");
   if (batch < 1 || batch > kMaxBatch) throw Error(HEDAP_ERR_ARG, "batch must lie in [1, 16]");
   auto c = std::make_unique<Ct>();
+  c->owner = &C;
   c->N = C.N;
   c->cap = level + 1;
   c->level = level;

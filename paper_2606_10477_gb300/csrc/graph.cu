@@ -11,7 +11,8 @@
 
 struct hedap_graph {
   hedap::Ctx* C = nullptr;
-  std::unique_ptr<hedap::Ct> in, out;
+  std::unique_ptr<hedap::Ct> in, out;               // one (batched) CryptoInvSqrt
+  std::vector<std::unique_ptr<hedap::Ct>> ins, outs;  // many single ciphertexts (hedap_invsqrt_mixed)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;
@@ -57,11 +58,12 @@ API hedap_status hedap_invsqrt_graph_create(hedap_ctx* ctx, const hedap_ct* exam
     if (!ctx || !example || !cfg || !out) throw Error(HEDAP_ERR_ARG, "null argument");
     *out = nullptr;
     if (prof_enabled()) throw Error(HEDAP_ERR_ARG, "graph capture with profiling enabled");
-    Ctx& C = *ctx->c;
+    Ctx& C = ctx_of(ctx);
     std::lock_guard<std::mutex> lk(C.mu);
+    const Ct& ex = ct_of(ctx, example);
     std::unique_ptr<hedap_graph> G(new hedap_graph);
     G->C = &C;
-    G->in = ct_copy(C, *example->c, example->c->level);
+    G->in = ct_copy(C, ex, ex.level);
     {  // ordinary run: builds every table the sequence needs, fixes the output shape
       auto w = invsqrt(C, *G->in, *cfg);
       G->out = ct_alloc(C, w->level, w->batch);
@@ -97,11 +99,12 @@ API hedap_status hedap_invsqrt_graph_create(hedap_ctx* ctx, const hedap_ct* exam
 
 API hedap_status hedap_graph_run(hedap_graph* g, const hedap_ct* in, hedap_ct** out) {
   return graph_guard([&] {
-    if (!g) throw Error(HEDAP_ERR_ARG, "null graph");
+    if (!g || !g->in) throw Error(HEDAP_ERR_ARG, "not a graph of one (batched) ciphertext");
     Ctx& C = *g->C;
     std::lock_guard<std::mutex> lk(C.mu);
     if (in) {
-      const Ct& a = *in->c;
+      const Ct& a = ct_of(nullptr, in);
+      if (a.owner != &C) throw Error(HEDAP_ERR_ARG, "graph input made by another context");
       if (a.level != g->in->level || a.batch != g->in->batch || a.scale != g->in->scale)
         throw Error(HEDAP_ERR_ARG, "graph input must match the captured level, batch and scale");
       copy_ct(C, a, *g->in);
@@ -114,6 +117,88 @@ API hedap_status hedap_graph_run(hedap_graph* g, const hedap_ct* in, hedap_ct** 
       copy_ct(C, *g->out, *r);
       *out = new hedap_ct;
       (*out)->c = std::move(r);
+    }
+  });
+}
+
+// CryptoInvSqrt of many single ciphertexts at their own levels (hedap_invsqrt_mixed) as one graph
+API hedap_status hedap_invsqrt_mixed_graph_create(hedap_ctx* ctx, const hedap_ct* const* examples,
+                                                  const hedap_invsqrt_cfg* cfgs, size_t n, hedap_graph** out) {
+  return graph_guard([&] {
+    if (!ctx || !examples || !cfgs || !out || n == 0) throw Error(HEDAP_ERR_ARG, "bad argument");
+    *out = nullptr;
+    if (prof_enabled()) throw Error(HEDAP_ERR_ARG, "graph capture with profiling enabled");
+    Ctx& C = ctx_of(ctx);
+    std::lock_guard<std::mutex> lk(C.mu);
+    std::unique_ptr<hedap_graph> G(new hedap_graph);
+    G->C = &C;
+    const std::vector<hedap_invsqrt_cfg> cv(cfgs, cfgs + n);
+    std::vector<const Ct*> in;
+    for (size_t i = 0; i < n; ++i) {
+      const Ct& e = ct_of(ctx, examples[i]);
+      G->ins.push_back(ct_copy(C, e, e.level));
+      in.push_back(G->ins.back().get());
+    }
+    {  // ordinary run: builds every table the sequence needs, fixes the outputs' shapes
+      auto w = invsqrt_mixed(C, in, cv);
+      for (auto& r : w) {
+        G->outs.push_back(ct_alloc(C, r->level, r->batch));
+        G->outs.back()->scale = r->scale;
+      }
+    }
+    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+    cudaStream_t cs, old = C.stream;
+    HEDAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const uint64_t k0 = prof_launches();
+    C.stream = cs;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    std::string failure;
+    if (ce == cudaSuccess) {
+      try {
+        auto r = invsqrt_mixed(C, in, cv);
+        for (size_t i = 0; i < n; ++i) copy_ct(C, *r[i], *G->outs[i]);
+      } catch (const std::exception& e) {
+        failure = e.what();
+      }
+      cudaGraph_t g = nullptr;
+      ce = cudaStreamEndCapture(cs, &g);
+      G->graph = g;
+    }
+    C.stream = old;
+    cudaStreamDestroy(cs);
+    if (!failure.empty()) throw Error(HEDAP_ERR_CUDA, "graph capture: " + failure);
+    if (ce != cudaSuccess) throw Error(HEDAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    G->kernels = prof_launches() - k0;
+    HEDAP_CUDA(cudaGraphInstantiate(&G->exec, G->graph, 0));
+    *out = G.release();
+  });
+}
+
+API hedap_status hedap_graph_run_many(hedap_graph* g, const hedap_ct* const* in, size_t n, hedap_ct** out) {
+  return graph_guard([&] {
+    if (!g || g->ins.empty()) throw Error(HEDAP_ERR_ARG, "not a graph of many ciphertexts");
+    if (n != g->ins.size()) throw Error(HEDAP_ERR_ARG, "graph input count differs");
+    Ctx& C = *g->C;
+    std::lock_guard<std::mutex> lk(C.mu);
+    if (in)
+      for (size_t i = 0; i < n; ++i) {
+        const Ct& a = ct_of(nullptr, in[i]);
+        if (a.owner != &C) throw Error(HEDAP_ERR_ARG, "graph input made by another context");
+        if (a.level != g->ins[i]->level || a.batch != 1 || a.scale != g->ins[i]->scale)
+          throw Error(HEDAP_ERR_ARG, "graph input must match the captured level and scale");
+      }
+    if (in)
+      for (size_t i = 0; i < n; ++i) copy_ct(C, ct_of(nullptr, in[i]), *g->ins[i]);
+    HEDAP_CUDA(cudaGraphLaunch(g->exec, C.stream));
+    if (out) {
+      for (size_t i = 0; i < n; ++i) out[i] = nullptr;
+      for (size_t i = 0; i < n; ++i) {
+        auto r = ct_alloc(C, g->outs[i]->level, 1);
+        r->scale = g->outs[i]->scale;
+        copy_ct(C, *g->outs[i], *r);
+        out[i] = new hedap_ct;
+        out[i]->c = std::move(r);
+      }
     }
   });
 }

@@ -187,8 +187,10 @@ double butterfly_rate(Ctx& C);  // butterflies per second of a register-only loo
 // ------------------------------------------------------------------ context and ciphertexts
 // One ciphertext, or a batch of `batch` ciphertexts at one level and scale:
 // [batch][2][cap][N] words, ciphertext k owning parts 2k (c0) and 2k+1 (c1).
+struct Ctx;
 struct Ct {
   DevBuf buf;
+  const Ctx* owner = nullptr;  // the context that made it
   int cap = 0;     // limbs allocated per part
   int level = 0;
   int batch = 1;
@@ -234,7 +236,18 @@ struct BtsStateDeleter {
   void operator()(BtsState* p) const;
 };
 
+// CUDA streams that a server's groups run on.  The context owns them (and destroys them last), so that
+// a buffer allocated on one of them -- a cached table, a key built during a group's step -- can still be
+// freed on it until the context goes.
+struct StreamPool {
+  std::vector<cudaStream_t> all, idle;
+  cudaStream_t get();           // an idle stream, created on demand (non-blocking)
+  void put(cudaStream_t s);     // back to the idle list (its work may still be in flight)
+  ~StreamPool();                // synchronises and destroys every stream
+};
+
 struct Ctx {
+  StreamPool streams;  // first member: destroyed after every buffer below
   int log_n = 0;
   size_t N = 0;
   int n_q = 0, n_p = 0, alpha = 1, hw = 0;
@@ -257,6 +270,7 @@ struct Ctx {
   std::map<int, std::unique_ptr<LevelConsts>> lc;
   std::unique_ptr<BtsState, BtsStateDeleter> bts;
   int device = 0;             // the CUDA device current at creation
+  cudaStream_t home = nullptr;  // the stream given at creation; `stream` is swapped while a server group steps
   u64* noalloc_scratch = nullptr;  // device address of hedap_rescale_noalloc's scratch array on `device`
   mutable std::mutex mu;      // held by every C-ABI call on this context and by a server's worker per step
   int L() const { return n_q - 1; }
@@ -310,6 +324,10 @@ std::vector<double> encode_slots(const Ctx& C, const std::vector<std::complex<do
 
 // ------------------------------------------------------------------ CryptoInvSqrt (invsqrt.cu)
 std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg);
+constexpr int kMaxBatchCts = 16;  // ciphertexts per batch (kernels.cuh's kMaxBatch)
+// CryptoInvSqrt of single ciphertexts at their own levels, batched where their states meet (invsqrt.cu)
+std::vector<std::unique_ptr<Ct>> invsqrt_mixed(Ctx& C, const std::vector<const Ct*>& in,
+                                               const std::vector<hedap_invsqrt_cfg>& cfgs);
 // CryptoInvSqrt in steps (construction = pre-BTS and pre-normalisation; then
 // chebyshev(); then newton(i) for i = 0, 1, ...), used by invsqrt and the selector
 struct InvSqrtRun {
@@ -367,10 +385,25 @@ inline int grid_for(size_t work, int threads) {
 
 }  // namespace hedap
 
-// opaque ABI handles
+// opaque ABI handles.  A live handle carries a magic word (cleared when it is freed) so that an entry
+// point can refuse a pointer that is not a live handle of the right kind; a ciphertext also records
+// the context it was made by (Ct::owner).
+constexpr uint64_t kCtxMagic = 0x6865646170437478ull, kCtMagic = 0x6865646170437431ull;
 struct hedap_ctx {
-  hedap::Ctx* c;
+  uint64_t magic = kCtxMagic;
+  hedap::Ctx* c = nullptr;
+  explicit hedap_ctx(hedap::Ctx* cc) : c(cc) {}
+  ~hedap_ctx() { magic = 0; }
 };
 struct hedap_ct {
+  uint64_t magic = kCtMagic;
   std::unique_ptr<hedap::Ct> c;
+  ~hedap_ct() { magic = 0; }
 };
+namespace hedap {
+// the ciphertext behind a handle, after checking that it is a live ciphertext handle made by ctx (any
+// context when ctx is null); HEDAP_ERR_ARG otherwise
+Ct& ct_of(const hedap_ctx* ctx, const hedap_ct* h);
+// the context behind a handle, after checking that it is a live context handle; HEDAP_ERR_ARG otherwise
+Ctx& ctx_of(const hedap_ctx* ctx);
+}  // namespace hedap

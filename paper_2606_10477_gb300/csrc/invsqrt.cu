@@ -261,4 +261,88 @@ std::unique_ptr<Ct> invsqrt(Ctx& C, const Ct& in, const hedap_invsqrt_cfg& cfg) 
   return std::move(run.y);
 }
 
+// CryptoInvSqrt of many single ciphertexts, each at its own level (no level is dropped).  Members with
+// equal input level, scale and configuration form a batch (input order, up to 16); after every stage --
+// the pre-normalisation with its Pre-BTS, the Chebyshev step, each Newton step -- batches of one
+// configuration whose carried ciphertexts (x, y, and t before the Chebyshev step) stand at equal
+// levels and scales are merged into one (up to 16 members).  Members whose inputs differ in level
+// meet where the algorithm brings them to the same level: after a Pre-BTS (all at the bootstrapped
+// level), or never when the configuration keeps ct_x at its input level (Alg. 1).  Every member's
+// result equals its own invsqrt() bit for bit: batches and merges only pack identical computations.
+std::vector<std::unique_ptr<Ct>> invsqrt_mixed(Ctx& C, const std::vector<const Ct*>& in,
+                                               const std::vector<hedap_invsqrt_cfg>& cfgs) {
+  struct Batch {
+    std::vector<size_t> m;  // members, in batch order
+    std::unique_ptr<InvSqrtRun> r;
+  };
+  const size_t n = in.size();
+  if (cfgs.size() != n) throw Error(HEDAP_ERR_ARG, "one configuration per input");
+  for (const Ct* c : in)
+    if (!c || c->batch != 1) throw Error(HEDAP_ERR_ARG, "inputs must be single ciphertexts");
+  std::vector<Batch> bs;
+  std::vector<bool> taken(n, false);
+  for (size_t i = 0; i < n; ++i) {
+    if (taken[i]) continue;
+    Batch b;
+    for (size_t j = i; j < n && b.m.size() < (size_t)kMaxBatchCts; ++j)
+      if (!taken[j] && in[j]->level == in[i]->level && in[j]->scale == in[i]->scale && same_cfg(cfgs[i], cfgs[j])) {
+        b.m.push_back(j);
+        taken[j] = true;
+      }
+    std::unique_ptr<Ct> packed;
+    if (b.m.size() > 1) {
+      std::vector<const Ct*> v;
+      for (size_t j : b.m) v.push_back(in[j]);
+      packed = batch_pack(C, v);
+    }
+    b.r.reset(new InvSqrtRun(C, packed ? *packed : *in[i], cfgs[i]));
+    bs.push_back(std::move(b));
+  }
+  auto same_state = [](const std::unique_ptr<Ct>& a, const std::unique_ptr<Ct>& b) {
+    return (!a && !b) || (a && b && a->level == b->level && a->scale == b->scale);
+  };
+  auto merge = [&]() {
+    for (size_t a = 0; a < bs.size(); ++a)
+      for (size_t b = a + 1; b < bs.size();) {
+        InvSqrtRun &ra = *bs[a].r, &rb = *bs[b].r;
+        if (!same_cfg(cfgs[bs[a].m[0]], cfgs[bs[b].m[0]]) || !same_state(ra.t, rb.t) || !same_state(ra.x, rb.x) ||
+            !same_state(ra.y, rb.y) || bs[a].m.size() + bs[b].m.size() > (size_t)kMaxBatchCts) {
+          ++b;
+          continue;
+        }
+        for (std::unique_ptr<Ct>* f : {&ra.t, &ra.x, &ra.y}) {
+          std::unique_ptr<Ct>& g = f == &ra.t ? rb.t : f == &ra.x ? rb.x : rb.y;
+          if (*f) *f = batch_pack(C, {f->get(), g.get()});
+        }
+        bs[a].m.insert(bs[a].m.end(), bs[b].m.begin(), bs[b].m.end());
+        bs.erase(bs.begin() + (long)b);
+      }
+  };
+  merge();
+  for (Batch& b : bs) {
+    b.r->chebyshev();
+    b.r->t.reset();  // needed by the Chebyshev step only
+  }
+  merge();
+  for (int i = 0;; ++i) {
+    bool any = false;
+    for (Batch& b : bs)
+      if (i < (int)b.r->cfg.newton_iters) {
+        b.r->newton(i);
+        any = true;
+      }
+    if (!any) break;
+    merge();
+  }
+  std::vector<std::unique_ptr<Ct>> out(n);
+  for (Batch& b : bs) {
+    InvSqrtRun& r = *b.r;
+    if (r.cfg.newton_iters == 0 && (r.cfg.bts_mask & 1)) r.y = bootstrap_scaled(C, *r.y, r.Y, (int)r.cfg.log_slots);
+    if (r.cfg.B != 1.0) r.y->scale *= std::sqrt(r.cfg.B);
+    for (size_t k = 0; k < b.m.size(); ++k)
+      out[b.m[k]] = b.m.size() > 1 ? batch_unpack(C, *r.y, (int)k) : std::move(r.y);
+  }
+  return out;
+}
+
 }  // namespace hedap

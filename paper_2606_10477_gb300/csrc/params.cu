@@ -178,4 +178,24 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
   return *this;
 }
 
+// ------------------------------------------------------------------ stream pool
+cudaStream_t StreamPool::get() {
+  if (!idle.empty()) {
+    cudaStream_t s = idle.back();
+    idle.pop_back();
+    return s;
+  }
+  cudaStream_t s = nullptr;
+  HEDAP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  all.push_back(s);
+  return s;
+}
+void StreamPool::put(cudaStream_t s) { idle.push_back(s); }
+StreamPool::~StreamPool() {
+  for (cudaStream_t s : all) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+}
+
 }  // namespace hedap

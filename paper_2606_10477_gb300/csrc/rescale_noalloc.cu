@@ -68,7 +68,7 @@ extern "C" __attribute__((visibility("default"))) hedap_status hedap_rescale_noa
     return HEDAP_ERR_ARG;
   }
   return hedap::run_on_ctx(ctx, [&] {
-    hedap::Ctx& C = *ctx->c;
+    hedap::Ctx& C = hedap::ctx_of(ctx);
     if (level < 1 || level > C.L()) throw hedap::Error(HEDAP_ERR_LEVEL, "rescale needs 1 <= level <= L");
     const size_t N = C.N, l = (size_t)level;
     const size_t need = (2 + 2 * l) * N;

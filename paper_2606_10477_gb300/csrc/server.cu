@@ -3,14 +3,11 @@
 // (the statistical workloads of Sec. 5.3: Z-score normalisation and the
 // Pearson correlation coefficient).
 //
-// One worker thread drives the context.  Submitted queries wait in a FIFO; at
-// every scheduling iteration the worker admits the oldest waiting query and
-// the later ones that can share its group (one kind, input level, input scale
-// and InvSqrt configuration; up to max_batch) while the estimated device
-// memory of the admitted queries stays within the budget, and makes them a
-// new group.  Groups advance one
-// step at a time, round-robin, so a group admitted while others are in flight
-// starts at once and its steps interleave with theirs:
+// One worker thread drives the context.  Submitted queries wait in a FIFO; the
+// worker admits the oldest waiting query and the later ones that can share its
+// group (one kind, input level, input scale and InvSqrt configuration; up to
+// max_batch) while the estimated device memory of the admitted queries stays
+// within the budget.  A group is a batch advanced one step at a time:
 //   stats      x^2 (and y^2, x*y) of every ciphertext of the group, batched;
 //              per query: their sums and the sum of x (and y) over its
 //              ciphertexts; over the group: rotate-and-sum over all slots;
@@ -21,12 +18,25 @@
 //   finish     a bootstrap of InvSqrt's result when it has no level left for
 //              the last product, then z = (x - mean) * InvSqrt(var) per ciphertext, or
 //              r = cov * InvSqrt(var_x var_y)
-// Each step is one batched launch sequence over the group, issued on the
-// context's stream without waiting; a finished group records an event and its
-// queries complete when the event does.  Batched operations equal single
-// operations bit for bit and every decision (a bootstrap, a level drop) is a
-// function of the group's common kind, level and configuration, so a query's
-// result does not depend on which other queries share its group or the GPU.
+// Every group runs on a CUDA stream of its own (from the context's pool), so the
+// work of groups in flight overlaps on the device.  A group's next step is issued
+// once its previous one has finished on the device (an event per step): groups
+// move at the device's pace, and a group admitted later can catch up with an
+// earlier one that needs the same steps.  At every step boundary groups with the
+// same signature at the same step are merged into one batch (up to max_batch):
+// a group with a partner further ahead (by at most kCatchUp steps) is stepped
+// first while the partner waits, and the two become one group when they meet.
+// Batched operations equal single operations bit for bit and every decision (a
+// bootstrap, a level drop) is a function of the group's common kind, level and
+// configuration, so a query's result does not depend on which other queries share
+// its group, on merging, or on the GPU.
+//
+// Host-side failure handling: hedap_server_cancel withdraws a query (waiting: at
+// once; in flight: at its group's next step boundary, the group dropped when
+// every query in it is withdrawn); hedap_server_inject makes the next admissions
+// fail as an allocation failure would (their queries end with HEDAP_ERR_OOM and
+// the server goes on); hedap_server_wait bounds the host's wait for a query
+// (HEDAP_ERR_TIMEOUT).  None of them touches the GPU.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -58,7 +68,9 @@ struct Query {
   double latency_ms = 0;
   uint32_t group_size = 0;
   bool done = false;
+  bool cancelled = false;  // withdrawn (hedap_server_cancel); ends with HEDAP_ERR_CANCELLED
   std::string error;
+  hedap_status error_code = HEDAP_OK;
 };
 
 bool same_group(const Query& a, const Query& b) {
@@ -67,14 +79,23 @@ bool same_group(const Query& a, const Query& b) {
 
 struct Group {
   std::vector<Query*> q;
-  int step = 0;  // 0 stats, 1 prepare, 2 chebyshev, 3 .. 2+iters newton, then finish
+  int step = 0;  // 0 stats, 1 prepare, 2 chebyshev, 3 .. 2+iters newton, then finish; -1 finished
   std::unique_ptr<InvSqrtRun> run;
+  cudaStream_t st = nullptr;  // the group's stream (context pool)
+  cudaEvent_t ev = nullptr;   // recorded after each issued step
+  bool in_flight = false;     // a step was issued and its event has not been seen complete
+  uint64_t seq = 0;           // admission order
 };
 
-struct Pending {
-  cudaEvent_t ev;
-  std::vector<Query*> q;
-};
+// the steps a group of this configuration goes through before `finish`
+int finish_step(const Query& q) { return 3 + (int)q.cfg.newton_iters; }
+
+// a group's buffers now belong to stream s: their stream-ordered frees go there
+void rehome(Ct* c, cudaStream_t s) {
+  if (c) c->buf.s = s;
+}
+
+constexpr int kCatchUp = 3;  // steps a group waits at most for a later partner with its signature
 
 // rotate-and-sum: every slot of the result holds the sum of all N/2 slots
 CtP all_slots_sum(Ctx& C, CtP a) {
@@ -108,14 +129,14 @@ std::vector<CtP> mul_many(Ctx& C, const std::vector<const Ct*>& a, const std::ve
 struct hedap_server {
   hedap::Ctx* C = nullptr;
   hedap_server_cfg cfg{};
-  std::mutex mu;  // guards everything below but groups and pending (the context has its own lock)
+  std::mutex mu;  // guards everything below but groups (worker-only; the context has its own lock)
   std::condition_variable cv, done_cv;
   std::deque<Query*> waiting;
   std::map<uint64_t, std::unique_ptr<Query>> all;
-  std::vector<std::unique_ptr<Group>> groups;  // worker-only
-  std::deque<Pending> pending;                 // worker-only
+  std::vector<std::unique_ptr<Group>> groups;  // worker-only: admitted, in flight or finishing
   size_t admitted_bytes = 0;
-  uint64_t next_id = 1;
+  uint64_t next_id = 1, next_seq = 1;
+  uint32_t inject_admission_oom = 0;  // fault injection: admissions still to fail
   bool stop = false;
   bool paused = false;
   std::thread worker;
@@ -123,12 +144,17 @@ struct hedap_server {
   Clock::time_point first_submit, last_done;
   bool any = false;
   std::vector<hedap_select_entry> table;  // HE-DAP per-level choices (guarded by mu)
+  uint64_t merges = 0;                    // groups merged into others (guarded by mu)
 
   size_t estimate_bytes(size_t n_out, int level) const;
   void loop();
   void step(Group& g);
-  void retire(bool block);
-  void fail(const std::vector<Query*>& qs, const std::string& why);
+  void issue(Group& g);
+  bool merge_ready();
+  Group* pick();
+  bool retire_finished();
+  void end(Group& g, hedap_status code, const std::string& why);
+  void fail(const std::vector<Query*>& qs, hedap_status code, const std::string& why);
 };
 
 // Device memory a query holds while admitted (its inputs are the caller's):
@@ -142,12 +168,17 @@ size_t hedap_server::estimate_bytes(size_t n_out, int level) const {
   return (n_out + 8) * ct + 2 * ks;
 }
 
-void hedap_server::fail(const std::vector<Query*>& qs, const std::string& why) {
+void hedap_server::fail(const std::vector<Query*>& qs, hedap_status code, const std::string& why) {
   std::lock_guard<std::mutex> lk(mu);
   for (Query* q : qs) {
+    if (q->done) continue;
     q->error = why;
+    q->error_code = code;
     q->done = true;
     q->out.clear();
+    q->mean_x.reset();
+    q->cov.reset();
+    q->var.reset();
     q->x.clear();
     q->y.clear();
     admitted_bytes -= q->bytes;
@@ -292,84 +323,247 @@ void hedap_server::step(Group& g) {
   g.step = -1;
 }
 
-// complete finished groups whose event has passed (FIFO: they share one stream)
-void hedap_server::retire(bool block) {
-  while (!pending.empty()) {
-    Pending& p = pending.front();
-    const cudaError_t e = block ? cudaEventSynchronize(p.ev) : cudaEventQuery(p.ev);
-    if (e == cudaErrorNotReady) return;
-    block = false;
-    cudaEventDestroy(p.ev);
-    std::vector<Query*> qs = std::move(p.q);
-    pending.pop_front();
-    if (e != cudaSuccess) {
-      fail(qs, std::string("CUDA: ") + cudaGetErrorString(e));
+// issue the group's next step on its own stream (the context's stream swapped in under the context's
+// lock), followed by its event
+void hedap_server::issue(Group& g) {
+  Ctx& Cx = *C;
+  std::lock_guard<std::mutex> lk(Cx.mu);
+  Cx.stream = g.st;
+  try {
+    step(g);
+    HEDAP_CUDA(cudaEventRecord(g.ev, g.st));
+    g.in_flight = true;
+  } catch (...) {
+    Cx.stream = Cx.home;
+    throw;
+  }
+  Cx.stream = Cx.home;
+}
+
+// merge groups that are idle on the device, share a signature and stand at the same step (after the
+// statistics, before the finish); the older group absorbs the younger.  Returns whether any merged.
+bool hedap_server::merge_ready() {
+  bool merged = false;
+  for (size_t a = 0; a < groups.size(); ++a) {
+    Group& A = *groups[a];
+    if (A.in_flight || A.step < 1 || A.step >= finish_step(*A.q[0])) continue;
+    for (size_t b = a + 1; b < groups.size();) {
+      Group& B = *groups[b];
+      if (B.in_flight || B.step != A.step || !same_group(*A.q[0], *B.q[0]) ||
+          A.q.size() + B.q.size() > cfg.max_batch) {
+        ++b;
+        continue;
+      }
+      Ctx& Cx = *C;
+      std::lock_guard<std::mutex> lk(Cx.mu);
+      // A's stream takes over B's state: it waits for B's work, copies, and B's old buffers are freed
+      // on A's stream after the copies
+      HEDAP_CUDA(cudaStreamWaitEvent(A.st, B.ev, 0));
+      for (Query* q : B.q) {
+        rehome(q->mean_x.get(), A.st);
+        rehome(q->cov.get(), A.st);
+        rehome(q->var.get(), A.st);
+      }
+      if (A.step >= 2) {  // InvSqrt's state: t, x, y of the two batches packed into one
+        Cx.stream = A.st;
+        try {
+          InvSqrtRun& ra = *A.run;
+          InvSqrtRun& rb = *B.run;
+          for (std::unique_ptr<Ct>* f : {&ra.t, &ra.x, &ra.y}) {
+            std::unique_ptr<Ct>& fb = f == &ra.t ? rb.t : f == &ra.x ? rb.x : rb.y;
+            if (!*f) continue;
+            rehome(f->get(), A.st);
+            rehome(fb.get(), A.st);
+            *f = batch_pack(Cx, {f->get(), fb.get()});
+          }
+        } catch (...) {
+          Cx.stream = Cx.home;
+          throw;
+        }
+        Cx.stream = Cx.home;
+        B.run.reset();
+      }
+      A.q.insert(A.q.end(), B.q.begin(), B.q.end());
+      HEDAP_CUDA(cudaEventDestroy(B.ev));
+      Cx.streams.put(B.st);
+      groups.erase(groups.begin() + (long)b);
+      {
+        std::lock_guard<std::mutex> lk2(mu);
+        ++merges;
+      }
+      merged = true;
+    }
+  }
+  return merged;
+}
+
+// the next group to step: idle on the device and not waiting for a partner to catch up (a partner:
+// same signature, room for both in one batch, and either a few steps behind or at the same step with
+// that step still running on the device -- `step` counts issued steps); the most behind first
+Group* hedap_server::pick() {
+  Group* best = nullptr;
+  for (auto& gp : groups) {
+    Group& g = *gp;
+    if (g.in_flight || g.step < 0) continue;
+    bool wait = false;
+    if (g.step >= 1 && g.step < finish_step(*g.q[0]))
+      for (auto& hp : groups) {
+        const Group& h = *hp;
+        if (&h == &g || h.step < 0 || !same_group(*g.q[0], *h.q[0]) || g.q.size() + h.q.size() > cfg.max_batch)
+          continue;
+        if ((h.step < g.step && g.step - h.step <= kCatchUp) || (h.step == g.step && h.in_flight)) {
+          wait = true;
+          break;
+        }
+      }
+    if (wait) continue;
+    if (!best || g.step < best->step || (g.step == best->step && g.seq < best->seq)) best = &g;
+  }
+  return best;
+}
+
+// a group leaves: its queries complete (code HEDAP_OK) or fail; its stream goes back to the pool
+void hedap_server::end(Group& g, hedap_status code, const std::string& why) {
+  const auto t = Clock::now();
+  std::lock_guard<std::mutex> lk(mu);
+  for (Query* q : g.q) {
+    if (q->done) continue;
+    q->group_size = (uint32_t)g.q.size();
+    if (code != HEDAP_OK || q->cancelled) {
+      q->error = code != HEDAP_OK ? why : "cancelled";
+      q->error_code = code != HEDAP_OK ? code : HEDAP_ERR_CANCELLED;
+      q->out.clear();
+    } else {
+      q->latency_ms = std::chrono::duration<double, std::milli>(t - q->submitted).count();
+      latencies.push_back(q->latency_ms);
+      for (auto& o : q->out) rehome(o.get(), C->home);  // the caller's buffers now: freed on its stream
+      last_done = t;
+    }
+    q->mean_x.reset();
+    q->cov.reset();
+    q->var.reset();
+    q->done = true;
+    q->x.clear();
+    q->y.clear();
+    admitted_bytes -= q->bytes;
+  }
+  done_cv.notify_all();
+}
+
+// groups whose last issued step finished on the device: finished groups leave, the others become idle
+bool hedap_server::retire_finished() {
+  bool any_change = false;
+  for (size_t i = 0; i < groups.size();) {
+    Group& g = *groups[i];
+    if (g.in_flight) {
+      const cudaError_t e = cudaEventQuery(g.ev);
+      if (e == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      g.in_flight = false;
+      any_change = true;
+      if (e != cudaSuccess) {
+        g.step = -1;
+        end(g, HEDAP_ERR_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+        cudaEventDestroy(g.ev);
+        C->streams.put(g.st);
+        groups.erase(groups.begin() + (long)i);
+        continue;
+      }
+    }
+    bool all_cancelled = true;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (Query* q : g.q) all_cancelled = all_cancelled && q->cancelled;
+    }
+    if (g.step < 0 || all_cancelled) {  // finished, or nobody wants the result any more
+      {
+        std::lock_guard<std::mutex> lk(C->mu);
+        g.run.reset();  // freed on the group's stream, ordered after its work
+      }
+      end(g, HEDAP_OK, "");
+      cudaEventDestroy(g.ev);
+      C->streams.put(g.st);
+      groups.erase(groups.begin() + (long)i);
+      any_change = true;
       continue;
     }
-    const auto t = Clock::now();
-    std::lock_guard<std::mutex> lk(mu);
-    for (Query* q : qs) {
-      q->latency_ms = std::chrono::duration<double, std::milli>(t - q->submitted).count();
-      q->done = true;
-      q->x.clear();
-      q->y.clear();
-      latencies.push_back(q->latency_ms);
-      admitted_bytes -= q->bytes;
-    }
-    last_done = t;
-    done_cv.notify_all();
+    ++i;
   }
+  return any_change;
 }
 
 void hedap_server::loop() {
   cudaSetDevice(C->device);
-  size_t rr = 0;
   for (;;) {
+    std::vector<std::unique_ptr<Group>> admitted;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] { return stop || (!waiting.empty() && !paused) || !groups.empty() || !pending.empty(); });
-      if (stop && waiting.empty() && groups.empty() && pending.empty()) return;
+      cv.wait(lk, [&] { return stop || (!waiting.empty() && !paused) || !groups.empty(); });
+      if (stop && waiting.empty() && groups.empty()) return;
       // the oldest waiting query, then the later ones that can share its group
-      std::unique_ptr<Group> g(new Group);
-      for (auto it = waiting.begin(); !paused && it != waiting.end() && g->q.size() < cfg.max_batch;) {
-        Query* q = *it;
-        if (!g->q.empty() && !same_group(*q, *g->q[0])) {
-          ++it;
-          continue;
+      const size_t admit = cfg.admit_max ? std::min(cfg.admit_max, cfg.max_batch) : cfg.max_batch;
+      while (!paused && !waiting.empty()) {
+        std::unique_ptr<Group> g(new Group);
+        for (auto it = waiting.begin(); it != waiting.end() && g->q.size() < admit;) {
+          Query* q = *it;
+          if (!g->q.empty() && !same_group(*q, *g->q[0])) {
+            ++it;
+            continue;
+          }
+          if (admitted_bytes + q->bytes > cfg.hbm_budget_bytes) break;
+          it = waiting.erase(it);
+          admitted_bytes += q->bytes;
+          g->q.push_back(q);
         }
-        if (admitted_bytes + q->bytes > cfg.hbm_budget_bytes) break;
-        it = waiting.erase(it);
-        admitted_bytes += q->bytes;
-        g->q.push_back(q);
+        if (g->q.empty()) break;
+        g->seq = next_seq++;
+        admitted.push_back(std::move(g));
       }
-      for (Query* q : g->q) q->group_size = (uint32_t)g->q.size();
-      if (!g->q.empty()) groups.push_back(std::move(g));
     }
-    if (!groups.empty()) {
-      rr %= groups.size();
-      Group& g = *groups[rr];
+    for (auto& g : admitted) {
       try {
-        std::lock_guard<std::mutex> lk(C->mu);
-        step(g);
-        if (g.step < 0) {
-          Pending p;
-          HEDAP_CUDA(cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming));
-          HEDAP_CUDA(cudaEventRecord(p.ev, C->stream));
-          p.q = g.q;
-          pending.push_back(std::move(p));
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          if (inject_admission_oom > 0) {
+            --inject_admission_oom;
+            throw Error(HEDAP_ERR_OOM, "device allocation failed at admission (injected)");
+          }
         }
-      } catch (const std::exception& e) {
-        fail(g.q, e.what());
-        g.step = -1;
+        std::lock_guard<std::mutex> lk(C->mu);
+        g->st = C->streams.get();
+        HEDAP_CUDA(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
+        // the inputs were made on the context's stream: the group's stream starts after that work
+        HEDAP_CUDA(cudaEventRecord(g->ev, C->home));
+        HEDAP_CUDA(cudaStreamWaitEvent(g->st, g->ev, 0));
+        groups.push_back(std::move(g));
+      } catch (const Error& e) {
+        fail(g->q, e.code, e.what());
+        if (g->ev) cudaEventDestroy(g->ev);
+        if (g->st) C->streams.put(g->st);
       }
-      if (g.step < 0)
-        groups.erase(groups.begin() + (long)rr);
-      else
-        ++rr;
     }
-    // with nothing to issue (waiting queries, if any, wait for memory), wait
-    // for the oldest finished group on the GPU
-    retire(groups.empty());
+    bool progressed = retire_finished();
+    progressed = merge_ready() || progressed;
+    if (Group* g = pick()) {
+      try {
+        issue(*g);
+      } catch (const Error& e) {
+        g->step = -1;
+        end(*g, e.code, e.what());
+      } catch (const std::exception& e) {
+        g->step = -1;
+        end(*g, HEDAP_ERR_ARG, e.what());
+      }
+      progressed = true;
+    }
+    if (!progressed) {
+      // nothing to issue until a step in flight finishes or a query arrives: poll again shortly (a step
+      // takes milliseconds on the device; the worker must notice whichever group finishes first)
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait_for(lk, std::chrono::microseconds(50));
+    }
   }
 }
 
@@ -399,7 +593,7 @@ API hedap_status hedap_server_create(hedap_ctx* ctx, const hedap_server_cfg* cfg
     if (!ctx || !cfg || !out) throw Error(HEDAP_ERR_ARG, "null argument");
     *out = nullptr;
     if (cfg->max_batch < 1 || cfg->max_batch > 16) throw Error(HEDAP_ERR_ARG, "max_batch must lie in [1, 16]");
-    Ctx& C = *ctx->c;
+    Ctx& C = ctx_of(ctx);
     {
       // the power-of-two rotation keys of rotate-and-sum stay resident from here on
       std::lock_guard<std::mutex> lk(C.mu);
@@ -429,13 +623,14 @@ API hedap_status hedap_server_submit(hedap_server* s, const hedap_query* q, uint
     Q->cfg = q->invsqrt;
     for (uint32_t k = 0; k < q->n_ct; ++k) {
       for (int side = 0; side < (pcc ? 2 : 1); ++side) {
-        const hedap_ct* c = side ? q->y[k] : q->x[k];
-        if (!c || c->c->batch != 1) throw Error(HEDAP_ERR_ARG, "query inputs must be single ciphertexts");
-        if (k + side > 0 && (c->c->level != Q->level || c->c->scale != Q->scale))
+        const Ct& c = ct_of(nullptr, side ? q->y[k] : q->x[k]);
+        if (c.owner != s->C) throw Error(HEDAP_ERR_ARG, "query input made by another context");
+        if (c.batch != 1) throw Error(HEDAP_ERR_ARG, "query inputs must be single ciphertexts");
+        if (k + side > 0 && (c.level != Q->level || c.scale != Q->scale))
           throw Error(HEDAP_ERR_ARG, "query inputs must share one level and scale");
-        Q->level = c->c->level;
-        Q->scale = c->c->scale;
-        (side ? Q->y : Q->x).push_back(c->c.get());
+        Q->level = c.level;
+        Q->scale = c.scale;
+        (side ? Q->y : Q->x).push_back(&c);
       }
     }
     if (Q->level < 4) throw Error(HEDAP_ERR_LEVEL, "query inputs need level >= 4");
@@ -484,8 +679,9 @@ API hedap_status hedap_server_poll(hedap_server* s, uint64_t id, int wait, int* 
     if (!q->done) return;
     if (!q->error.empty()) {
       const std::string why = "query failed: " + q->error;
+      const hedap_status code = q->error_code != HEDAP_OK ? q->error_code : HEDAP_ERR_ARG;
       s->all.erase(it);
-      throw Error(HEDAP_ERR_ARG, why);
+      throw Error(code, why);
     }
     if (n_out) *n_out = q->out.size();
     if (latency_ms) *latency_ms = q->latency_ms;
@@ -521,6 +717,59 @@ API hedap_status hedap_server_stats(hedap_server* s, double* p50_ms, double* p99
           s->any && !v.empty() ? std::chrono::duration<double>(s->last_done - s->first_submit).count() : 0;
       *qps = span > 0 ? (double)v.size() / span : 0;
     }
+  });
+}
+
+API hedap_status hedap_server_wait(hedap_server* s, uint64_t id, double timeout_ms) {
+  return srv_guard([&] {
+    if (!s || !(timeout_ms >= 0)) throw Error(HEDAP_ERR_ARG, "bad argument");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) throw Error(HEDAP_ERR_ARG, "unknown query id");
+    Query* q = it->second.get();
+    const auto until = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                          std::chrono::duration<double, std::milli>(timeout_ms));
+    if (!s->done_cv.wait_until(lk, until, [&] { return q->done; }))
+      throw Error(HEDAP_ERR_TIMEOUT, "query not done within the timeout");
+  });
+}
+
+API hedap_status hedap_server_cancel(hedap_server* s, uint64_t id) {
+  return srv_guard([&] {
+    if (!s) throw Error(HEDAP_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) throw Error(HEDAP_ERR_ARG, "unknown query id");
+    Query* q = it->second.get();
+    if (q->done) throw Error(HEDAP_ERR_ARG, "query already finished");
+    q->cancelled = true;
+    auto w = std::find(s->waiting.begin(), s->waiting.end(), q);
+    if (w != s->waiting.end()) {  // not admitted yet: withdrawn at once
+      s->waiting.erase(w);
+      q->done = true;
+      q->error = "cancelled";
+      q->error_code = HEDAP_ERR_CANCELLED;
+      q->x.clear();
+      q->y.clear();
+      s->done_cv.notify_all();
+    }
+  });
+}
+
+API hedap_status hedap_server_inject(hedap_server* s, uint32_t fault, uint32_t count) {
+  return srv_guard([&] {
+    if (!s) throw Error(HEDAP_ERR_ARG, "null argument");
+    if (fault != HEDAP_FAULT_ADMISSION_OOM) throw Error(HEDAP_ERR_ARG, "unknown fault");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->inject_admission_oom = count;
+  });
+}
+
+API hedap_status hedap_server_merges(hedap_server* s, uint64_t* merged) {
+  return srv_guard([&] {
+    if (!s || !merged) throw Error(HEDAP_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *merged = s->merges;
   });
 }
 

@@ -19,7 +19,9 @@ _lock = threading.Lock()
 _lib = None
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "not enough levels", -3: "scale mismatch", -4: "out of device memory",
-          -5: "CUDA error", -6: "device wait timed out", -7: "input out of range", -8: "missing switching key"}
+          -5: "CUDA error", -6: "wait timed out", -7: "input out of range", -8: "missing switching key",
+          -9: "cancelled"}
+FAULT_ADMISSION_OOM = 1
 
 EXPORTED = [
     "hedap_status_str", "hedap_last_error", "hedap_ctx_create", "hedap_ctx_destroy", "hedap_ctx_primes", "hedap_sync",
@@ -31,11 +33,12 @@ EXPORTED = [
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_bootstrap_encapsulate",
     "hedap_encapsulation_switch", "hedap_bootstrap_slots", "hedap_bootstrap_scaled_slots", "hedap_sub_sum", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
-    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_ntt_batch",
+    "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_invsqrt_mixed", "hedap_ntt_batch",
     "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
-    "hedap_server_resume", "hedap_server_estimate", "hedap_server_set_table", "hedap_invsqrt_graph_create", "hedap_graph_run",
-    "hedap_graph_kernels", "hedap_graph_destroy",
+    "hedap_server_resume", "hedap_server_estimate", "hedap_server_wait", "hedap_server_cancel", "hedap_server_inject",
+    "hedap_server_merges", "hedap_server_set_table", "hedap_invsqrt_graph_create", "hedap_graph_run",
+    "hedap_graph_kernels", "hedap_graph_destroy", "hedap_invsqrt_mixed_graph_create", "hedap_graph_run_many",
 ]
 
 
@@ -86,7 +89,8 @@ class InvSqrtCfg(C.Structure):
 
 
 class ServerCfg(C.Structure):
-    _fields_ = [("max_batch", C.c_uint32), ("start_paused", C.c_uint32), ("hbm_budget_bytes", C.c_uint64)]
+    _fields_ = [("max_batch", C.c_uint32), ("start_paused", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
+                ("admit_max", C.c_uint32)]
 
 
 class Query(C.Structure):
@@ -172,6 +176,7 @@ def _declare(L):
         "hedap_ct_batch_size": (st, [vp, C.POINTER(C.c_int)]),
         "hedap_invsqrt_batch": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, pp]),
         "hedap_invsqrt_many": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, C.c_int, pp]),
+        "hedap_invsqrt_mixed": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, pp]),
         "hedap_ntt_batch": (st, [vp, u64p, C.c_size_t, C.c_size_t, C.c_uint32, C.c_int, C.c_int]),
         "hedap_ntt_tune": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -189,9 +194,15 @@ def _declare(L):
         "hedap_server_poll": (st, [vp, C.c_uint64, C.c_int, C.POINTER(C.c_int), pp, C.c_size_t,
                                    C.POINTER(C.c_size_t), dp, C.POINTER(C.c_uint32)]),
         "hedap_server_resume": (st, [vp]),
+        "hedap_server_wait": (st, [vp, C.c_uint64, C.c_double]),
+        "hedap_server_cancel": (st, [vp, C.c_uint64]),
+        "hedap_server_inject": (st, [vp, C.c_uint32, C.c_uint32]),
+        "hedap_server_merges": (st, [vp, u64p]),
         "hedap_server_set_table": (st, [vp, C.POINTER(SelectEntry), C.c_size_t]),
         "hedap_invsqrt_graph_create": (st, [vp, vp, C.POINTER(InvSqrtCfg), pp]),
         "hedap_graph_run": (st, [vp, vp, pp]),
+        "hedap_invsqrt_mixed_graph_create": (st, [vp, pp, C.POINTER(InvSqrtCfg), C.c_size_t, pp]),
+        "hedap_graph_run_many": (st, [vp, pp, C.c_size_t, pp]),
         "hedap_graph_kernels": (st, [vp, u64p]),
         "hedap_graph_destroy": (None, [vp]),
         "hedap_server_estimate": (st, [vp, C.c_uint32, C.c_uint32, C.c_int, u64p]),
@@ -552,6 +563,28 @@ class Context:
         return [Ciphertext(self, C.c_void_p(o)) for o in outs]
 
 
+    def invsqrt_mixed(self, cts, cfgs):
+        """Single ciphertexts at their own levels (none dropped), batched where their states meet (see
+        hedap.h, hedap_invsqrt_mixed); cfgs as for invsqrt_batch (an 8th entry is log_slots)."""
+        n = len(cts)
+        arr = (C.c_void_p * n)(*[c.h for c in cts])
+        cf = (InvSqrtCfg * n)(*[InvSqrtCfg(*c) for c in cfgs])
+        outs = (C.c_void_p * n)()
+        _check(load().hedap_invsqrt_mixed(self.h, arr, cf, n, outs))
+        return [Ciphertext(self, C.c_void_p(o)) for o in outs]
+
+    def invsqrt_mixed_graph(self, cts, cfgs) -> "Graph":
+        """invsqrt_mixed captured as one CUDA graph for these inputs' levels and scales."""
+        n = len(cts)
+        arr = (C.c_void_p * n)(*[c.h for c in cts])
+        cf = (InvSqrtCfg * n)(*[InvSqrtCfg(*c) for c in cfgs])
+        h = C.c_void_p()
+        _check(load().hedap_invsqrt_mixed_graph_create(self.h, arr, cf, n, C.byref(h)))
+        g = Graph(self, h)
+        g.n = n
+        return g
+
+
 PROFILE_CLASSES = ("ntt", "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph", "elementwise")
 
 
@@ -568,6 +601,14 @@ class Graph:
         _check(load().hedap_graph_run(self.h, a.h if a is not None else None,
                                       C.byref(out) if want_output else None))
         return Ciphertext(self.ctx, out) if want_output else None
+
+    def run_many(self, cts=None, want_output=True):
+        """Replay a graph of many ciphertexts (Context.invsqrt_mixed_graph) on `cts` (or the previous inputs)."""
+        n = self.n
+        arr = (C.c_void_p * n)(*[c.h for c in cts]) if cts is not None else None
+        outs = (C.c_void_p * n)()
+        _check(load().hedap_graph_run_many(self.h, arr, n, outs if want_output else None))
+        return [Ciphertext(self.ctx, C.c_void_p(o)) for o in outs] if want_output else None
 
     @property
     def kernels(self) -> int:
@@ -591,11 +632,12 @@ class Server:
     Inputs are borrowed by the library until a query is done; this wrapper
     keeps references to them until then."""
 
-    def __init__(self, ctx: Context, max_batch: int = 8, hbm_budget_bytes: int = 64 << 30, paused: bool = False):
+    def __init__(self, ctx: Context, max_batch: int = 8, hbm_budget_bytes: int = 64 << 30, paused: bool = False,
+                 admit_max: int = 0):
         self.ctx = ctx
         self._held = {}
         h = C.c_void_p()
-        cfg = ServerCfg(max_batch, 1 if paused else 0, hbm_budget_bytes)
+        cfg = ServerCfg(max_batch, 1 if paused else 0, hbm_budget_bytes, admit_max)
         _check(load().hedap_server_create(ctx.h, C.byref(cfg), C.byref(h)))
         self.h = h
 
@@ -631,6 +673,22 @@ class Server:
 
     def resume(self) -> None:
         _check(load().hedap_server_resume(self.h))
+
+    def wait(self, qid: int, timeout_ms: float) -> None:
+        """Block until the query is done (HedapError code -6 when timeout_ms passes first)."""
+        _check(load().hedap_server_wait(self.h, qid, float(timeout_ms)))
+
+    def cancel(self, qid: int) -> None:
+        _check(load().hedap_server_cancel(self.h, qid))
+
+    def inject(self, fault: int, count: int) -> None:
+        """Host-side fault injection (FAULT_ADMISSION_OOM: the next `count` admissions fail)."""
+        _check(load().hedap_server_inject(self.h, fault, count))
+
+    def merges(self) -> int:
+        n = C.c_uint64()
+        _check(load().hedap_server_merges(self.h, C.byref(n)))
+        return n.value
 
     def set_table(self, R) -> None:
         """Install HE-DAP's per-level table (list of dicts as returned by Context.select)."""

@@ -135,3 +135,33 @@ def test_invsqrt_many_level_bands_against_oracle():
     for i, (oc, out) in enumerate(zip(ocs, outs)):
         floor = min(l for l in levels if l // band == levels[i] // band)
         same(out, o.invsqrt(o.drop(oc, floor), *cfg), f"input {i} (level {levels[i]}, band floor {floor})")
+
+
+# ------------------------------------------------------------------ mixed levels, none dropped
+def test_invsqrt_mixed_levels_against_oracle(bts12):
+    """Single ciphertexts at their own levels with their own configurations (Pre-BTS for the low ones,
+    sparse packing for one): each output equals the oracle's CryptoInvSqrt of that input alone, through
+    hedap_invsqrt_mixed and through its captured CUDA graph."""
+    g, o, lvl = bts12
+    lazy = 1 << 63
+    pre = (0.05, 1.0, 1.0, 7, 2, 1, lazy, 0)
+    top = (0.05, 1.0, 1.0, 7, 2, 0, lazy, 0)
+    sparse = (0.05, 1.0, 1.0, 7, 2, 1, lazy, 7)
+    plan = [(3, pre), (5, pre), (lvl, top), (lvl, top), (lvl - 2, top), (4, sparse)]
+    ocs, cfgs = [], []
+    for i, (level, cfg) in enumerate(plan):
+        n = 1 << cfg[7] if cfg[7] else o.N // 2
+        a = np.tile(inputs.uniform_values(130 + i, n, 0.05, 1.0), o.N // 2 // n)
+        ocs.append(o.encrypt(a, level, 140 + i))
+        cfgs.append(cfg)
+    gcs = [g.ct_import(c.limbs(), c.level, c.scale) for c in ocs]
+    outs = g.invsqrt_mixed(gcs, cfgs)
+    for i, (oc, cfg, out) in enumerate(zip(ocs, cfgs, outs)):
+        same(out, o.invsqrt(oc, *cfg), f"input {i} (level {oc.level})")
+    graph = g.invsqrt_mixed_graph(gcs, cfgs)
+    try:
+        again = graph.run_many(gcs)
+        for i, (a, b) in enumerate(zip(outs, again)):
+            assert np.array_equal(a.limbs(), b.limbs()), f"graph replay, input {i}"
+    finally:
+        graph.close()
