@@ -503,8 +503,10 @@ hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, 
  * which the transforms' rate is read.  Synchronises. */
 hedap_status hedap_butterfly_rate(hedap_ctx* ctx, double* per_s);
 /* Select NTT launch shapes directly (0 <= variant < 8); every shape computes
- * the same transform.  Context creation runs the autotuner once. */
+ * the same transform.  Context creation runs the autotuner once;
+ * hedap_ntt_get_variant reports the shapes in use (to persist them). */
 hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant);
+hedap_status hedap_ntt_get_variant(const hedap_ctx* ctx, int* fwd_variant, int* inv_variant);
 
 /* Profiling (process-wide, not part of the paper's interface).
  * hedap_profile_enable(1) resets the counters and, until disabled, records a

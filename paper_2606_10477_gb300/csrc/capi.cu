@@ -564,6 +564,13 @@ API hedap_status hedap_butterfly_rate(hedap_ctx* ctx, double* per_s) {
     *per_s = hedap::butterfly_rate(*ctx->c);
   });
 }
+API hedap_status hedap_ntt_get_variant(const hedap_ctx* ctx, int* fwd_variant, int* inv_variant) {
+  return guarded_on(ctx, [&] {
+    need(ctx && fwd_variant && inv_variant, "null argument");
+    *fwd_variant = ctx->c->tab.ntt_fwd_variant;
+    *inv_variant = ctx->c->tab.ntt_inv_variant;
+  });
+}
 API hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant) {
   return guarded_on(ctx, [&] {
     need(ctx && fwd_variant >= 0 && fwd_variant < hedap::kNttVariants && inv_variant >= 0 &&

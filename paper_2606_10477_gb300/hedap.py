@@ -34,7 +34,7 @@ EXPORTED = [
     "hedap_encapsulation_switch", "hedap_bootstrap_slots", "hedap_bootstrap_scaled_slots", "hedap_sub_sum", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_invsqrt_mixed", "hedap_ntt_batch",
-    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
+    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_ntt_get_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
     "hedap_server_resume", "hedap_server_estimate", "hedap_server_wait", "hedap_server_cancel", "hedap_server_inject",
     "hedap_server_merges", "hedap_server_set_table", "hedap_invsqrt_graph_create", "hedap_graph_run",
@@ -181,6 +181,7 @@ def _declare(L):
         "hedap_ntt_tune": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "hedap_ntt_set_variant": (st, [vp, C.c_int, C.c_int]),
+        "hedap_ntt_get_variant": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "hedap_butterfly_rate": (st, [vp, dp]),
         "hedap_select": (st, [vp, C.POINTER(SelectCfg), C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t),
                               C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t), C.POINTER(SelectTrace),
@@ -361,6 +362,12 @@ class Context:
 
     def ntt_set_variant(self, fwd: int, inv: int):
         _check(load().hedap_ntt_set_variant(self.h, fwd, inv))
+
+    def ntt_get_variant(self):
+        """(forward, inverse) NTT launch shapes in use."""
+        f, i = C.c_int(), C.c_int()
+        _check(load().hedap_ntt_get_variant(self.h, C.byref(f), C.byref(i)))
+        return f.value, i.value
 
     def ntt_batch(self, limbs, n_limbs: int, first_prime: int, inverse=False):
         """In-place NTT of a CUDA tensor holding polynomials of n_limbs limbs each."""

@@ -121,6 +121,7 @@ def main(argv=None):
     ap.add_argument("--out", default="provisioning.json")
     ap.add_argument("--table4-levels", default="", help="comma-separated levels for the Table 4 analogue")
     ap.add_argument("--fixed", default="510,6", help="the fixed (degree, Newton steps) compared in Table 4")
+    ap.add_argument("--checkpoint", default="", help="also write a checkpoint (R and the NTT shapes) here")
     args = ap.parse_args(argv)
 
     p = inputs.PRESETS[args.preset]
@@ -145,6 +146,9 @@ def main(argv=None):
     }
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
+    if args.checkpoint:
+        from . import checkpoint
+        checkpoint.save(args.checkpoint, ctx, p, R)
     print(json.dumps({"exploration_s": explore_s, "levels": sorted({r["level"] for r in R}),
                       "R": [(r["level"], r["kind"], r["degree"], r["c"], r["iters"], r["mre"], round(r["ms"], 2))
                             for r in R], "table1": table1, "table4": t4}))

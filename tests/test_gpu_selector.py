@@ -43,3 +43,18 @@ def test_select_tables_follow_from_trace():
     hi = max(lv for lv in levels if any(e["c"] == 0 and e["level"] == lv for e in D))
     rows = sorted((t for t in T if t["level"] == hi and t["c"] == 0 and t["degree"] == 14), key=lambda t: t["iter"])
     assert rows[0]["mre"] > 100 * min(t["mre"] for t in rows)
+
+
+def test_checkpoint_round_trip_on_a_context(tmp_path):
+    """The NTT launch shapes and a table saved from one context are applied to a fresh one with the same key."""
+    from paper_2606_10477_gb300 import checkpoint
+    p = inputs.PRESETS["toy"]
+    a = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
+    a.ntt_set_variant(2, 5)
+    path = str(tmp_path / "ckpt.json")
+    checkpoint.save(path, a, p, [], device="this GPU", git="rev")
+    b = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
+    b.ntt_set_variant(0, 0)
+    assert checkpoint.load(path, b, p, device="this GPU", git="rev")
+    assert b.ntt_get_variant() == (2, 5)
+    assert not checkpoint.load(path, b, inputs.PRESETS["n13"], device="this GPU", git="rev")
