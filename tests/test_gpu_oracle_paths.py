@@ -4,7 +4,7 @@ oracle, bit for bit:
 - Pre-BTS (the paper's c = 1, Sec. 4.1) and a forced bootstrap right after the
   Chebyshev step (Alg. 1's BTS placement, bts_mask bit 0) at N = 2^12;
 - the benchmarked configuration at N = 2^16 (24 + 2 primes, two per digit,
-  degree 31, 3 Newton steps from the top level), one ciphertext through
+  degree 15, 4 Newton steps from the top level), one ciphertext through
   hedap_invsqrt and a batch of 8 through a captured CUDA graph, each member
   unpacked and compared with its own oracle run;
 - mixed levels grouped by level band (hedap_invsqrt_many): each output against
@@ -82,7 +82,7 @@ def test_forced_bootstrap_after_chebyshev_bit_exact(bts12):
 
 
 # ------------------------------------------------------------------ the benchmarked configuration, N = 2^16
-BENCH_CFG = (1e-3, 1.0, 1.0, 31, 3)
+BENCH_CFG = (1e-3, 1.0, 1.0, 15, 4)
 N16_BATCH = 8
 
 
