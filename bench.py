@@ -357,6 +357,16 @@ def run_ours(args):
                     "launch_groups": n_dom, "avg_group_us": 1e3 * ms_dom / max(1, n_dom)}
     roofline["hbm_view"] = {"achieved_gbs": achieved, "peak_gbs": peaks["hbm_gbs"],
                             "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind}
+    # the HBM-bound kernel classes of the same step, against measured HBM (algorithmic bytes: each input word
+    # read once, each output word written once, per launch group)
+    hbm_kernels = []
+    for cls in ("tensor", "elementwise", "ksk_inner", "automorph", "rescale", "moddown", "modup"):
+        n_c, ms_c, by_c = prof[cls]
+        if n_c and ms_c > 0:
+            a_c = by_c / (ms_c / 1e3) / 1e9
+            hbm_kernels.append({"kernel": cls, "bound": "hbm", "achieved": a_c, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                "frac": a_c / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                                "launch_groups_per_step": n_c / n_prof_steps, "avg_group_us": 1e3 * ms_c / n_c})
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     host_in = [torch.empty((2, L + 1, ctx.N), dtype=torch.int64, pin_memory=True) for _ in range(batch)]
@@ -420,6 +430,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
+            "roofline_hbm_kernels": hbm_kernels,
             "profile_share": {k: round(v[1] / total_prof_ms, 4) for k, v in prof.items()} if total_prof_ms else {},
             "profile_classes": {k: {"groups_per_step": v[0] / n_prof_steps, "ms_per_step": v[1] / n_prof_steps,
                                     "us_per_group": 1e3 * v[1] / v[0], "algorithmic_gbs": v[2] / (v[1] / 1e3) / 1e9}
