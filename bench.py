@@ -102,11 +102,11 @@ def measured_peaks():
 # multiply-pipe slots, and 4 low ones = 16 slots per butterfly, against 64 multiply-add lanes per SM.
 NTT_MUL_SLOTS_PER_BUTTERFLY = 16
 IMAD_LANES_PER_SM = 64
-# DRAM bytes per transformed limb, dram__bytes_read.sum + dram__bytes_write.sum of the 12 transform
-# launches of one batched HMult at the top level (`--only hmult --batch 2 --profile-region` under ncu:
-# 1336 MB for 824 limb transforms, the mix of fused ModUp / ModDown / rescale transforms of the step),
+# DRAM bytes per transformed limb: dram__bytes_read.sum + dram__bytes_write.sum of the transform launches of one
+# batched HMult at the top level (`--only hmult --batch 8 --profile-region` under ncu: 5317 MB for 3296 limb
+# transforms, the mix of fused ModUp (with the key inner product), ModDown and rescale transforms of the step),
 # scaled to a launch group by its limbs
-NTT_DRAM_BYTES_PER_LIMB = 1.62e6
+NTT_DRAM_BYTES_PER_LIMB = 1.613e6
 
 
 def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, clk):
