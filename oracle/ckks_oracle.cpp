@@ -1083,9 +1083,11 @@ static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target,
     long o = e.first <= n / 2 ? e.first : e.first - n;
     long k = o / h0; byk[k] = &e.second; kmin = std::min(kmin, k); kmax = std::max(kmax, k);
   }
+  // n1 baby steps: the power of two with n1^2 >= 4 span (a giant step's full key switch costs about four
+  // hoisted baby-step rotations, so the split leans to baby steps), at most 16 per giant step
   long span = kmax - kmin + 1, n1 = 1;
-  while (n1 * n1 < span) n1 <<= 1;
-  n1 = std::min(n1, 16L);  // at most 16 baby steps per giant step
+  while (n1 * n1 < 4 * span) n1 <<= 1;
+  n1 = std::min(n1, 16L);
   long giants = (span + n1 - 1) / n1;
   double sp = target * (double)C.q[v.level] / v.scale;
   // baby steps: every rotation of v used by some giant step, hoisted

@@ -104,9 +104,12 @@ static void layout_group(LTGroup& G, size_t n) {
     G.kmin = std::min(G.kmin, k);
     kmax = std::max(kmax, k);
   }
+  // n1 baby steps: the power of two with n1^2 >= 4 span -- a giant step is a full key switch (ModUp and
+  // ModDown), a baby step a hoisted rotation (inner product and ModDown only), about a quarter of the
+  // transform work -- at most 16 per giant step (one diagonal MAC launch)
   const long span = kmax - G.kmin + 1;
-  while (G.n1 * G.n1 < span) G.n1 <<= 1;
-  G.n1 = std::min(G.n1, 16L);  // at most 16 baby steps per giant step (one diagonal MAC launch)
+  while (G.n1 * G.n1 < 4 * span) G.n1 <<= 1;
+  G.n1 = std::min(G.n1, 16L);
   G.giants = (span + G.n1 - 1) / G.n1;
 }
 static std::vector<LTGroup> make_groups(size_t n, int groups, bool inverse) {
