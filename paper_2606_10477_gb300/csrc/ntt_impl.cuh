@@ -674,7 +674,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S,
 // radix 8, the latter with half the registers per thread); threads per CTA = E / 2^RL.  The autotuner in
 // ntt_tune() times every variant and keeps the fastest per direction.
 // launch shape of the second phase fused with the key inner product (k_ntt_fwd_rows_ksk): 2048 words
-// per CTA, radix-8 passes (256 threads, 8 words and 32 accumulator registers each), 3 CTAs per SM
+// per CTA, radix-8 passes (256 threads, 8 words and 32 accumulator registers each), 2 CTAs per SM (with 3
+// the registers spill and a batched HMult at the top level took 4059 against 3928 us)
 constexpr int kKskWords = 2048, kKskMinBlocks = 2, kKskRL = 3;
 
 template <int L1, int L2, int E, int MINB, int RL>

@@ -225,3 +225,18 @@ def test_sparse_slot_bootstrap_full_size():
     assert b.level == lvl
     err = np.abs(g.decrypt(b) - zt)
     assert np.max(err) < 1e-3 and np.mean(err) < 1e-4
+
+
+def test_bootstrap_full_size_bit_exact():
+    """N = 2^16, 32768 complex slots, log2(QP) = 1555, h = 192: one scaled bootstrap through the library
+    and through the CPU oracle from the same ciphertext, compared bit for bit (the oracle takes about a
+    minute here), and decrypting to its input."""
+    g, lvl = make("bts16", hedap.Context, seed=6)
+    o, lo = make("bts16", oracle.Context, seed=6)
+    assert lvl == lo
+    z = inputs.uniform_values(81, o.N // 2, -1, 1) + 1j * inputs.uniform_values(82, o.N // 2, -1, 1)
+    oc = o.encrypt(z, 1, 83)
+    gc = g.ct_import(oc.limbs(), oc.level, oc.scale)
+    gb, ob = g.bootstrap_scaled(gc, 1), o.bootstrap_scaled(oc, 1)
+    same(gb, ob)
+    assert np.max(np.abs(g.decrypt(gb) - z)) < 1e-3
