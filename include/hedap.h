@@ -520,6 +520,11 @@ hedap_status hedap_ntt_get_variant(const hedap_ctx* ctx, int* fwd_variant, int* 
  * since it was loaded (profiling on or off). */
 hedap_status hedap_profile_enable(int on);
 hedap_status hedap_profile_read(const char* kernel_class, uint64_t* groups, double* ms, double* bytes);
+/* The class's algorithmic multiply work over the same groups, in 32-bit
+ * multiply-pipe slots (kept for "ntt": 16 per Shoup product by a constant --
+ * every butterfly and every term of a fused basis conversion -- and 8 per
+ * 64 x 64 -> 128-bit product of the fused key inner product). */
+hedap_status hedap_profile_read_slots(const char* kernel_class, double* slots);
 hedap_status hedap_launch_count(uint64_t* out);
 
 #ifdef __cplusplus

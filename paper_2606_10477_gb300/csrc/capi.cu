@@ -288,6 +288,14 @@ API hedap_status hedap_profile_enable(int on) {
     hedap::prof_enable(on != 0);
   });
 }
+API hedap_status hedap_profile_read_slots(const char* cls, double* slots) {
+  return guarded([&] {
+    need(cls && slots, "null argument");
+    const int c = hedap::prof_class_of(cls);
+    need(c >= 0, "unknown kernel class");
+    *slots = hedap::prof_read_slots(c);
+  });
+}
 API hedap_status hedap_profile_read(const char* cls, uint64_t* scopes, double* ms, double* bytes) {
   return guarded([&] {
     need(cls != nullptr, "null argument");

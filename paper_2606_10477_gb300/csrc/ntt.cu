@@ -46,7 +46,18 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   const int v = inverse ? T.ntt_inv_variant : T.ntt_fwd_variant;
   // algorithmic bytes: each transformed limb read once and written once (a digit's own limbs are skipped)
   const double limbs = (double)S.n_parts * S.n_limbs - (A.own_alpha ? (double)S.n_parts / A.own_dn * A.own_limit : 0.0);
-  ProfScope prof_(PROF_NTT, st, 16.0 * limbs * ((size_t)1 << T.log_n));
+  const double n = (double)((size_t)1 << T.log_n);
+  ProfScope prof_(PROF_NTT, st, 16.0 * limbs * n);
+  // algorithmic multiply work in 32-bit multiply-pipe slots: a Shoup product by a constant is 6 wide (2 slots
+  // each) and 4 low products = 16 slots; every butterfly has one, and so does every term of a fused basis
+  // conversion (ModUp: min(alpha, own_limit) per word of a converted limb; ModDown: K per word); the fused key
+  // inner product multiplies every word of every digit by two key words, a full 64 x 64 -> 128-bit product of 4
+  // wide products = 8 slots each
+  double shoup = limbs * n / 2 * T.log_n;
+  if (A.z) shoup += limbs * n * std::min(A.own_alpha, A.own_limit);
+  if (A.pconv) shoup += limbs * n * A.pconv_K;
+  prof_.slots = 16.0 * shoup;
+  if (F) prof_.slots += 8.0 * 2.0 * F->batch * (double)S.n_limbs * A.own_dn * n;
   prof_count_launches(2);
   ntt_launch(T.log_n, v, S, T, st, inverse, A, F);
 }

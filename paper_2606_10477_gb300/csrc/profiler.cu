@@ -13,12 +13,12 @@ std::atomic<bool> g_on{false};
 std::mutex g_mu;
 struct Rec {
   int cls;
-  double bytes;
+  double bytes, slots;
   cudaEvent_t a, b;
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_free;
-double g_ms[PROF_N_CLASSES], g_bytes[PROF_N_CLASSES];
+double g_ms[PROF_N_CLASSES], g_bytes[PROF_N_CLASSES], g_slots[PROF_N_CLASSES];
 uint64_t g_scopes[PROF_N_CLASSES];
 const char* kNames[PROF_N_CLASSES] = {"ntt", "modup", "ksk_inner", "moddown", "tensor", "rescale", "automorph",
                                       "elementwise"};
@@ -40,6 +40,7 @@ void drain() {  // caller holds g_mu
     cudaEventElapsedTime(&ms, r.a, r.b);
     g_ms[r.cls] += ms;
     g_bytes[r.cls] += r.bytes;
+    g_slots[r.cls] += r.slots;
     g_scopes[r.cls] += 1;
     g_free.push_back(r.a);
     g_free.push_back(r.b);
@@ -57,6 +58,7 @@ void prof_reset() {
   drain();
   memset(g_ms, 0, sizeof(g_ms));
   memset(g_bytes, 0, sizeof(g_bytes));
+  memset(g_slots, 0, sizeof(g_slots));
   memset(g_scopes, 0, sizeof(g_scopes));
 }
 void prof_read(int cls, uint64_t* scopes, double* ms, double* bytes) {
@@ -66,6 +68,11 @@ void prof_read(int cls, uint64_t* scopes, double* ms, double* bytes) {
   if (scopes) *scopes = g_scopes[cls];
   if (ms) *ms = g_ms[cls];
   if (bytes) *bytes = g_bytes[cls];
+}
+double prof_read_slots(int cls) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  drain();
+  return cls >= 0 && cls < PROF_N_CLASSES ? g_slots[cls] : 0.0;
 }
 int prof_class_of(const char* name) {
   for (int i = 0; i < PROF_N_CLASSES; ++i)
@@ -84,7 +91,7 @@ ProfScope::~ProfScope() {
   if (!a) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEventRecord(b, st);
-  g_recs.push_back(Rec{cls, bytes, a, b});
+  g_recs.push_back(Rec{cls, bytes, slots, a, b});
   if (g_recs.size() > 8192) drain();
 }
 

@@ -18,12 +18,15 @@ bool prof_enabled();
 void prof_reset();
 // sum of event-timed milliseconds, enclosed launches and algorithmic bytes of a class (synchronises)
 void prof_read(int cls, uint64_t* scopes, double* ms, double* bytes);
+// the same class's algorithmic multiply work in 32-bit multiply-pipe slots (see ProfScope::slots)
+double prof_read_slots(int cls);
 int prof_class_of(const char* name);
 
 struct ProfScope {
   int cls;
   cudaStream_t st;
   double bytes;
+  double slots = 0;  // algorithmic multiply work of the enclosed launches, in 32-bit multiply-pipe slots
   cudaEvent_t a = nullptr, b = nullptr;
   ProfScope(int cls_, cudaStream_t st_, double bytes_);
   ~ProfScope();

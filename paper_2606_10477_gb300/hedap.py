@@ -28,7 +28,7 @@ EXPORTED = [
     "hedap_gen_galois_key", "hedap_galois_element", "hedap_export_key", "hedap_encrypt", "hedap_decrypt", "hedap_ct_import",
     "hedap_ct_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
     "hedap_rescale", "hedap_rotate", "hedap_rotate_hoisted", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
-    "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read",
+    "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read", "hedap_profile_read_slots",
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
     "hedap_bootstrap_setup", "hedap_bootstrap", "hedap_bootstrap_scaled", "hedap_bootstrap_encapsulate",
     "hedap_encapsulation_switch", "hedap_bootstrap_slots", "hedap_bootstrap_scaled_slots", "hedap_sub_sum", "hedap_mod_raise", "hedap_mul_monomial",
@@ -151,6 +151,7 @@ def _declare(L):
         "hedap_ntt": (st, [vp, u64p, C.c_size_t, C.c_uint32, C.c_int, C.c_int]),
         "hedap_profile_enable": (st, [C.c_int]),
         "hedap_profile_read": (st, [C.c_char_p, u64p, dp, dp]),
+        "hedap_profile_read_slots": (st, [C.c_char_p, dp]),
         "hedap_launch_count": (st, [u64p]),
         "hedap_modup": (st, [vp, u64p, C.c_int, u64p]),
         "hedap_moddown": (st, [vp, u64p, C.c_int, u64p]),
@@ -736,6 +737,13 @@ def profile_read() -> dict:
         _check(load().hedap_profile_read(c.encode(), C.byref(n), C.byref(ms), C.byref(by)))
         out[c] = (n.value, ms.value, by.value)
     return out
+
+
+def profile_read_slots(kernel_class: str) -> float:
+    """Algorithmic multiply work (32-bit multiply-pipe slots) of a class since profile_enable(True)."""
+    v = C.c_double()
+    _check(load().hedap_profile_read_slots(kernel_class.encode(), C.byref(v)))
+    return v.value
 
 
 def launch_count() -> int:
