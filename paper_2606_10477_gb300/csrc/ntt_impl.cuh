@@ -98,6 +98,20 @@ __device__ __forceinline__ const u64* first_src(const NttAux& A, const LimbSet& 
 
 // shared-memory index of element x of a row block: one pad word every 16
 __device__ __forceinline__ uint32_t padx(uint32_t x) { return x + (x >> 4); }
+// Row layout (rows of 2^L2 words, R = 2^L2 + 2^(L2-4) apart).  For the words idx = t + i TPB of an unrolled
+// loop (t = threadIdx.x; TPB and 2^L2 powers of two, TPB a multiple of 16) the offset is a per-thread part
+// row_off(t) plus a compile-time part row_step(i): no index arithmetic per word.
+template <int L2>
+__device__ __forceinline__ uint32_t row_off(uint32_t t) {
+  return (t >> L2) * ((1u << L2) + (1u << (L2 - 4))) + padx(t & ((1u << L2) - 1));
+}
+template <int L2, int TPB>
+__host__ __device__ constexpr uint32_t row_step(int i) {
+  constexpr uint32_t P2 = 1u << L2, R = P2 + (P2 >> 4);
+  return (uint32_t)TPB >= P2 ? (uint32_t)i * ((uint32_t)TPB >> L2) * R
+                             : (uint32_t)(i / (int)(P2 / TPB)) * R + (uint32_t)(i % (int)(P2 / TPB)) * TPB +
+                                   (((uint32_t)(i % (int)(P2 / TPB)) * TPB) >> 4);
+}
 
 // ---------------------------------------------------------------- forward, column phase
 // element (c, col) at sm[c * C + col]; global index j = r0 + col + c * 2^L2;
@@ -387,10 +401,12 @@ __device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* tw, u
       const uint32_t b = g / GPB, gg = g % GPB;
       const uint32_t low = gg & (TL - 1), high = gg >> (L2 - S0 - K);
       const uint32_t base = (high << (L2 - S0)) | low;
-      u64* blk = sm + b * R;
+      // padx(base + m TL) = padx(base) + m TL + (m TL >> 4): base is aligned to the group's span except for
+      // low < TL, so the pad words between the group's elements depend on m only
+      u64* blk = sm + b * R + padx(base);
       u64 v[1 << K];
 #pragma unroll
-      for (int m = 0; m < (1 << K); ++m) v[m] = blk[padx(base + m * TL)];
+      for (int m = 0; m < (1 << K); ++m) v[m] = blk[m * TL + ((m * TL) >> 4)];
 #pragma unroll
       for (int u = 0; u < K; ++u) {
         const int sl = S0 + u, half = 1 << (K - 1 - u);
@@ -402,7 +418,7 @@ __device__ __forceinline__ void fwd_rows_passes(u64* sm, const ulonglong2* tw, u
         }
       }
 #pragma unroll
-      for (int m = 0; m < (1 << K); ++m) blk[padx(base + m * TL)] = v[m];
+      for (int m = 0; m < (1 << K); ++m) blk[m * TL + ((m * TL) >> 4)] = v[m];
     }
     __syncthreads();
     fwd_rows_passes<L1, L2, BPC, RL, S0 + K>(sm, tw, q);
@@ -421,8 +437,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   u64* a = S.limb(part, li, N);
   ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + BPC * R);
   const size_t j0 = (size_t)blockIdx.x * E;
+  u64* smt = sm + row_off<L2>(threadIdx.x);  // this thread's words: smt[row_step(i)] holds word t + i TPB
 #pragma unroll
-  for (int idx = threadIdx.x; idx < E; idx += TPB) cp_async8(sm + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), a + j0 + idx);
+  for (int i = 0; i < E / TPB; ++i) cp_async8(smt + row_step<L2, TPB>(i), a + j0 + threadIdx.x + i * TPB);
   fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
   cp_async_commit();
   if (A.fin_dst) {  // the epilogue's operands: fetched into L2 while the passes run (128-byte lines)
@@ -443,8 +460,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
     const u64 w = A.fin_w[li], wp = A.fin_wsh[li];
     const bool acc = (part & 1) ? A.fin_acc_odd : A.fin_acc_even;
 #pragma unroll
-    for (int idx = threadIdx.x; idx < E; idx += TPB) {
-      const u64 v = reduce8q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+    for (int i = 0; i < E / TPB; ++i) {
+      const int idx = threadIdx.x + i * TPB;
+      const u64 v = reduce8q(smt[row_step<L2, TPB>(i)], q);
       u64 z = shoup_mul(sub_mod(cp[idx], v, q), w, wp, q);
       if (acc) z = add_mod(z, dp[idx], q);
       dp[idx] = z;
@@ -452,8 +470,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
     return;
   }
 #pragma unroll
-  for (int idx = threadIdx.x; idx < E; idx += TPB)
-    a[j0 + idx] = reduce8q(sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+  for (int i = 0; i < E / TPB; ++i) a[j0 + threadIdx.x + i * TPB] = reduce8q(smt[row_step<L2, TPB>(i)], q);
 }
 
 // ---------------------------------------------------------------- forward, block phase fused with the key inner product
@@ -481,11 +498,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows_ksk(Tables T, LimbSe
   const size_t j0 = (size_t)blk * E;
   const int dn = A.own_dn;
   const int own = (A.own_alpha && t < A.own_limit) ? t / A.own_alpha : -1;
+  const uint32_t toff = row_off<L2>(threadIdx.x);  // word t + i TPB of a buffer at toff + row_step(i)
   auto fetch = [&](int j, u64* dst) {
-    const u64* src = j == own ? F.d + (size_t)k * F.d_stride + (size_t)t * N + j0
-                              : S.limb(k * dn + j, t, N) + j0;
-    for (int idx = threadIdx.x; idx < E; idx += TPB)
-      cp_async8(dst + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), src + idx);
+    const u64* src = (j == own ? F.d + (size_t)k * F.d_stride + (size_t)t * N + j0
+                               : S.limb(k * dn + j, t, N) + j0) + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < E / TPB; ++i) cp_async8(dst + toff + row_step<L2, TPB>(i), src + i * TPB);
   };
   fwd_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.psi2 + (size_t)pt * N, (uint32_t)(blk * BPC));
   fetch(0, buf[0]);
@@ -510,7 +528,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows_ksk(Tables T, LimbSe
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int idx = threadIdx.x + i * TPB;  // consecutive threads, consecutive words
-      const u64 v = reduce8q(cur[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))], q);
+      const u64 v = reduce8q(cur[toff + row_step<L2, TPB>(i)], q);
       mac128(ab[i], v, __ldg(kbj + idx));
       mac128(aa[i], v, __ldg(kaj + idx));
     }
@@ -554,10 +572,10 @@ __device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* tw, u
       const uint32_t b = g / GPB, gg = g % GPB;
       const uint32_t low = gg & ((1u << LT0) - 1), high = gg >> LT0;
       const uint32_t base = (high << (LT0 + K)) | low;
-      u64* blk = sm + b * R;
+      u64* blk = sm + b * R + padx(base);  // as in the forward passes: the pads depend on m only
       u64 v[1 << K];
 #pragma unroll
-      for (int m = 0; m < (1 << K); ++m) v[m] = blk[padx(base + (m << LT0))];
+      for (int m = 0; m < (1 << K); ++m) v[m] = blk[(m << LT0) + ((m << LT0) >> 4)];
 #pragma unroll
       for (int u = 0; u < K; ++u) {
         const int lt = LT0 + u, half = 1 << u;
@@ -570,7 +588,7 @@ __device__ __forceinline__ void inv_rows_passes(u64* sm, const ulonglong2* tw, u
         }
       }
 #pragma unroll
-      for (int m = 0; m < (1 << K); ++m) blk[padx(base + (m << LT0))] = v[m];
+      for (int m = 0; m < (1 << K); ++m) blk[(m << LT0) + ((m << LT0) >> 4)] = v[m];
     }
     __syncthreads();
     inv_rows_passes<L1, L2, BPC, RL, LT0 + K>(sm, tw, q);
@@ -590,16 +608,16 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_rows(Tables T, LimbSet S,
   const u64* src = first_src(A, S, part, li, N);
   ulonglong2* tw = reinterpret_cast<ulonglong2*>(sm + BPC * R);
   const size_t j0 = (size_t)blockIdx.x * E;
+  u64* smt = sm + row_off<L2>(threadIdx.x);  // this thread's words: smt[row_step(i)] holds word t + i TPB
 #pragma unroll
-  for (int idx = threadIdx.x; idx < E; idx += TPB) cp_async8(sm + (idx >> L2) * R + padx(idx & ((1 << L2) - 1)), src + j0 + idx);
+  for (int i = 0; i < E / TPB; ++i) cp_async8(smt + row_step<L2, TPB>(i), src + j0 + threadIdx.x + i * TPB);
   inv_rows_stage_twiddles<L1, L2, BPC, TPB>(tw, T.ipsi2 + (size_t)pi * N, (uint32_t)(blockIdx.x * BPC));
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
   inv_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
 #pragma unroll
-  for (int idx = threadIdx.x; idx < E; idx += TPB)
-    a[j0 + idx] = sm[(idx >> L2) * R + padx(idx & ((1 << L2) - 1))];  // [0, 2q)
+  for (int i = 0; i < E / TPB; ++i) a[j0 + threadIdx.x + i * TPB] = smt[row_step<L2, TPB>(i)];  // [0, 2q)
 }
 
 // ---------------------------------------------------------------- inverse, column phase (+ N^-1)
