@@ -493,7 +493,9 @@ def test_homomorphic_invsqrt_tracks_plain_model():
         out = ctx.invsqrt(ct, 0.01, 1.0, 1.0, d, k)
         y = ctx.decrypt(out).real
         plain = oracle.plain_invsqrt(a, 0.01, 1.0, 1.0, d, k)
-        assert np.max(np.abs(y - plain) / plain) < 1e-6
+        # CKKS noise at scale 2^40 keeps the homomorphic result within about 2e-8 of the FP64 model; a dropped
+        # term, a wrong coefficient or a mislabelled scale would show far above 1e-7
+        assert np.max(np.abs(y - plain) / plain) < 1e-7
         # no bootstrapping: the fewest-products Chebyshev plan (ceil(log2(d+1)) + 1 levels for d = 2^m - 1)
         depth = 1 + (math.ceil(math.log2(d + 1)) + 1) + 2 * k
         assert out.level == 10 - depth
