@@ -48,6 +48,36 @@ hedap_status graph_guard(F&& f) {
   }
 }
 
+// Capture `work` (issued on the context's stream) into G's graph and instantiate it: the context's stream is
+// swapped for a fresh capturing stream meanwhile; G->kernels counts the launches captured.  The caller holds
+// the context's lock and has run the same work once already (every lazily built table exists).
+template <class F>
+void capture(Ctx& C, hedap_graph& G, F&& work) {
+  HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  cudaStream_t cs, old = C.stream;
+  HEDAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const uint64_t k0 = prof_launches();
+  C.stream = cs;
+  cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  std::string failure;
+  if (ce == cudaSuccess) {
+    try {
+      work();
+    } catch (const std::exception& e) {
+      failure = e.what();
+    }
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(cs, &g);
+    G.graph = g;
+  }
+  C.stream = old;
+  cudaStreamDestroy(cs);
+  if (!failure.empty()) throw Error(HEDAP_ERR_CUDA, "graph capture: " + failure);
+  if (ce != cudaSuccess) throw Error(HEDAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  G.kernels = prof_launches() - k0;
+  HEDAP_CUDA(cudaGraphInstantiate(&G.exec, G.graph, 0));
+}
+
 }  // namespace
 
 #define API extern "C" __attribute__((visibility("default")))
@@ -69,30 +99,7 @@ API hedap_status hedap_invsqrt_graph_create(hedap_ctx* ctx, const hedap_ct* exam
       G->out = ct_alloc(C, w->level, w->batch);
       G->out->scale = w->scale;
     }
-    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
-    cudaStream_t cs, old = C.stream;
-    HEDAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    const uint64_t k0 = prof_launches();
-    C.stream = cs;
-    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    std::string failure;
-    if (ce == cudaSuccess) {
-      try {
-        auto r = invsqrt(C, *G->in, *cfg);
-        copy_ct(C, *r, *G->out);
-      } catch (const std::exception& e) {
-        failure = e.what();
-      }
-      cudaGraph_t g = nullptr;
-      ce = cudaStreamEndCapture(cs, &g);
-      G->graph = g;
-    }
-    C.stream = old;
-    cudaStreamDestroy(cs);
-    if (!failure.empty()) throw Error(HEDAP_ERR_CUDA, "graph capture: " + failure);
-    if (ce != cudaSuccess) throw Error(HEDAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-    G->kernels = prof_launches() - k0;
-    HEDAP_CUDA(cudaGraphInstantiate(&G->exec, G->graph, 0));
+    capture(C, *G, [&] { copy_ct(C, *invsqrt(C, *G->in, *cfg), *G->out); });
     *out = G.release();
   });
 }
@@ -146,30 +153,10 @@ API hedap_status hedap_invsqrt_mixed_graph_create(hedap_ctx* ctx, const hedap_ct
         G->outs.back()->scale = r->scale;
       }
     }
-    HEDAP_CUDA(cudaStreamSynchronize(C.stream));
-    cudaStream_t cs, old = C.stream;
-    HEDAP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    const uint64_t k0 = prof_launches();
-    C.stream = cs;
-    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    std::string failure;
-    if (ce == cudaSuccess) {
-      try {
-        auto r = invsqrt_mixed(C, in, cv);
-        for (size_t i = 0; i < n; ++i) copy_ct(C, *r[i], *G->outs[i]);
-      } catch (const std::exception& e) {
-        failure = e.what();
-      }
-      cudaGraph_t g = nullptr;
-      ce = cudaStreamEndCapture(cs, &g);
-      G->graph = g;
-    }
-    C.stream = old;
-    cudaStreamDestroy(cs);
-    if (!failure.empty()) throw Error(HEDAP_ERR_CUDA, "graph capture: " + failure);
-    if (ce != cudaSuccess) throw Error(HEDAP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-    G->kernels = prof_launches() - k0;
-    HEDAP_CUDA(cudaGraphInstantiate(&G->exec, G->graph, 0));
+    capture(C, *G, [&] {
+      auto r = invsqrt_mixed(C, in, cv);
+      for (size_t i = 0; i < n; ++i) copy_ct(C, *r[i], *G->outs[i]);
+    });
     *out = G.release();
   });
 }
