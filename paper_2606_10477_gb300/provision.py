@@ -67,7 +67,7 @@ def chebyshev_vs_bts(ctx, lmax, A, B_max, B, degrees, reps=3):
     return rows
 
 
-def table4(ctx, R, levels, A, B_max, B, fixed, reps=3):
+def table4(ctx, R, levels, A, B_max, B, fixed, reps=3, extra=()):
     """Table 4 analogue: at each level, CryptoInvSqrt with HE-DAP's accuracy (u1) and speed (u2) choices
     against a fixed (degree, Newton steps) configuration (PP-STAT's d = 510, i = 6 in the paper), each with
     lazy bootstrapping in the Newton loop and Pre-BTS only where the fixed degree needs it; time (CUDA
@@ -90,6 +90,12 @@ def table4(ctx, R, levels, A, B_max, B, fixed, reps=3):
                 continue
             cands.append((f"fixed d={d}, i={i}", d, c, i))
             break
+        for d, c, i in extra:  # other named configurations, where they fit the level
+            try:
+                ctx.invsqrt(ct, A, B_max, B, d, 0, c, 1 << 63)
+            except hedap.HedapError:
+                continue
+            cands.append((f"given d={d}, c={c}, i={i}", d, c, i))
         for name, d, c, i in cands:
             best = float("inf")
             y = None
@@ -122,6 +128,7 @@ def main(argv=None):
     ap.add_argument("--table4-levels", default="", help="comma-separated levels for the Table 4 analogue")
     ap.add_argument("--fixed", default="510,6", help="the fixed (degree, Newton steps) compared in Table 4")
     ap.add_argument("--checkpoint", default="", help="also write a checkpoint (R and the NTT shapes) here")
+    ap.add_argument("--extra", default="", help="more (degree,c,iters) configurations for Table 4, ';'-separated")
     args = ap.parse_args(argv)
 
     p = inputs.PRESETS[args.preset]
@@ -138,7 +145,8 @@ def main(argv=None):
                               [(1 << e) - 2 for e in range(args.de_min, args.de_max + 1)]) if p["hw"] else []
     levels4 = [int(v) for v in args.table4_levels.split(",") if v]
     fixed = tuple(int(v) for v in args.fixed.split(","))
-    t4 = table4(ctx, R, levels4, args.A, args.B_max, args.B, fixed) if levels4 else []
+    extra = [tuple(int(v) for v in e.split(",")) for e in args.extra.split(";") if e]
+    t4 = table4(ctx, R, levels4, args.A, args.B_max, args.B, fixed, extra=extra) if levels4 else []
     out = {
         "key": {"device": device_name(), "preset": args.preset, "params": p, "git": git_revision()},
         "config": vars(args), "l_max": lmax, "exploration_s": explore_s,
