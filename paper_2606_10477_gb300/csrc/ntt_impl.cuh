@@ -691,10 +691,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_inv_cols(Tables T, LimbSet S,
 // allocation must allow (MINB) and the stages per register pass (RL: radix 16 or
 // radix 8, the latter with half the registers per thread); threads per CTA = E / 2^RL.  The autotuner in
 // ntt_tune() times every variant and keeps the fastest per direction.
-// launch shape of the second phase fused with the key inner product (k_ntt_fwd_rows_ksk): 2048 words
-// per CTA, radix-8 passes (256 threads, 8 words and 32 accumulator registers each), 2 CTAs per SM (with 3
-// the registers spill and a batched HMult at the top level took 4059 against 3928 us)
-constexpr int kKskWords = 2048, kKskMinBlocks = 2, kKskRL = 3;
+// launch shape of the second phase fused with the key inner product (k_ntt_fwd_rows_ksk): 1024 words
+// per CTA, radix-8 passes (128 threads, 8 words and 32 accumulator registers each), registers left
+// uncapped (168 a thread, 3 CTAs per SM).  A batched HMult at the top level (N = 2^16, batch 8) took
+// 3.72 ms, against 3.95 ms with 2048 words and 2 CTAs per SM (128 registers, spilling), 3.82 ms with
+// 1024 words and 4 CTAs per SM (128 registers) and 3.78 ms with 512 words in radix-4 passes.
+constexpr int kKskWords = 1024, kKskMinBlocks = 2, kKskRL = 3;
 
 template <int L1, int L2, int E, int MINB, int RL>
 static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool inverse, const NttAux& A,
