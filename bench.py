@@ -439,6 +439,7 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "ntt_gbs": ntt_gbs,
             "ntt_batched": ntt,
+            "ntt_shapes": ctx.ntt_get_roles(),
             "per_op_us": ops,
             "clocks": clk,
             "gpu_launches": launches,
@@ -965,7 +966,8 @@ def run_hmult_only(args):
         torch.cuda.profiler.stop()
     print(json.dumps({"hmult": {"batch": args.batch, "level": L, "ms": e0.elapsed_time(e1) / reps,
                                 "ntt_launch_groups": n_ntt, "ntt_ms": ms_ntt, "ntt_algorithmic_bytes": by_ntt,
-                                "ntt_limbs": by_ntt / (16.0 * ctx.N)}}), flush=True)
+                                "ntt_limbs": by_ntt / (16.0 * ctx.N), "ntt_shapes": ctx.ntt_get_roles()}}),
+          flush=True)
 
 
 def run_ntt_only(args):

@@ -495,7 +495,11 @@ void hedap_graph_destroy(hedap_graph* g);
  * SM, radix 16 or 8 register passes) on `limbs` limbs of scratch, forward and inverse separately (best of
  * `reps`), and makes the fastest the context's shape.  Per-variant times go
  * to fwd_ms / inv_ms (capacity cap, may be NULL); the chosen variant indices
- * to *fwd_variant / *inv_variant. */
+ * to *fwd_variant / *inv_variant.  The forward transforms with a fused key-switch
+ * conversion (HEDAP_NTT_ROLE_MODUP) or a fused ModDown / rescale
+ * (HEDAP_NTT_ROLE_FINISH) are then tuned apart, each on a key switch of a batch of
+ * 4 ciphertexts at the top level followed by a rescale (when the relinearisation
+ * key exists); hedap_ntt_get_role_variant reports their choices. */
 hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
                             int* fwd_variant, int* inv_variant);
 /* Butterflies per second of a register-only loop of the NTT's butterfly (no
@@ -503,10 +507,21 @@ hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, 
  * which the transforms' rate is read.  Synchronises. */
 hedap_status hedap_butterfly_rate(hedap_ctx* ctx, double* per_s);
 /* Select NTT launch shapes directly (0 <= variant < 8); every shape computes
- * the same transform.  Context creation runs the autotuner once;
- * hedap_ntt_get_variant reports the shapes in use (to persist them). */
+ * the same transform.  Context creation runs the autotuner once.
+ * hedap_ntt_set_variant gives every forward role fwd_variant and the inverse
+ * inv_variant; hedap_ntt_get_variant reports the plain forward and inverse shapes.
+ * The per-role calls read or set one role (to persist the autotuner's choice or
+ * to run one fused kernel in a given shape); HEDAP_ERR_ARG for an unknown role
+ * or a variant out of range. */
+#define HEDAP_NTT_ROLE_FORWARD 0 /* plain forward transform */
+#define HEDAP_NTT_ROLE_INVERSE 1 /* inverse transform */
+#define HEDAP_NTT_ROLE_MODUP 2   /* forward with the ModUp conversion fused into its load */
+#define HEDAP_NTT_ROLE_FINISH 3  /* forward with a fused ModDown / rescale (load and store) */
+#define HEDAP_NTT_ROLES 4
 hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_variant);
 hedap_status hedap_ntt_get_variant(const hedap_ctx* ctx, int* fwd_variant, int* inv_variant);
+hedap_status hedap_ntt_set_role_variant(hedap_ctx* ctx, int role, int variant);
+hedap_status hedap_ntt_get_role_variant(const hedap_ctx* ctx, int role, int* variant);
 
 /* Profiling (process-wide, not part of the paper's interface).
  * hedap_profile_enable(1) resets the counters and, until disabled, records a

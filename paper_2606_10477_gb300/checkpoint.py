@@ -1,5 +1,6 @@
 """Persist and reload what a deployment measures once (Sec. 4.2: HE-DAP's table is provisioned "during the
-installation" and reused): the per-level table R of Alg. 3 and the NTT autotuner's launch shapes.
+installation" and reused): the per-level table R of Alg. 3 and the NTT autotuner's launch shapes (one per role: plain forward, inverse,
+forward with the ModUp conversion, forward with a fused ModDown / rescale).
 
 A checkpoint is a JSON file keyed by device name, CKKS parameter set and git revision.  It is applied only when
 the key matches the running context: a table measured on another GPU, parameter set or library revision would
@@ -15,7 +16,7 @@ import os
 
 from .provision import device_name, git_revision
 
-FORMAT = 1
+FORMAT = 2
 
 
 def checkpoint_key(params: dict, device: str | None = None, git: str | None = None) -> dict:
@@ -26,8 +27,7 @@ def checkpoint_key(params: dict, device: str | None = None, git: str | None = No
 
 
 def save(path: str, ctx, params: dict, R=None, device: str | None = None, git: str | None = None) -> dict:
-    fwd, inv = ctx.ntt_get_variant()
-    doc = {"key": checkpoint_key(params, device, git), "ntt_variant": {"forward": fwd, "inverse": inv},
+    doc = {"key": checkpoint_key(params, device, git), "ntt_variant": dict(ctx.ntt_get_roles()),
            "R": list(R or [])}
     tmp = f"{path}.tmp{os.getpid()}"
     with open(tmp, "w") as f:
@@ -45,8 +45,7 @@ def load(path: str, ctx, params: dict, server=None, device: str | None = None, g
         doc = json.load(f)
     if doc.get("key") != checkpoint_key(params, device, git):
         return False
-    v = doc["ntt_variant"]
-    ctx.ntt_set_variant(int(v["forward"]), int(v["inverse"]))
+    ctx.ntt_set_roles({k: int(v) for k, v in doc["ntt_variant"].items()})
     if server is not None and doc.get("R"):
         server.set_table(doc["R"])
     return True

@@ -584,8 +584,23 @@ API hedap_status hedap_ntt_set_variant(hedap_ctx* ctx, int fwd_variant, int inv_
     need(ctx && fwd_variant >= 0 && fwd_variant < hedap::kNttVariants && inv_variant >= 0 &&
              inv_variant < hedap::kNttVariants,
          "variant out of range");
-    ctx->c->tab.ntt_fwd_variant = fwd_variant;
-    ctx->c->tab.ntt_inv_variant = inv_variant;
+    hedap::Tables& T = ctx->c->tab;
+    T.ntt_fwd_variant = T.ntt_modup_variant = T.ntt_fin_variant = fwd_variant;
+    T.ntt_inv_variant = inv_variant;
+  });
+}
+API hedap_status hedap_ntt_set_role_variant(hedap_ctx* ctx, int role, int variant) {
+  return guarded_on(ctx, [&] {
+    need(ctx && variant >= 0 && variant < hedap::kNttVariants, "variant out of range");
+    need(role >= 0 && role < HEDAP_NTT_ROLES, "unknown NTT role");
+    hedap::ntt_role_variant(ctx->c->tab, role) = variant;
+  });
+}
+API hedap_status hedap_ntt_get_role_variant(const hedap_ctx* ctx, int role, int* variant) {
+  return guarded_on(ctx, [&] {
+    need(ctx && variant, "null argument");
+    need(role >= 0 && role < HEDAP_NTT_ROLES, "unknown NTT role");
+    *variant = hedap::ntt_role_variant(ctx->c->tab, role);
   });
 }
 

@@ -94,7 +94,7 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   upload(*C, C->d_ninv_sh, ninv_sh);
   upload(*C, C->d_r64, r64);
   C->tab = Tables{(const PrimeDev*)C->d_primes.p, (const ulonglong2*)C->d_psi2.p, (const ulonglong2*)C->d_ipsi2.p,
-                  C->d_ninv.p, C->d_ninv_sh.p, C->log_n, 3, 3};
+                  C->d_ninv.p, C->d_ninv_sh.p, C->log_n, 3, 3, 3, 3};
 
   // P = prod p_k; ModDown constants and P mod q_t
   const int K = C->n_p, nq = C->n_q;

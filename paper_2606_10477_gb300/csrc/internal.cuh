@@ -87,10 +87,17 @@ struct Tables {
   const u64* ninv;           // [n_primes] N^-1
   const u64* ninv_sh;
   int log_n;
-  int ntt_fwd_variant;       // NTT launch shape (see ntt.cu), chosen by ntt_tune
+  // NTT launch shapes (see ntt_impl.cuh) per role, chosen by ntt_tune: the plain forward transform, the
+  // inverse, the forward with the ModUp conversion fused into its load (the key switch's extended digits),
+  // and the forward with a fused ModDown / rescale (conversion or spread load, finishing store)
+  int ntt_fwd_variant;
   int ntt_inv_variant;
+  int ntt_modup_variant;
+  int ntt_fin_variant;
 };
 constexpr int kNttVariants = 8;
+enum NttRole { NTT_ROLE_FORWARD = 0, NTT_ROLE_INVERSE = 1, NTT_ROLE_MODUP = 2, NTT_ROLE_FINISH = 3 };
+int& ntt_role_variant(Tables& T, int role);
 
 // A set of limbs: parts p in [0, n_parts), limbs li in [limb_begin, limb_begin+n_limbs)
 // at base + p*part_stride + li*N.  Limb li < q_count uses prime prime_offset+li,

@@ -43,7 +43,9 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
     throw Error(HEDAP_ERR_ARG, "NTT: bad ModDown fusion");
   if (A.spread && (A.z || A.src || !A.spread_sub)) throw Error(HEDAP_ERR_ARG, "NTT: bad spread fusion");
   if (A.fin_dst && (!A.fin_c || !A.fin_w || !A.fin_wsh)) throw Error(HEDAP_ERR_ARG, "NTT: bad epilogue fusion");
-  const int v = inverse ? T.ntt_inv_variant : T.ntt_fwd_variant;
+  const int v = inverse ? T.ntt_inv_variant
+                        : A.z ? T.ntt_modup_variant
+                              : (A.pconv || A.spread || A.fin_dst) ? T.ntt_fin_variant : T.ntt_fwd_variant;
   // algorithmic bytes: each transformed limb read once and written once (a digit's own limbs are skipped)
   const double limbs = (double)S.n_parts * S.n_limbs - (A.own_alpha ? (double)S.n_parts / A.own_dn * A.own_limit : 0.0);
   const double n = (double)((size_t)1 << T.log_n);
@@ -116,8 +118,22 @@ double butterfly_rate(Ctx& C) {
   return (double)threads * blocks * iters * 4 / (best / 1e3);
 }
 
-// Time every variant on `limbs` limbs of scratch (forward and inverse separately,
-// best of `reps` after one warm-up) and keep the fastest in C.tab.
+int& ntt_role_variant(Tables& T, int role) {
+  switch (role) {
+    case NTT_ROLE_FORWARD: return T.ntt_fwd_variant;
+    case NTT_ROLE_INVERSE: return T.ntt_inv_variant;
+    case NTT_ROLE_MODUP: return T.ntt_modup_variant;
+    case NTT_ROLE_FINISH: return T.ntt_fin_variant;
+    default: throw Error(HEDAP_ERR_ARG, "unknown NTT role");
+  }
+}
+
+// Time every variant on `limbs` limbs of scratch (forward and inverse separately, best of `reps` after
+// one warm-up) and keep the fastest in C.tab.  The fused roles run other code around the same passes
+// (the ModUp conversion, the ModDown / rescale finish), and the shape that suits the plain transform
+// need not suit them, so when the relinearisation key exists they are tuned on what they serve: a key
+// switch of a batch of 4 at the top level followed by a rescale, timed for every shape of one role with
+// the other roles fixed.
 void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vector<float>* inv_ms) {
   const int n = std::max(1, std::min(limbs / C.n_q, 65535 / std::max(1, C.n_q)));
   DevBuf buf((size_t)n * C.n_q * C.N, C.stream);
@@ -126,28 +142,55 @@ void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vect
   cudaEvent_t a, b;
   HEDAP_CUDA(cudaEventCreate(&a));
   HEDAP_CUDA(cudaEventCreate(&b));
+  auto best_of = [&](const std::function<void()>& run) {
+    float ms = 1e30f;
+    for (int r = 0; r <= reps; ++r) {
+      HEDAP_CUDA(cudaEventRecord(a, C.stream));
+      run();
+      HEDAP_CUDA(cudaEventRecord(b, C.stream));
+      HEDAP_CUDA(cudaEventSynchronize(b));
+      float t = 0;
+      HEDAP_CUDA(cudaEventElapsedTime(&t, a, b));
+      if (r > 0) ms = std::min(ms, t);
+    }
+    return ms;
+  };
   for (int dir = 0; dir < 2; ++dir) {
     float best = 1e30f;
     int best_v = 0;
     for (int v = 0; v < kNttVariants; ++v) {
       Tables T = C.tab;
       T.ntt_fwd_variant = T.ntt_inv_variant = v;
-      float ms = 1e30f;
-      for (int r = 0; r <= reps; ++r) {
-        HEDAP_CUDA(cudaEventRecord(a, C.stream));
-        dispatch(T, S, C.stream, dir == 1, nullptr);
-        HEDAP_CUDA(cudaEventRecord(b, C.stream));
-        HEDAP_CUDA(cudaEventSynchronize(b));
-        float t = 0;
-        HEDAP_CUDA(cudaEventElapsedTime(&t, a, b));
-        if (r > 0) ms = std::min(ms, t);
-      }
+      const float ms = best_of([&] { dispatch(T, S, C.stream, dir == 1, nullptr); });
       if (dir == 0 && fwd_ms) fwd_ms->push_back(ms);
       if (dir == 1 && inv_ms) inv_ms->push_back(ms);
       if (ms < best) { best = ms; best_v = v; }
     }
     if (dir == 0) C.tab.ntt_fwd_variant = best_v;
     else C.tab.ntt_inv_variant = best_v;
+  }
+  C.tab.ntt_modup_variant = C.tab.ntt_fin_variant = C.tab.ntt_fwd_variant;
+  if (C.keys.count(0) && C.L() >= 1) {
+    const int l = C.L(), batch = 4;
+    const size_t per = (size_t)(l + 1) * C.N;
+    DevBuf d(batch * per, C.stream);
+    HEDAP_CUDA(cudaMemsetAsync(d.p, 0, d.words * 8, C.stream));
+    auto ct = ct_alloc(C, l, batch);
+    HEDAP_CUDA(cudaMemsetAsync(ct->buf.p, 0, ct->buf.words * 8, C.stream));
+    for (int role : {NTT_ROLE_MODUP, NTT_ROLE_FINISH}) {
+      int& slot = ntt_role_variant(C.tab, role);
+      float best = 1e30f;
+      int best_v = slot;
+      for (int v = 0; v < kNttVariants; ++v) {
+        slot = v;
+        const float ms = best_of([&] {
+          key_switch(C, d.p, per, batch, l, 0, ct->part(0), ct->part_stride(), false, false);
+          ev_rescale(C, *ct);
+        });
+        if (ms < best) { best = ms; best_v = v; }
+      }
+      slot = best_v;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

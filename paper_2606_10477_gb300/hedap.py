@@ -22,6 +22,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "not enough levels", -3: "scale m
           -5: "CUDA error", -6: "wait timed out", -7: "input out of range", -8: "missing switching key",
           -9: "cancelled"}
 FAULT_ADMISSION_OOM = 1
+# NTT launch-shape roles (HEDAP_NTT_ROLE_*)
+NTT_ROLES = {"forward": 0, "inverse": 1, "modup": 2, "finish": 3}
 
 EXPORTED = [
     "hedap_status_str", "hedap_last_error", "hedap_ctx_create", "hedap_ctx_destroy", "hedap_ctx_primes", "hedap_sync",
@@ -34,7 +36,8 @@ EXPORTED = [
     "hedap_encapsulation_switch", "hedap_bootstrap_slots", "hedap_bootstrap_scaled_slots", "hedap_sub_sum", "hedap_mod_raise", "hedap_mul_monomial",
     "hedap_bts_linear_transform", "hedap_eval_mod", "hedap_set_scale", "hedap_encode", "hedap_bts_diagonal",
     "hedap_batch_pack", "hedap_batch_unpack", "hedap_ct_batch_size", "hedap_invsqrt_batch", "hedap_invsqrt_many", "hedap_invsqrt_mixed", "hedap_ntt_batch",
-    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_ntt_get_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
+    "hedap_ntt_tune", "hedap_ntt_set_variant", "hedap_ntt_get_variant", "hedap_ntt_set_role_variant",
+    "hedap_ntt_get_role_variant", "hedap_butterfly_rate", "hedap_select", "hedap_getoptiter_rule", "hedap_select_level_rule",
     "hedap_server_create", "hedap_server_submit", "hedap_server_poll", "hedap_server_stats", "hedap_server_destroy",
     "hedap_server_resume", "hedap_server_estimate", "hedap_server_wait", "hedap_server_cancel", "hedap_server_inject",
     "hedap_server_merges", "hedap_server_set_table", "hedap_invsqrt_graph_create", "hedap_graph_run",
@@ -183,6 +186,8 @@ def _declare(L):
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "hedap_ntt_set_variant": (st, [vp, C.c_int, C.c_int]),
         "hedap_ntt_get_variant": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "hedap_ntt_set_role_variant": (st, [vp, C.c_int, C.c_int]),
+        "hedap_ntt_get_role_variant": (st, [vp, C.c_int, C.POINTER(C.c_int)]),
         "hedap_butterfly_rate": (st, [vp, dp]),
         "hedap_select": (st, [vp, C.POINTER(SelectCfg), C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t),
                               C.POINTER(SelectEntry), C.c_size_t, C.POINTER(C.c_size_t), C.POINTER(SelectTrace),
@@ -369,6 +374,22 @@ class Context:
         f, i = C.c_int(), C.c_int()
         _check(load().hedap_ntt_get_variant(self.h, C.byref(f), C.byref(i)))
         return f.value, i.value
+
+    def ntt_set_role_variant(self, role: int, variant: int):
+        _check(load().hedap_ntt_set_role_variant(self.h, role, variant))
+
+    def ntt_get_roles(self) -> dict:
+        """Launch shape of every NTT role, by role name."""
+        out = {}
+        for name, role in NTT_ROLES.items():
+            v = C.c_int()
+            _check(load().hedap_ntt_get_role_variant(self.h, role, C.byref(v)))
+            out[name] = v.value
+        return out
+
+    def ntt_set_roles(self, roles: dict):
+        for name, v in roles.items():
+            self.ntt_set_role_variant(NTT_ROLES[name], int(v))
 
     def ntt_batch(self, limbs, n_limbs: int, first_prime: int, inverse=False):
         """In-place NTT of a CUDA tensor holding polynomials of n_limbs limbs each."""

@@ -122,6 +122,31 @@ def test_every_ntt_launch_shape_is_bit_exact(name, request):
         g.ntt_tune(4 * g.n_q, 1)
 
 
+@pytest.mark.parametrize("name", ["n10", "n13"])
+def test_fused_roles_every_launch_shape_bit_exact(name, request):
+    """The key switch's ModUp column phase and the fused ModDown / rescale run in the shape of their own
+    role: every shape of each role gives the oracle's HMult, rescale and rotation bit for bit."""
+    g, o = request.getfixturevalue(name)
+    L = o.n_q - 1
+    ga, oa = imported_pair(g, o, 41, L)
+    gb, ob = imported_pair(g, o, 42, L)
+    want = (o.mul(oa, ob), o.rotate(oa, 3))
+    saved = g.ntt_get_roles()
+    try:
+        for role in ("modup", "finish"):
+            for v in range(8):
+                g.ntt_set_role_variant(hedap.NTT_ROLES[role], v)
+                same_ct(g.mul(ga, gb), want[0])
+                same_ct(g.rotate(ga, 3), want[1])
+            g.ntt_set_roles(saved)
+    finally:
+        g.ntt_set_roles(saved)
+    with pytest.raises(hedap.HedapError):
+        g.ntt_set_role_variant(4, 0)
+    with pytest.raises(hedap.HedapError):
+        g.ntt_set_role_variant(hedap.NTT_ROLES["modup"], 8)
+
+
 def test_ntt_ragged_batch_offset_primes(n13):
     g, o = n13
     primes = o.primes()

@@ -51,10 +51,12 @@ def test_checkpoint_round_trip_on_a_context(tmp_path):
     p = inputs.PRESETS["toy"]
     a = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
     a.ntt_set_variant(2, 5)
+    a.ntt_set_role_variant(hedap.NTT_ROLES["finish"], 7)
     path = str(tmp_path / "ckpt.json")
     checkpoint.save(path, a, p, [], device="this GPU", git="rev")
     b = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1)
     b.ntt_set_variant(0, 0)
     assert checkpoint.load(path, b, p, device="this GPU", git="rev")
     assert b.ntt_get_variant() == (2, 5)
+    assert b.ntt_get_roles() == {"forward": 2, "inverse": 5, "modup": 2, "finish": 7}
     assert not checkpoint.load(path, b, inputs.PRESETS["n13"], device="this GPU", git="rev")
