@@ -497,9 +497,9 @@ void hedap_graph_destroy(hedap_graph* g);
  * to fwd_ms / inv_ms (capacity cap, may be NULL); the chosen variant indices
  * to *fwd_variant / *inv_variant.  The forward transforms with a fused key-switch
  * conversion (HEDAP_NTT_ROLE_MODUP) or a fused ModDown / rescale
- * (HEDAP_NTT_ROLE_FINISH) are then tuned apart, each on a key switch of a batch of
- * 4 ciphertexts at the top level followed by a rescale (when the relinearisation
- * key exists); hedap_ntt_get_role_variant reports their choices. */
+ * (HEDAP_NTT_ROLE_FINISH) are then tuned apart, each on an HMult with rescale of a
+ * batch of 4 ciphertexts at the top level (when the relinearisation key exists);
+ * hedap_ntt_get_role_variant reports their choices. */
 hedap_status hedap_ntt_tune(hedap_ctx* ctx, int limbs, int reps, float* fwd_ms, float* inv_ms, int cap,
                             int* fwd_variant, int* inv_variant);
 /* Butterflies per second of a register-only loop of the NTT's butterfly (no

@@ -151,6 +151,17 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   for (int k = 0; k < K; ++k) md2.push_back(p_of(k));
   upload(*C, C->d_moddown, md);
   upload(*C, C->d_moddown2, md2);
+  // ModDown fused with a rescale: the conversion scaled by P^-1, i.e. phat_k P^-1 = p_k^-1 mod q_i and
+  // floor(P/2) P^-1 mod q_i
+  std::vector<u64> mdr((size_t)2 * K * nq + nq);
+  for (int k = 0; k < K; ++k)
+    for (int i = 0; i < nq; ++i) {
+      const u64 qi = C->primes[i], f = h_invmod(p_of(k) % qi, qi);
+      mdr[(size_t)k * nq + i] = f;
+      mdr[(size_t)(K + k) * nq + i] = h_shoup(f, qi);
+    }
+  for (int i = 0; i < nq; ++i) mdr[(size_t)2 * K * nq + i] = h_mulmod(halfq[i], pinv[i], C->primes[i]);
+  upload(*C, C->d_mdr, mdr);
 
   std::vector<u64> pm(T);
   for (int t = 0; t < T; ++t) pm[t] = P_mod(C->primes[t]);

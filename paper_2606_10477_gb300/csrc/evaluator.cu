@@ -152,6 +152,40 @@ const LevelConsts& level_consts(Ctx& C, int l) {
     }
     L->d_rescale = DevBuf(r.size(), C.stream);
     HEDAP_CUDA(cudaMemcpyAsync(L->d_rescale.p, r.data(), r.size() * 8, cudaMemcpyHostToDevice, C.stream));
+    // ModDown fused with this level's rescale (ks_moddown_rescale)
+    const int K = C.n_p;
+    auto P_mod = [&](u64 m) {
+      u64 v = 1 % m;
+      for (int k = 0; k < K; ++k) v = h_mulmod(v, q[C.n_q + k] % m, m);
+      return v;
+    };
+    std::vector<u64> w(2 * (size_t)l);
+    for (int i = 0; i < l; ++i) {
+      w[i] = h_mulmod(h_invmod(P_mod(q[i]), q[i]), L->rescale.inv[i], q[i]);
+      w[l + i] = h_shoup(w[i], q[i]);
+    }
+    L->d_mdr = DevBuf(w.size(), C.stream);
+    HEDAP_CUDA(cudaMemcpyAsync(L->d_mdr.p, w.data(), w.size() * 8, cudaMemcpyHostToDevice, C.stream));
+    MdrLast& M = L->mdr_last;
+    M = MdrLast{};
+    M.K = std::min(K, 8);
+    const u64 pinv = h_invmod(P_mod(ql), ql);
+    for (int k = 0; k < M.K; ++k) {
+      const u64 pk = q[C.n_q + k];
+      u64 h = 1;  // phinv_k = (P / p_k)^-1 mod p_k
+      for (int m = 0; m < K; ++m)
+        if (m != k) h = h_mulmod(h, q[C.n_q + m] % pk, pk);
+      const u64 phinv = h_invmod(h, pk);
+      const u64 halfp = h_mulmod((P_mod(pk) + pk - 1) % pk, h_invmod(2, pk), pk);  // floor(P/2) mod p_k
+      M.p[k] = pk;
+      M.c[k] = h_mulmod(halfp, phinv, pk);
+      M.f[k] = h_invmod(pk % ql, ql);
+      M.fs[k] = h_shoup(M.f[k], ql);
+    }
+    const u64 halfq = h_mulmod((P_mod(ql) + ql - 1) % ql, h_invmod(2, ql), ql);  // floor(P/2) mod q_l
+    M.off = (ql - h_mulmod(halfq, pinv, ql)) % ql;
+    M.pinv = pinv;
+    M.pinv_sh = h_shoup(pinv, ql);
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   }
   auto& ref = *L;
@@ -249,10 +283,10 @@ static void ks_finish(Ctx& C, const DevBuf& y, const u64* d, size_t d_stride, in
   ks_moddown(C, acc, batch, l, out, out_stride, acc0, acc1);
 }
 
-// One key switch: iNTT of d, the extended digits' forward transform with the key inner product fused
-// into its second phase (the transformed digits are never stored), then ModDown.
-void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
-                bool acc0, bool acc1) {
+// The key switch up to the inner product: iNTT of d, the extended digits' forward transform with the
+// key inner product fused into its second phase (the transformed digits are never stored).  Returns the
+// sums acc [batch][2][ext][N] (NTT domain).
+static DevBuf ks_inner(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois) {
   const DevBuf& key = key_for(C, galois);
   const int T = C.total_primes();
   DevBuf acc((size_t)batch * 2 * (l + 1 + C.n_p) * C.N, C.stream);
@@ -267,7 +301,64 @@ void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 gal
   F.r64 = C.d_r64.p;
   F.batch = batch;
   ks_modup(C, d, d_stride, batch, l, &F);  // its column-phase buffer is released stream-ordered
+  return acc;
+}
+
+// One key switch: the inner product, then ModDown.
+void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 galois, u64* out, size_t out_stride,
+                bool acc0, bool acc1) {
+  DevBuf acc = ks_inner(C, d, d_stride, batch, l, galois);
   ks_moddown(C, acc, batch, l, out, out_stride, acc0, acc1);
+}
+
+// ModDown of the key-switch sums acc added to e (NTT domain, level l, part stride e_stride), followed
+// by the rescale by q_l, written to out (level l - 1).  Separately, ModDown transforms its conversion
+// v back over the l + 1 limbs and the rescale transforms the spread w of the centred last limb over
+// the l remaining ones; the transforms are linear, so
+//   ((e + (acc - NTT(v)) P^-1) - NTT(w)) q_l^-1 = acc (P q_l)^-1 + (e - NTT(v P^-1 + w)) q_l^-1
+// and one forward transform of v P^-1 + w over l limbs does both (v P^-1 is the conversion with
+// constants scaled by P^-1).  The last limb's coefficients come first: INTT(e_l + acc_l P^-1) minus
+// the conversion of the special limbs into q_l scaled by P^-1.  Every residue equals that of ModDown
+// followed by the rescale.
+static void ks_moddown_rescale(Ctx& C, const DevBuf& acc, int batch, int l, const u64* e, size_t e_stride, u64* out,
+                               size_t out_stride) {
+  const size_t N = C.N;
+  const int K = C.n_p, ext = l + 1 + K, nq = C.n_q;
+  const LevelConsts& LC = level_consts(C, l);
+  NttAux inv{};
+  inv.post = C.d_moddown2.p;  // the special limbs end with N^-1 phinv_k
+  ntt_inverse(C.tab, LimbSet{acc.p, (size_t)ext * N, 2 * batch, l + 1, K, l + 1, 0, C.n_q}, C.stream, &inv);
+  DevBuf t((size_t)2 * batch * N, C.stream), x((size_t)2 * batch * N, C.stream);
+  k_mdr_last_eval(C, e + (size_t)l * N, e_stride, acc.p + (size_t)l * N, (size_t)ext * N, t.p, 2 * batch, l,
+                  LC.mdr_last);
+  ntt_inverse(C.tab, qset(t.p, N, 2 * batch, 0, 1, l), C.stream);
+  k_mdr_last_coef(C, t.p, acc.p + (size_t)(l + 1) * N, (size_t)ext * N, x.p, 2 * batch, l, LC.mdr_last);
+  DevBuf v((size_t)2 * batch * l * N, C.stream);
+  NttAux fw{};
+  fw.pconv = acc.p + (size_t)(l + 1) * N;
+  fw.pconv_stride = (size_t)ext * N;
+  fw.pconv_K = K;
+  fw.pconv_ld = nq;
+  fw.pconv_q = C.d_moddown2.p + 3 * K + (size_t)K * nq;
+  fw.pconv_c = C.d_moddown2.p + 2 * K;
+  fw.pconv_phat = C.d_mdr.p;
+  fw.pconv_phat_sh = C.d_mdr.p + (size_t)K * nq;
+  fw.pconv_half = C.d_mdr.p + 2 * (size_t)K * nq;
+  fw.spread = x.p;
+  fw.spread_stride = N;
+  fw.spread_sub = LC.d_rescale.p;
+  fw.spread_prime = l;
+  fw.fin_dst = out;
+  fw.fin_dst_stride = out_stride;
+  fw.fin_c = acc.p;
+  fw.fin_c_stride = (size_t)ext * N;
+  fw.fin_w = LC.d_mdr.p;
+  fw.fin_wsh = LC.d_mdr.p + l;
+  fw.fin_e = e;
+  fw.fin_e_stride = e_stride;
+  fw.fin_w2 = LC.d_rescale.p + l;
+  fw.fin_w2sh = LC.d_rescale.p + 2 * l;
+  ntt_forward(C.tab, qset(v.p, (size_t)l * N, 2 * batch, 0, l), C.stream, &fw);
 }
 
 // Rotations of one (batched) ciphertext by several Galois elements sharing one ModUp of its
@@ -337,7 +428,25 @@ std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a) {
   return o;
 }
 
-std::unique_ptr<Ct> ev_mul(Ctx& C, const Ct& a, const Ct& b) { return ev_rescale(C, *ev_mul_relin(C, a, b)); }
+// HMult and rescale: the tensor product, the relinearising key switch up to its inner product, then
+// ModDown and the rescale in one transform (ks_moddown_rescale); equal, residue for residue, to
+// ev_rescale(ev_mul_relin(a, b)).
+std::unique_ptr<Ct> ev_mul(Ctx& C, const Ct& a, const Ct& b) {
+  const int l = std::min(a.level, b.level);
+  if (l < 1) throw Error(HEDAP_ERR_LEVEL, "rescale needs level >= 1");
+  if (C.n_p > 8) return ev_rescale(C, *ev_mul_relin(C, a, b));
+  check_batches(a, b);
+  auto e = ct_alloc(C, l, a.batch);
+  const size_t per = (size_t)(l + 1) * C.N;
+  DevBuf d2(a.batch * per, C.stream);
+  k_tensor(C, a.part(0), a.part_stride(), b.part(0), b.part_stride(), e->part(0), e->part_stride(), d2.p, a.batch,
+           l + 1);
+  DevBuf acc = ks_inner(C, d2.p, per, a.batch, l, 0);
+  auto o = ct_alloc(C, l - 1, a.batch);
+  o->scale = a.scale * b.scale / (double)C.primes[l];
+  ks_moddown_rescale(C, acc, a.batch, l, e->part(0), e->part_stride(), o->part(0), o->part_stride());
+  return o;
+}
 
 u64 galois_for_rotation(const Ctx& C, i64 steps) {
   const i64 h = (i64)(C.N / 2);

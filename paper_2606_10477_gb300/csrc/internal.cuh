@@ -168,6 +168,14 @@ struct NttAux {
   const u64* fin_w = nullptr;
   const u64* fin_wsh = nullptr;
   int fin_acc_even = 0, fin_acc_odd = 0;
+  // with fin_e: a key switch's ModDown fused with the rescale that follows it (see ks_moddown_rescale):
+  //   fin_dst[part][li] = fin_c[part][li] * fin_w[li] + (fin_e[part][li] - v) * fin_w2[li]
+  // (fin_w = (P q_l)^-1, fin_w2 = q_l^-1), and the first phase loads the ModDown conversion with its
+  // constants scaled by P^-1 plus the spread of the centred last limb (pconv and spread both set)
+  const u64* fin_e = nullptr;
+  size_t fin_e_stride = 0;
+  const u64* fin_w2 = nullptr;
+  const u64* fin_w2sh = nullptr;
 };
 // Forward only: the second phase of the ModUp transform of a key switch fused with the key inner
 // product (k_ntt_fwd_rows_ksk): the transformed digits are multiplied by the switching key and summed
@@ -231,11 +239,20 @@ struct RescaleConsts {
   u64 inv_sh[kMaxLimbs];
 };
 
+// ModDown of limb l (prime q_l) scaled by P^-1: x - (sum_k [z_k + c_k]_{p_k} p_k^-1 + off) mod q_l
+struct MdrLast {
+  u64 p[8], c[8], f[8], fs[8];  // p_k, floor(P/2) phinv_k mod p_k, p_k^-1 mod q_l and its Shoup companion
+  u64 off;                      // -floor(P/2) P^-1 mod q_l
+  u64 pinv, pinv_sh;            // P^-1 mod q_l and its Shoup companion
+  int K;
+};
 struct LevelConsts {  // device constants for one level (evaluator.cu)
   DevBuf modup;       // qhat_inv (+shoup) per Q prime, qhat mod target per digit (+shoup)
   DevBuf intt_post;   // per Q prime i <= l: N^-1 qhat_i^-1 mod q_i and its Shoup companion
   DevBuf d_rescale;   // [ql_mod l][inv l][inv_sh l] (the rescale constants below, on the device)
   RescaleConsts rescale;
+  DevBuf d_mdr;       // ModDown fused with the rescale: [(P q_l)^-1 mod q_i][its Shoup companion], i < l
+  MdrLast mdr_last;   // ... and the constants of its last limb (prime q_l)
 };
 
 struct BtsState;  // bootstrapping state (bootstrap.cu)
@@ -266,6 +283,8 @@ struct Ctx {
   DevBuf d_primes, d_psi2, d_ipsi2, d_ninv, d_ninv_sh;
   DevBuf d_moddown;   // level-independent ModDown constants
   DevBuf d_moddown2;  // fused ModDown: [N^-1 phinv_k, Shoup][K] pairs, c_k [K], phat_q Shoup [K][n_q], p_k [K]
+  DevBuf d_mdr;       // ModDown scaled by P^-1 (fused with a rescale): p_k^-1 mod q_i [K][n_q], their Shoup
+                      // companions [K][n_q], floor(P/2) P^-1 mod q_i [n_q]
   DevBuf d_r64;       // per prime: 2^64 mod q and its Shoup companion
   DevBuf d_pmod;      // per prime: P mod q_t (key generation)
   Tables tab{};

@@ -212,6 +212,50 @@ void k_rescale_spread(const Ctx& C, const u64* last, size_t ls, u64* tmp, size_t
                                                                      C.log_n, R);
   HEDAP_LAUNCH_CHECK();
 }
+// ---------------------------------------------------------------- ModDown fused with a rescale: the last limb
+__global__ void k_mdr_last_eval_kernel(const u64* __restrict__ e, size_t es, const u64* __restrict__ acc, size_t as,
+                                       u64* __restrict__ t, int n_parts, int log_n, u64 q, u64 w, u64 wsh) {
+  const size_t N = (size_t)1 << log_n;
+  GRID_LOOP(i, (size_t)n_parts * N) {
+    const size_t p = i >> log_n, n = i & (N - 1);
+    t[i] = add_mod(e[p * es + n], shoup_mul(acc[p * as + n], w, wsh, q), q);
+  }
+}
+void k_mdr_last_eval(const Ctx& C, const u64* e, size_t es, const u64* acc, size_t as, u64* t, int n_parts, int l,
+                     const MdrLast& M) {
+  ProfScope prof_(PROF_RESCALE, C.stream, 3.0 * n_parts * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)n_parts * C.N;
+  k_mdr_last_eval_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(e, es, acc, as, t, n_parts, C.log_n,
+                                                                    C.primes[l], M.pinv, M.pinv_sh);
+  HEDAP_LAUNCH_CHECK();
+}
+// x = t - (off + sum_k [z_k + c_k]_{p_k} f_k) mod q_l: the K canonical products and off sum below
+// (K + 1) q_l <= 9 q_l < 2^64, reduced once
+__global__ void k_mdr_last_coef_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ t,
+                                       const u64* __restrict__ z, size_t zs, u64* __restrict__ x, int n_parts,
+                                       int log_n, int l, MdrLast M) {
+  const size_t N = (size_t)1 << log_n;
+  const PrimeDev P = pr[l];
+  GRID_LOOP(i, (size_t)n_parts * N) {
+    const size_t p = i >> log_n, n = i & (N - 1);
+    const u64* zp = z + p * zs + n;
+    u64 v = M.off;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < M.K) v += shoup_mul(add_mod(zp[(size_t)k * N], M.c[k], M.p[k]), M.f[k], M.fs[k], P.q);
+    x[i] = sub_mod(t[i], barrett_reduce(v, 0, P), P.q);
+  }
+}
+void k_mdr_last_coef(const Ctx& C, const u64* t, const u64* z, size_t zs, u64* x, int n_parts, int l,
+                     const MdrLast& M) {
+  ProfScope prof_(PROF_RESCALE, C.stream, (2.0 + M.K) * n_parts * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)n_parts * C.N;
+  k_mdr_last_coef_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, t, z, zs, x, n_parts, C.log_n, l, M);
+  HEDAP_LAUNCH_CHECK();
+}
+
 __global__ void k_rescale_finish_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ in, size_t is,
                                         const u64* __restrict__ tmp, size_t ts, u64* __restrict__ out, size_t os,
                                         int n_parts, int l, int log_n, RescaleConsts R) {

@@ -26,6 +26,13 @@ void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const
 void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
                  int level, u64 galois_perm = 0);
 void k_moddown_spread(const Ctx& C, const u64* acc, u64* v, int n_parts, int level);
+// ModDown fused with a rescale (evaluator.cu, ks_moddown_rescale): limb l of the ModDown output, first
+// t = e_l + acc_l P^-1 (NTT domain), then, with t back in the coefficient domain, x = t minus the
+// conversion of the special limbs z into q_l scaled by P^-1 (canonical)
+void k_mdr_last_eval(const Ctx& C, const u64* e, size_t es, const u64* acc, size_t as, u64* t, int n_parts, int l,
+                     const MdrLast& M);
+void k_mdr_last_coef(const Ctx& C, const u64* t, const u64* z, size_t zs, u64* x, int n_parts, int l,
+                     const MdrLast& M);
 void k_moddown_finish(const Ctx& C, const u64* acc, const u64* v, u64* out, size_t os, int n_parts, int level,
                       bool acc_even, bool acc_odd);
 void k_keygen_combine(const Ctx& C, u64* b, const u64* a, const u64* s, const u64* sp, const u64* pmod, int lo,

@@ -39,8 +39,10 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   if (A.post && !inverse) throw Error(HEDAP_ERR_ARG, "NTT: post factors apply to the inverse only");
   if ((A.spread || A.fin_dst || A.pconv) && inverse)
     throw Error(HEDAP_ERR_ARG, "NTT: fused rescale / ModDown applies to the forward only");
-  if (A.pconv && (A.pconv_K < 1 || A.pconv_K > 8 || A.z || A.src || A.spread))
+  if (A.pconv && (A.pconv_K < 1 || A.pconv_K > 8 || A.z || A.src || (A.spread && !A.fin_e)))
     throw Error(HEDAP_ERR_ARG, "NTT: bad ModDown fusion");
+  if (A.fin_e && (!A.fin_dst || !A.fin_w2 || !A.fin_w2sh || !A.pconv || !A.spread))
+    throw Error(HEDAP_ERR_ARG, "NTT: bad ModDown-rescale fusion");
   if (A.spread && (A.z || A.src || !A.spread_sub)) throw Error(HEDAP_ERR_ARG, "NTT: bad spread fusion");
   if (A.fin_dst && (!A.fin_c || !A.fin_w || !A.fin_wsh)) throw Error(HEDAP_ERR_ARG, "NTT: bad epilogue fusion");
   const int v = inverse ? T.ntt_inv_variant
@@ -131,9 +133,9 @@ int& ntt_role_variant(Tables& T, int role) {
 // Time every variant on `limbs` limbs of scratch (forward and inverse separately, best of `reps` after
 // one warm-up) and keep the fastest in C.tab.  The fused roles run other code around the same passes
 // (the ModUp conversion, the ModDown / rescale finish), and the shape that suits the plain transform
-// need not suit them, so when the relinearisation key exists they are tuned on what they serve: a key
-// switch of a batch of 4 at the top level followed by a rescale, timed for every shape of one role with
-// the other roles fixed.
+// need not suit them, so when the relinearisation key exists they are tuned on what they serve: an
+// HMult with rescale of a batch of 4 at the top level (tensor, key switch, ModDown fused with the
+// rescale), timed for every shape of one role with the other roles fixed.
 void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vector<float>* inv_ms) {
   const int n = std::max(1, std::min(limbs / C.n_q, 65535 / std::max(1, C.n_q)));
   DevBuf buf((size_t)n * C.n_q * C.N, C.stream);
@@ -172,9 +174,6 @@ void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vect
   C.tab.ntt_modup_variant = C.tab.ntt_fin_variant = C.tab.ntt_fwd_variant;
   if (C.keys.count(0) && C.L() >= 1) {
     const int l = C.L(), batch = 4;
-    const size_t per = (size_t)(l + 1) * C.N;
-    DevBuf d(batch * per, C.stream);
-    HEDAP_CUDA(cudaMemsetAsync(d.p, 0, d.words * 8, C.stream));
     auto ct = ct_alloc(C, l, batch);
     HEDAP_CUDA(cudaMemsetAsync(ct->buf.p, 0, ct->buf.words * 8, C.stream));
     for (int role : {NTT_ROLE_MODUP, NTT_ROLE_FINISH}) {
@@ -183,10 +182,7 @@ void ntt_tune(Ctx& C, int limbs, int reps, std::vector<float>* fwd_ms, std::vect
       int best_v = slot;
       for (int v = 0; v < kNttVariants; ++v) {
         slot = v;
-        const float ms = best_of([&] {
-          key_switch(C, d.p, per, batch, l, 0, ct->part(0), ct->part_stride(), false, false);
-          ev_rescale(C, *ct);
-        });
+        const float ms = best_of([&] { ev_mul(C, *ct, *ct); });
         if (ms < best) { best = ms; best_v = v; }
       }
       slot = best_v;

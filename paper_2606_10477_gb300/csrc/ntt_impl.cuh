@@ -218,6 +218,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
         }
       if (v >= q8) v -= q8;
       if (v >= q4) v -= q4;
+      if (A.spread) {  // a ModDown fused with a rescale: plus the centred last limb, [0, 5q)
+        const u64 x = A.spread[(size_t)part * A.spread_stride + n];
+        const u64 half = T.pr[A.spread_prime].q >> 1;
+        u64 m = barrett_reduce(x, 0, T.pr[pi]);
+        if (x > half) m = sub_mod(m, A.spread_sub[li], q);
+        v += m;
+      }
       sm[idx] = v;
     }
   } else if (A.spread) {  // fused rescale spread: centred residue of the last limb in this prime
@@ -269,9 +276,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, Lim
   const int groups = (S.n_limbs + lpc - 1) / lpc;
   const int part = blockIdx.y / groups, g = blockIdx.y % groups;
   const int l0 = S.limb_begin + g * lpc, l1 = min(l0 + lpc, S.limb_begin + S.n_limbs);
-  // the shared tiles: ns limbs at src + t N
+  // the shared tiles: ns limbs at src + t N (and, for a ModDown fused with a rescale, the last limb's
+  // coefficients as tile ns)
   int ns, j = 0;
   const u64* src;
+  const u64* spread_src = A.spread ? A.spread + (size_t)part * A.spread_stride : nullptr;
   if (A.z) {
     j = part % A.own_dn;
     const int lo = j * A.own_alpha;
@@ -281,15 +290,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, Lim
     ns = A.pconv_K;
     src = A.pconv + (size_t)part * A.pconv_stride;
   } else {
-    ns = 1;
-    src = A.spread + (size_t)part * A.spread_stride;
+    ns = 0;
+    src = nullptr;
   }
+  const int nt = ns + (spread_src ? 1 : 0);
   const int r0 = blockIdx.x * C;
   // row c of tile t holds words r0 .. r0 + C - 1 of column c (16-byte copies)
-  for (int idx = threadIdx.x; idx < ns * (E / 2); idx += TPB) {
+  for (int idx = threadIdx.x; idx < nt * (E / 2); idx += TPB) {
     const int t = idx / (E / 2), e = 2 * (idx % (E / 2));
     const int c = e / C, col = e % C;
-    cp_async16(zt + (size_t)t * E + e, src + (size_t)t * N + ((size_t)c << L2) + r0 + col);
+    const u64* base = t < ns ? src + (size_t)t * N : spread_src;
+    cp_async16(zt + (size_t)t * E + e, base + ((size_t)c << L2) + r0 + col);
   }
   auto fetch_tw = [&](int li, int buf) {
     const ulonglong2* W = T.psi2 + (size_t)S.prime(li) * N;
@@ -338,6 +349,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, Lim
         fs[k] = on ? A.pconv_phat_sh[(size_t)k * A.pconv_ld + li] : 0;
       }
       const u64 off = q4 - A.pconv_half[li];
+      // a ModDown fused with a rescale adds the centred last limb (tile ns, below q): [0, 5q)
+      const u64 half = spread_src ? T.pr[A.spread_prime].q >> 1 : 0, sub = spread_src ? A.spread_sub[li] : 0;
+      const PrimeDev P = T.pr[pi];
 #pragma unroll
       for (int idx = threadIdx.x; idx < E; idx += TPB) {
         u64 v = off;
@@ -346,6 +360,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, Lim
           if (k < ns) v += shoup_mul_lazy(add_mod(zt[(size_t)k * E + idx], c[k], pk[k]), f[k], fs[k], q);
         if (v >= q8) v -= q8;
         if (v >= q4) v -= q4;
+        if (spread_src) {
+          const u64 x = zt[(size_t)ns * E + idx];
+          u64 m = barrett_reduce(x, 0, P);
+          if (x > half) m = sub_mod(m, sub, q);
+          v += m;
+        }
         sm[idx] = v;
       }
     } else {  // rescale spread: centred residue of the last limb in this prime
@@ -444,8 +464,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   cp_async_commit();
   if (A.fin_dst) {  // the epilogue's operands: fetched into L2 while the passes run (128-byte lines)
     const u64* cp = A.fin_c + (size_t)part * A.fin_c_stride + (size_t)li * N + j0;
-    const u64* dp = A.fin_dst + (size_t)part * A.fin_dst_stride + (size_t)li * N + j0;
-    const bool acc = (part & 1) ? A.fin_acc_odd : A.fin_acc_even;
+    const u64* dp = A.fin_e ? A.fin_e + (size_t)part * A.fin_e_stride + (size_t)li * N + j0
+                            : A.fin_dst + (size_t)part * A.fin_dst_stride + (size_t)li * N + j0;
+    const bool acc = A.fin_e || ((part & 1) ? A.fin_acc_odd : A.fin_acc_even);
     for (int idx = 16 * threadIdx.x; idx < E; idx += 16 * TPB) {
       asm volatile("prefetch.global.L2 [%0];" ::"l"(cp + idx));
       if (acc) asm volatile("prefetch.global.L2 [%0];" ::"l"(dp + idx));
@@ -454,6 +475,19 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
   cp_async_wait_all();
   __syncthreads();
   fwd_rows_passes<L1, L2, BPC, RL, 0>(sm, tw, q);
+  if (A.fin_e) {  // ModDown fused with the rescale: c (P q_l)^-1 + (e - v) q_l^-1
+    const u64* cp = A.fin_c + (size_t)part * A.fin_c_stride + (size_t)li * N + j0;
+    const u64* ep = A.fin_e + (size_t)part * A.fin_e_stride + (size_t)li * N + j0;
+    u64* dp = A.fin_dst + (size_t)part * A.fin_dst_stride + (size_t)li * N + j0;
+    const u64 w = A.fin_w[li], wp = A.fin_wsh[li], w2 = A.fin_w2[li], w2p = A.fin_w2sh[li];
+#pragma unroll
+    for (int i = 0; i < E / TPB; ++i) {
+      const int idx = threadIdx.x + i * TPB;
+      const u64 v = reduce8q(smt[row_step<L2, TPB>(i)], q);
+      dp[idx] = add_mod(shoup_mul(cp[idx], w, wp, q), shoup_mul(sub_mod(ep[idx], v, q), w2, w2p, q), q);
+    }
+    return;
+  }
   if (A.fin_dst) {  // fused epilogue of a rescale / ModDown: (c - v) * w (+ dst)
     const u64* cp = A.fin_c + (size_t)part * A.fin_c_stride + (size_t)li * N + j0;
     u64* dp = A.fin_dst + (size_t)part * A.fin_dst_stride + (size_t)li * N + j0;
@@ -732,8 +766,12 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
   A2.spread = nullptr;
   A2.pconv = nullptr;
   if (!inverse) {
-    const int ns_max = A.z ? std::min(A.own_alpha, A.own_limit) : A.pconv ? A.pconv_K : A.spread ? 1 : 0;
-    if (ns_max >= 1 && ns_max <= 3 && !A.src) {
+    // staged tiles: the digit's limbs (ModUp), the special limbs (ModDown, plus the last limb when a
+    // rescale is fused) or the last limb (rescale); at most 3 products per word in the load
+    const int ns_max = A.z ? std::min(A.own_alpha, A.own_limit)
+                           : A.pconv ? A.pconv_K + (A.spread ? 1 : 0) : A.spread ? 1 : 0;
+    const int n_prod = A.z ? ns_max : A.pconv ? A.pconv_K : 0;
+    if (ns_max >= 1 && ns_max <= 4 && n_prod <= 3 && !A.src) {
       // several output limbs per CTA, sharing the staged tiles: enough limb groups for about
       // four waves of 4 CTAs on 152 SMs, at most all the limbs in one group
       const size_t per_group = (size_t)grid.x * S.n_parts;
@@ -745,7 +783,7 @@ static void launch_pair(const LimbSet& S, const Tables& T, cudaStream_t st, bool
       static const bool attr_m = [&] {
         HEDAP_CUDA(cudaFuncSetAttribute(k_ntt_fwd_cols_shared<L1, L2, C, TPB, MINB, RL>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((size_t)EE * 8 + 2 * ((size_t)1 << L1) * 16 + 3 * (size_t)EE * 8)));
+                                        (int)((size_t)EE * 8 + 2 * ((size_t)1 << L1) * 16 + 4 * (size_t)EE * 8)));
         return true;
       }();
       (void)attr_m;
