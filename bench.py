@@ -402,7 +402,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    k_e2e = max(1, min(args.steps, 3))
+    k_e2e = max(1, min(args.steps, 10))
     for _ in range(k_e2e):
         e2e_step()
     torch.cuda.synchronize()

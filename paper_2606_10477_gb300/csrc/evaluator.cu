@@ -321,7 +321,7 @@ void key_switch(Ctx& C, const u64* d, size_t d_stride, int batch, int l, u64 gal
 // the conversion of the special limbs into q_l scaled by P^-1.  Every residue equals that of ModDown
 // followed by the rescale.
 static void ks_moddown_rescale(Ctx& C, const DevBuf& acc, int batch, int l, const u64* e, size_t e_stride, u64* out,
-                               size_t out_stride) {
+                               size_t out_stride, bool negate = false) {
   const size_t N = C.N;
   const int K = C.n_p, ext = l + 1 + K, nq = C.n_q;
   const LevelConsts& LC = level_consts(C, l);
@@ -358,6 +358,7 @@ static void ks_moddown_rescale(Ctx& C, const DevBuf& acc, int batch, int l, cons
   fw.fin_e_stride = e_stride;
   fw.fin_w2 = LC.d_rescale.p + l;
   fw.fin_w2sh = LC.d_rescale.p + 2 * l;
+  fw.fin_neg = negate ? 1 : 0;
   ntt_forward(C.tab, qset(v.p, (size_t)l * N, 2 * batch, 0, l), C.stream, &fw);
 }
 
@@ -425,6 +426,43 @@ std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a) {
   fw.fin_w = LC.d_rescale.p + l;
   fw.fin_wsh = LC.d_rescale.p + 2 * l;
   ntt_forward(C.tab, qset(tmp.p, (size_t)l * N, P, 0, l), C.stream, &fw);
+  return o;
+}
+
+// A relinearised product entering a linear combination that is rescaled next, as one fused
+// operation: rescale(m (d01 + ModDown(acc)) + sum_j c_j t_j + c0), m the product's integer constant.
+// With m = 1 the sum e = d01 + sum_j c_j t_j + c0 is formed first (one linear-combination pass) and
+// ks_moddown_rescale finishes e + ModDown(acc).  With m = -1 every other constant is negated instead
+// (std::round is odd, so each integer constant is exactly negated), giving -(the sum), and the fused
+// rescale stores the negated residues: the centred residue is odd for an odd q_l, so rescale(-x) =
+// -rescale(x) residue for residue.  Any other m, or a chain too wide for one linear-combination pass,
+// takes the unfused sequence.
+std::unique_ptr<Ct> ev_mul_lincomb_rescale(Ctx& C, const Ct& a, const Ct& b, double prod_scale, double prod_coef,
+                                           const std::vector<std::pair<const Ct*, double>>& terms, double target,
+                                           double c0) {
+  const int l = std::min(a.level, b.level);
+  check_batches(a, b);
+  const double m = l >= 1 ? std::round(prod_coef * target * (double)C.primes[l] / prod_scale) : 0.0;
+  if (l < 1 || (m != 1.0 && m != -1.0) || l + 1 > kLcLimbs || C.n_p > 8 || terms.size() + 1 > kLcTerms) {
+    auto pr = ev_mul_relin(C, a, b);
+    pr->scale = prod_scale;
+    std::vector<std::pair<const Ct*, double>> all{{pr.get(), prod_coef}};
+    all.insert(all.end(), terms.begin(), terms.end());
+    return ev_rescale(C, *ev_lincomb_raw(C, all, l, target, c0));
+  }
+  auto d01 = ct_alloc(C, l, a.batch);
+  d01->scale = prod_scale;
+  const size_t per = (size_t)(l + 1) * C.N;
+  DevBuf d2(a.batch * per, C.stream);
+  k_tensor(C, a.part(0), a.part_stride(), b.part(0), b.part_stride(), d01->part(0), d01->part_stride(), d2.p,
+           a.batch, l + 1);
+  DevBuf acc = ks_inner(C, d2.p, per, a.batch, l, 0);
+  std::vector<std::pair<const Ct*, double>> all{{d01.get(), m * prod_coef}};
+  for (const auto& t : terms) all.emplace_back(t.first, m * t.second);
+  auto e = ev_lincomb_raw(C, all, l, target, m * c0);
+  auto o = ct_alloc(C, l - 1, a.batch);
+  o->scale = e->scale / (double)C.primes[l];
+  ks_moddown_rescale(C, acc, a.batch, l, e->part(0), e->part_stride(), o->part(0), o->part_stride(), m < 0);
   return o;
 }
 

@@ -176,6 +176,7 @@ struct NttAux {
   size_t fin_e_stride = 0;
   const u64* fin_w2 = nullptr;
   const u64* fin_w2sh = nullptr;
+  int fin_neg = 0;  // with fin_e: store the negated residues
 };
 // Forward only: the second phase of the ModUp transform of a key switch fused with the key inner
 // product (k_ntt_fwd_rows_ksk): the transformed digits are multiplied by the switching key and summed
@@ -311,6 +312,11 @@ std::unique_ptr<Ct> ev_add(Ctx& C, const Ct& a, const Ct& b, bool sub);
 std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b);
 std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a);
 std::unique_ptr<Ct> ev_mul(Ctx& C, const Ct& a, const Ct& b);
+// rescale(lincomb({relin(a b) labelled prod_scale, prod_coef}, terms..., level min(a, b), target, c0)),
+// with the key switch's ModDown fused into the rescale; residues equal the unfused sequence
+std::unique_ptr<Ct> ev_mul_lincomb_rescale(Ctx& C, const Ct& a, const Ct& b, double prod_scale, double prod_coef,
+                                           const std::vector<std::pair<const Ct*, double>>& terms, double target,
+                                           double c0);
 std::unique_ptr<Ct> ev_galois(Ctx& C, const Ct& a, u64 g);
 std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const std::vector<u64>& gs);
 std::unique_ptr<Ct> ev_drop(Ctx& C, const Ct& a, int level);

@@ -123,7 +123,29 @@ struct ChebPS {
     return ev_add(C, *prod, *rv, false);
   }
   CtP eval(const std::vector<double>& p, int level, double scale) {
-    CtP r = ev_rescale(C, *eval_raw(p, level, scale));
+    CtP r;
+    const int D = degree(p);
+    if (!leaf_at(D, level)) {  // an inner node: its product's ModDown is fused into this rescale
+      const int G = split_at(D);
+      std::vector<double> qt, rm;
+      divide(p, G, qt, rm);
+      if (degree(qt) > 0) {
+        const Ct& tg = *T.at(G);
+        const double raw = scale * (double)C.primes[level + 1];
+        CtP qv = eval(qt, level + 1, raw / tg.scale);
+        CtP rv = eval_raw(rm, level, scale);
+        const int lp = std::min(qv->level, tg.level);
+        if (rv->level == lp) {
+          // prod + rv with both constants round(out q / raw) = 1, out = raw / q_lp
+          r = ev_mul_lincomb_rescale(C, *qv, tg, raw, 1.0, {{rv.get(), 1.0}}, raw / (double)C.primes[lp], 0.0);
+        } else {
+          CtP prod = ev_mul_relin(C, *qv, tg);
+          prod->scale = raw;
+          r = ev_rescale(C, *ev_add(C, *prod, *rv, false));
+        }
+      }
+    }
+    if (!r) r = ev_rescale(C, *eval_raw(p, level, scale));
     r->scale = scale;
     return r;
   }
@@ -134,11 +156,11 @@ struct ChebPS {
     if (c == 0) {
       return ev_add_const_mul_int(C, *ev_mul(C, ta, tb), -0.5, 2);
     } else {
-      CtP pr = ev_mul_relin(C, ta, tb);
-      const int l = pr->level;
-      const double out = pr->scale / (double)C.primes[l];
-      // pr * 1 - 0.5 T_c in one pass (the constant of pr is round(sp) = 1, sp = out q_l / pr.scale)
-      diff = ev_rescale(C, *ev_lincomb_raw(C, {{pr.get(), 1.0}, {T.at(c).get(), -0.5}}, l, out, 0.0));
+      const int l = std::min(ta.level, tb.level);
+      const double ps = ta.scale * tb.scale, out = ps / (double)C.primes[l];
+      // pr * 1 - 0.5 T_c in one pass (the constant of pr is round(sp) = 1, sp = out q_l / pr.scale),
+      // the product's ModDown fused into the rescale
+      diff = ev_mul_lincomb_rescale(C, ta, tb, ps, 1.0, {{T.at(c).get(), -0.5}}, out, 0.0);
       diff->scale = out;
     }
     return ev_mul_int(C, *diff, 2);
@@ -179,11 +201,11 @@ std::unique_ptr<Ct> cheb_eval(Ctx& C, const Ct& t, const std::vector<double>& co
 static CtP newton_step(Ctx& C, const Ct& x, const Ct& y) {
   CtP yy = ev_mul(C, y, y);
   CtP xy = ev_mul(C, x, y);
-  CtP tb = ev_mul_relin(C, *xy, *yy);
-  const int l = tb->level;
-  const double out = tb->scale / (double)C.primes[l];
-  // 1.5 y - tmp_beta in one pass (the constant of tmp_beta is -round(sp) = -1, sp = out q_l / tb.scale)
-  CtP r = ev_rescale(C, *ev_lincomb_raw(C, {{&y, 1.5}, {tb.get(), -1.0}}, l, out, 0.0));
+  const int l = std::min(xy->level, yy->level);
+  const double ps = xy->scale * yy->scale, out = ps / (double)C.primes[l];
+  // 1.5 y - tmp_beta in one pass (the constant of tmp_beta is -round(sp) = -1, sp = out q_l / tb.scale),
+  // tmp_beta's ModDown fused into the rescale
+  CtP r = ev_mul_lincomb_rescale(C, *xy, *yy, ps, -1.0, {{&y, 1.5}}, out, 0.0);
   r->scale = out;
   return r;
 }

@@ -484,7 +484,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_rows(Tables T, LimbSet S,
     for (int i = 0; i < E / TPB; ++i) {
       const int idx = threadIdx.x + i * TPB;
       const u64 v = reduce8q(smt[row_step<L2, TPB>(i)], q);
-      dp[idx] = add_mod(shoup_mul(cp[idx], w, wp, q), shoup_mul(sub_mod(ep[idx], v, q), w2, w2p, q), q);
+      const u64 z = add_mod(shoup_mul(cp[idx], w, wp, q), shoup_mul(sub_mod(ep[idx], v, q), w2, w2p, q), q);
+      dp[idx] = A.fin_neg ? sub_mod(0, z, q) : z;
     }
     return;
   }
