@@ -97,10 +97,10 @@ def measured_peaks():
 
 
 # The NTT is bound by the integer multiply-add pipe (there is no 64-bit multiplier): a lazy Shoup
-# butterfly needs the exact high half of x * w' (four 32 x 32 -> 64 products) and the low halves of
-# x * w and qh * q (two 32 x 32 -> 64 and four 32 x 32 -> 32 products): 6 wide products, each two
-# multiply-pipe slots, and 4 low ones = 16 slots per butterfly, against 64 multiply-add lanes per SM.
-NTT_MUL_SLOTS_PER_BUTTERFLY = 16
+# butterfly needs the exact high half of x * w' (seven 32 x 32 half products: the low half of x0 w'0 is
+# never needed) and the low halves of x * w and qh * q (two 32 x 32 -> 64 products, two slots each, and
+# four low products) = 15 multiply-pipe slots per butterfly, against 64 multiply-add lanes per SM.
+NTT_MUL_SLOTS_PER_BUTTERFLY = 15
 IMAD_LANES_PER_SM = 64
 # DRAM bytes per transformed limb: dram__bytes_read.sum + dram__bytes_write.sum of the transform launches of one
 # batched HMult at the top level (`--only hmult --batch 8 --profile-region` under ncu: 5317 MB for 3296 limb
@@ -111,9 +111,9 @@ NTT_DRAM_BYTES_PER_LIMB = 1.613e6
 
 def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, slots):
     """The transform class against the multiply pipe.  Work = the library's algorithmic count of 32-bit
-    multiply-pipe slots of the class (16 per Shoup product by a constant: every butterfly and every term of a
-    fused basis conversion; 8 per 64 x 64 -> 128-bit product of the fused key inner product); peak = SMs x 64
-    multiply-add lanes x clock.  The butterfly-only view (the transforms' butterflies against 16 slots each) is
+    multiply-pipe slots of the class (15 per Shoup product by a constant: every butterfly and every product of
+    a fused basis conversion; 8 per 64 x 64 -> 128-bit product of the fused key inner product); peak = SMs x 64
+    multiply-add lanes x clock.  The butterfly-only view (the transforms' butterflies against 15 slots each) is
     kept beside it."""
     log_n = int(n).bit_length() - 1
     limbs = alg_bytes / (16.0 * n)

@@ -115,7 +115,10 @@ hedap_status hedap_gen_galois_key(hedap_ctx* ctx, uint64_t galois);
  * conjugation, 2N - 1 (steps ignored).  Host only. */
 hedap_status hedap_galois_element(const hedap_ctx* ctx, int64_t steps, int conjugate, uint64_t* out);
 /* Export digit j of the key for g (g = 0: relinearisation key) into host
- * arrays b, a of [n_q + n_p][N] words each (NTT domain). */
+ * arrays b, a of [n_q + n_p][N] words each (NTT domain), as the key is defined
+ * (Sec. 2.1's hybrid key switching).  The library stores limbs outside the
+ * digit multiplied by one ModUp conversion factor (so that the fused ModUp
+ * skips that product); the export divides it out on the host. */
 hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t galois, uint32_t digit, uint64_t* b, uint64_t* a);
 
 /* Enc (symmetric, with the server's secret key): n_slots must be N/2. */

@@ -133,6 +133,16 @@ API hedap_status hedap_export_key(hedap_ctx* ctx, uint64_t g, uint32_t digit, ui
     HEDAP_CUDA(cudaMemcpyAsync(b, base, part * 8, cudaMemcpyDeviceToHost, C.stream));
     HEDAP_CUDA(cudaMemcpyAsync(a, base + part, part * 8, cudaMemcpyDeviceToHost, C.stream));
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+    // the key as defined, without the conversion factors folded into its stored limbs
+    const int T = C.total_primes();
+    for (int t = 0; t < T; ++t) {
+      const uint64_t u = C.key_unscale[(size_t)digit * T + t], pt = C.primes[t];
+      if (u == 1) continue;
+      for (size_t n = 0; n < C.N; ++n) {
+        b[(size_t)t * C.N + n] = hedap::h_mulmod(b[(size_t)t * C.N + n], u, pt);
+        a[(size_t)t * C.N + n] = hedap::h_mulmod(a[(size_t)t * C.N + n], u, pt);
+      }
+    }
   });
 }
 API hedap_status hedap_encrypt(hedap_ctx* ctx, const double* re, const double* im, size_t n_slots, int level,

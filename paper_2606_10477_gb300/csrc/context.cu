@@ -167,6 +167,41 @@ Ctx* ctx_create(const hedap_params& P, u64 seed, cudaStream_t st) {
   for (int t = 0; t < T; ++t) pm[t] = P_mod(C->primes[t]);
   upload(*C, C->d_pmod, pm);
 
+  // the factors folded into the switching keys (see Ctx::key_scale): for digit j and a limb t outside
+  // it, the digit's smallest prime q_i0 is added to the ModUp sum unmultiplied when the sum still meets
+  // the transform's input bound (q_i0 + 2 (a - 1) p_t below 8 p_t for digits of a <= 3 primes, whose
+  // load reduces once, below 16 p_t otherwise); the key then carries qhat_i0 = prod_{m != i0} q_m mod p_t
+  {
+    const int dnL = C->dnum(C->L());
+    C->key_scale.assign((size_t)dnL * T, 1);
+    C->key_unscale.assign((size_t)dnL * T, 1);
+    C->key_scale_i0.assign((size_t)dnL * T, -1);
+    const unsigned __int128 bound = C->alpha <= 3 ? 8 : 16;
+    for (int j = 0; j < dnL; ++j) {
+      const int lo = j * C->alpha, hi = std::min(lo + C->alpha, nq);
+      int i0 = lo;
+      for (int i = lo; i < hi; ++i)
+        if (C->primes[i] < C->primes[i0]) i0 = i;
+      for (int t = 0; t < T; ++t) {
+        if (t >= lo && t < hi) continue;
+        const u64 pt = C->primes[t];
+        if ((unsigned __int128)C->primes[i0] + (unsigned __int128)2 * (hi - lo - 1) * pt >= bound * pt) continue;
+        u64 h = 1 % pt;
+        for (int m = lo; m < hi; ++m)
+          if (m != i0) h = h_mulmod(h, C->primes[m] % pt, pt);
+        C->key_scale[(size_t)j * T + t] = h;
+        C->key_unscale[(size_t)j * T + t] = h_invmod(h, pt);
+        C->key_scale_i0[(size_t)j * T + t] = i0;
+      }
+    }
+    std::vector<u64> ks((size_t)2 * dnL * T);
+    for (size_t e = 0; e < (size_t)dnL * T; ++e) {
+      ks[2 * e] = C->key_scale[e];
+      ks[2 * e + 1] = h_shoup(C->key_scale[e], C->primes[e % T]);
+    }
+    upload(*C, C->d_key_scale, ks);
+  }
+
   // secret key: ternary coefficients, NTT domain over every prime
   SplitMix ss(seed, tags::sk);
   C->sk = draw_ternary(ss, C->log_n, C->hw);
@@ -204,6 +239,9 @@ void gen_switch_key(Ctx& C, u64 g, const u64* sp, const u64* s_to) {
     ntt_forward(C.tab, LimbSet{b, 0, 1, 0, T, nq, 0, nq}, C.stream);
     const int lo = j * C.alpha, hi = std::min(lo + C.alpha, nq);
     k_keygen_combine(C, b, a, s_to, sp, C.d_pmod.p, lo, hi);
+    const u64* f = C.d_key_scale.p + (size_t)2 * j * T;  // the folded conversion factors (Ctx::key_scale)
+    k_scale_limbs(C, b, T, f);
+    k_scale_limbs(C, a, T, f);
     HEDAP_CUDA(cudaStreamSynchronize(C.stream));  // host buffers are reused
   }
   C.keys[g] = std::move(key);

@@ -129,6 +129,30 @@ const LevelConsts& level_consts(Ctx& C, int l) {
   }
   L->modup = DevBuf(v.size(), C.stream);
   HEDAP_CUDA(cudaMemcpyAsync(L->modup.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, C.stream));
+  // the key switch's fused ModUp: every factor divided by the key's scale (Ctx::key_scale); the factor
+  // of the folded limb becomes 1 and is marked by a Shoup companion 0
+  std::vector<u64> vk(v);
+  double products = 0;
+  const int T = C.total_primes();
+  for (int j = 0; j < dn; ++j) {
+    const int lo = j * a, hi = std::min(lo + a, l + 1);
+    for (int t = 0; t < ext; ++t) {
+      if (t >= lo && t < hi) continue;  // the digit's own limbs are not converted
+      const int gt = t <= l ? t : C.n_q + (t - l - 1);
+      const u64 pt = prime_of_ext(t), un = C.key_unscale[(size_t)j * T + gt];
+      const int i0 = C.key_scale_i0[(size_t)j * T + gt];
+      for (int i = lo; i < hi; ++i) {
+        const size_t at = 2 * (l + 1) + ((size_t)j * a + (i - lo)) * ext + t;
+        const u64 f = h_mulmod(v[at], un, pt);
+        vk[at] = f;
+        vk[at + nb] = (i == i0 && f == 1) ? 0 : h_shoup(f, pt);
+        products += vk[at + nb] ? 1 : 0;
+      }
+    }
+  }
+  L->modup_products = products;
+  L->modup_ks = DevBuf(vk.size(), C.stream);
+  HEDAP_CUDA(cudaMemcpyAsync(L->modup_ks.p, vk.data(), vk.size() * 8, cudaMemcpyHostToDevice, C.stream));
   // the key switch's inverse NTT ends with N^-1 qhat_i^-1 instead of N^-1, so that its output is the
   // first factor [x_i qhat_i^-1]_{q_i} of the fast basis conversion
   std::vector<u64> post(2 * (l + 1));
@@ -220,9 +244,10 @@ static DevBuf ks_modup(Ctx& C, const u64* d, size_t d_stride, int batch, int l, 
   up.own_limit = l + 1;
   up.z = dc.p;
   up.z_stride = nl * N;
-  up.bconv = LC.modup.p + 2 * nl;
+  up.bconv = LC.modup_ks.p + 2 * nl;  // factors divided by the key's folded ones
   up.bconv_sh_offset = (size_t)dn * C.alpha * ext;
   up.ext = ext;
+  up.z_products = LC.modup_products * batch * (double)N;
   ntt_forward(C.tab, LimbSet{y.p, (size_t)ext * N, batch * dn, 0, ext, l + 1, 0, C.n_q}, C.stream, &up, fuse);
   return y;
 }

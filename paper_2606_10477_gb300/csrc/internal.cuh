@@ -137,8 +137,9 @@ struct NttAux {
   const u64* z = nullptr;
   size_t z_stride = 0;
   const u64* bconv = nullptr;  // [dn][alpha][ext]; their Shoup companions at bconv + bconv_sh_offset
-  size_t bconv_sh_offset = 0;
+  size_t bconv_sh_offset = 0;  // a companion 0 marks a factor 1: z is added without a product
   int ext = 0;
+  double z_products = -1;  // products of the whole launch's conversion (word x term), for the profiler
   // forward only: the first phase loads the centred residue of one coefficient-domain limb (the
   // last limb of a rescale, prime index spread_prime) into the prime of limb li:
   //   m = x mod q_li, minus spread_sub[li] when x > q_spread / 2,  x = spread[part * spread_stride + n]
@@ -249,6 +250,9 @@ struct MdrLast {
 };
 struct LevelConsts {  // device constants for one level (evaluator.cu)
   DevBuf modup;       // qhat_inv (+shoup) per Q prime, qhat mod target per digit (+shoup)
+  DevBuf modup_ks;    // the same with every factor divided by the key's scale (key_scale); a factor 1
+                      // folded into the key has Shoup companion 0 (the load adds z without a product)
+  double modup_products = 0;  // products per word of one ciphertext's fused ModUp (folded terms excluded)
   DevBuf intt_post;   // per Q prime i <= l: N^-1 qhat_i^-1 mod q_i and its Shoup companion
   DevBuf d_rescale;   // [ql_mod l][inv l][inv_sh l] (the rescale constants below, on the device)
   RescaleConsts rescale;
@@ -292,6 +296,13 @@ struct Ctx {
   std::vector<i64> sk;
   DevBuf d_sk;        // [n_q+n_p][N] NTT domain
   std::map<u64, DevBuf> keys;  // galois (0 = relinearisation; 2, 4 encapsulation) -> [dnum][2][n_q+n_p][N]
+  // Limb t of key digit j, t outside the digit, is stored multiplied by key_scale[j][t]: the conversion
+  // factor qhat_{i0} mod p_t of one digit limb i0 = key_scale_i0[j][t] (-1 and factor 1 where none is
+  // folded), so that the ModUp conversion adds z_{i0} without a product (see ks_modup).  Exported keys
+  // are multiplied back by key_unscale.  [dnum(L)][n_q + n_p] each; d_key_scale: (factor, Shoup) pairs.
+  std::vector<u64> key_scale, key_unscale;
+  std::vector<int> key_scale_i0;
+  DevBuf d_key_scale;
   int enc_hw = 0;             // sparse-secret encapsulation of bootstrapping: weight of s~ (0 = off)
   DevBuf d_sk_sparse;         // s~, [n_q+n_p][N] NTT domain
   std::map<int, std::unique_ptr<LevelConsts>> lc;

@@ -548,6 +548,20 @@ void k_keygen_combine(const Ctx& C, u64* b, const u64* a, const u64* s, const u6
                                                                      C.total_primes(), C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
+__global__ void k_scale_limbs_kernel(const PrimeDev* __restrict__ pr, u64* __restrict__ x, int limbs, int log_n,
+                                     const u64* __restrict__ f) {
+  GRID_LOOP(e, (size_t)limbs << log_n) {
+    const int t = (int)(e >> log_n);
+    x[e] = shoup_mul(x[e], f[2 * t], f[2 * t + 1], pr[t].q);
+  }
+}
+void k_scale_limbs(const Ctx& C, u64* x, int limbs, const u64* f) {
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, 2.0 * limbs * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)limbs * C.N;
+  k_scale_limbs_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, x, limbs, C.log_n, f);
+  HEDAP_LAUNCH_CHECK();
+}
 // out = x (op) y*z elementwise over `limbs` limbs (prime = limb index): op 0: x - y*z, 1: x + y*z, 2: y*z
 __global__ void k_fma_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ x, const u64* __restrict__ y,
                              const u64* __restrict__ z, u64* __restrict__ out, int limbs, int log_n, int op) {

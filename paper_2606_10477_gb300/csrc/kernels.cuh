@@ -37,6 +37,8 @@ void k_moddown_finish(const Ctx& C, const u64* acc, const u64* v, u64* out, size
                       bool acc_even, bool acc_odd);
 void k_keygen_combine(const Ctx& C, u64* b, const u64* a, const u64* s, const u64* sp, const u64* pmod, int lo,
                       int hi);
+// x[t][n] *= f[2t] mod prime t (Shoup companion f[2t + 1]) for the limbs t < limbs, canonical
+void k_scale_limbs(const Ctx& C, u64* x, int limbs, const u64* f);
 void k_fma(const Ctx& C, const u64* x, const u64* y, const u64* z, u64* out, int limbs, int op);
 
 }  // namespace hedap

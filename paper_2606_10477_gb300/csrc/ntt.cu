@@ -52,15 +52,16 @@ static void dispatch(const Tables& T, const LimbSet& S, cudaStream_t st, bool in
   const double limbs = (double)S.n_parts * S.n_limbs - (A.own_alpha ? (double)S.n_parts / A.own_dn * A.own_limit : 0.0);
   const double n = (double)((size_t)1 << T.log_n);
   ProfScope prof_(PROF_NTT, st, 16.0 * limbs * n);
-  // algorithmic multiply work in 32-bit multiply-pipe slots: a Shoup product by a constant is 6 wide (2 slots
-  // each) and 4 low products = 16 slots; every butterfly has one, and so does every term of a fused basis
-  // conversion (ModUp: min(alpha, own_limit) per word of a converted limb; ModDown: K per word); the fused key
-  // inner product multiplies every word of every digit by two key words, a full 64 x 64 -> 128-bit product of 4
-  // wide products = 8 slots each
+  // algorithmic multiply work in 32-bit multiply-pipe slots (one 32 x 32 -> 32 product, low or high half):
+  // a Shoup product by a constant is 7 half products for the exact high half of x w' and 2 wide (2 slots each)
+  // plus 4 low products for x w - qh q = 15 slots; every butterfly has one, and so does every product of a
+  // fused basis conversion (ModUp: one per digit limb, less a factor folded into the key; ModDown: K per word);
+  // the fused key inner product multiplies every word of every digit by two key words, a full 64 x 64 ->
+  // 128-bit product of 8 half products = 8 slots each
   double shoup = limbs * n / 2 * T.log_n;
-  if (A.z) shoup += limbs * n * std::min(A.own_alpha, A.own_limit);
+  if (A.z) shoup += A.z_products >= 0 ? A.z_products : limbs * n * std::min(A.own_alpha, A.own_limit);
   if (A.pconv) shoup += limbs * n * A.pconv_K;
-  prof_.slots = 16.0 * shoup;
+  prof_.slots = 15.0 * shoup;
   if (F) prof_.slots += 8.0 * 2.0 * F->batch * (double)S.n_limbs * A.own_dn * n;
   prof_count_launches(2);
   ntt_launch(T.log_n, v, S, T, st, inverse, A, F);

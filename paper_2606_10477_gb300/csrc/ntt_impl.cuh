@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
   const int r0 = blockIdx.x * C;
   if (A.z) {  // fused ModUp: fast basis conversion of digit j into this limb's prime
     // sum of na <= 8 Shoup products, each in [0, 2q), brought into [0, 4q): the
-    // first butterflies accept any input below 4q
+    // first butterflies accept any input below 4q (a term folded into the key is z itself, below the
+    // bound the key's construction checked)
     const int j = part % A.own_dn, lo = j * A.own_alpha, na = min(A.own_alpha, A.own_limit - lo);
     const u64* zk = A.z + (size_t)(part / A.own_dn) * A.z_stride + (size_t)lo * N;
     const u64* bc = A.bconv + (size_t)j * A.own_alpha * A.ext + li;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols(Tables T, LimbSet S,
       u64 v = 0;
 #pragma unroll
       for (int t = 0; t < 8; ++t)
-        if (t < na) v += shoup_mul_lazy(zk[(size_t)t * N + n], f[t], fs[t], q);
+        if (t < na) v += fs[t] ? shoup_mul_lazy(zk[(size_t)t * N + n], f[t], fs[t], q) : zk[(size_t)t * N + n];
       if (v >= q8) v -= q8;
       if (v >= q4) v -= q4;
       sm[idx] = v;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, Lim
     cp_async_commit();
     const int pi = S.prime(li);
     const u64 q = T.pr[pi].q, q4 = q << 2, q8 = q << 3;
-    if (A.z) {  // ModUp: sum of na Shoup products (each < 2q) brought into [0, 4q)
+    if (A.z) {  // ModUp: sum of na Shoup products (each < 2q; a folded term is z) brought into [0, 4q)
       const u64* bc = A.bconv + (size_t)j * A.own_alpha * A.ext + li;
       const u64* bcs = bc + A.bconv_sh_offset;
       u64 f[3], fs[3];
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_ntt_fwd_cols_shared(Tables T, Lim
         u64 v = 0;
 #pragma unroll
         for (int t = 0; t < 3; ++t)
-          if (t < ns) v += shoup_mul_lazy(zt[(size_t)t * E + idx], f[t], fs[t], q);
+          if (t < ns) v += fs[t] ? shoup_mul_lazy(zt[(size_t)t * E + idx], f[t], fs[t], q) : zt[(size_t)t * E + idx];
         if (v >= q4) v -= q4;
         sm[idx] = v;
       }
