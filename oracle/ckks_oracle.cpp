@@ -27,6 +27,7 @@
 //    Alkim et al. 2016), ternary secrets dense or of fixed Hamming weight.
 // ============================================================================
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -1058,6 +1059,92 @@ static std::vector<DiagMap> fft_groups(size_t n, int groups, bool inverse) {
 static Poly encode_at(const Ctx& C, const std::vector<cd>& z, double scale, int level) {
   return coeffs_to_ntt(C, encode_coeffs(C, z, scale), level);
 }
+// Baby steps of a linear transform kept in the extended basis Q_l u P (double hoisting, Bossuat,
+// Mouchet, Troncoso-Pastoriza and Hubaux, Eurocrypt 2021): rotation g of a is represented, before
+// its ModDown, as the pair (P sigma_g(c0) + ks0, ks1) over Q_l u P (NTT domain), ks the key-switch
+// sums of sigma_g(c1) (the hoisted digits, as in rotate_hoisted).  P x vanishes mod every p_k.
+// Giant steps then sum plaintext products of these pairs and divide by P once (ModDown).
+static std::vector<int> ext_primes(const Ctx& C, int l) {
+  std::vector<int> ext;
+  for (int i = 0; i <= l; ++i) ext.push_back(i);
+  for (int k = 0; k < C.n_p; ++k) ext.push_back(C.n_q + k);
+  return ext;
+}
+static u64 P_mod(const Ctx& C, u64 m) {
+  u64 r = 1 % m;
+  for (int k = 0; k < C.n_p; ++k) r = mulmod(r, C.q[C.n_q + k] % m, m);
+  return r;
+}
+typedef std::array<Poly, 2> PolyPair;
+// a itself over Q_l u P: (P c0, P c1)
+static PolyPair lift_qp(const Ctx& C, const Ct& a) {
+  const int l = a.level;
+  const std::vector<int> ext = ext_primes(C, l);
+  PolyPair r;
+  for (int p = 0; p < 2; ++p) {
+    r[p].assign(ext.size(), Limb(C.N, 0));
+    for (int i = 0; i <= l; ++i) {
+      const u64 Pm = P_mod(C, C.q[i]);
+      for (size_t n = 0; n < C.N; ++n) r[p][i][n] = mulmod(a.c[p][i][n], Pm, C.q[i]);
+    }
+  }
+  return r;
+}
+static std::vector<PolyPair> rotate_hoisted_qp(Ctx& C, const Ct& a, const std::vector<i64>& steps) {
+  const int l = a.level;
+  Poly x1 = a.c[1];
+  PER_LIMB
+  for (int i = 0; i <= l; ++i) ntt_inverse(C, x1[i], i);
+  const std::vector<int> ext = ext_primes(C, l);
+  std::vector<Poly> ys;
+  for (int j = 0; j < n_digits(C, l); ++j) ys.push_back(modup_coeff(C, x1, l, j));
+  std::vector<PolyPair> out;
+  for (i64 st : steps) {
+    const u64 g = galois_of_rotation(C, st);
+    gen_key(C, g);
+    const std::vector<KeyDigit>& key = C.keys.find(g)->second;
+    PolyPair acc;
+    acc[0].assign(ext.size(), Limb(C.N, 0));
+    acc[1].assign(ext.size(), Limb(C.N, 0));
+    for (size_t j = 0; j < ys.size(); ++j) {
+      PER_LIMB
+      for (size_t e = 0; e < ext.size(); ++e) {
+        const int t = ext[e];
+        const u64 qt = C.q[t];
+        Limb yg = automorph_coeff(C, ys[j][e], g, qt);
+        ntt_forward(C, yg, t);
+        for (size_t n = 0; n < C.N; ++n) {
+          acc[0][e][n] = addmod(acc[0][e][n], mulmod(yg[n], key[j].b[t][n], qt), qt);
+          acc[1][e][n] = addmod(acc[1][e][n], mulmod(yg[n], key[j].a[t][n], qt), qt);
+        }
+      }
+    }
+    PER_LIMB
+    for (int i = 0; i <= l; ++i) {  // + P sigma_g(c0) on the Q limbs
+      Limb x0 = a.c[0][i];
+      ntt_inverse(C, x0, i);
+      Limb p0 = automorph_coeff(C, x0, g, C.q[i]);
+      ntt_forward(C, p0, i);
+      const u64 Pm = P_mod(C, C.q[i]);
+      for (size_t n = 0; n < C.N; ++n) acc[0][i][n] = addmod(acc[0][i][n], mulmod(p0[n], Pm, C.q[i]), C.q[i]);
+    }
+    out.push_back(acc);
+  }
+  return out;
+}
+// ModDown of a pair over Q_l u P (NTT domain) into a ciphertext at level l
+static Ct moddown_pair(const Ctx& C, PolyPair x, int l, double scale) {
+  const std::vector<int> ext = ext_primes(C, l);
+  Ct r; r.level = l; r.scale = scale;
+  for (int p = 0; p < 2; ++p) {
+    PER_LIMB
+    for (size_t e = 0; e < ext.size(); ++e) ntt_inverse(C, x[p][e], ext[e]);
+    r.c[p] = moddown_coeff(C, x[p], l);
+    PER_LIMB
+    for (int i = 0; i <= l; ++i) ntt_forward(C, r.c[p][i], i);
+  }
+  return r;
+}
 static Ct mul_plain(const Ctx& C, const Ct& a, const Poly& pt) {
   Ct r = a;
   PER_LIMB
@@ -1090,34 +1177,51 @@ static Ct linear_transform(Ctx& C, const Ct& v, const DiagMap& M, double target,
   n1 = std::min(n1, 16L);
   long giants = (span + n1 - 1) / n1;
   double sp = target * (double)C.q[v.level] / v.scale;
-  // baby steps: every rotation of v used by some giant step, hoisted
-  std::vector<Ct> baby(n1);
-  baby[0] = v;
+  const int l = v.level;
+  const std::vector<int> ext = ext_primes(C, l);
+  // baby steps: every rotation of v used by some giant step, hoisted and kept over Q_l u P
+  std::vector<PolyPair> baby(n1);
+  std::vector<bool> have(n1, false);
   {
     std::vector<long> need;
     std::vector<i64> steps;
     for (long b = 1; b < n1; ++b)
       for (long g = 0; g < giants; ++g)
         if (byk.count(kmin + g * n1 + b)) { need.push_back(b); steps.push_back(b * h0); break; }
-    std::vector<Ct> rot = rotate_hoisted(C, v, steps);
-    for (size_t i = 0; i < need.size(); ++i) baby[need[i]] = rot[i];
+    std::vector<PolyPair> rot = rotate_hoisted_qp(C, v, steps);
+    for (size_t i = 0; i < need.size(); ++i) { baby[need[i]] = rot[i]; have[need[i]] = true; }
+    for (long g = 0; g < giants; ++g)
+      if (byk.count(kmin + g * n1)) { baby[0] = lift_qp(C, v); have[0] = true; break; }
   }
   Ct acc; bool acc_set = false;
   for (long g = 0; g < giants; ++g) {
     long G = h0 * (kmin + g * n1);
-    Ct inner; bool inner_set = false;
+    // sum_b diag o baby_b over Q_l u P, then one ModDown
+    PolyPair inner;
+    inner[0].assign(ext.size(), Limb(C.N, 0));
+    inner[1].assign(ext.size(), Limb(C.N, 0));
+    bool inner_set = false;
     for (long b = 0; b < n1; ++b) {
       long k = kmin + g * n1 + b;
       auto it = byk.find(k);
-      if (it == byk.end()) continue;
-      Poly pt = encode_at(C, tiled(C, rot_vec(*it->second, -G)), sp, v.level);
-      Ct term = mul_plain(C, baby[b], pt);
-      term.scale = v.scale * sp;
-      inner = inner_set ? add_sub(C, inner, term, false) : term; inner_set = true;
+      if (it == byk.end() || !have[b]) continue;
+      const std::vector<double> m = encode_coeffs(C, tiled(C, rot_vec(*it->second, -G)), sp);
+      PER_LIMB
+      for (size_t e = 0; e < ext.size(); ++e) {
+        const int t = ext[e];
+        const u64 qt = C.q[t];
+        Limb pt(C.N);
+        for (size_t n = 0; n < C.N; ++n) pt[n] = double_to_mod(m[n], qt);
+        ntt_forward(C, pt, t);
+        for (int p = 0; p < 2; ++p)
+          for (size_t n = 0; n < C.N; ++n) inner[p][e][n] = addmod(inner[p][e][n], mulmod(baby[b][p][e][n], pt[n], qt), qt);
+      }
+      inner_set = true;
     }
     if (!inner_set) continue;
+    Ct in = moddown_pair(C, inner, l, v.scale * sp);
     long Gm = ((G % n) + n) % n;
-    Ct r = Gm ? rotate(C, inner, G) : inner;
+    Ct r = Gm ? rotate(C, in, G) : in;
     acc = acc_set ? add_sub(C, acc, r, false) : r; acc_set = true;
   }
   Ct out = rescale(C, acc);

@@ -10,8 +10,11 @@
 //                factors, each applied as a baby-step / giant-step sum of
 //                plaintext diagonals times rotations (Halevi-Shoup, Chen-
 //                Chillotti-Song 2019), the baby-step rotations hoisted (one
-//                ModUp shared by all of them); real / imaginary parts split by
-//                conjugation and taken through EvalMod as one batch
+//                ModUp shared by all of them) and kept over Q_l u P: each
+//                giant step sums its plaintext products there and divides by
+//                P once (double hoisting, Bossuat et al. 2021); real /
+//                imaginary parts split by conjugation and taken through
+//                EvalMod as one batch
 //   EvalMod      u = t / (q_0 K) -> sin(2 pi K u) = sin(2 pi m / q_0): Chebyshev
 //                interpolant of cos(2 pi (K u - 1/4) / 2^r) and r double angles
 //                (Bossuat et al. 2021)
@@ -215,18 +218,21 @@ __global__ void k_monomial_kernel(const PrimeDev* __restrict__ pr, const u64* __
     out[p * os + r] = v;
   }
 }
-// integer coefficients (|c| < 2^63) to residues on limbs 0..level
+// integer coefficients (|c| < 2^63) to residues on `limbs` limbs: limb li < q_count of prime li, the
+// others of prime p_first + (li - q_count)
 __global__ void k_coeffs_to_limbs_kernel(const PrimeDev* __restrict__ pr, const long long* __restrict__ c,
-                                         u64* __restrict__ out, int limbs, int log_n) {
+                                         u64* __restrict__ out, int limbs, int log_n, int q_count, int p_first) {
   const size_t N = (size_t)1 << log_n, total = (size_t)limbs << log_n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const PrimeDev P = pr[e >> log_n];
+    const int li = (int)(e >> log_n);
+    const PrimeDev P = pr[li < q_count ? li : p_first + (li - q_count)];
     const long long v = c[e & (N - 1)];
     const u64 a = barrett_reduce(v < 0 ? (u64)(-(v + 1)) + 1 : (u64)v, 0, P);
     out[e] = (v < 0 && a) ? P.q - a : a;
   }
 }
-// acc[p][i][k] = sum_b ct_b[p][i][k] * pt_b[i][k]  (plaintext-ciphertext products of one giant step)
+// acc[p][i][k] = sum_b ct_b[p][i][k] * pt_b[i][k]  (plaintext-ciphertext products of one giant step);
+// limb i < q_count has prime i, the others prime p_first + (i - q_count)
 struct PtMacArgs {
   const u64* ct[16];
   size_t cs[16];
@@ -234,12 +240,13 @@ struct PtMacArgs {
   int count;
 };
 __global__ void k_pt_mac_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s, PtMacArgs A,
-                                u64* __restrict__ out, size_t os, int n_parts, int limbs, int log_n) {
+                                u64* __restrict__ out, size_t os, int n_parts, int limbs, int log_n, int q_count,
+                                int p_first) {
   const size_t per = (size_t)limbs << log_n, total = n_parts * per;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / per);
     const size_t r = e - p * per;
-    const int i = (int)(r >> log_n);
+    const int li = (int)(r >> log_n), i = li < q_count ? li : p_first + (li - q_count);
     Acc128 s{0, 0};
     for (int b = 0; b < A.count; ++b) mac128(s, A.ct[b][p * A.cs[b] + r], A.pt[b][r]);
     out[p * os + r] = reduce128(s, pr[i], r64s[2 * i], r64s[2 * i + 1]);
@@ -304,7 +311,7 @@ static const std::vector<LTGroup>& groups_for(Ctx& C, BtsState& S, size_t n, boo
 }
 
 // encode a diagonal (n values, repeated over the N/2 slots) at plaintext scale sp onto limbs
-// 0..level (NTT domain)
+// 0..level and the special limbs (Q_level u P, NTT domain)
 static DevBuf encode_diag(Ctx& C, const std::vector<cplx>& dn, double sp, int level) {
   std::vector<cplx> d(C.N / 2);
   for (size_t s = 0; s < d.size(); ++s) d[s] = dn[s % dn.size()];
@@ -314,13 +321,14 @@ static DevBuf encode_diag(Ctx& C, const std::vector<cplx>& dn, double sp, int le
     if (!(std::fabs(m[k]) < 9.0e18)) throw Error(HEDAP_ERR_RANGE, "diagonal coefficient exceeds 63 bits");
     ci[k] = (long long)m[k];
   }
-  DevBuf coef(C.N, C.stream), out((size_t)(level + 1) * C.N, C.stream);
+  const int ext = level + 1 + C.n_p;
+  DevBuf coef(C.N, C.stream), out((size_t)ext * C.N, C.stream);
   HEDAP_CUDA(cudaMemcpyAsync(coef.p, ci.data(), C.N * 8, cudaMemcpyHostToDevice, C.stream));
-  k_coeffs_to_limbs_kernel<<<grid_for((size_t)(level + 1) * C.N, 256), 256, 0, C.stream>>>(
-      C.tab.pr, (const long long*)coef.p, out.p, level + 1, C.log_n);
+  k_coeffs_to_limbs_kernel<<<grid_for((size_t)ext * C.N, 256), 256, 0, C.stream>>>(
+      C.tab.pr, (const long long*)coef.p, out.p, ext, C.log_n, level + 1, C.n_q);
   HEDAP_LAUNCH_CHECK();
   prof_count_launches(1);
-  ntt_forward(C.tab, LimbSet{out.p, 0, 1, 0, level + 1, INT_MAX, 0, 0}, C.stream);
+  ntt_forward(C.tab, LimbSet{out.p, 0, 1, 0, ext, level + 1, 0, C.n_q}, C.stream);
   HEDAP_CUDA(cudaStreamSynchronize(C.stream));  // ci is a host temporary
   return out;
 }
@@ -344,8 +352,11 @@ static std::unique_ptr<Ct> lt_apply(Ctx& C, const Ct& v, const LTGroup& G, Plain
     P.level = l;
     P.sp = sp;
   }
-  // baby steps: every rotation of v any giant step uses, hoisted (one ModUp of v)
-  std::vector<std::unique_ptr<Ct>> baby(G.n1);
+  // baby steps: every rotation of v any giant step uses, hoisted (one ModUp of v) and kept over Q_l u P
+  // before its ModDown (double hoisting, Bossuat et al. 2021); b = 0 is v itself, (P c0, P c1)
+  const int ext = l + 1 + C.n_p;
+  const size_t qp_stride = (size_t)ext * C.N;  // part stride of a pair batch [batch][2][ext][N]
+  std::vector<DevBuf> baby(G.n1);
   {
     std::vector<long> need;
     for (long b = 1; b < G.n1; ++b)
@@ -356,8 +367,14 @@ static std::unique_ptr<Ct> lt_apply(Ctx& C, const Ct& v, const LTGroup& G, Plain
         }
     std::vector<u64> gs;
     for (long b : need) gs.push_back(galois_for_rotation(C, b * G.h0));
-    auto rot = ev_galois_hoisted(C, v, gs);
+    auto rot = ev_galois_hoisted_qp(C, v, gs);
     for (size_t i = 0; i < need.size(); ++i) baby[need[i]] = std::move(rot[i]);
+    for (long g = 0; g < G.giants; ++g)
+      if (P.pt.count({g, 0})) {
+        baby[0] = DevBuf((size_t)v.parts() * qp_stride, C.stream);
+        k_lift_qp(C, v.part(0), v.part_stride(), baby[0].p, v.parts(), l);
+        break;
+      }
   }
   std::unique_ptr<Ct> acc;
   const long n = (long)slots;
@@ -367,23 +384,25 @@ static std::unique_ptr<Ct> lt_apply(Ctx& C, const Ct& v, const LTGroup& G, Plain
     for (long b = 0; b < G.n1; ++b) {
       auto it = P.pt.find({g, b});
       if (it == P.pt.end()) continue;
-      const Ct& src = b ? *baby[b] : v;
       if (A.count == 16) throw Error(HEDAP_ERR_ARG, "more than 16 baby steps");
-      A.ct[A.count] = src.part(0);
-      A.cs[A.count] = src.part_stride();
+      A.ct[A.count] = baby[b].p;
+      A.cs[A.count] = qp_stride;
       A.pt[A.count] = it->second.p;
       ++A.count;
     }
     if (!A.count) continue;
-    auto inner = ct_alloc(C, l, v.batch);
-    inner->scale = v.scale * sp;
+    // sum_b diag o baby_b over Q_l u P, then one ModDown for the giant step
+    DevBuf sum((size_t)v.parts() * qp_stride, C.stream);
     {
-      ProfScope prof_(PROF_ELEMENTWISE, C.stream, (1.5 * A.count + 1.0) * v.parts() * (l + 1) * C.N * 8);
+      ProfScope prof_(PROF_ELEMENTWISE, C.stream, (1.5 * A.count + 1.0) * v.parts() * ext * C.N * 8);
       prof_count_launches(1);
-      k_pt_mac_kernel<<<grid_for((size_t)v.parts() * (l + 1) * C.N, 256), 256, 0, C.stream>>>(
-          C.tab.pr, C.d_r64.p, A, inner->part(0), inner->part_stride(), v.parts(), l + 1, C.log_n);
+      k_pt_mac_kernel<<<grid_for((size_t)v.parts() * ext * C.N, 256), 256, 0, C.stream>>>(
+          C.tab.pr, C.d_r64.p, A, sum.p, qp_stride, v.parts(), ext, C.log_n, l + 1, C.n_q);
       HEDAP_LAUNCH_CHECK();
     }
+    auto inner = ct_alloc(C, l, v.batch);
+    inner->scale = v.scale * sp;
+    ev_moddown_into(C, sum, v.batch, l, *inner);
     const long Gs = G.h0 * (G.kmin + g * G.n1);
     std::unique_ptr<Ct> r = (((Gs % n) + n) % n) ? ev_galois(C, *inner, galois_for_rotation(C, Gs)) : std::move(inner);
     acc = acc ? ev_add(C, *acc, *r, false) : std::move(r);

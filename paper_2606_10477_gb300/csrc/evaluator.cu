@@ -409,6 +409,24 @@ std::vector<std::unique_ptr<Ct>> ev_galois_hoisted(Ctx& C, const Ct& a, const st
   return out;
 }
 
+std::vector<DevBuf> ev_galois_hoisted_qp(Ctx& C, const Ct& a, const std::vector<u64>& gs) {
+  const int l = a.level;
+  for (u64 g : gs) key_for(C, g);
+  const u64* d = a.part(1);
+  const size_t ds = 2 * a.part_stride();
+  DevBuf y = ks_modup(C, d, ds, a.batch, l);
+  std::vector<DevBuf> out;
+  for (u64 g : gs) {
+    DevBuf acc((size_t)a.batch * 2 * (l + 1 + C.n_p) * C.N, C.stream);
+    k_ksk_inner(C, y.p, d, ds, key_for(C, g).p, acc.p, a.batch, l, g, a.part(0), ds);
+    out.push_back(std::move(acc));
+  }
+  return out;
+}
+void ev_moddown_into(Ctx& C, DevBuf& acc, int batch, int level, Ct& out) {
+  ks_moddown(C, acc, batch, level, out.part(0), out.part_stride(), false, false);
+}
+
 std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b) {
   const int l = std::min(a.level, b.level);
   check_batches(a, b);

@@ -323,6 +323,11 @@ std::unique_ptr<Ct> ev_add(Ctx& C, const Ct& a, const Ct& b, bool sub);
 std::unique_ptr<Ct> ev_mul_relin(Ctx& C, const Ct& a, const Ct& b);
 std::unique_ptr<Ct> ev_rescale(Ctx& C, const Ct& a);
 std::unique_ptr<Ct> ev_mul(Ctx& C, const Ct& a, const Ct& b);
+// Rotations of a by the Galois elements gs sharing one ModUp, each kept over Q_l u P before its ModDown:
+// [batch][2][l + 1 + K][N] = (P sigma_g(c0) + ks0, ks1), NTT domain (double hoisting)
+std::vector<DevBuf> ev_galois_hoisted_qp(Ctx& C, const Ct& a, const std::vector<u64>& gs);
+// ModDown of such a pair batch (it is modified: its special limbs are transformed in place) into out
+void ev_moddown_into(Ctx& C, DevBuf& acc, int batch, int level, Ct& out);
 // rescale(lincomb({relin(a b) labelled prod_scale, prod_coef}, terms..., level min(a, b), target, c0)),
 // with the key switch's ModDown fused into the rescale; residues equal the unfused sequence
 std::unique_ptr<Ct> ev_mul_lincomb_rescale(Ctx& C, const Ct& a, const Ct& b, double prod_scale, double prod_coef,

@@ -381,7 +381,8 @@ __device__ __forceinline__ uint32_t galois_index(uint32_t n, u64 g, int log_n) {
 __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ r64s,
                                    const u64* __restrict__ y, const u64* __restrict__ d, size_t ds,
                                    const u64* __restrict__ key, u64* __restrict__ acc, int l, int dn, int alpha,
-                                   int n_q, int K, int log_n, u64 g) {
+                                   int n_q, int K, int log_n, u64 g, const u64* __restrict__ c0, size_t c0s,
+                                   const u64* __restrict__ pmod) {
   // two consecutive coefficients per thread (16-byte loads: longer runs per DRAM page
   // across the dn x B digit streams); a permuted source is read word by word
   const size_t N = (size_t)1 << log_n;
@@ -419,6 +420,13 @@ __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* _
       mac128(b1, v1, wa.y);
     }
   }
+  if (c0 && t <= l) {  // the rotation kept over Q_l u P: part 0 gains P sigma_g(c0) on the Q limbs
+    const u64* ck = c0 + k * c0s + (size_t)t * N;
+    const size_t s0 = g ? galois_index((uint32_t)n, g, log_n) : n;
+    const size_t s1 = g ? galois_index((uint32_t)n + 1, g, log_n) : n + 1;
+    mac128(a0, ck[s0], pmod[pt]);
+    mac128(b0, ck[s1], pmod[pt]);
+  }
   const PrimeDev P = pr[pt];
   const u64 r64 = r64s[2 * pt], r64p = r64s[2 * pt + 1];
   st2(acc + (((size_t)k * 2) * ext + t) * N + n,
@@ -427,7 +435,7 @@ __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* _
       ulonglong2{reduce128(a1, P, r64, r64p), reduce128(b1, P, r64, r64p)});
 }
 void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
-                 int level, u64 galois_perm) {
+                 int level, u64 galois_perm, const u64* c0, size_t c0_stride) {
   if (batch < 1 || batch > kMaxBatch) throw Error(HEDAP_ERR_ARG, "batch must lie in [1, 16]");
   const int dn = C.dnum(level), ext = level + 1 + C.n_p;
   ProfScope prof_(PROF_KSK_INNER, C.stream, ((double)batch * dn + 2.0 * dn + 2.0 * batch) * ext * C.N * 8);
@@ -435,7 +443,28 @@ void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, cons
   const unsigned tx = 32u * (unsigned)std::max(1, 8 / batch);  // about 256 threads per CTA
   const dim3 block(tx, (unsigned)batch), grid((unsigned)(C.N / 2 / tx), (unsigned)ext);
   k_ksk_inner_kernel<<<grid, block, 0, C.stream>>>(C.tab.pr, C.d_r64.p, y, d, d_stride, key, acc, level, dn, C.alpha,
-                                                   C.n_q, C.n_p, C.log_n, galois_perm);
+                                                   C.n_q, C.n_p, C.log_n, galois_perm, c0, c0_stride, C.d_pmod.p);
+  HEDAP_LAUNCH_CHECK();
+}
+
+// a batch over Q_l u P: (P c0, P c1) on the Q limbs (P mod q_i by Barrett), 0 on the special limbs
+__global__ void k_lift_qp_kernel(const PrimeDev* __restrict__ pr, const u64* __restrict__ pmod,
+                                 const u64* __restrict__ in, size_t is, u64* __restrict__ out, int n_parts, int l,
+                                 int ext, int log_n) {
+  const size_t N = (size_t)1 << log_n, per = (size_t)ext << log_n;
+  GRID_LOOP(e, (size_t)n_parts * per) {
+    const size_t p = e / per, r = e - p * per;
+    const int t = (int)(r >> log_n);
+    out[e] = t <= l ? mul_mod(in[p * is + r], pmod[t], pr[t]) : 0;
+  }
+}
+void k_lift_qp(const Ctx& C, const u64* in, size_t is, u64* out, int n_parts, int level) {
+  const int ext = level + 1 + C.n_p;
+  ProfScope prof_(PROF_ELEMENTWISE, C.stream, (double)n_parts * (level + 1 + ext) * C.N * 8);
+  prof_count_launches(1);
+  const size_t work = (size_t)n_parts * ext * C.N;
+  k_lift_qp_kernel<<<grid_for(work, 256), 256, 0, C.stream>>>(C.tab.pr, C.d_pmod.p, in, is, out, n_parts, level,
+                                                                ext, C.log_n);
   HEDAP_LAUNCH_CHECK();
 }
 

@@ -23,8 +23,12 @@ void k_rescale_finish(const Ctx& C, const u64* in, size_t is, const u64* tmp, si
                       int n_parts, int l, const RescaleConsts& R);
 void k_automorph(const Ctx& C, const u64* in, size_t is, u64* out, size_t os, int n_parts, int limbs, u64 g);
 void k_modup(const Ctx& C, const u64* dcoef, u64* y, int batch, int level, const u64* d_consts);
+// with c0 (part 0 of the input batch, member stride c0_stride): part 0 of acc also receives P sigma_g(c0) on
+// the Q limbs, the rotated ciphertext over Q_l u P before its ModDown
 void k_ksk_inner(const Ctx& C, const u64* y, const u64* d, size_t d_stride, const u64* key, u64* acc, int batch,
-                 int level, u64 galois_perm = 0);
+                 int level, u64 galois_perm = 0, const u64* c0 = nullptr, size_t c0_stride = 0);
+// out [n_parts][ext][N] = (P x) on the Q limbs 0..level of in (part stride is), 0 on the special limbs
+void k_lift_qp(const Ctx& C, const u64* in, size_t is, u64* out, int n_parts, int level);
 void k_moddown_spread(const Ctx& C, const u64* acc, u64* v, int n_parts, int level);
 // ModDown fused with a rescale (evaluator.cu, ks_moddown_rescale): limb l of the ModDown output, first
 // t = e_l + acc_l P^-1 (NTT domain), then, with t back in the coefficient domain, x = t minus the
