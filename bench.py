@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--ntt-limbs", type=int, default=384, help="limbs per batched NTT in --only ntt")
     ap.add_argument("--profile-region", action="store_true",
                     help="--only ntt: one forward and one inverse transform between cudaProfilerStart/Stop "
-                         "(for ncu --profile-from-start off); --only hmult: one batched HMult")
+                         "(for ncu --profile-from-start off); --only hmult: one batched HMult; --only bts: one batched "
+                         "bootstrap")
     return ap.parse_args()
 
 
@@ -970,6 +971,38 @@ def run_hmult_only(args):
           flush=True)
 
 
+def bts_profile(args):
+    """One batched bootstrap (bts16 chain, full slots, batch --batch) after a warm-up, its time by kernel class
+    from the library's event profiler, and the same bootstrap once more between cudaProfilerStart/Stop (for
+    ncu --profile-from-start off)."""
+    import torch
+    from paper_2606_10477_gb300 import hedap, inputs
+    p, b = inputs.PRESETS["bts16"], inputs.BTS
+    stream = torch.cuda.current_stream()
+    ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 11,
+                        stream=stream.cuda_stream)
+    ctx.bts_setup(b["K"], b["r"], b["deg"], b["cts"], b["stc"])
+    vals = [inputs.uniform_values(5000 + i, ctx.N // 2, -0.5, 0.5) for i in range(args.batch)]
+    ct = ctx.pack([ctx.encrypt(v, 1, 5100 + i) for i, v in enumerate(vals)])
+    ctx.bootstrap_scaled(ct, 1)  # warm-up: keys and diagonals are built here
+    torch.cuda.synchronize()
+    hedap.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.bootstrap_scaled(ct, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = hedap.profile_read()
+    hedap.profile_enable(False)
+    torch.cuda.profiler.start()
+    ctx.bootstrap_scaled(ct, 1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"bootstrap": {"batch": args.batch, "ms": e0.elapsed_time(e1),
+                                    "classes": {k: {"groups": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}}}),
+          flush=True)
+
+
 def run_ntt_only(args):
     import torch
     from paper_2606_10477_gb300 import hedap, inputs
@@ -996,6 +1029,8 @@ def main():
         run_ops_only(args)
     elif args.only == "serving":
         run_serving_only(args)
+    elif args.only == "bts" and args.profile_region:
+        bts_profile(args)
     elif args.only == "bts":
         import torch
         from paper_2606_10477_gb300 import hedap, inputs
