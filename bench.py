@@ -104,10 +104,10 @@ def measured_peaks():
 NTT_MUL_SLOTS_PER_BUTTERFLY = 15
 IMAD_LANES_PER_SM = 64
 # DRAM bytes per transformed limb: dram__bytes_read.sum + dram__bytes_write.sum of the transform launches of one
-# batched HMult at the top level (`--only hmult --batch 8 --profile-region` under ncu: 5317 MB for 3296 limb
-# transforms, the mix of fused ModUp (with the key inner product), ModDown and rescale transforms of the step),
-# scaled to a launch group by its limbs
-NTT_DRAM_BYTES_PER_LIMB = 1.613e6
+# batched HMult with rescale at the top level (`--only hmult --batch 8 --profile-region` under ncu: 4553.6 MB for
+# 2912 limb transforms, the mix of fused ModUp (with the key inner product) and ModDown-rescale transforms of the
+# step), scaled to a launch group by its limbs
+NTT_DRAM_BYTES_PER_LIMB = 1.564e6
 
 
 def ntt_alu_roofline(n, alg_bytes, ms, groups, peaks, slots):
@@ -1014,9 +1014,11 @@ def run_ntt_only(args):
     fwd, inv, fv, iv = ctx.ntt_tune(args.ntt_limbs, 3)
     r = measure_ntt(ctx, inputs, torch, stream, args.ntt_limbs, reps=max(1, args.steps),
                     profile_region=args.profile_region)
+    loop = ctx.butterfly_rate() / 1e9  # the register-only butterfly loop (k_butterfly_loop), outside the region
     print(json.dumps({"metric": "NTT GB/s (N=2^16, 64-bit limbs, batched)", "value": r["forward"]["gbs"],
                       "unit": "GB/s", "ntt": r, "tune": {"forward_ms": fwd, "inverse_ms": inv,
-                                                         "chosen": [fv, iv]}}), flush=True)
+                                                         "chosen": [fv, iv], "roles": ctx.ntt_get_roles()},
+                      "register_loop_gbutterfly_s": loop}), flush=True)
 
 
 def main():
