@@ -1012,9 +1012,9 @@ def run_ntt_only(args):
     ctx = hedap.Context(p["log_n"], p["q_bits"], p["p_bits"], p["alpha"], p["log_scale"], p["hw"], 1,
                         stream=stream.cuda_stream)
     fwd, inv, fv, iv = ctx.ntt_tune(args.ntt_limbs, 3)
+    loop = ctx.butterfly_rate() / 1e9  # the register-only butterfly loop (k_butterfly_loop), before the region
     r = measure_ntt(ctx, inputs, torch, stream, args.ntt_limbs, reps=max(1, args.steps),
                     profile_region=args.profile_region)
-    loop = ctx.butterfly_rate() / 1e9  # the register-only butterfly loop (k_butterfly_loop), outside the region
     print(json.dumps({"metric": "NTT GB/s (N=2^16, 64-bit limbs, batched)", "value": r["forward"]["gbs"],
                       "unit": "GB/s", "ntt": r, "tune": {"forward_ms": fwd, "inverse_ms": inv,
                                                          "chosen": [fv, iv], "roles": ctx.ntt_get_roles()},
