@@ -384,20 +384,18 @@ def run_ours(args):
                                 "launch_groups_per_step": n_c / n_prof_steps, "avg_group_us": 1e3 * ms_c / n_c})
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    host_in = [torch.empty((2, L + 1, ctx.N), dtype=torch.int64, pin_memory=True) for _ in range(batch)]
-    for h, c in zip(host_in, cts):
-        h.numpy()[...] = c.limbs().view(np.int64)
-    host_out = [torch.empty((2, out_level + 1, ctx.N), dtype=torch.int64, pin_memory=True) for _ in range(batch)]
-    h2d = sum(h.numel() * 8 for h in host_in)
-    d2h = sum(h.numel() * 8 for h in host_out)
+    host_in = torch.empty((batch, 2, L + 1, ctx.N), dtype=torch.int64, pin_memory=True)
+    for k, c in enumerate(cts):
+        host_in[k].numpy()[...] = c.limbs().view(np.int64)
+    host_out = torch.empty((batch, 2, out_level + 1, ctx.N), dtype=torch.int64, pin_memory=True)
+    h2d = host_in.numel() * 8
+    d2h = host_out.numel() * 8
 
     graph_e = ctx.invsqrt_graph(packed, LO, HI, B, args.degree, args.iters)
 
-    def e2e_step():  # host limbs in, the batch packed and run through the captured step, host limbs out
-        ins = [ctx.ct_import(hi, L, ctx.scale) for hi in host_in]
-        out = graph_e.run(ctx.pack(ins))
-        for k, ho in enumerate(host_out):
-            ctx.unpack(out, k).export_to(ho)
+    def e2e_step():  # the batch's host limbs in (one copy), the captured step, the batch's host limbs out (one copy)
+        out = graph_e.run(ctx.batch_import(host_in, batch, L, ctx.scale))
+        ctx.batch_export(out, host_out)
 
     e2e_step()
     torch.cuda.synchronize()

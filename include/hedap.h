@@ -183,6 +183,16 @@ hedap_status hedap_invsqrt(hedap_ctx* ctx, const hedap_ct* in, const hedap_invsq
  * packed (up to 16 per batch, in input order) and run together; out[i]
  * receives input i's result.  On error every out[i] is NULL. */
 hedap_status hedap_batch_pack(hedap_ctx* ctx, const hedap_ct* const* cts, size_t n, hedap_ct** out);
+/* A whole batch in one copy each way: hedap_batch_import reads n (1..16)
+ * ciphertexts [n][2][level+1][N] (NTT domain) into one batch handle, with
+ * hedap_ct_import's semantics (host: one residue check, returns once copied;
+ * device: stream ordered, unchecked); hedap_batch_export writes a batch's
+ * [n][2][level+1][N] words into out (capacity cap words; host: returns once
+ * copied).  HEDAP_ERR_ARG for a bad size or capacity, HEDAP_ERR_RANGE for a
+ * host word not below its prime. */
+hedap_status hedap_batch_import(hedap_ctx* ctx, const uint64_t* limbs, size_t n, int level, double scale,
+                                int on_device, hedap_ct** out);
+hedap_status hedap_batch_export(hedap_ctx* ctx, const hedap_ct* batch, uint64_t* out, size_t cap, int on_device);
 hedap_status hedap_batch_unpack(hedap_ctx* ctx, const hedap_ct* batch, size_t index, hedap_ct** out);
 hedap_status hedap_ct_batch_size(const hedap_ct* ct, int* n);
 hedap_status hedap_invsqrt_batch(hedap_ctx* ctx, const hedap_ct* const* in, const hedap_invsqrt_cfg* cfgs, size_t n,

@@ -203,6 +203,47 @@ API hedap_status hedap_ct_export(hedap_ctx* ctx, const hedap_ct* ct, uint64_t* o
     if (!on_device) HEDAP_CUDA(cudaStreamSynchronize(C.stream));
   });
 }
+API hedap_status hedap_batch_import(hedap_ctx* ctx, const uint64_t* limbs, size_t n, int level, double scale,
+                                    int on_device, hedap_ct** out) {
+  return guarded_on(ctx, [&] {
+    need(ctx && limbs && out, "null argument");
+    *out = nullptr;
+    hedap::Ctx& C = *ctx->c;
+    need(n >= 1 && n <= (size_t)hedap::kMaxBatchCts, "batch size must lie in [1, 16]");
+    need(level >= 0 && level <= C.L(), "level out of range");
+    need(scale > 0, "scale must be positive");
+    auto c = hedap::ct_alloc(C, level, (int)n);
+    c->scale = scale;
+    // cap = level + 1: the batch's parts are contiguous, [n][2][level+1][N] as the host holds them
+    const size_t words = (size_t)n * 2 * (level + 1) * C.N;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    HEDAP_CUDA(cudaMemcpyAsync(c->part(0), limbs, words * 8, kind, C.stream));
+    if (!on_device) {  // host words are checked on the device after the copy (residues below their primes)
+      hedap::DevBuf flag(1, C.stream);
+      HEDAP_CUDA(cudaMemsetAsync(flag.p, 0, 8, C.stream));
+      hedap::k_check_residues(C, c->part(0), c->part_stride(), c->parts(), level + 1, (unsigned int*)flag.p);
+      uint64_t bad = 0;
+      HEDAP_CUDA(cudaMemcpyAsync(&bad, flag.p, 8, cudaMemcpyDeviceToHost, C.stream));
+      HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+      if (bad) throw hedap::Error(HEDAP_ERR_RANGE, "residue not below its prime");
+    }
+    *out = wrap(std::move(c));
+  });
+}
+API hedap_status hedap_batch_export(hedap_ctx* ctx, const hedap_ct* batch, uint64_t* out, size_t cap, int on_device) {
+  return guarded_on(ctx, [&] {
+    need(ctx && batch && out, "null argument");
+    hedap::Ctx& C = *ctx->c;
+    const hedap::Ct& b = hedap::ct_of(ctx, batch);
+    const size_t per = (size_t)(b.level + 1) * C.N;
+    need(cap >= (size_t)b.parts() * per, "capacity too small");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // one copy: the parts are cap limbs apart on the device and level + 1 limbs apart in out
+    HEDAP_CUDA(cudaMemcpy2DAsync(out, per * 8, b.part(0), b.part_stride() * 8, per * 8, (size_t)b.parts(), kind,
+                                 C.stream));
+    if (!on_device) HEDAP_CUDA(cudaStreamSynchronize(C.stream));
+  });
+}
 API hedap_status hedap_ct_info(const hedap_ct* ct, int* level, double* scale) {
   return guarded([&] {
     need(ct, "null argument");

@@ -28,7 +28,7 @@ NTT_ROLES = {"forward": 0, "inverse": 1, "modup": 2, "finish": 3}
 EXPORTED = [
     "hedap_status_str", "hedap_last_error", "hedap_ctx_create", "hedap_ctx_destroy", "hedap_ctx_primes", "hedap_sync",
     "hedap_gen_galois_key", "hedap_galois_element", "hedap_export_key", "hedap_encrypt", "hedap_decrypt", "hedap_ct_import",
-    "hedap_ct_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
+    "hedap_ct_export", "hedap_batch_import", "hedap_batch_export", "hedap_ct_info", "hedap_ct_free", "hedap_add", "hedap_sub", "hedap_mul_relin", "hedap_mul",
     "hedap_rescale", "hedap_rotate", "hedap_rotate_hoisted", "hedap_conjugate", "hedap_mul_const", "hedap_add_const", "hedap_mul_int",
     "hedap_drop_level", "hedap_invsqrt", "hedap_ntt", "hedap_profile_enable", "hedap_profile_read", "hedap_profile_read_slots",
     "hedap_launch_count", "hedap_modup", "hedap_moddown", "hedap_key_switch", "hedap_rescale_noalloc",
@@ -136,6 +136,8 @@ def _declare(L):
         "hedap_decrypt": (st, [vp, vp, dp, dp, C.c_size_t]),
         "hedap_ct_import": (st, [vp, u64p, C.c_int, C.c_double, C.c_int, pp]),
         "hedap_ct_export": (st, [vp, vp, u64p, C.c_size_t, C.c_int]),
+        "hedap_batch_import": (st, [vp, u64p, C.c_size_t, C.c_int, C.c_double, C.c_int, pp]),
+        "hedap_batch_export": (st, [vp, vp, u64p, C.c_size_t, C.c_int]),
         "hedap_ct_info": (st, [vp, C.POINTER(C.c_int), dp]),
         "hedap_ct_free": (None, [vp]),
         "hedap_add": (st, [vp, vp, vp, pp]),
@@ -554,6 +556,19 @@ class Context:
         return Graph(self, h)
 
     # ---- batches
+    def batch_import(self, limbs, n: int, level: int, scale: float) -> Ciphertext:
+        """n ciphertexts [n][2][level+1][N] (numpy array or torch tensor, host or CUDA) as one batch, one copy."""
+        if isinstance(limbs, np.ndarray):
+            limbs = np.ascontiguousarray(limbs, dtype=np.uint64)
+        p, dev = _u64ptr(limbs)
+        return self._ct(load().hedap_batch_import, p, n, level, float(scale), dev)
+
+    def batch_export(self, b: Ciphertext, dst) -> None:
+        """Copy a batch's [n][2][level+1][N] words into dst (numpy array or torch tensor, host or CUDA)."""
+        p, dev = _u64ptr(dst)
+        cap = dst.size if isinstance(dst, np.ndarray) else dst.numel()
+        _check(load().hedap_batch_export(self.h, b.h, p, cap, dev))
+
     def pack(self, cts) -> Ciphertext:
         arr = (C.c_void_p * len(cts))(*[c.h for c in cts])
         return self._ct(load().hedap_batch_pack, arr, len(cts))

@@ -86,3 +86,32 @@ def test_invsqrt_many_level_bands():
     same = g.invsqrt_many(cts, [cfg] * len(cts), 0)  # band 0: exact levels, as invsqrt_batch
     for ct, o in zip(cts, same):
         assert np.array_equal(o.limbs(), g.invsqrt(ct, *cfg).limbs())
+
+
+def test_batch_import_export_in_one_copy():
+    """hedap_batch_import / hedap_batch_export move a whole batch [n][2][level+1][N] in one copy each way: the
+    imported batch equals the single imports packed, the export equals the members' exports (also for a batch whose
+    parts are more limbs apart than its level needs, after a rescale), and bad input is refused."""
+    g = ctx("n13")
+    L = g.n_q - 1
+    pr = g.primes()
+    host = np.stack([inputs.random_ciphertext_limbs(300 + i, pr, L, g.N) for i in range(5)])
+    b = g.batch_import(host, 5, L, g.scale)
+    check(g, b, [g.ct_import(host[i], L, g.scale) for i in range(5)])
+    out = np.zeros_like(host)
+    g.batch_export(b, out)
+    assert np.array_equal(out, host)
+    r = g.rescale(g.mul(b, b))  # a derived batch two levels down
+    want = np.stack([g.unpack(r, k).limbs() for k in range(5)])
+    got = np.zeros((5, 2, r.level + 1, g.N), dtype=np.uint64)
+    g.batch_export(r, got)
+    assert np.array_equal(got, want)
+    with pytest.raises(hedap.HedapError):
+        g.batch_export(r, np.zeros((4, 2, r.level + 1, g.N), dtype=np.uint64))  # capacity below 5 ciphertexts
+    bad = host.copy()
+    bad[3, 1, 2, 7] = pr[2]  # not below its prime
+    with pytest.raises(hedap.HedapError) as e:
+        g.batch_import(bad, 5, L, g.scale)
+    assert e.value.code == -7
+    with pytest.raises(hedap.HedapError):
+        g.batch_import(host, 17, L, g.scale)
