@@ -22,6 +22,9 @@
 //    embedding restricted to the 5^j orbit);
 //  * rescale and ModDown round to nearest (centred remainders);
 //  * key switching: hybrid, digits of alpha consecutive Q primes (Han-Ki 2020);
+//  * bootstrapping's linear transforms: baby-step / giant-step sums (Halevi-
+//    Shoup), the baby steps hoisted and kept over Q_l u P, one ModDown per giant
+//    step (double hoisting, Bossuat, Mouchet, Troncoso-Pastoriza, Hubaux 2021);
 //  * randomness: SplitMix64 (Steele, Lea, Flood 2014), one stream per object,
 //    errors from the centred binomial distribution with eta = 21 (sigma ~ 3.24,
 //    Alkim et al. 2016), ternary secrets dense or of fixed Hamming weight.
