@@ -62,6 +62,24 @@ def test_grouped_factors_are_the_decoding_matrix(ctx):
     assert all(len(ctx.fft_group(3, inv, g)) <= 31 for inv in (True, False) for g in range(3))
 
 
+@pytest.mark.parametrize("inverse", [True, False])
+def test_linear_transform_decrypts_to_the_diagonal_product(ctx, inverse):
+    """Each CoeffToSlot / SlotToCoeff group applied homomorphically (baby steps hoisted and kept over Q_l u P, one
+    ModDown per giant step, one rescale) decrypts to the group's diagonals applied to the decrypted input in numpy,
+    within CKKS noise: a dropped baby or giant step, a wrong rotation offset or a misplaced ModDown fails it."""
+    n = ctx.N // 2
+    z = inputs.uniform_values(21, n, -1, 1) + 1j * inputs.uniform_values(22, n, -1, 1)
+    c = ctx.encrypt(z, ctx.n_q - 1, 23)
+    x = ctx.decrypt(c)
+    for g in range(3):
+        target = c.scale / 16  # plaintext scale q_l / 16 keeps the encoded diagonals below 2^63
+        c = ctx.linear_transform_group(c, 3, inverse, g, target)
+        want = apply(ctx.fft_group(3, inverse, g), x)
+        got = ctx.decrypt(c)
+        assert np.max(np.abs(got - want)) < 1e-6, f"group {g}"
+        x = got
+
+
 def test_monomial_half_n_is_i_in_every_slot(ctx):
     z = inputs.uniform_values(2, ctx.N // 2, -1, 1) + 1j * inputs.uniform_values(3, ctx.N // 2, -1, 1)
     ct = ctx.encrypt(z, 3, 4)
