@@ -22,9 +22,9 @@
 // the first phase may read another buffer (out of place) or compute its input as
 // the fast basis conversion of a key-switching digit (ModUp fused into the load),
 // the inverse may end with a per-limb factor other than N^-1, a digit's own
-// limbs may be skipped, and a rescale / ModDown may be fused around a forward
-// transform (its spread into the first phase's load, its finish into the second
-// phase's store).  Butterflies keep residues
+// limbs may be skipped, and a rescale, a ModDown or both (one transform, see
+// ks_moddown_rescale) may be fused around a forward transform (conversion and
+// spread into the first phase's load, the finish into the second phase's store).  Butterflies keep residues
 // lazily (Harvey 2014): forward below 8q with the first operand reduced at every
 // other stage, inverse in [0, 2q); the final launch writes canonical residues.
 #pragma once
