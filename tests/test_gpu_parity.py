@@ -194,6 +194,26 @@ def test_add_sub_mul_rescale_bit_exact(name, request):
     same_ct(g.drop(ga, 1), o.drop(oa, 1))
 
 
+def test_mul_with_rescale_at_every_level_bit_exact(n10):
+    """HMult with its ModDown and rescale in one transform, at every level down to 1 (the last digit partial at
+    every other level), against the oracle's relinearised product followed by its rescale."""
+    g, o = n10
+    for level in range(o.n_q - 1, 0, -1):
+        ga, oa = imported_pair(g, o, 300 + level, level)
+        gb, ob = imported_pair(g, o, 400 + level, level)
+        same_ct(g.mul(ga, gb), o.mul(oa, ob))
+
+
+def test_mul_with_rescale_bootstrapping_chain_bit_exact():
+    """The bts12 chain: three special primes (four staged tiles in the fused column phase) and primes of 45, 55 and 60
+    bits, so that some ModUp factors cannot be folded into the key (their bound check fails)."""
+    g, o = make_pair("bts12")
+    for level in (o.n_q - 1, o.n_q - 5, 12, 3, 1):
+        ga, oa = imported_pair(g, o, 500 + level, level)
+        gb, ob = imported_pair(g, o, 600 + level, level)
+        same_ct(g.mul(ga, gb), o.mul(oa, ob))
+
+
 @pytest.mark.parametrize("name", ["n10", "toy"])
 def test_constants_bit_exact(name, request):
     g, o = request.getfixturevalue(name)
