@@ -398,7 +398,7 @@ __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* _
   const u64* dk = d + k * ds + (size_t)t * N;
   Acc128 a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};  // (coefficient n, n+1) x (key b, key a)
   if (!g) {
-#pragma unroll 4
+#pragma unroll 8
     for (int j = 0; j < dn; ++j) {
       const ulonglong2 v = j == own ? ld2(dk + n) : ld2(yk + j * y_step + n);
       const ulonglong2 wb = ld2(kb + j * key_step), wa = ld2(ka + j * key_step);
@@ -409,7 +409,7 @@ __global__ void k_ksk_inner_kernel(const PrimeDev* __restrict__ pr, const u64* _
     }
   } else {
     const size_t s0 = galois_index((uint32_t)n, g, log_n), s1 = galois_index((uint32_t)n + 1, g, log_n);
-#pragma unroll 4
+#pragma unroll 8
     for (int j = 0; j < dn; ++j) {
       const u64* src = j == own ? dk : yk + j * y_step;
       const u64 v0 = src[s0], v1 = src[s1];
