@@ -67,6 +67,36 @@ def chebyshev_vs_bts(ctx, lmax, A, B_max, B, degrees, reps=3):
     return rows
 
 
+def parse_levels(text: str) -> list:
+    """Comma-separated levels, e.g. "12,7" (empty: none)."""
+    out = [int(v) for v in text.split(",") if v.strip()]
+    if any(v < 0 for v in out):
+        raise ValueError(f"bad level list {text!r}")
+    return out
+
+
+def parse_fixed(text: str) -> tuple:
+    """The fixed configuration "degree,iters" (PP-STAT's is "510,6")."""
+    v = tuple(int(x) for x in text.split(","))
+    if len(v) != 2 or v[0] < 1 or v[1] < 0:
+        raise ValueError(f"bad fixed configuration {text!r}: want degree,iters")
+    return v
+
+
+def parse_configs(text: str) -> list:
+    """';'-separated (degree, c, iters) triples, e.g. "254,0,4;126,1,4": degree >= 1, c (Pre-BTS) 0 or 1,
+    iters >= 0 (empty: none)."""
+    out = []
+    for e in text.split(";"):
+        if not e.strip():
+            continue
+        v = tuple(int(x) for x in e.split(","))
+        if len(v) != 3 or v[0] < 1 or v[1] not in (0, 1) or v[2] < 0:
+            raise ValueError(f"bad configuration {e!r}: want degree,c,iters")
+        out.append(v)
+    return out
+
+
 def table4(ctx, R, levels, A, B_max, B, fixed, reps=3, extra=()):
     """Table 4 analogue: at each level, CryptoInvSqrt with HE-DAP's accuracy (u1) and speed (u2) choices
     against a fixed (degree, Newton steps) configuration (PP-STAT's d = 510, i = 6 in the paper), each with
@@ -143,9 +173,9 @@ def main(argv=None):
     explore_s = time.perf_counter() - t0
     table1 = chebyshev_vs_bts(ctx, lmax, args.A, args.B_max, args.B,
                               [(1 << e) - 2 for e in range(args.de_min, args.de_max + 1)]) if p["hw"] else []
-    levels4 = [int(v) for v in args.table4_levels.split(",") if v]
-    fixed = tuple(int(v) for v in args.fixed.split(","))
-    extra = [tuple(int(v) for v in e.split(",")) for e in args.extra.split(";") if e]
+    levels4 = parse_levels(args.table4_levels)
+    fixed = parse_fixed(args.fixed)
+    extra = parse_configs(args.extra)
     t4 = table4(ctx, R, levels4, args.A, args.B_max, args.B, fixed, extra=extra) if levels4 else []
     out = {
         "key": {"device": device_name(), "preset": args.preset, "params": p, "git": git_revision()},
